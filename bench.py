@@ -1,0 +1,305 @@
+"""Benchmark of the GB300 Line Segment Tracking chain.
+
+Workload: PU200 events of the full outer tracker (seeded synthetic events shaped like the paper's
+ttbar + PU200 sample: ~6000 helices, pT ~ pT^-3 above 0.8 GeV, |eta| < 2.4, 3% noise, one pixel seed
+per particle), processed in batches of --batch events (default 64). One step = one batch through the
+whole chain (binning, MD, LS, T3, T5, pT3, pT5, TC) with the inputs already resident in HBM.
+
+Printed (rank 0, one JSON line): events/s of the batched path (`value`), the plain one-event-at-a-time
+path, p50/p99 per-event latency, the end-to-end number through the public API with host buffers,
+the roofline of the dominant kernel, the CPU oracle baseline, and the SM clocks seen during timing.
+`--impl reference` times the CPU oracle (the reference arm) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PU200 events/s on 1 GB300 (batched vs plain per-event) + p50/p99 event latency"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_events(n, seed0=0):
+    from paper_2207_08207_gb300 import gen
+    det = gen.make_detector(barrel_only=False, pt_thr=0.8)
+    evs = [gen.config_event(2, seed0 + e, pu=200.0)[1] for e in range(n)]
+    return det, evs
+
+
+def oracle_events_per_s(det, evs, threads):
+    """CPU oracle on the given events (threads across events); returns (events/s, wall s)."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    if threads <= 1:
+        for ev in evs:
+            oracle.run(det, ev)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda ev: oracle.run(det, ev), evs))
+    dt = time.perf_counter() - t
+    return len(evs) / dt, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the same PU200 workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = min(os.cpu_count() or 1, 16)
+    det, evs = make_events(threads, seed0=0)
+    for _ in range(args.warmup):
+        oracle_events_per_s(det, evs[:1], 1)
+    times = []
+    for k in range(args.steps):
+        r, dt = oracle_events_per_s(det, evs, threads)
+        times.append(dt / len(evs))
+    per_event = statistics.mean(times)
+    value = 1.0 / per_event
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_event * len(evs) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"PU200 events (full outer tracker), {len(evs)} events per step on {threads} threads",
+                   "events_per_step": len(evs)},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{len(evs)} PU200 events per step, one thread per event"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2207_08207_gb300 import lst
+
+    B = args.batch
+    # every rank processes its own events (events are independent: no collective on the data path)
+    det, evs = make_events(B, seed0=1000 * rank)
+    ctx = lst.Context(det, device=local)
+    ctx.reserve(B, max(e.n_hits for e in evs), max(e.n_pls for e in evs))
+
+    # inputs resident in HBM
+    dev = []
+    for ev in evs:
+        dev.append({"x": torch.as_tensor(ev.x, device="cuda"), "y": torch.as_tensor(ev.y, device="cuda"),
+                    "z": torch.as_tensor(ev.z, device="cuda"), "sensor": torch.as_tensor(ev.sensor, device="cuda"),
+                    "pls": torch.as_tensor(ev.pls.view(np.uint8).copy(), device="cuda"), "n_pls": ev.n_pls})
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.submit(dev, stream=stream)
+        ctx.sync()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    ctx.set_timing(True)
+    launches0 = ctx.launch_count()
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms, stage_acc, kern_acc = [], {}, {}
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, v in ctx.stage_ms().items():
+            stage_acc[k] = stage_acc.get(k, 0.0) + v
+        for k, v in ctx.kernel_ms().items():
+            kern_acc[k] = kern_acc.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = ctx.launch_count() - launches0
+    ctx.set_timing(False)
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    t_max = float(t.item())
+    value = B * args.steps * world / t_max
+    counts = [ctx.counts(e) for e in range(B)]
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / average duration)
+    hbm_peak, peak_kind = _peaks()
+    kavg = {k: v / args.steps for k, v in kern_acc.items()}
+    dom = max(kavg, key=kavg.get) if kavg else None
+    n_md = sum(c["n_md"] for c in counts)
+    n_ls = sum(c["n_ls"] for c in counts)
+    n_t3 = sum(c["n_t3"] for c in counts)
+    n_t5 = sum(c["n_t5"] for c in counts)
+    alg_bytes = ctx.kernel_algorithmic_bytes(dom, counts, sum(e.n_hits for e in evs), sum(e.n_pls for e in evs)) if dom else 0
+    achieved = alg_bytes / (kavg[dom] * 1e-3) / 1e9 if dom and kavg[dom] > 0 else 0.0
+    traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel_ms": kavg.get(dom) if dom else None, "algorithmic_bytes": alg_bytes,
+                "kernels_ms": {k: round(v, 4) for k, v in sorted(kavg.items(), key=lambda kv: -kv[1])}}
+
+    # plain path: one event per call, inputs resident
+    plain = None
+    if not args.no_plain:
+        lat = []
+        for i in range(min(B, 32)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.submit([dev[i]], stream=stream)
+            ctx.sync()
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        lat_s = sorted(lat)
+        plain = {"events_per_s": 1e3 / statistics.mean(lat), "p50_ms": float(np.percentile(lat_s, 50)),
+                 "p99_ms": float(np.percentile(lat_s, 99)), "events": len(lat)}
+
+    # end to end through the public API: host buffers in, track candidates out
+    e2e_ms = []
+    h2d = sum(e.n_hits * 16 + e.n_pls * 48 for e in evs) + 2 * (B + 1) * 4
+    d2h = 0
+    for _ in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.submit(evs, stream=stream)
+        ctx.sync()
+        d2h = 0
+        for e in range(B):
+            tc = ctx.copy_tc(e)
+            d2h += sum(a.nbytes for a in tc.values())
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = B / (statistics.mean(e2e_ms) / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = min(os.cpu_count() or 1, 16)
+        r, dt = oracle_events_per_s(det, evs[:threads], threads)
+        cpu = {"value": r, "unit": "events/s", "cores": threads, "kind": "oracle",
+               "sample": f"{threads} of the PU200 events, one thread per event ({dt:.1f} s wall)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"PU200 events, full outer tracker (9138 modules), batch of {B} events per step",
+                       "events_per_step": B, "l2": "256 MB buffer written between timed steps",
+                       "parallelism": f"events sharded over {world} GPU(s)"},
+            "latency_ms": {"batched_p50": float(np.percentile(step_ms, 50)),
+                           "batched_p99": float(np.percentile(step_ms, 99))},
+            "plain": plain,
+            "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "stage_ms": {k: v / args.steps for k, v in stage_acc.items()},
+            "objects_per_event": {"md": n_md / B, "ls": n_ls / B, "t3": n_t3 / B, "t5": n_t5 / B,
+                                  "tc": sum(c["n_tc"] for c in counts) / B},
+            "retries": max(c["retries"] for c in counts),
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

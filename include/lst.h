@@ -1,0 +1,274 @@
+/*
+ * lst.h - C ABI of the GB300 (sm_103a) Line Segment Tracking library, liblst.so.
+ *
+ * Line Segment Tracking (arXiv:2207.08207) builds tracks bottom-up in the CMS outer tracker:
+ *   hits, binned by detector module                      (Sec. 4.2, "pre-processing the hits")
+ *   -> Mini-Doublets (MD): hit pairs in a module's two sensors            (Sec. 2.2)
+ *   -> Line Segments (LS): MD pairs in modules linked by the module map   (Sec. 2.2)
+ *   -> Triplets (T3): two LS sharing an MD; Quintuplets (T5): two T3 sharing an MD  (Sec. 2.3)
+ *   -> pixel seeds (pLS) linked to T3 / T5 as pT3 / pT5                  (Sec. 2.4)
+ *   -> Track Candidates (TC): pT5, pT3, T5, pLS in that order, cross-cleaned in eta-phi (Sec. 2.5)
+ * The paper's statement of the problem (Fig. "GPU implementation flowchart", Sec. 4.2) is: hits and
+ * pixel tracks in, MD/LS/T3/T5/pT3/pT5/TC objects out, track candidates copied to the CPU. The
+ * calls below follow it.
+ *
+ * Conventions
+ *  - Every function returns an lst_status (0 = LST_OK). No exception crosses this boundary and
+ *    nothing aborts the process; lst_last_error() gives a one-line reason for the last failure.
+ *  - Pointers are plain host or device pointers; sizes are element counts unless stated.
+ *  - A context (lst_ctx) owns its device memory (object arenas, allocated from a per-context CUDA
+ *    memory pool) and is used by one host thread at a time. Several contexts may share a device.
+ *  - Units: cm, GeV, Tesla; the solenoid field is along +z.
+ */
+#ifndef LST_H_
+#define LST_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LST_OK = 0,
+  LST_EINVAL = 1,                 /* bad argument or input (ids out of range, NaN coordinates) */
+  LST_ENOMEM = 2,                 /* device or pinned-host allocation failed */
+  LST_ECUDA = 3,                  /* a CUDA runtime call failed (see lst_last_error) */
+  LST_ETIMEOUT = 4,               /* a kernel exceeded its cycle budget and stopped early */
+  LST_EOVERFLOW_UNRESOLVED = 5,   /* object capacity still exceeded after the retry limit */
+  LST_ESTATE = 6                  /* call out of order (e.g. no geometry loaded) */
+} lst_status;
+
+enum { LST_MEM_HOST = 0, LST_MEM_DEVICE = 1 };
+
+/* Stage indices used by the per-stage arrays of lst_counts. */
+enum {
+  LST_STAGE_MD = 0, LST_STAGE_LS = 1, LST_STAGE_T3 = 2, LST_STAGE_T5 = 3,
+  LST_STAGE_PT3 = 4, LST_STAGE_PT5 = 5, LST_STAGE_TC = 6, LST_STAGE_QUEUE = 7, LST_N_STAGES = 8
+};
+
+/* Track-candidate types, in the order the paper adds them to the collection (Sec. 2.5). */
+enum { LST_TC_PT5 = 0, LST_TC_PT3 = 1, LST_TC_T5 = 2, LST_TC_PLS = 3 };
+
+/*
+ * Selection constants and execution settings. The paper prints no cut value except the pT
+ * threshold (0.8 GeV, Sec. 2.2); every other constant is this library's reading, fixed here once.
+ * lst_config_default() fills the values below. The float fields are the cut constants; the
+ * integer fields control execution only and never change which objects are built.
+ */
+typedef struct {
+  float k;             /* pT = k * R [GeV/cm]; 0.003 * 3.8 T = 0.0114 */
+  float pt_thr;        /* pT threshold (Sec. 2.2), 0.8 */
+  float sin_max;       /* cap on sin(alpha_thr), 0.95 */
+  float z_lum;         /* luminous-region half length, 15 cm */
+  float d0_max;        /* impact-parameter allowance of MD/LS windows, 0.1 cm */
+  float n_sigma;       /* window width in resolutions, 3 */
+  float sigma_rphi;    /* hit resolution in r-phi, 0.003 cm */
+  float sigma_z;       /* barrel hit resolution in z, 0.1 cm */
+  float sigma_r;       /* endcap hit resolution in r, 0.1 cm */
+  float chi2_t3;       /* T3 r-z chi2 cut, 9 */
+  float chi2_t5_c;     /* T5 global circle-fit chi2 cut, 20 */
+  float chi2_t5_rz;    /* T5 r-z chi2 cut, 16 */
+  float chi2_pt3_xy, chi2_pt3_rz;   /* pT3 cuts, 16 / 16 */
+  float chi2_pt5_xy, chi2_pt5_rz;   /* pT5 cuts, 25 / 25 */
+  float f_t3;          /* T3 pT estimate >= f_t3 * pt_thr, 0.8 */
+  float d0_t3;         /* T3 circle impact parameter, 2 cm */
+  float c_rel, c_abs;  /* T5 curvature compatibility, 0.2 and 1.5e-4 / cm */
+  float dr_min;        /* eta-phi cross-cleaning distance, 0.01 */
+  float pt_cap;        /* cap on pT estimates, 1e4 GeV */
+  float pls_dir_err;   /* pixel-seed direction uncertainty, 1e-3 rad */
+  float pls_pt_err;    /* pixel-seed relative pT uncertainty, 0.01 */
+  float sigma_floor;   /* floor on r-z per-anchor uncertainties, 1e-4 cm */
+  int32_t t5_overlap_hits;  /* T5 duplicate removal: >= this many of 10 hits shared, 7 */
+
+  /* execution settings (chosen by the autotuner; defaults are safe) */
+  int32_t persistent;       /* 1: persistent kernels pulling (event, module) work items */
+  int32_t use_graph;        /* 1: capture the MD->TC chain in a CUDA graph and replay it */
+  int32_t block_ls;         /* threads per LS block (64, 128, 256) */
+  int32_t warps_px;         /* warps per block in the pT3/pT5 candidate kernels */
+  float cap_scale;          /* multiplier on predicted per-module capacities (>= 0.25) */
+  int32_t max_retries;      /* capacity-overflow retries before LST_EOVERFLOW_UNRESOLVED */
+  int64_t cycle_budget;     /* per-block clock64 budget of the candidate kernels; 0 = none */
+} lst_config;
+
+/* One detector module (a pair of closely spaced sensors, "bi-layer pT module", Sec. 1). */
+typedef struct {
+  int32_t id;        /* must equal its index */
+  int32_t subdet;    /* 0 barrel, 1 endcap */
+  int32_t layer;     /* barrel layer 1..6 or endcap disk 1..5 */
+  int32_t side;      /* 0 barrel, -1 / +1 endcap side */
+  int32_t type;      /* 0 PS, 1 2S */
+  float surf;        /* radius (barrel) or |z| (endcap) of the lower sensor */
+  float spacing;     /* sensor separation */
+  float phi_lo, phi_hi, w_lo, w_hi;   /* patch bounds: phi and z (barrel) or r (endcap) */
+} lst_module;
+
+/* A pixel seed, used as a line segment (pLS, Sec. 2.4). The helix is given at (x0, y0, z0) with
+ * direction phi, pseudorapidity eta and charge; pix_hit are the seed's 4 hit ids (any int32 ids
+ * that do not collide with the event's outer-tracker hit indices). */
+typedef struct {
+  float pt, eta, phi, x0, y0, z0;
+  int32_t charge;
+  int32_t pix_hit[4];
+  int32_t pad;
+} lst_pls;
+
+/* One event. sensor[i] = 2 * module + (0 lower sensor | 1 upper sensor). Inputs are read during
+ * lst_run_events (copied into the context) and may be released when it returns. */
+typedef struct {
+  const float* x;
+  const float* y;
+  const float* z;
+  const int32_t* sensor;
+  int32_t n_hits;
+  const lst_pls* pls;
+  int32_t n_pls;
+  int32_t mem_space;   /* LST_MEM_HOST or LST_MEM_DEVICE, for all five arrays */
+} lst_event_in;
+
+/* Per-event object counts and status. overflow[s] counts objects that did not fit stage s's
+ * capacity on the first pass; they were recovered by a retry (retries > 0) unless status is
+ * LST_EOVERFLOW_UNRESOLVED. recheck[s] counts candidates whose float32 cut margins were too close
+ * to a threshold and were decided again in float64. */
+typedef struct {
+  int32_t n_hits, n_pls;
+  int32_t n_md, n_ls, n_t3, n_t5, n_pt3, n_pt5, n_tc;
+  int32_t n_tc_type[4];
+  int32_t overflow[LST_N_STAGES];
+  int32_t recheck[LST_N_STAGES];
+  int32_t retries;
+  int32_t status;
+} lst_counts;
+
+/*
+ * Device pointers to one event's objects, inside the context's arenas. Valid until the next
+ * lst_run_events on the same context. Objects of each type are dense and ordered: MD by
+ * (module, lower hit, upper hit), LS by (inner MD, outer MD), T3 by (inner LS, outer LS), T5 by
+ * (inner T3, outer T3), pT3 / pT5 by (seed, object), TC by (type, sorted hit tuple).
+ * Member indices (ls_md_in, t3_ls_in, ...) are event-local indices into the same event's arrays.
+ * Hit indices are the event's input hit indices.
+ */
+typedef struct {
+  lst_counts counts;
+  const int32_t *md_hit_lo, *md_hit_up, *md_module;
+  const float *md_dphichange, *md_pt_est;
+  const int32_t *ls_md_in, *ls_md_out;
+  const float *ls_z0, *ls_dphi;
+  const int32_t *t3_ls_in, *t3_ls_out;
+  const float *t3_r, *t3_xc, *t3_yc, *t3_chi2_rz, *t3_pt_est;
+  const int32_t *t5_t3_in, *t5_t3_out;
+  const float *t5_kappa_in, *t5_kappa_out, *t5_kappa_fit, *t5_chi2_c, *t5_chi2_rz, *t5_eta,
+      *t5_phi, *t5_pt;
+  const int32_t *pt3_pls, *pt3_t3;
+  const float *pt3_chi2_xy, *pt3_chi2_rz;
+  const int32_t *pt5_pls, *pt5_t5;
+  const float *pt5_chi2_xy, *pt5_chi2_rz;
+  const int32_t *tc_type, *tc_obj, *tc_hits;   /* tc_hits: [n_tc][14], -1 padded */
+  const float *tc_pt, *tc_eta, *tc_phi;
+} lst_event_out;
+
+typedef struct lst_ctx lst_ctx;
+
+/* Fill cfg with the default constants and execution settings. Host only; needs no GPU. */
+void lst_config_default(lst_config* cfg);
+
+/* Create a context on CUDA device `device` (ownership of *out passes to the caller, release with
+ * lst_destroy). cfg may be NULL for defaults; it is copied. */
+int lst_create(lst_ctx** out, const lst_config* cfg, int device);
+
+/* Release every device and host resource of the context. Waits for its pending work first, so it
+ * is safe to call while a run is in flight. NULL is ignored. */
+void lst_destroy(lst_ctx* ctx);
+
+/*
+ * Load the detector geometry (host arrays, copied once into resident device tables).
+ *  mods[n_mods]: module table, mods[i].id == i.
+ *  conn_off[n_mods + 1], conn_tgt[conn_off[n_mods]]: the module map as CSR - the modules of the
+ *    next layer reachable from each module by helices above the pT threshold (Sec. 2.2).
+ *  pix_off[n_pix_bins + 1], pix_tgt[...]: pixel-seed map as CSR over (eta, phi, charge) bins:
+ *    bin = ((floor(20 eta + 50)) * 128 + floor(phi_[0,2pi) * 64 / pi)) * 2 + (charge > 0); the
+ *    targets are modules where a seed's T3 / T5 may start. n_pix_bins may be 0 (no seeds used).
+ * Returns LST_EINVAL on inconsistent tables (ids, offsets not monotone, targets out of range).
+ */
+int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, const int32_t* conn_off,
+                      const int32_t* conn_tgt, const int32_t* pix_off, const int32_t* pix_tgt,
+                      int32_t n_pix_bins);
+
+/*
+ * Reserve arenas for batches of up to n_events events of up to max_hits hits and max_pls seeds
+ * each (optional: lst_run_events grows the arenas on demand).
+ */
+int lst_reserve(lst_ctx* ctx, int32_t n_events, int32_t max_hits, int32_t max_pls);
+
+/*
+ * Enqueue the whole chain for n_ev events on `cuda_stream` (a cudaStream_t; NULL means the
+ * context's own stream) and return without waiting. out[n_ev] (host array, may be NULL) receives
+ * the per-event device pointers once lst_sync returns. Events are independent: the objects of one
+ * event never depend on another event in the batch.
+ */
+int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event_out* out,
+                   void* cuda_stream);
+
+/*
+ * Wait for the last lst_run_events. Re-runs the batch with enlarged capacities if any stage
+ * overflowed (at most cfg.max_retries times). status_per_event[n_ev] (may be NULL) receives each
+ * event's lst_status. Returns the first non-OK event status, or a context-level error.
+ */
+int lst_sync(lst_ctx* ctx, int32_t* status_per_event);
+
+/*
+ * Bin one event's hits by sensor on the device (the hit pre-processing of Sec. 4.2): a counting sort
+ * that is stable in the input order.
+ *  d_sensor[n_hits] (device, in): sensor ids, 0 <= id < 2 * n_mods of the loaded geometry.
+ *  d_order[n_hits] (device, out): input index of the hit at each binned position; the hits of one
+ *    sensor are contiguous and in input order.
+ *  d_offsets[2 * n_mods + 1] (device, out): first binned position of each sensor; the last entry is
+ *    n_hits.
+ * Scratch memory comes from the context. Runs on cuda_stream (NULL: the context's stream) and
+ * waits for it before returning, because it reports an out-of-range sensor id as LST_EINVAL (the
+ * outputs are then unspecified).
+ */
+int lst_bin_hits(lst_ctx* ctx, const int32_t* d_sensor, int32_t n_hits, int32_t* d_order,
+                 int32_t* d_offsets, void* cuda_stream);
+
+/* Non-blocking: 1 if the last run (including retries it needs) has finished, 0 otherwise, <0 on
+ * error. A run that needs a retry is finished only after lst_sync. */
+int lst_query(lst_ctx* ctx);
+
+/* Counts of event `ev` of the last completed run (host copy). */
+int lst_get_counts(const lst_ctx* ctx, int32_t ev, lst_counts* c);
+
+/*
+ * Copy event `ev`'s track candidates to host memory: type[n], obj[n], hits[n * 14], pt/eta/phi[n]
+ * with n = counts.n_tc (any pointer may be NULL to skip that array).
+ */
+int lst_copy_tc(lst_ctx* ctx, int32_t ev, int32_t* type, int32_t* obj, int32_t* hits, float* pt,
+                float* eta, float* phi);
+
+/* Device time of each stage of the last run, in ms (CUDA events on the run's stream), indexed by
+ * LST_STAGE_*; stage_ms[LST_N_STAGES] receives the whole chain. Needs lst_set_timing(ctx, 1). */
+int lst_set_timing(lst_ctx* ctx, int enable);
+int lst_get_stage_ms(const lst_ctx* ctx, float* stage_ms);
+
+/*
+ * Device time, in ms, of individual kernels of the last run (CUDA events on the run's stream;
+ * needs lst_set_timing(ctx, 1)). Index order: hit binning sort/gather, MD, MD compaction, LS,
+ * LS compaction, T3 pre-filter, T3 float64 decision, T3 compaction, T5 pre-filter, T5 decision,
+ * pT3 pre-filter, pT5 pre-filter, pT3 decision, pT5 decision, T5 duplicate removal, TC assembly.
+ * Writes min(n, count) values and returns the count (16), or a negative lst_status on error.
+ */
+int lst_get_kernel_ms(const lst_ctx* ctx, float* ms, int32_t n);
+
+/* Number of kernel launches issued by this context since creation (graph replays count each
+ * kernel node). */
+int64_t lst_launch_count(const lst_ctx* ctx);
+
+/* One-line description of the last error on this context (or of the last failed lst_create when
+ * ctx is NULL). Never NULL. */
+const char* lst_last_error(const lst_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LST_H_ */

@@ -763,10 +763,14 @@ struct Runner {
     struct Cand { int32_t type, obj; std::vector<int32_t> hits, key; float pt, eta, phi; };
     std::vector<Cand> acc_pt5, acc_pt3, acc_t5, acc_pls;
     // accepted (eta, phi) points, searched in an eta window: dR < dr_min implies |deta| < dr_min
-    std::vector<std::pair<float, float>> near_set;
+    struct EtaPhi { float first, second; };
+    auto ep_less = [](const EtaPhi& a, const EtaPhi& b) {
+      return a.first < b.first || (a.first == b.first && a.second < b.second);
+    };
+    std::vector<EtaPhi> near_set;
     auto add_near = [&](float eta, float phi) {
-      near_set.insert(std::upper_bound(near_set.begin(), near_set.end(), std::make_pair(eta, phi)),
-                      std::make_pair(eta, phi));
+      EtaPhi v{eta, phi};
+      near_set.insert(std::upper_bound(near_set.begin(), near_set.end(), v, ep_less), v);
     };
     auto is_near = [&](float eta, float phi) {
       if (brute) {
@@ -775,7 +779,7 @@ struct Runner {
         return false;
       }
       auto it = std::lower_bound(near_set.begin(), near_set.end(),
-                                 std::make_pair((float)((double)eta - P.dr_min), -1e30f));
+                                 EtaPhi{(float)((double)eta - 2.0 * P.dr_min), -1e30f}, ep_less);
       for (; it != near_set.end() && (double)it->first <= (double)eta + P.dr_min; ++it)
         if (dr_close(P, eta, phi, it->first, it->second)) return true;
       return false;

@@ -1,0 +1,201 @@
+// Internal layout of the LST library: resident geometry, the per-batch workspace, status words and
+// the host-side launchers of each stage. Shared by the .cu files of the library; not installed.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lst.h"
+#include "lst_common.cuh"
+
+namespace lst {
+
+// Resident geometry (device pointers).
+struct Geo {
+  int32_t n_mods = 0;
+  int32_t n_pix_bins = 0;
+  const uint8_t* endcap = nullptr;   // [n_mods] 1 for endcap modules
+  const float* spacing = nullptr;    // [n_mods]
+  const int32_t* conn_off = nullptr; // [n_mods + 1]
+  const int32_t* conn_tgt = nullptr;
+  const int32_t* pix_off = nullptr;  // [n_pix_bins + 1]
+  const int32_t* pix_tgt = nullptr;
+};
+
+// Status words (int32, device; copied to the host after each run).
+enum StatusWord : int {
+  ST_ERROR = 0,          // bit flags, below
+  ST_OVF_MD, ST_OVF_LS, ST_OVF_T3, ST_OVF_T5, ST_OVF_PT3, ST_OVF_PT5,   // objects beyond capacity
+  ST_ARENA_MD, ST_ARENA_LS, ST_ARENA_T3, ST_ARENA_T5, ST_ARENA_PT3, ST_ARENA_PT5,  // slot totals
+  ST_Q_MD, ST_Q_LS, ST_Q_T3, ST_Q_T5, ST_Q_PT3, ST_Q_PT5,   // queue pushes attempted
+  ST_REC_MD, ST_REC_LS,  // float64 re-decisions of MD / LS candidates
+  ST_N_PT3, ST_N_PT5,    // appended pT3 / pT5 objects
+  ST_TIMEOUT,            // blocks that ran out of their cycle budget
+  ST_N_WORDS
+};
+enum ErrorBit : int { ERR_BAD_SENSOR = 1, ERR_BAD_COORD = 2, ERR_BAD_PLS = 4 };
+
+// Per-event summary written by the final kernel: object counts [0..6] (MD, LS, T3, T5, pT3, pT5, TC),
+// TC counts per type [7..10], first dense index of the event in each object array [11..17]
+// (same order; TC: first row), error bits [kEvErr].
+constexpr int kEvWords = 24;
+constexpr int kEvErr = 23;
+
+// Capacities of one workspace (element counts).
+struct Caps {
+  int64_t E = 0, H = 0, P = 0;
+  int64_t md_slots = 0, ls_slots = 0, t3_slots = 0, t5_slots = 0, p3_slots = 0, p5_slots = 0;
+  int64_t q_md = 0, q_ls = 0, q_t3 = 0, q_t5 = 0, q_p3 = 0, q_p5 = 0;
+  int64_t n_mods = 0;
+};
+
+// Per-batch workspace: every device array the chain uses. Passed to kernels by value.
+struct Ws {
+  int32_t E = 0, V = 0, S = 0, H = 0, P = 0;   // events, virtual modules / sensors, hits, seeds
+  Caps cap;
+  float cap_scale = 1.0f;
+  long long cycle_budget = 0;
+  // inputs (concatenated events)
+  float *x = nullptr, *y = nullptr, *z = nullptr;
+  int32_t* sensor = nullptr;
+  int32_t* ev_hit_off = nullptr;  // [E + 1]
+  int32_t* ev_pls_off = nullptr;  // [E + 1]
+  lst_pls* pls = nullptr;
+  // binning
+  int32_t *hit_vs = nullptr, *sens_cnt = nullptr, *sens_off = nullptr, *sens_cur = nullptr;
+  int32_t* bidx = nullptr;
+  float *bx = nullptr, *by = nullptr, *bz = nullptr;
+  int32_t* borig = nullptr;
+  // MD
+  int32_t *md_cap = nullptr, *md_base = nullptr, *md_cnt = nullptr, *md_ovr = nullptr;
+  int32_t *ms_lo = nullptr, *ms_up = nullptr;
+  float *ms_dpc = nullptr, *ms_pte = nullptr;
+  int32_t* md_off = nullptr;
+  int32_t *md_lo = nullptr, *md_up = nullptr, *md_vm = nullptr;
+  float *md_x = nullptr, *md_y = nullptr, *md_z = nullptr, *md_r = nullptr, *md_sthr = nullptr;
+  float *md_dpc = nullptr, *md_pte = nullptr;
+  uint8_t* md_ec = nullptr;
+  // LS
+  int32_t *ls_cap = nullptr, *ls_base = nullptr, *ls_cnt = nullptr, *ls_ovr = nullptr;
+  int32_t *lss_in = nullptr, *lss_out = nullptr;
+  float *lss_z0 = nullptr, *lss_dphi = nullptr;
+  int32_t* ls_off = nullptr;
+  int32_t *ls_in = nullptr, *ls_out = nullptr;
+  float *ls_z0 = nullptr, *ls_dphi = nullptr;
+  int32_t *lsin_cnt = nullptr, *lsin_off = nullptr;   // LS by inner MD, [md_slots (+1)]
+  // T3
+  int32_t *t3_cap = nullptr, *t3_base = nullptr, *t3_cnt = nullptr, *t3_ovr = nullptr;
+  int32_t *t3s_a = nullptr, *t3s_b = nullptr;
+  float *t3s_R = nullptr, *t3s_xc = nullptr, *t3s_yc = nullptr, *t3s_chi2 = nullptr, *t3s_pte = nullptr;
+  int32_t* t3_off = nullptr;
+  int32_t *t3_a = nullptr, *t3_b = nullptr, *t3_md0 = nullptr, *t3_md1 = nullptr, *t3_md2 = nullptr;
+  float *t3_R = nullptr, *t3_xc = nullptr, *t3_yc = nullptr, *t3_chi2 = nullptr, *t3_pte = nullptr;
+  int32_t *t3md_cnt = nullptr, *t3md_off = nullptr;   // T3 by first MD
+  // T5
+  int32_t *t5_cap = nullptr, *t5_base = nullptr, *t5_cnt = nullptr, *t5_ovr = nullptr;
+  int32_t *t5s_a = nullptr, *t5s_b = nullptr;
+  float* t5s_f = nullptr;   // [8][t5_slots]: kin, kout, kfit, chi2c, chi2rz, eta, phi, pt
+  int32_t* t5_off = nullptr;
+  int32_t *t5_a = nullptr, *t5_b = nullptr;
+  int32_t* t5_md = nullptr;  // [5][t5_slots]
+  float* t5_f = nullptr;     // [8][t5_slots]
+  // pixel seeds and pT3 / pT5: passing objects are appended, then grouped by seed
+  int32_t* pls_bin = nullptr;
+  int32_t *p3a_pls = nullptr, *p3a_obj = nullptr;
+  float *p3a_xy = nullptr, *p3a_rz = nullptr, *p3a_sc = nullptr;
+  int32_t *p3_cnt = nullptr, *p3_cur = nullptr, *pt3_off = nullptr;   // [P], [P], [P + 1]
+  int32_t *pt3_pls = nullptr, *pt3_obj = nullptr;
+  float *pt3_xy = nullptr, *pt3_rz = nullptr, *pt3_sc = nullptr;
+  int32_t *p5a_pls = nullptr, *p5a_obj = nullptr;
+  float *p5a_xy = nullptr, *p5a_rz = nullptr, *p5a_sc = nullptr;
+  int32_t *p5_cnt = nullptr, *p5_cur = nullptr, *pt5_off = nullptr;
+  int32_t *pt5_pls = nullptr, *pt5_obj = nullptr;
+  float *pt5_xy = nullptr, *pt5_rz = nullptr, *pt5_sc = nullptr;
+  // track candidates
+  int32_t *best5 = nullptr, *best3 = nullptr;   // [P]
+  uint8_t *pls_member = nullptr, *acc3 = nullptr, *accl = nullptr;   // [P]
+  uint8_t *t5_kept = nullptr, *acc5t = nullptr;  // [t5_slots]
+  int32_t *h5_cnt = nullptr, *h5_off = nullptr, *h5_cur = nullptr, *h5_idx = nullptr;  // hit -> T5
+  int32_t *cell_cnt = nullptr, *cell_off = nullptr, *cell_cur = nullptr, *cell_item = nullptr;
+  int32_t n_cells = 0;   // per event
+  int32_t* tc_cnt = nullptr;   // [E]
+  int32_t* tc_code = nullptr;  // [tc_capacity] candidate codes (type << 29 | index), per-event regions
+  unsigned long long* tc_key = nullptr;   // [tc_capacity] sort keys
+  int32_t* tc_hit_key = nullptr;          // [tc_capacity][14] sorted hit tuples
+  int32_t* grp_tmp = nullptr;             // [max(p3_slots, p5_slots)] grouping scratch
+  int32_t *tc_type = nullptr, *tc_obj = nullptr, *tc_hits = nullptr;
+  float *tc_pt = nullptr, *tc_eta = nullptr, *tc_phi = nullptr;
+  int64_t tc_capacity = 0;
+  // event-local output copies
+  int32_t *o_md_lo = nullptr, *o_md_up = nullptr, *o_md_mod = nullptr;
+  int32_t *o_ls_in = nullptr, *o_ls_out = nullptr, *o_t3_a = nullptr, *o_t3_b = nullptr;
+  int32_t *o_t5_a = nullptr, *o_t5_b = nullptr, *o_pt3_pls = nullptr, *o_pt3_obj = nullptr;
+  int32_t *o_pt5_pls = nullptr, *o_pt5_obj = nullptr;
+  // float64 decision queues
+  int4 *q_md = nullptr, *q_ls = nullptr;
+  int2 *q_t3 = nullptr, *q_t5 = nullptr, *q_p3 = nullptr, *q_p5 = nullptr;
+  // scan scratch and status
+  int32_t* scan_tmp = nullptr;
+  int32_t* status = nullptr;   // [ST_N_WORDS]
+  int32_t* ev_stat = nullptr;  // [E][kEvWords]
+  int32_t* work = nullptr;     // persistent-kernel work lists and counters
+  int32_t* work_ctr = nullptr;
+};
+
+// Launch settings (from lst_config).
+struct Launch {
+  cudaStream_t stream = nullptr;
+  int block_ls = 128;
+  int warps_px = 4;
+  bool persistent = false;
+  int n_sm = 152;
+  long long* launches = nullptr;   // host counter
+  cudaEvent_t* kev = nullptr;      // when set: [2 * kernel id] start / end events of timed kernels
+};
+
+// kernels timed individually when timing is enabled (index order of lst_get_kernel_ms)
+enum KernelId : int {
+  K_BIN = 0, K_MD, K_MD_COMPACT, K_LS, K_LS_COMPACT, K_T3_PRE, K_T3_DECIDE, K_T3_COMPACT, K_T5_PRE,
+  K_T5_DECIDE, K_PT3_PRE, K_PT5_PRE, K_PT3_DECIDE, K_PT5_DECIDE, K_TC_CLEAN, K_TC_ASSEMBLE, K_N_TIMED
+};
+#define KT_BEGIN(L, id) \
+  if ((L).kev) cudaEventRecord((L).kev[2 * (id)], (L).stream)
+#define KT_END(L, id) \
+  if ((L).kev) cudaEventRecord((L).kev[2 * (id) + 1], (L).stream)
+
+// scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
+void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);
+int64_t scan_tmp_elems(int64_t n);
+
+// effective per-module object count = min(count, capacity, room left in the slot arena), with the
+// excess added to status[ovf_word] and the needed arena size to status[arena_word]
+void launch_effective(const Ws& w, const int32_t* cnt, const int32_t* cap, const int32_t* base,
+                      int64_t slots, int32_t* eff, int ovf_word, int arena_word, int n, const Launch& L);
+
+// single-event hit binning on plain device arrays; cnt, cur (n_sens each) and err must be zero
+void run_bin_raw(const int32_t* sensor, int n, int n_sens, int32_t* order, int32_t* offsets, int32_t* cnt,
+                 int32_t* cur, int32_t* err, int32_t* scan_tmp, const Launch& L);
+
+// stages
+void run_binning(const Ws& w, const Geo& g, const Launch& L);
+void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
+void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
+void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
+void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
+void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
+void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
+void run_finalize(const Ws& w, const Geo& g, const Launch& L);
+int tc_cells_per_event();
+void tc_configure();
+// after an overflowing run: raise the per-module capacity overrides to the observed counts
+void run_raise_overrides(const Ws& w, const Launch& L);
+
+inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {
+  int64_t b = (n + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+#define LST_LAUNCH(L) (++*(L).launches)
+
+}  // namespace lst

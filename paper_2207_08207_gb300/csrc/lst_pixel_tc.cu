@@ -1,0 +1,742 @@
+// Pixel seeds, pT3 / pT5 (paper Sec. 2.4) and Track Candidates with cross-cleaning (Sec. 2.5).
+//
+// pT3 / pT5: a seed (pLS) is linked to a T3 / T5 whose first MD lies in a module the pixel map
+// lists for the seed's (eta, phi, charge) bin. The seed's helix is not refitted: the outer anchor
+// hits are tested against the circle and the r-z line the seed's parameters define (chi2_xy and
+// chi2_rz cuts; per-anchor uncertainties from the hit resolution and the seed's direction and pT
+// uncertainties).
+// Track candidates: pT5, then pT3, then T5, then pLS (Sec. 2.5). One pT5 and one pT3 per seed (lowest
+// (score, hit tuple)); T5 duplicates removed (a T5 sharing >= 7 of 10 hits with a T5 of lower
+// (chi2, hit tuple) is dropped); pT3 kept only if no accepted pT5 uses its seed or lies within
+// dR < dr_min; T5 only if no accepted pT5 / pT3 is within dR; pLS only if it is in no pT3 / pT5 and
+// no accepted candidate is within dR. Output ordered by type, then sorted hit tuple.
+#include "lst_internal.h"
+
+namespace lst {
+namespace {
+
+__device__ __forceinline__ int find_seg(const int32_t* off, int n, int i) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------------
+// pixel seeds: validation and pixel-map bin. The bin index is computed in float64 with explicitly
+// rounded operations (floor(20 eta + 50), floor(phi_[0,2pi) * 64 / pi)), the same sequence of IEEE
+// operations any implementation of the definition performs.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_pls_prep(Ws w, Geo g) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+    const lst_pls s = w.pls[p];
+    const bool ok = isfinite(s.pt) && isfinite(s.eta) && isfinite(s.phi) && isfinite(s.x0) &&
+                    isfinite(s.y0) && isfinite(s.z0) && s.pt > 0.f && (s.charge == 1 || s.charge == -1);
+    int bin = -1;
+    if (!ok) {
+      const int e = find_seg(w.ev_pls_off, w.E, p);
+      atomicOr(&w.status[ST_ERROR], ERR_BAD_PLS);
+      atomicOr(&w.ev_stat[e * kEvWords + kEvErr], ERR_BAD_PLS);
+    } else if (g.n_pix_bins > 0) {
+      const double ie = floor(__dadd_rn(__dmul_rn((double)s.eta, 20.0), 50.0));
+      if (ie >= 0.0 && ie < (double)kPixNEta) {
+        double ph = (double)s.phi;
+        if (ph < 0.0) ph = __dadd_rn(ph, kTwoPiD);
+        double ip = floor(__dmul_rn(ph, 64.0 / kPiD));
+        ip = fmin(fmax(ip, 0.0), (double)(kPixNPhi - 1));
+        bin = ((int)ie * kPixNPhi + (int)ip) * 2 + (s.charge > 0 ? 1 : 0);
+        if (bin >= g.n_pix_bins) bin = -1;
+      }
+    }
+    w.pls_bin[p] = bin;
+  }
+}
+
+// seed helix in precision T: circle centre c = (x0, y0) + (1/rho) n, n = (sin phi, -cos phi),
+// rho = q / R, R = pT / k
+template <class T>
+struct Seed {
+  T x0, y0, z0, rho, akap, sp, cp, cot, R;
+};
+
+template <class T>
+__device__ __forceinline__ Seed<T> make_seed(const lst_pls& s, const Cst<T>& c) {
+  Seed<T> o;
+  o.x0 = s.x0; o.y0 = s.y0; o.z0 = s.z0;
+  o.R = (T)s.pt / c.k;
+  o.akap = T(1) / o.R;
+  o.rho = s.charge > 0 ? o.akap : -o.akap;
+  if constexpr (sizeof(T) == 4) {
+    sincosf(s.phi, &o.sp, &o.cp);
+    o.cot = sinhf(s.eta);
+  } else {
+    sincos((double)s.phi, &o.sp, &o.cp);
+    o.cot = sinh((double)s.eta);
+  }
+  return o;
+}
+
+// distance of (x, y) from the seed circle, |p - c| - R up to sign, as 2A / (1 + sqrt(1 + 2 rho A))
+// with A = rho/2 |u|^2 - u.n, u = p - (x0, y0): exact, and free of the cancellation of |p-c| - R
+template <class T>
+__device__ __forceinline__ T seed_dist(const Seed<T>& s, T x, T y) {
+  const T ux = x - s.x0, uy = y - s.y0;
+  const T A = T(0.5) * s.rho * (ux * ux + uy * uy) - (ux * s.sp - uy * s.cp);
+  return T(2) * A / (T(1) + m_sqrt(T(1) + T(2) * s.rho * A));
+}
+
+template <class T>
+__device__ __forceinline__ void seed_terms(const Seed<T>& s, const Cst<T>& c, T x, T y, T z, T r,
+                                           bool ec, T& xy_term, T& rz_term) {
+  const T d = seed_dist(s, x, y);
+  const T e1 = r * c.pls_dir_err;
+  const T e2 = c.pls_pt_err * r * r * T(0.5) * s.akap;
+  xy_term = d * d / (c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2);
+  const T sa = arc_len(s.akap, r);
+  const T zp = s.z0 + sa * s.cot;
+  const T sz = ec ? c.sigma_r * m_abs(s.cot) : c.sigma_z;
+  const T th = sa * (T(1) + s.cot * s.cot) * c.pls_dir_err;
+  rz_term = (z - zp) * (z - zp) / (sz * sz + th * th);
+}
+
+struct ObjMd {
+  const int32_t* md[5];   // first..last MD of each object (T3: 3, T5: 5)
+  int64_t stride;         // unused for T3; T5 md arrays are [5][S]
+};
+
+// Candidate pre-filter: one warp per seed; the candidates (objects in every module of the seed's
+// pixel-map row) are flattened across the warp with a shuffle-based search over the per-module
+// object counts.
+template <int N>
+__global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjMd om, int2* queue,
+                         int q_word, int64_t q_cap, float cut_xy, float cut_rz) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const float lim_xy = cut_xy * (1.0f + kGuardChi2) + kGuardChi2Abs;
+  const float lim_rz = cut_rz * (1.0f + kGuardChi2) + kGuardChi2Abs;
+  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < w.P; p += nwarps) {
+    const int bin = w.pls_bin[p];
+    if (bin < 0) continue;
+    const int e = find_seg(w.ev_pls_off, w.E, p);
+    const int e0 = e * g.n_mods;
+    const Seed<float> s = make_seed<float>(w.pls[p], c);
+    const int tb = g.pix_off[bin], nt = g.pix_off[bin + 1] - tb;
+    for (int t0 = 0; t0 < nt; t0 += 32) {
+      const int k = t0 + lane;
+      int start = 0, size = 0;
+      if (k < nt) {
+        const int vmk = e0 + g.pix_tgt[tb + k];
+        start = obj_off[vmk];
+        size = obj_off[vmk + 1] - start;
+      }
+      int incl = size;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int excl = incl - size;
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      for (int b = 0; b < total; b += 32) {
+        const int cidx = b + lane;
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int cand = lo + step;
+          const int ex = __shfl_sync(0xffffffffu, excl, cand);
+          if (ex <= cidx) lo = cand;
+        }
+        const int st = __shfl_sync(0xffffffffu, start, lo);
+        const int ex0 = __shfl_sync(0xffffffffu, excl, lo);
+        bool keep = false;
+        int obj = 0;
+        if (cidx < total) {
+          obj = st + (cidx - ex0);
+          float xy = 0.f, rz = 0.f;
+          keep = true;
+          int md[N];
+#pragma unroll
+          for (int a = 0; a < N; ++a) md[a] = om.md[a][obj];
+#pragma unroll
+          for (int a = 0; a < N; ++a) {
+            const int d = md[a];
+            const float x = w.md_x[d], y = w.md_y[d], r = w.md_r[d];
+            const float dd = seed_dist(s, x, y);
+            const float e1 = r * c.pls_dir_err;
+            const float e2 = c.pls_pt_err * r * r * 0.5f * s.akap;
+            xy += dd * dd / (c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2);
+            if (xy > lim_xy) { keep = false; break; }
+          }
+          if (keep) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+              const int d = md[a];
+              const float r = w.md_r[d], z = w.md_z[d];
+              const float sa = arc_len(s.akap, r);
+              const float zp = s.z0 + sa * s.cot;
+              const float sz = w.md_ec[d] ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
+              const float th = sa * (1.0f + s.cot * s.cot) * c.pls_dir_err;
+              rz += (z - zp) * (z - zp) / (sz * sz + th * th);
+              if (rz > lim_rz) { keep = false; break; }
+            }
+          }
+        }
+        const int q = warp_agg_slot(keep, &w.status[q_word]);
+        if (q >= 0 && q < q_cap) queue[q] = make_int2(p, obj);
+      }
+    }
+  }
+}
+
+template <int N>
+__global__ void k_pt_decide(Ws w, Cst<double> c, ObjMd om, const int2* queue, int q_word, int64_t q_cap,
+                            double cut_xy, double cut_rz, int32_t* a_pls, int32_t* a_obj, float* a_xy,
+                            float* a_rz, float* a_sc, int n_word, int64_t a_cap, int32_t* per_pls) {
+  const int n = min((int64_t)w.status[q_word], q_cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int2 q = queue[k];
+    const Seed<double> s = make_seed<double>(w.pls[q.x], c);
+    double xy = 0.0, rz = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const int d = om.md[a][q.y];
+      const double x = w.md_x[d], y = w.md_y[d], z = w.md_z[d];
+      const double r = sqrt(x * x + y * y);
+      double t1, t2;
+      seed_terms<double>(s, c, x, y, z, r, w.md_ec[d] != 0, t1, t2);
+      xy += t1;
+      rz += t2;
+    }
+    if (!(cut_xy - xy >= 0.0) || !(cut_rz - rz >= 0.0)) continue;
+    const int slot = atomicAdd(&w.status[n_word], 1);
+    if (slot >= a_cap) continue;
+    a_pls[slot] = q.x;
+    a_obj[slot] = q.y;
+    a_xy[slot] = (float)xy;
+    a_rz[slot] = (float)rz;
+    a_sc[slot] = (float)(xy + rz);
+    atomicAdd(&per_pls[q.x], 1);
+  }
+}
+
+// group appended pT objects by seed (ordered by object index within a seed)
+__global__ void k_pt_group(Ws w, int n_word, int64_t a_cap, const int32_t* a_pls, const int32_t* a_obj,
+                           const int32_t* off, int32_t* cur, int32_t* tmp_idx) {
+  const int n = (int)min((int64_t)w.status[n_word], a_cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int p = a_pls[k];
+    tmp_idx[off[p] + atomicAdd(&cur[p], 1)] = k;
+  }
+  (void)a_obj;
+}
+
+__global__ void k_pt_order(Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls,
+                           const int32_t* a_obj, const float* a_xy, const float* a_rz, const float* a_sc,
+                           int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+    const int a = off[p], b = off[p + 1];
+    for (int i = a + 1; i < b; ++i) {
+      const int v = tmp_idx[i];
+      const int key = a_obj[v];
+      int j = i - 1;
+      while (j >= a && a_obj[tmp_idx[j]] > key) {
+        tmp_idx[j + 1] = tmp_idx[j];
+        --j;
+      }
+      tmp_idx[j + 1] = v;
+    }
+    for (int i = a; i < b; ++i) {
+      const int v = tmp_idx[i];
+      d_pls[i] = a_pls[v];
+      d_obj[i] = a_obj[v];
+      d_xy[i] = a_xy[v];
+      d_rz[i] = a_rz[v];
+      d_sc[i] = a_sc[v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// track candidates
+// ---------------------------------------------------------------------------------------------
+enum TcType : int { TC_PT5 = 0, TC_PT3 = 1, TC_T5 = 2, TC_PLS = 3 };
+
+// hits of an object in output order: seed hits, then (lower, upper) of each MD inner -> outer;
+// event-local input indices
+__device__ __forceinline__ int md_hits(const Ws& w, int d, int* h) {
+  h[0] = w.borig[w.md_lo[d]];
+  h[1] = w.borig[w.md_up[d]];
+  return 2;
+}
+__device__ int t5_hits(const Ws& w, int i, int* h) {
+  const int64_t S = w.cap.t5_slots;
+  int n = 0;
+  for (int k = 0; k < 5; ++k) n += md_hits(w, w.t5_md[k * S + i], h + n);
+  return n;
+}
+__device__ int t3_hits(const Ws& w, int i, int* h) {
+  int n = md_hits(w, w.t3_md0[i], h);
+  n += md_hits(w, w.t3_md1[i], h + n);
+  n += md_hits(w, w.t3_md2[i], h + n);
+  return n;
+}
+__device__ int pls_hits(const Ws& w, int p, int* h) {
+  const lst_pls s = w.pls[p];
+  for (int k = 0; k < 4; ++k) h[k] = s.pix_hit[k];
+  return 4;
+}
+// type / index as stored in a candidate code: pT5 / pT3 -> dense pT index, T5 -> T5, pLS -> seed
+__device__ int code_hits(const Ws& w, int type, int idx, int* h) {
+  if (type == TC_PT5) {
+    const int n = pls_hits(w, w.pt5_pls[idx], h);
+    return n + t5_hits(w, w.pt5_obj[idx], h + n);
+  }
+  if (type == TC_PT3) {
+    const int n = pls_hits(w, w.pt3_pls[idx], h);
+    return n + t3_hits(w, w.pt3_obj[idx], h + n);
+  }
+  if (type == TC_T5) return t5_hits(w, idx, h);
+  return pls_hits(w, idx, h);
+}
+__device__ __forceinline__ void sort_small(int* h, int n) {
+  for (int i = 1; i < n; ++i) {
+    const int v = h[i];
+    int j = i - 1;
+    while (j >= 0 && h[j] > v) {
+      h[j + 1] = h[j];
+      --j;
+    }
+    h[j + 1] = v;
+  }
+}
+// lexicographic comparison of the sorted hit tuples of two candidates of the same type
+__device__ bool key_less(const Ws& w, int type, int a, int b) {
+  int ha[14], hb[14];
+  const int na = code_hits(w, type, a, ha), nb = code_hits(w, type, b, hb);
+  sort_small(ha, na);
+  sort_small(hb, nb);
+  const int n = min(na, nb);
+  for (int k = 0; k < n; ++k)
+    if (ha[k] != hb[k]) return ha[k] < hb[k];
+  return na < nb;
+}
+
+__global__ void k_tc_best(Ws w) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+    int b5 = -1;
+    for (int i = w.pt5_off[p]; i < w.pt5_off[p + 1]; ++i)
+      if (b5 < 0 || w.pt5_sc[i] < w.pt5_sc[b5] || (w.pt5_sc[i] == w.pt5_sc[b5] && key_less(w, TC_PT5, i, b5)))
+        b5 = i;
+    int b3 = -1;
+    for (int i = w.pt3_off[p]; i < w.pt3_off[p + 1]; ++i)
+      if (b3 < 0 || w.pt3_sc[i] < w.pt3_sc[b3] || (w.pt3_sc[i] == w.pt3_sc[b3] && key_less(w, TC_PT3, i, b3)))
+        b3 = i;
+    w.best5[p] = b5;
+    w.best3[p] = b3;
+    w.pls_member[p] = (b5 >= 0 || b3 >= 0) ? 1 : 0;
+  }
+}
+
+// hit -> T5 adjacency (binned hit indices)
+__global__ void k_h5_count(Ws w, int fill) {
+  const int n = w.t5_off[w.V];
+  const int64_t S = w.cap.t5_slots;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int k = 0; k < 5; ++k) {
+      const int d = w.t5_md[k * S + i];
+      const int hs[2] = {w.md_lo[d], w.md_up[d]};
+      for (int t = 0; t < 2; ++t) {
+        if (!fill) atomicAdd(&w.h5_cnt[hs[t]], 1);
+        else w.h5_idx[w.h5_off[hs[t]] + atomicAdd(&w.h5_cur[hs[t]], 1)] = i;
+      }
+    }
+  }
+}
+
+__global__ void k_t5_clean(Ws w, int overlap) {
+  const int n = w.t5_off[w.V];
+  const int64_t S = w.cap.t5_slots;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+    int ha[10];
+    for (int k = 0; k < 5; ++k) {
+      const int d = w.t5_md[k * S + a];
+      ha[2 * k] = w.md_lo[d];
+      ha[2 * k + 1] = w.md_up[d];
+    }
+    const float ca = w.t5_f[3 * S + a];
+    bool drop = false;
+    for (int t = 0; t < 10 && !drop; ++t) {
+      const int h = ha[t];
+      for (int k = w.h5_off[h]; k < w.h5_off[h + 1] && !drop; ++k) {
+        const int b = w.h5_idx[k];
+        if (b == a) continue;
+        int shared = 0;
+        for (int kb = 0; kb < 5; ++kb) {
+          const int d = w.t5_md[kb * S + b];
+          const int hb0 = w.md_lo[d], hb1 = w.md_up[d];
+          for (int u = 0; u < 10; ++u) shared += (ha[u] == hb0) + (ha[u] == hb1);
+        }
+        if (shared < overlap) continue;
+        const float cb = w.t5_f[3 * S + b];
+        if (cb < ca || (cb == ca && key_less(w, TC_T5, b, a))) drop = true;
+      }
+    }
+    w.t5_kept[a] = drop ? 0 : 1;
+  }
+}
+
+// eta-phi grid of 0.02 x (2 pi / 314) cells, wider than dr_min, so any pair closer than dr_min lies
+// in the same or adjacent cells
+constexpr int kCellsEta = 320;
+constexpr int kCellsPhi = 314;
+constexpr float kCellEtaMin = -3.2f;
+constexpr float kCellEtaW = 0.02f;
+
+__device__ __forceinline__ int cell_eta(float eta) {
+  int i = (int)floorf((eta - kCellEtaMin) / kCellEtaW);
+  return min(max(i, 0), kCellsEta - 1);
+}
+__device__ __forceinline__ int cell_phi(float phi) {
+  float p = fmodf(phi, 6.2831853f);
+  if (p < 0.f) p += 6.2831853f;
+  int i = (int)floorf(p * (kCellsPhi / 6.2831853f));
+  return min(max(i, 0), kCellsPhi - 1);
+}
+
+// dR < dr_min decided in float64 on the stored float32 eta / phi, with explicitly rounded
+// operations (the same IEEE sequence as any evaluation of the definition)
+__device__ __forceinline__ bool dr_close(double dr2, float ea, float pa, float eb, float pb) {
+  const double de = __dsub_rn((double)ea, (double)eb);
+  double dp = __dsub_rn((double)pa, (double)pb);
+  if (dp > kPiD) dp = __dsub_rn(dp, kTwoPiD);
+  if (dp <= -kPiD) dp = __dadd_rn(dp, kTwoPiD);
+  const double d2 = __dadd_rn(__dmul_rn(de, de), __dmul_rn(dp, dp));
+  return d2 < dr2;
+}
+
+__device__ __forceinline__ void item_of(const Ws& w, int code, float& eta, float& phi, int& type, int& idx) {
+  type = code >> 29;
+  idx = code & ((1 << 29) - 1);
+  if (type == TC_T5) {
+    const int64_t S = w.cap.t5_slots;
+    eta = w.t5_f[5 * S + idx];
+    phi = w.t5_f[6 * S + idx];
+  } else {
+    eta = w.pls[idx].eta;
+    phi = w.pls[idx].phi;
+  }
+}
+
+// pass 0: count, pass 1: fill; items: accepted pT5 seeds (type 0), pT3 candidates (1), kept T5 (2)
+__global__ void k_grid_items(Ws w, Geo g, int fill) {
+  const int n_t5 = w.t5_off[w.V];
+  const int total = w.P + n_t5;
+  const int NC = kCellsEta * kCellsPhi;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    int code, e;
+    if (k < w.P) {
+      const int p = k;
+      if (w.best5[p] >= 0) code = (TC_PT5 << 29) | p;
+      else if (w.best3[p] >= 0) code = (TC_PT3 << 29) | p;
+      else continue;
+      e = find_seg(w.ev_pls_off, w.E, p);
+    } else {
+      const int i = k - w.P;
+      if (!w.t5_kept[i]) continue;
+      code = (TC_T5 << 29) | i;
+      e = w.md_vm[w.t5_md[i]] / g.n_mods;
+    }
+    float eta, phi;
+    int type, idx;
+    item_of(w, code, eta, phi, type, idx);
+    const int cell = e * NC + cell_eta(eta) * kCellsPhi + cell_phi(phi);
+    if (!fill) atomicAdd(&w.cell_cnt[cell], 1);
+    else w.cell_item[w.cell_off[cell] + atomicAdd(&w.cell_cur[cell], 1)] = code;
+  }
+}
+
+// is (eta, phi) of event e within dr_min of an item accepted so far? mask: which item types count
+__device__ bool near_accepted(const Ws& w, double dr2, int e, float eta, float phi, int mask) {
+  const int NC = kCellsEta * kCellsPhi;
+  const int ce = cell_eta(eta), cp = cell_phi(phi);
+  for (int de = -1; de <= 1; ++de) {
+    const int ie = ce + de;
+    if (ie < 0 || ie >= kCellsEta) continue;
+    for (int dp = -1; dp <= 1; ++dp) {
+      const int ip = (cp + dp + kCellsPhi) % kCellsPhi;
+      const int cell = e * NC + ie * kCellsPhi + ip;
+      for (int k = w.cell_off[cell]; k < w.cell_off[cell + 1]; ++k) {
+        float eb, pb;
+        int type, idx;
+        item_of(w, w.cell_item[k], eb, pb, type, idx);
+        if (!((mask >> type) & 1)) continue;
+        if (type == TC_PT3 && !w.acc3[idx]) continue;
+        if (type == TC_T5 && !w.acc5t[idx]) continue;
+        if (dr_close(dr2, eta, phi, eb, pb)) return true;
+      }
+    }
+  }
+  return false;
+}
+
+__global__ void k_clean_pt3(Ws w, double dr2) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+    uint8_t acc = 0;
+    if (w.best5[p] < 0 && w.best3[p] >= 0) {
+      const int e = find_seg(w.ev_pls_off, w.E, p);
+      acc = near_accepted(w, dr2, e, w.pls[p].eta, w.pls[p].phi, 1 << TC_PT5) ? 0 : 1;
+    }
+    w.acc3[p] = acc;
+  }
+}
+
+__global__ void k_clean_t5(Ws w, Geo g, double dr2) {
+  const int n = w.t5_off[w.V];
+  const int64_t S = w.cap.t5_slots;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint8_t acc = 0;
+    if (w.t5_kept[i]) {
+      const int e = w.md_vm[w.t5_md[i]] / g.n_mods;
+      acc = near_accepted(w, dr2, e, w.t5_f[5 * S + i], w.t5_f[6 * S + i], (1 << TC_PT5) | (1 << TC_PT3)) ? 0 : 1;
+    }
+    w.acc5t[i] = acc;
+  }
+}
+
+__global__ void k_clean_pls(Ws w, double dr2) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+    uint8_t acc = 0;
+    if (!w.pls_member[p]) {
+      const int e = find_seg(w.ev_pls_off, w.E, p);
+      acc = near_accepted(w, dr2, e, w.pls[p].eta, w.pls[p].phi,
+                          (1 << TC_PT5) | (1 << TC_PT3) | (1 << TC_T5)) ? 0 : 1;
+    }
+    w.accl[p] = acc;
+  }
+}
+
+// Per-event assembly: one block per event collects the accepted candidates, sorts them by
+// (type, sorted hit tuple) and writes the output rows. The sort is a bitonic sort of 64-bit keys
+// (type, smallest hit) in shared memory, followed by an exact ordering of equal-key runs.
+constexpr int kTcSortMax = 8192;
+
+__device__ __forceinline__ unsigned long long tc_sort_key(int type, int first_hit) {
+  return ((unsigned long long)(unsigned)type << 32) | (unsigned)(first_hit ^ (int)0x80000000);
+}
+
+__device__ __forceinline__ int hit_key_cmp(const int* a, const int* b) {
+  for (int k = 0; k < 14; ++k)
+    if (a[k] != b[k]) return a[k] < b[k] ? -1 : 1;
+  return 0;
+}
+
+__global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem_raw);
+  int* sidx = reinterpret_cast<int*>(skey + kTcSortMax);
+  __shared__ int n_sh;
+  const int e = blockIdx.x;
+  if (e >= w.E) return;
+  const int p0 = w.ev_pls_off[e], p1 = w.ev_pls_off[e + 1];
+  const int t0 = w.t5_off[e * g.n_mods], t1 = w.t5_off[(e + 1) * g.n_mods];
+  const int region = p0 + t0;
+  int* code = w.tc_code + region;
+  unsigned long long* key = w.tc_key + region;
+  int* hk = w.tc_hit_key + (int64_t)region * 14;
+  if (threadIdx.x == 0) n_sh = 0;
+  __syncthreads();
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    if (w.best5[p] >= 0) code[atomicAdd(&n_sh, 1)] = (TC_PT5 << 29) | p;
+    if (w.acc3[p]) code[atomicAdd(&n_sh, 1)] = (TC_PT3 << 29) | p;
+    if (w.accl[p]) code[atomicAdd(&n_sh, 1)] = (TC_PLS << 29) | p;
+  }
+  for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x)
+    if (w.acc5t[i]) code[atomicAdd(&n_sh, 1)] = (TC_T5 << 29) | i;
+  __syncthreads();
+  const int n = n_sh;
+  // sorted hit tuples (padded with INT_MAX) and 64-bit prefix keys
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int type = code[k] >> 29, idx = code[k] & ((1 << 29) - 1);
+    int h[14];
+    const int obj = (type == TC_PT5) ? w.best5[idx] : (type == TC_PT3 ? w.best3[idx] : idx);
+    const int nh = code_hits(w, type, obj, h);
+    sort_small(h, nh);
+    for (int t = 0; t < 14; ++t) hk[(int64_t)k * 14 + t] = t < nh ? h[t] : 0x7fffffff;
+    key[k] = tc_sort_key(type, h[0]);
+  }
+  __syncthreads();
+  const bool in_smem = n <= kTcSortMax;
+  int m = 1;
+  while (m < n) m <<= 1;
+  if (in_smem) {
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+      skey[k] = k < n ? key[k] : ~0ull;
+      sidx[k] = k < n ? k : 0x7fffffff;
+    }
+    __syncthreads();
+    for (int size = 2; size <= m; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = threadIdx.x; t < m / 2; t += blockDim.x) {
+          const int lo = 2 * t - (t & (stride - 1));
+          const int hi = lo + stride;
+          const bool up = ((lo & size) == 0);
+          const unsigned long long a = skey[lo], b = skey[hi];
+          const bool gt = (a > b) || (a == b && sidx[lo] > sidx[hi]);
+          if (gt == up) {
+            skey[lo] = b; skey[hi] = a;
+            const int ti = sidx[lo]; sidx[lo] = sidx[hi]; sidx[hi] = ti;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // exact order inside runs of equal prefix keys (short runs: insertion sort on full tuples)
+    if (threadIdx.x == 0) {
+      int r0 = 0;
+      while (r0 < n) {
+        int r1 = r0 + 1;
+        while (r1 < n && skey[r1] == skey[r0]) ++r1;
+        for (int i = r0 + 1; i < r1; ++i) {
+          const int v = sidx[i];
+          int j = i - 1;
+          while (j >= r0 && hit_key_cmp(hk + (int64_t)sidx[j] * 14, hk + (int64_t)v * 14) > 0) {
+            sidx[j + 1] = sidx[j];
+            --j;
+          }
+          sidx[j + 1] = v;
+        }
+        r0 = r1;
+      }
+    }
+    __syncthreads();
+  }
+  // write rows in order (ranks computed directly when the event does not fit the shared sort)
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    int src, rank;
+    if (in_smem) {
+      src = sidx[k];
+      rank = k;
+    } else {
+      src = k;
+      rank = 0;
+      const int ts = code[k] >> 29;
+      for (int j = 0; j < n; ++j) {
+        const int tj = code[j] >> 29;
+        const int c = (tj != ts) ? (tj < ts ? -1 : 1) : hit_key_cmp(hk + (int64_t)j * 14, hk + (int64_t)k * 14);
+        rank += c < 0;
+      }
+    }
+    const int type = code[src] >> 29, idx = code[src] & ((1 << 29) - 1);
+    const int row = region + rank;
+    int h[14];
+    int obj, nh;
+    float pt, eta, phi;
+    if (type == TC_PT5 || type == TC_PT3) {
+      const int dense = type == TC_PT5 ? w.best5[idx] : w.best3[idx];
+      nh = code_hits(w, type, dense, h);
+      obj = dense - (type == TC_PT5 ? w.pt5_off[p0] : w.pt3_off[p0]);
+      pt = w.pls[idx].pt; eta = w.pls[idx].eta; phi = w.pls[idx].phi;
+    } else if (type == TC_T5) {
+      nh = code_hits(w, type, idx, h);
+      obj = idx - t0;
+      const int64_t S = w.cap.t5_slots;
+      pt = w.t5_f[7 * S + idx]; eta = w.t5_f[5 * S + idx]; phi = w.t5_f[6 * S + idx];
+    } else {
+      nh = code_hits(w, type, idx, h);
+      obj = idx - p0;
+      pt = w.pls[idx].pt; eta = w.pls[idx].eta; phi = w.pls[idx].phi;
+    }
+    w.tc_type[row] = type;
+    w.tc_obj[row] = obj;
+    for (int t = 0; t < 14; ++t) w.tc_hits[(int64_t)row * 14 + t] = t < nh ? h[t] : -1;
+    w.tc_pt[row] = pt;
+    w.tc_eta[row] = eta;
+    w.tc_phi[row] = phi;
+  }
+  if (threadIdx.x == 0) w.tc_cnt[e] = n;
+}
+
+}  // namespace
+
+void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
+  k_pls_prep<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, g);
+  LST_LAUNCH(L);
+  const int threads = 32 * L.warps_px;
+  const int blocks = grid_for((int64_t)w.P * 32, threads, 152 * 16);
+  ObjMd om3{{w.t3_md0, w.t3_md1, w.t3_md2, nullptr, nullptr}, 0};
+  const int64_t S = w.cap.t5_slots;
+  ObjMd om5{{w.t5_md, w.t5_md + S, w.t5_md + 2 * S, w.t5_md + 3 * S, w.t5_md + 4 * S}, S};
+  if (g.n_pix_bins > 0) {
+    KT_BEGIN(L, K_PT3_PRE);
+  k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
+                                                   c.f.chi2_pt3_xy, c.f.chi2_pt3_rz);
+  KT_END(L, K_PT3_PRE);
+    LST_LAUNCH(L);
+    KT_BEGIN(L, K_PT5_PRE);
+  k_pt_pre<5><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t5_off, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5,
+                                                   c.f.chi2_pt5_xy, c.f.chi2_pt5_rz);
+  KT_END(L, K_PT5_PRE);
+    LST_LAUNCH(L);
+  }
+  KT_BEGIN(L, K_PT3_DECIDE);
+  k_pt_decide<3><<<grid_for(w.cap.q_p3, 128, 152 * 8), 128, 0, L.stream>>>(
+      w, c.d, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3, c.d.chi2_pt3_xy, c.d.chi2_pt3_rz, w.p3a_pls, w.p3a_obj,
+      w.p3a_xy, w.p3a_rz, w.p3a_sc, ST_N_PT3, w.cap.p3_slots, w.p3_cnt);
+  KT_END(L, K_PT3_DECIDE);
+  LST_LAUNCH(L);
+  KT_BEGIN(L, K_PT5_DECIDE);
+  k_pt_decide<5><<<grid_for(w.cap.q_p5, 128, 152 * 8), 128, 0, L.stream>>>(
+      w, c.d, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5, c.d.chi2_pt5_xy, c.d.chi2_pt5_rz, w.p5a_pls, w.p5a_obj,
+      w.p5a_xy, w.p5a_rz, w.p5a_sc, ST_N_PT5, w.cap.p5_slots, w.p5_cnt);
+  KT_END(L, K_PT5_DECIDE);
+  LST_LAUNCH(L);
+  scan_exclusive(w.p3_cnt, w.pt3_off, w.P, w.scan_tmp, L);
+  scan_exclusive(w.p5_cnt, w.pt5_off, w.P, w.scan_tmp, L);
+  k_pt_group<<<grid_for(w.cap.p3_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT3, w.cap.p3_slots, w.p3a_pls,
+                                                                   w.p3a_obj, w.pt3_off, w.p3_cur, w.grp_tmp);
+  k_pt_order<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, w.pt3_off, w.grp_tmp, w.p3a_pls, w.p3a_obj,
+                                                      w.p3a_xy, w.p3a_rz, w.p3a_sc, w.pt3_pls, w.pt3_obj,
+                                                      w.pt3_xy, w.pt3_rz, w.pt3_sc);
+  k_pt_group<<<grid_for(w.cap.p5_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT5, w.cap.p5_slots, w.p5a_pls,
+                                                                   w.p5a_obj, w.pt5_off, w.p5_cur, w.grp_tmp);
+  k_pt_order<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, w.pt5_off, w.grp_tmp, w.p5a_pls, w.p5a_obj,
+                                                      w.p5a_xy, w.p5a_rz, w.p5a_sc, w.pt5_pls, w.pt5_obj,
+                                                      w.pt5_xy, w.pt5_rz, w.pt5_sc);
+  *L.launches += 4;
+}
+
+void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
+  const double dr2 = c.d.dr_min * c.d.dr_min;
+  k_tc_best<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w);
+  k_h5_count<<<grid_for(w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, 0);
+  *L.launches += 2;
+  scan_exclusive(w.h5_cnt, w.h5_off, w.cap.H, w.scan_tmp, L);
+  k_h5_count<<<grid_for(w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, 1);
+  KT_BEGIN(L, K_TC_CLEAN);
+  k_t5_clean<<<grid_for(w.cap.t5_slots, 128), 128, 0, L.stream>>>(w, c.d.t5_overlap_hits);
+  KT_END(L, K_TC_CLEAN);
+  k_grid_items<<<grid_for(w.P + w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, g, 0);
+  *L.launches += 3;
+  scan_exclusive(w.cell_cnt, w.cell_off, (int64_t)w.E * w.n_cells, w.scan_tmp, L);
+  k_grid_items<<<grid_for(w.P + w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, g, 1);
+  k_clean_pt3<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, dr2);
+  k_clean_t5<<<grid_for(w.cap.t5_slots, 128), 128, 0, L.stream>>>(w, g, dr2);
+  k_clean_pls<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, dr2);
+  const size_t smem = kTcSortMax * (sizeof(unsigned long long) + sizeof(int));
+  KT_BEGIN(L, K_TC_ASSEMBLE);
+  k_tc_assemble<<<w.E, 1024, smem, L.stream>>>(w, g);
+  KT_END(L, K_TC_ASSEMBLE);
+  *L.launches += 5;
+}
+
+// the grid's cells per event
+int tc_cells_per_event() { return kCellsEta * kCellsPhi; }
+
+void tc_configure() {
+  const size_t smem = kTcSortMax * (sizeof(unsigned long long) + sizeof(int));
+  cudaFuncSetAttribute(k_tc_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace lst

@@ -1,0 +1,101 @@
+// Exclusive prefix sum over int32 counts (three passes: per-tile scan, scan of tile totals,
+// add-back). Used for every count -> offset step of the chain (sensor offsets, per-module object
+// offsets, per-MD adjacency offsets).
+#include "lst_internal.h"
+
+namespace lst {
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kTile = kScanBlock * kScanItems;
+
+__device__ __forceinline__ int block_excl_scan(int v, int& total) {
+  __shared__ int warp_sums[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const int warp_prefix = wid > 0 ? warp_sums[wid - 1] : 0;
+  total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return warp_prefix + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(const int32_t* in, int32_t* out, int64_t n,
+                                                           int32_t* tile_sums) {
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int local = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    local += v[k];
+  }
+  int total;
+  int pre = block_excl_scan(local, total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(int32_t* tile_sums, int64_t n_tiles, int32_t* out,
+                                                          int64_t n) {
+  int carry = 0;
+  for (int64_t b0 = 0; b0 < n_tiles; b0 += kScanBlock) {
+    const int64_t i = b0 + threadIdx.x;
+    const int v = i < n_tiles ? tile_sums[i] : 0;
+    int total;
+    const int pre = block_excl_scan(v, total);
+    if (i < n_tiles) tile_sums[i] = carry + pre;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_add(int32_t* out, int64_t n, const int32_t* tile_sums) {
+  const int add = tile_sums[blockIdx.x];
+  if (add == 0) return;
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) out[base + k] += add;
+}
+
+}  // namespace
+
+int64_t scan_tmp_elems(int64_t n) { return (n + kTile - 1) / kTile + 1; }
+
+void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L) {
+  const int64_t tiles = (n + kTile - 1) / kTile;
+  if (tiles == 0) {
+    k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, 0, out, 0);
+    LST_LAUNCH(L);
+    return;
+  }
+  k_scan_tiles<<<(unsigned)tiles, kScanBlock, 0, L.stream>>>(in, out, n, tmp);
+  k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, tiles, out, n);
+  k_scan_add<<<(unsigned)tiles, kScanBlock, 0, L.stream>>>(out, n, tmp);
+  *L.launches += 3;
+}
+
+}  // namespace lst

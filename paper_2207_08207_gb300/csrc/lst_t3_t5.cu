@@ -1,0 +1,384 @@
+// Triplets and Quintuplets (paper Sec. 2.3).
+//
+// T3: two LS sharing an MD. The circle through the three anchor hits gives a pT estimate
+// (pT = k R >= f_t3 pT_thr) and an impact parameter (|hypot(centre) - R| <= d0_t3); a straight
+// line in (arc length, z) through the anchors gives chi2_rz <= chi2_t3.
+// T5: two T3 sharing an MD. Inner and outer T3 curvatures must agree
+// (|k_in - k_out| <= c_rel max + c_abs); Karimaki's circle fit of the five anchors and an r-z line
+// fit give chi2_c <= chi2_t5_c and chi2_rz <= chi2_t5_rz.
+//
+// Candidates are enumerated in float32 with a conservative pre-filter; the survivors are decided
+// (and their stored floats computed) in float64 from the float32 hit coordinates.
+#include "lst_internal.h"
+
+namespace lst {
+namespace {
+
+// chi2 pre-filter: reject only when clearly above the cut (float32 error is far below the guard)
+__device__ __forceinline__ bool chi2_clear_fail(float chi2, float cut) {
+  return chi2 > cut * (1.0f + kGuardChi2) + kGuardChi2Abs;
+}
+
+template <class T>
+struct Anchor {
+  T x, y, z, r;
+  bool ec;
+};
+
+template <class T>
+__device__ __forceinline__ Anchor<T> anchor(const Ws& w, int d) {
+  Anchor<T> a;
+  a.x = (T)w.md_x[d];
+  a.y = (T)w.md_y[d];
+  a.z = (T)w.md_z[d];
+  if constexpr (sizeof(T) == 4) a.r = w.md_r[d];
+  else a.r = sqrt(a.x * a.x + a.y * a.y);
+  a.ec = w.md_ec[d] != 0;
+  return a;
+}
+
+// T3 selection on anchors (h1, h2, h3). Returns the verdict (float: pre-filter semantics, where
+// kAccept means "not clearly rejected").
+template <class T>
+__device__ __forceinline__ int t3_eval(const Cst<T>& c, const Anchor<T>& h1, const Anchor<T>& h2,
+                                       const Anchor<T>& h3, Circle3<T>& circ, T& chi2) {
+  circ = circle3<T>(h1.x, h1.y, h2.x, h2.y, h3.x, h3.y);
+  const T ak = m_abs(circ.kappa);
+  chi2 = T(0);
+  if constexpr (sizeof(T) == 4) {
+    Acc32 acc(kGuardWindow * 4.0f);
+    acc.cut_ge(c.f_t3 * c.pt_thr, c.k / ak);
+    acc.cut(c.d0_t3, circ.d0);
+    if (acc.fail) return kReject;
+    const T r[3] = {h1.r, h2.r, h3.r}, z[3] = {h1.z, h2.z, h3.z};
+    const bool ec[3] = {h1.ec, h2.ec, h3.ec};
+    T slope;
+    if (!rz_fit<T, 3>(c, ak, r, z, ec, chi2, slope)) return kAccept;  // decided in float64
+    return chi2_clear_fail(chi2, c.chi2_t3) ? kReject : kAccept;
+  } else {
+    Acc64 acc;
+    acc.cut_ge(c.f_t3 * c.pt_thr, c.k * circ.R);
+    acc.cut(c.d0_t3, circ.d0);
+    const T r[3] = {h1.r, h2.r, h3.r}, z[3] = {h1.z, h2.z, h3.z};
+    const bool ec[3] = {h1.ec, h2.ec, h3.ec};
+    T slope;
+    if (!rz_fit<T, 3>(c, ak, r, z, ec, chi2, slope)) {
+      acc.reject();
+      chi2 = T(1) / T(0);
+    } else {
+      acc.cut(c.chi2_t3, chi2);
+    }
+    return acc.verdict();
+  }
+}
+
+__global__ void k_t3_pre(Ws w, Cst<float> c) {
+  const int n_ls = w.ls_off[w.V];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ls; i += gridDim.x * blockDim.x) {
+    const int m2 = w.ls_out[i];
+    const int j0 = w.lsin_off[m2], j1 = w.lsin_off[m2 + 1];
+    if (j0 == j1) continue;
+    const Anchor<float> h1 = anchor<float>(w, w.ls_in[i]);
+    const Anchor<float> h2 = anchor<float>(w, m2);
+    for (int j = j0; j < j1; ++j) {
+      const Anchor<float> h3 = anchor<float>(w, w.ls_out[j]);
+      Circle3<float> circ;
+      float chi2;
+      const int v = t3_eval<float>(c, h1, h2, h3, circ, chi2);
+      const int q = warp_agg_slot(v != kReject, &w.status[ST_Q_T3]);
+      if (q >= 0 && q < w.cap.q_t3) w.q_t3[q] = make_int2(i, j);
+    }
+  }
+}
+
+__global__ void k_t3_decide(Ws w, Cst<double> c) {
+  const int n = min((int64_t)w.status[ST_Q_T3], w.cap.q_t3);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int2 q = w.q_t3[k];
+    const int md0 = w.ls_in[q.x], md1 = w.ls_out[q.x], md2 = w.ls_out[q.y];
+    Circle3<double> circ;
+    double chi2;
+    const int v = t3_eval<double>(c, anchor<double>(w, md0), anchor<double>(w, md1),
+                                  anchor<double>(w, md2), circ, chi2);
+    if (v != kAccept) continue;
+    const int vm = w.md_vm[md0];
+    const int slot = atomicAdd(&w.t3_cnt[vm], 1);
+    const int cap = w.t3_cap[vm], base = w.t3_base[vm];
+    if (slot < cap && (int64_t)base + slot < w.cap.t3_slots) {
+      const int s = base + slot;
+      w.t3s_a[s] = q.x;
+      w.t3s_b[s] = q.y;
+      w.t3s_R[s] = (float)circ.R;
+      w.t3s_xc[s] = (float)circ.xc;
+      w.t3s_yc[s] = (float)circ.yc;
+      w.t3s_chi2[s] = (float)chi2;
+      w.t3s_pte[s] = (float)fmin(c.k * circ.R, c.pt_cap);
+    }
+  }
+}
+
+__device__ __forceinline__ int clamp_cap2(double pred, long long bound, int ovr) {
+  long long p = (long long)ceil(pred);
+  if (p < ovr) p = ovr;
+  if (p > bound) p = bound;
+  if (p > (1 << 28)) p = 1 << 28;
+  return (int)p;
+}
+
+// T3 capacity of module vm: bound = number of (inner LS, outer LS) pairs whose inner LS starts in vm
+__global__ void k_t3_caps(Ws w) {
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
+    long long bound = 0;
+    for (int i = w.ls_off[vm]; i < w.ls_off[vm + 1]; ++i) {
+      const int m2 = w.ls_out[i];
+      bound += w.lsin_off[m2 + 1] - w.lsin_off[m2];
+    }
+    const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.2 * (double)bound), bound, w.t3_ovr[vm]);
+    w.t3_cap[vm] = cc;
+    w.t3_base[vm] = cc;
+  }
+}
+
+__global__ void k_t3_compact(Ws w) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+    const int o = w.t3_off[vm], n = w.t3_off[vm + 1] - o;
+    if (n == 0) continue;
+    const int base = w.t3_base[vm];
+    for (int j = lane; j < n; j += 32) {
+      const unsigned long long kj = ((unsigned long long)(unsigned)w.t3s_a[base + j] << 32) |
+                                    (unsigned)w.t3s_b[base + j];
+      int rank = 0;
+      for (int i = 0; i < n; ++i) {
+        const unsigned long long ki = ((unsigned long long)(unsigned)w.t3s_a[base + i] << 32) |
+                                      (unsigned)w.t3s_b[base + i];
+        rank += ki < kj;
+      }
+      const int d = o + rank, s = base + j;
+      const int a = w.t3s_a[s], b = w.t3s_b[s];
+      w.t3_a[d] = a;
+      w.t3_b[d] = b;
+      const int md0 = w.ls_in[a];
+      w.t3_md0[d] = md0;
+      w.t3_md1[d] = w.ls_out[a];
+      w.t3_md2[d] = w.ls_out[b];
+      w.t3_R[d] = w.t3s_R[s];
+      w.t3_xc[d] = w.t3s_xc[s];
+      w.t3_yc[d] = w.t3s_yc[s];
+      w.t3_chi2[d] = w.t3s_chi2[s];
+      w.t3_pte[d] = w.t3s_pte[s];
+      atomicAdd(&w.t3md_cnt[md0], 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Karimaki's circle fit (V. Karimaki, NIM A305 (1991) 187) with equal weights, float64.
+// Circle: 1/2 rho (x^2 + y^2) - (1 + rho d)(x sin phi - y cos phi) + 1/2 rho d^2 + d = 0;
+// phi is the direction at the point of closest approach to the origin, oriented first -> last.
+// ---------------------------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void karimaki(const double* x, const double* y, double& rho, double& phi,
+                                         double& d) {
+  double mx = 0, my = 0, mxx = 0, mxy = 0, myy = 0, mr2 = 0, mxr = 0, myr = 0, mrr = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double r2 = x[i] * x[i] + y[i] * y[i];
+    mx += x[i]; my += y[i];
+    mxx += x[i] * x[i]; mxy += x[i] * y[i]; myy += y[i] * y[i];
+    mr2 += r2; mxr += x[i] * r2; myr += y[i] * r2; mrr += r2 * r2;
+  }
+  const double inv = 1.0 / N;
+  mx *= inv; my *= inv; mxx *= inv; mxy *= inv; myy *= inv; mr2 *= inv; mxr *= inv; myr *= inv; mrr *= inv;
+  const double Cxx = mxx - mx * mx, Cxy = mxy - mx * my, Cyy = myy - my * my;
+  const double Cxr = mxr - mx * mr2, Cyr = myr - my * mr2, Crr = mrr - mr2 * mr2;
+  const double q1 = Crr * Cxy - Cxr * Cyr;
+  const double q2 = Crr * (Cxx - Cyy) - Cxr * Cxr + Cyr * Cyr;
+  phi = 0.5 * atan2(2.0 * q1, q2);
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < 0.0) {
+    phi += kPiD;
+    sp = -sp;
+    cp = -cp;
+  }
+  if (phi > kPiD) phi -= kTwoPiD;
+  if (phi <= -kPiD) phi += kTwoPiD;
+  const double kap = (sp * Cxr - cp * Cyr) / Crr;
+  const double del = -kap * mr2 + sp * mx - cp * my;
+  const double root = sqrt(1.0 - 4.0 * del * kap);
+  rho = 2.0 * kap / root;
+  d = 2.0 * del / (1.0 + root);
+}
+
+__global__ void k_t5_caps(Ws w) {
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
+    long long bound = 0;
+    for (int i = w.t3_off[vm]; i < w.t3_off[vm + 1]; ++i) {
+      const int m3 = w.t3_md2[i];
+      bound += w.t3md_off[m3 + 1] - w.t3md_off[m3];
+    }
+    const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
+    w.t5_cap[vm] = cc;
+    w.t5_base[vm] = cc;
+  }
+}
+
+__device__ __forceinline__ float kappa_of(float R) { return isinf(R) ? 0.0f : 1.0f / R; }
+
+__global__ void k_t5_pre(Ws w, Cst<float> c) {
+  const int n_t3 = w.t3_off[w.V];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_t3; i += gridDim.x * blockDim.x) {
+    const int m3 = w.t3_md2[i];
+    const int j0 = w.t3md_off[m3], j1 = w.t3md_off[m3 + 1];
+    const float kin = kappa_of(w.t3_R[i]);
+    for (int j = j0; j < j1; ++j) {
+      const float kout = kappa_of(w.t3_R[j]);
+      Acc32 acc(kGuardWindow);
+      acc.cut(c.c_rel * fmaxf(kin, kout) + c.c_abs, fabsf(kin - kout));
+      const int q = warp_agg_slot(!acc.fail, &w.status[ST_Q_T5]);
+      if (q >= 0 && q < w.cap.q_t5) w.q_t5[q] = make_int2(i, j);
+    }
+  }
+}
+
+__global__ void k_t5_decide(Ws w, Cst<double> c) {
+  const int n = min((int64_t)w.status[ST_Q_T5], w.cap.q_t5);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int2 q = w.q_t5[k];
+    const int i = q.x, j = q.y;
+    const float Ri = w.t3_R[i], Rj = w.t3_R[j];
+    const double kin = isinf(Ri) ? 0.0 : 1.0 / (double)Ri;
+    const double kout = isinf(Rj) ? 0.0 : 1.0 / (double)Rj;
+    Acc64 acc;
+    acc.cut(c.c_rel * fmax(kin, kout) + c.c_abs, fabs(kin - kout));
+    if (acc.fail) continue;
+    const int md[5] = {w.t3_md0[i], w.t3_md1[i], w.t3_md2[i], w.t3_md1[j], w.t3_md2[j]};
+    double x[5], y[5], z[5], r[5];
+    bool ec[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      x[a] = w.md_x[md[a]];
+      y[a] = w.md_y[md[a]];
+      z[a] = w.md_z[md[a]];
+      r[a] = sqrt(x[a] * x[a] + y[a] * y[a]);
+      ec[a] = w.md_ec[md[a]] != 0;
+    }
+    double rho, phi, d;
+    karimaki<5>(x, y, rho, phi, d);
+    double sp, cp;
+    sincos(phi, &sp, &cp);
+    double chi2c = 0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      // geometric residual |p - c| - R, as 2 eps / (1 + sqrt(1 + 2 rho eps)) (exact, stable)
+      const double eps = 0.5 * rho * (x[a] * x[a] + y[a] * y[a]) - (1.0 + rho * d) * (x[a] * sp - y[a] * cp) +
+                         0.5 * rho * d * d + d;
+      const double res = 2.0 * eps / (1.0 + sqrt(1.0 + 2.0 * rho * eps)) / c.sigma_rphi;
+      chi2c += res * res;
+    }
+    acc.cut(c.chi2_t5_c, chi2c);
+    double chi2rz, slope;
+    if (!rz_fit<double, 5>(c, fabs(rho), r, z, ec, chi2rz, slope)) {
+      acc.reject();
+    } else {
+      acc.cut(c.chi2_t5_rz, chi2rz);
+    }
+    if (acc.fail) continue;
+    const int vm = w.md_vm[md[0]];
+    const int slot = atomicAdd(&w.t5_cnt[vm], 1);
+    const int cap = w.t5_cap[vm], base = w.t5_base[vm];
+    if (slot < cap && (int64_t)base + slot < w.cap.t5_slots) {
+      const int s = base + slot;
+      const int64_t S = w.cap.t5_slots;
+      w.t5s_a[s] = i;
+      w.t5s_b[s] = j;
+      w.t5s_f[0 * S + s] = (float)kin;
+      w.t5s_f[1 * S + s] = (float)kout;
+      w.t5s_f[2 * S + s] = (float)rho;
+      w.t5s_f[3 * S + s] = (float)chi2c;
+      w.t5s_f[4 * S + s] = (float)chi2rz;
+      w.t5s_f[5 * S + s] = (float)asinh(slope);
+      w.t5s_f[6 * S + s] = (float)phi;
+      w.t5s_f[7 * S + s] = (float)(rho == 0.0 ? c.pt_cap : fmin(c.k / fabs(rho), c.pt_cap));
+    }
+  }
+}
+
+__global__ void k_t5_compact(Ws w) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int64_t S = w.cap.t5_slots;
+  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+    const int o = w.t5_off[vm], n = w.t5_off[vm + 1] - o;
+    if (n == 0) continue;
+    const int base = w.t5_base[vm];
+    for (int j = lane; j < n; j += 32) {
+      const unsigned long long kj = ((unsigned long long)(unsigned)w.t5s_a[base + j] << 32) |
+                                    (unsigned)w.t5s_b[base + j];
+      int rank = 0;
+      for (int i = 0; i < n; ++i) {
+        const unsigned long long ki = ((unsigned long long)(unsigned)w.t5s_a[base + i] << 32) |
+                                      (unsigned)w.t5s_b[base + i];
+        rank += ki < kj;
+      }
+      const int d = o + rank, s = base + j;
+      const int a = w.t5s_a[s], b = w.t5s_b[s];
+      w.t5_a[d] = a;
+      w.t5_b[d] = b;
+      w.t5_md[0 * S + d] = w.t3_md0[a];
+      w.t5_md[1 * S + d] = w.t3_md1[a];
+      w.t5_md[2 * S + d] = w.t3_md2[a];
+      w.t5_md[3 * S + d] = w.t3_md1[b];
+      w.t5_md[4 * S + d] = w.t3_md2[b];
+#pragma unroll
+      for (int f = 0; f < 8; ++f) w.t5_f[f * S + d] = w.t5s_f[f * S + s];
+    }
+  }
+}
+
+}  // namespace
+
+void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
+  (void)g;
+  k_t3_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
+  LST_LAUNCH(L);
+  scan_exclusive(w.t3_base, w.t3_base, w.V, w.scan_tmp, L);
+  KT_BEGIN(L, K_T3_PRE);
+  k_t3_pre<<<152 * 8, 256, 0, L.stream>>>(w, c.f);
+  KT_END(L, K_T3_PRE);
+  LST_LAUNCH(L);
+  KT_BEGIN(L, K_T3_DECIDE);
+  k_t3_decide<<<grid_for(w.cap.q_t3, 128, 152 * 8), 128, 0, L.stream>>>(w, c.d);
+  KT_END(L, K_T3_DECIDE);
+  LST_LAUNCH(L);
+  launch_effective(w, w.t3_cnt, w.t3_cap, w.t3_base, w.cap.t3_slots, w.t3_off, ST_OVF_T3, ST_ARENA_T3, w.V, L);
+  scan_exclusive(w.t3_off, w.t3_off, w.V, w.scan_tmp, L);
+  KT_BEGIN(L, K_T3_COMPACT);
+  k_t3_compact<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w);
+  KT_END(L, K_T3_COMPACT);
+  LST_LAUNCH(L);
+  scan_exclusive(w.t3md_cnt, w.t3md_off, w.cap.md_slots, w.scan_tmp, L);
+}
+
+void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
+  (void)g;
+  k_t5_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
+  LST_LAUNCH(L);
+  scan_exclusive(w.t5_base, w.t5_base, w.V, w.scan_tmp, L);
+  KT_BEGIN(L, K_T5_PRE);
+  k_t5_pre<<<152 * 4, 256, 0, L.stream>>>(w, c.f);
+  KT_END(L, K_T5_PRE);
+  LST_LAUNCH(L);
+  KT_BEGIN(L, K_T5_DECIDE);
+  k_t5_decide<<<grid_for(w.cap.q_t5, 128, 152 * 8), 128, 0, L.stream>>>(w, c.d);
+  KT_END(L, K_T5_DECIDE);
+  LST_LAUNCH(L);
+  launch_effective(w, w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, w.t5_off, ST_OVF_T5, ST_ARENA_T5, w.V, L);
+  scan_exclusive(w.t5_off, w.t5_off, w.V, w.scan_tmp, L);
+  k_t5_compact<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w);
+  LST_LAUNCH(L);
+}
+
+}  // namespace lst
