@@ -127,10 +127,13 @@ typedef struct {
   int32_t mem_space;   /* LST_MEM_HOST or LST_MEM_DEVICE, for all five arrays */
 } lst_event_in;
 
-/* Per-event object counts and status. overflow[s] counts objects that did not fit stage s's
- * capacity on the first pass; they were recovered by a retry (retries > 0) unless status is
- * LST_EOVERFLOW_UNRESOLVED. recheck[s] counts candidates whose float32 cut margins were too close
- * to a threshold and were decided again in float64. */
+/* Per-event object counts and status. overflow[s] counts, for the whole batch the event was part
+ * of, the objects that did not fit stage s's capacities on the first pass (per-module capacity or
+ * the stage's slot arena; overflow[LST_STAGE_QUEUE]: entries beyond a float64-decision queue); they
+ * were recovered by a retry (retries > 0) unless status is LST_EOVERFLOW_UNRESOLVED.
+ * recheck[s] (batch totals) counts candidates decided in float64: for MD and LS those whose float32
+ * cut margins were too close to a threshold, for T3 / T5 / pT3 / pT5 every candidate that survived
+ * the float32 pre-filter. */
 typedef struct {
   int32_t n_hits, n_pls;
   int32_t n_md, n_ls, n_t3, n_t5, n_pt3, n_pt5, n_tc;

@@ -281,9 +281,9 @@ Launch make_launch(lst_ctx* ctx) {
 Caps default_caps(int64_t E, int64_t H, int64_t P, int64_t n_mods) {
   Caps c;
   c.E = E; c.H = H; c.P = P; c.n_mods = n_mods;
-  c.md_slots = 3 * H + 4096;
-  c.ls_slots = 24 * H + 16384;
-  c.t3_slots = 8 * H + 8192;
+  c.md_slots = 4 * H + 4096;
+  c.ls_slots = 40 * H + 16384;
+  c.t3_slots = 16 * H + 8192;
   c.t5_slots = 2 * H + 4096;
   c.p3_slots = H + 4096;
   c.p5_slots = H / 2 + 4096;
@@ -822,6 +822,16 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
       ctx->first_ovf[LST_STAGE_T5] = st[ST_OVF_T5];
       ctx->first_ovf[LST_STAGE_PT3] = std::max<int64_t>(0, (int64_t)st[ST_N_PT3] - ctx->caps.p3_slots);
       ctx->first_ovf[LST_STAGE_PT5] = std::max<int64_t>(0, (int64_t)st[ST_N_PT5] - ctx->caps.p5_slots);
+      // slot arenas too small for the predicted capacities
+      const int64_t arena_need[4] = {st[ST_ARENA_MD], st[ST_ARENA_LS], st[ST_ARENA_T3], st[ST_ARENA_T5]};
+      const int64_t arena_cap[4] = {ctx->caps.md_slots, ctx->caps.ls_slots, ctx->caps.t3_slots, ctx->caps.t5_slots};
+      for (int k = 0; k < 4; ++k)
+        if (arena_need[k] > arena_cap[k]) ctx->first_ovf[k] += (int)(arena_need[k] - arena_cap[k]);
+      // float64 decision queues
+      const int64_t qn[6] = {st[ST_Q_MD], st[ST_Q_LS], st[ST_Q_T3], st[ST_Q_T5], st[ST_Q_PT3], st[ST_Q_PT5]};
+      const int64_t qc[6] = {ctx->caps.q_md, ctx->caps.q_ls, ctx->caps.q_t3, ctx->caps.q_t5, ctx->caps.q_p3, ctx->caps.q_p5};
+      for (int k = 0; k < 6; ++k)
+        if (qn[k] > qc[k]) ctx->first_ovf[LST_STAGE_QUEUE] += (int)(qn[k] - qc[k]);
     }
     // capacity problems: grow arenas / queues, raise per-module capacities, run again
     Caps c = ctx->caps;

@@ -133,7 +133,7 @@ __global__ void k_t3_caps(Ws w) {
       const int m2 = w.ls_out[i];
       bound += w.lsin_off[m2 + 1] - w.lsin_off[m2];
     }
-    const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.2 * (double)bound), bound, w.t3_ovr[vm]);
+    const int cc = clamp_cap2(w.cap_scale * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
     w.t3_cap[vm] = cc;
     w.t3_base[vm] = cc;
   }
