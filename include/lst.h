@@ -235,6 +235,25 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event);
 int lst_bin_hits(lst_ctx* ctx, const int32_t* d_sensor, int32_t n_hits, int32_t* d_order,
                  int32_t* d_offsets, void* cuda_stream);
 
+/*
+ * The same binning as lst_bin_hits, for callers that may not allocate device memory at all: for
+ * example a trigger process whose device memory is fixed when it starts, or a plugin inside a
+ * framework that owns every device allocation. It needs no context. Its scratch is a fixed array in
+ * the library's device memory (about 0.5 MB, present on every GPU that loads the library until the
+ * process exits), so it handles at most 65536 sensors and returns LST_EINVAL for more.
+ * The paper has no counterpart of this call; it exists for such embedding constraints only.
+ *  d_sensor[n_hits] (device, in), d_order[n_hits] and d_offsets[n_sensors + 1] (device, out): as in
+ *    lst_bin_hits, with the sensor count given explicitly.
+ * The first call on a device looks up the scratch array's device address (a one-time set-up per
+ * device, done with that device current); make that first call before any stream capture. Every
+ * call on a device shares the one scratch array, so calls whose work overlaps on the GPU (several
+ * streams, or several host threads) race and must be serialized by the caller. The call waits for
+ * cuda_stream (NULL: the legacy default stream) before returning. Errors: LST_EINVAL for bad sizes
+ * or an out-of-range sensor id, LST_ECUDA for a CUDA failure; lst_last_error(NULL) says which.
+ */
+int lst_bin_hits_noalloc(const int32_t* d_sensor, int32_t n_hits, int32_t n_sensors, int32_t* d_order,
+                         int32_t* d_offsets, void* cuda_stream);
+
 /* Non-blocking: 1 if the last run (including retries it needs) has finished, 0 otherwise, <0 on
  * error. A run that needs a retry is finished only after lst_sync. */
 int lst_query(lst_ctx* ctx);

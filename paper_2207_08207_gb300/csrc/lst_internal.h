@@ -171,6 +171,9 @@ int64_t scan_tmp_elems(int64_t n);
 void launch_effective(const Ws& w, const int32_t* cnt, const int32_t* cap, const int32_t* base,
                       int64_t slots, int32_t* eff, int ovf_word, int arena_word, int n, const Launch& L);
 
+// message returned by lst_last_error(NULL) (calls that have no context)
+void set_global_error(const char* msg);
+
 // single-event hit binning on plain device arrays; cnt, cur (n_sens each) and err must be zero
 void run_bin_raw(const int32_t* sensor, int n, int n_sens, int32_t* order, int32_t* offsets, int32_t* cnt,
                  int32_t* cur, int32_t* err, int32_t* scan_tmp, const Launch& L);

@@ -219,6 +219,8 @@ struct lst_ctx {
 
 static std::string g_create_error;
 
+void lst::set_global_error(const char* msg) { g_create_error = msg; }
+
 namespace {
 
 int fail(lst_ctx* c, int code, const std::string& msg) {

@@ -112,6 +112,8 @@ def lib():
         L.lst_query.argtypes = [ctypes.c_void_p]
         L.lst_bin_hits.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p]
+        L.lst_bin_hits_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]
         L.lst_get_counts.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Counts)]
         L.lst_copy_tc.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 6
         L.lst_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -316,6 +318,19 @@ class Context:
     @staticmethod
     def kernel_algorithmic_bytes(kernel, counts, n_hits, n_pls) -> int:
         return algorithmic_bytes(kernel, counts, n_hits, n_pls)
+
+
+def bin_hits_noalloc(sensor_dev, n_sensors, order_dev, offsets_dev, stream=None):
+    """Hit binning without any device allocation (lst_bin_hits_noalloc): for callers whose device
+    memory is fixed up front. torch CUDA int32 tensors; at most 65536 sensors."""
+    L = lib()
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = L.lst_bin_hits_noalloc(_ptr(sensor_dev), int(sensor_dev.numel()), int(n_sensors), _ptr(order_dev),
+                                _ptr(offsets_dev), st)
+    if rc != LST_OK:
+        raise LSTError(rc, L.lst_last_error(None).decode())
 
 
 def exported_symbols():
