@@ -342,6 +342,8 @@ __device__ __forceinline__ bool rz_fit(const Cst<T>& c, T akappa, const T* r, co
   return true;
 }
 
+__host__ __device__ __forceinline__ int64_t lst_min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
 // ---------------------------------------------------------------------------------------------
 // warp helpers
 // ---------------------------------------------------------------------------------------------

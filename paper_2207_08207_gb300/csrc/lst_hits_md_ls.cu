@@ -21,7 +21,8 @@ __device__ __forceinline__ int find_seg(const int32_t* off, int n, int i) {
 // hit binning: counting sort by virtual sensor (2 * vm + side), stable in the input order
 // ---------------------------------------------------------------------------------------------
 __global__ void k_bin_count(Ws w, int n_sens) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w.H; i += gridDim.x * blockDim.x) {
+  const int H = w.n_hits();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H; i += gridDim.x * blockDim.x) {
     const int e = find_seg(w.ev_hit_off, w.E, i);
     const int s = w.sensor[i];
     const float x = w.x[i], y = w.y[i], z = w.z[i];
@@ -41,7 +42,8 @@ __global__ void k_bin_count(Ws w, int n_sens) {
 }
 
 __global__ void k_bin_scatter(Ws w) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w.H; i += gridDim.x * blockDim.x) {
+  const int H = w.n_hits();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H; i += gridDim.x * blockDim.x) {
     const int vs = w.hit_vs[i];
     if (vs < 0) continue;
     const int pos = w.sens_off[vs] + atomicAdd(&w.sens_cur[vs], 1);
@@ -170,39 +172,26 @@ __global__ void k_md_recheck(Ws w, Geo g, Cst<double> c) {
   }
 }
 
-__global__ void k_md_compact(Ws w, Geo g, Cst<float> c) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
-    const int o = w.md_off[vm], n = w.md_off[vm + 1] - o;
-    if (n == 0) continue;
-    const int base = w.md_base[vm];
-    const int m = vm % g.n_mods;
-    for (int j = lane; j < n; j += 32) {
-      const unsigned long long kj = ((unsigned long long)(unsigned)w.ms_lo[base + j] << 32) |
-                                    (unsigned)w.ms_up[base + j];
-      int rank = 0;
-      for (int i = 0; i < n; ++i) {
-        const unsigned long long ki = ((unsigned long long)(unsigned)w.ms_lo[base + i] << 32) |
-                                      (unsigned)w.ms_up[base + i];
-        rank += ki < kj;
-      }
-      const int d = o + rank;
-      const int lo = w.ms_lo[base + j];
-      w.md_lo[d] = lo;
-      w.md_up[d] = w.ms_up[base + j];
-      w.md_vm[d] = vm;
-      w.md_dpc[d] = w.ms_dpc[base + j];
-      w.md_pte[d] = w.ms_pte[base + j];
-      const float x = w.bx[lo], y = w.by[lo];
-      const float r = sqrtf(x * x + y * y);
-      w.md_x[d] = x;
-      w.md_y[d] = y;
-      w.md_z[d] = w.bz[lo];
-      w.md_r[d] = r;
-      w.md_sthr[d] = c.two_rthr * asinf(fminf(r / c.two_rthr, 1.0f));
-      w.md_ec[d] = g.endcap[m];
-    }
+// dense MDs ordered by (lower hit, upper hit), with the anchor (lower hit) data downstream stages read
+__global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
+  const int n = (int)lst_min64(w.md_off[w.V], w.cap.md_dense);
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
+    const int s = w.perm[d];
+    const int lo = w.ms_lo[s];
+    const int vm = w.hit_vs[w.bidx[lo]] >> 1;
+    w.md_lo[d] = lo;
+    w.md_up[d] = w.ms_up[s];
+    w.md_vm[d] = vm;
+    w.md_dpc[d] = w.ms_dpc[s];
+    w.md_pte[d] = w.ms_pte[s];
+    const float x = w.bx[lo], y = w.by[lo];
+    const float r = sqrtf(x * x + y * y);
+    w.md_x[d] = x;
+    w.md_y[d] = y;
+    w.md_z[d] = w.bz[lo];
+    w.md_r[d] = r;
+    w.md_sthr[d] = c.two_rthr * asinf(fminf(r / c.two_rthr, 1.0f));
+    w.md_ec[d] = g.endcap[vm % g.n_mods];
   }
 }
 
@@ -215,7 +204,12 @@ constexpr int kMaxTargets = 256;   // module-map degree limit (checked when load
 
 __device__ __forceinline__ int md_count(const Ws& w, int vm) { return w.md_off[vm + 1] - w.md_off[vm]; }
 
+// LS capacity of each module (exact bound: its MDs x the MDs of its connected modules) and its
+// cost bucket floor(log2(bound)) for the persistent kernel's work list
 __global__ void k_ls_caps(Ws w, Geo g) {
+  __shared__ int hist[32];
+  if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+  __syncthreads();
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const int m = vm % g.n_mods, e0 = vm - m;
     const long long na = md_count(w, vm);
@@ -227,10 +221,42 @@ __global__ void k_ls_caps(Ws w, Geo g) {
     const int cc = clamp_cap(pred, bound, w.ls_ovr[vm]);
     w.ls_cap[vm] = cc;
     w.ls_base[vm] = cc;
+    int b = -1;
+    if (bound > 0) {
+      b = 63 - __clzll((unsigned long long)bound);
+      if (b > 31) b = 31;
+      atomicAdd(&hist[b], 1);
+    }
+    w.work_bucket[vm] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&w.work_cnt[threadIdx.x], hist[threadIdx.x]);
+}
+
+// offsets of the cost buckets, most expensive first
+__global__ void k_ls_work_scan(Ws w) {
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 31; b >= 0; --b) {
+      w.work_off[b] = acc;
+      acc += w.work_cnt[b];
+    }
+    w.work_off[32] = acc;
   }
 }
 
-__global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c) {
+__global__ void k_ls_work_fill(Ws w) {
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
+    const int b = w.work_bucket[vm];
+    if (b >= 0) w.work[w.work_off[b] + atomicAdd(&w.work_cur[b], 1)] = vm;
+  }
+}
+
+// One block per module at a time: stage the module's MDs (A) and all MDs of its connected modules
+// (B) in shared memory, then evaluate every (a, b) pair across the block. Persistent mode: the grid
+// is sized to the GPU and blocks pull modules from the cost-ordered work list; otherwise a
+// grid-stride loop over all modules.
+__global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persistent) {
   __shared__ float ax[kLsA], ay[kLsA], az[kLsA], ar[kLsA], as_[kLsA];
   __shared__ int aid[kLsA];
   __shared__ uint8_t aec[kLsA];
@@ -239,8 +265,22 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c) {
   __shared__ uint8_t bec[kLsB];
   __shared__ int tpre[kMaxTargets + 1];
   __shared__ int tbase[kMaxTargets];
+  __shared__ int s_item;
   const int tid = threadIdx.x;
-  for (int vm = blockIdx.x; vm < w.V; vm += gridDim.x) {
+  const int n_items = persistent ? w.work_off[32] : w.V;
+  for (int it = blockIdx.x;; it += gridDim.x) {
+    int vm;
+    if (persistent) {
+      if (tid == 0) s_item = atomicAdd(w.work_ctr, 1);
+      __syncthreads();
+      const int item = s_item;
+      __syncthreads();
+      if (item >= n_items) break;
+      vm = w.work[item];
+    } else {
+      if (it >= n_items) break;
+      vm = it;
+    }
     const int na = md_count(w, vm);
     if (na == 0) continue;
     const int m = vm % g.n_mods, e0 = vm - m;
@@ -339,35 +379,20 @@ __global__ void k_ls_recheck(Ws w, Cst<double> c) {
   }
 }
 
-__global__ void k_ls_compact(Ws w) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
-    const int o = w.ls_off[vm], n = w.ls_off[vm + 1] - o;
-    if (n == 0) continue;
-    const int base = w.ls_base[vm];
-    for (int j = lane; j < n; j += 32) {
-      const unsigned long long kj = ((unsigned long long)(unsigned)w.lss_in[base + j] << 32) |
-                                    (unsigned)w.lss_out[base + j];
-      int rank = 0;
-      for (int i = 0; i < n; ++i) {
-        const unsigned long long ki = ((unsigned long long)(unsigned)w.lss_in[base + i] << 32) |
-                                      (unsigned)w.lss_out[base + i];
-        rank += ki < kj;
-      }
-      const int d = o + rank;
-      const int a = w.lss_in[base + j], b = w.lss_out[base + j];
-      w.ls_in[d] = a;
-      w.ls_out[d] = b;
-      // stored z0 in float64: z0_r = (z1 r2 - z2 r1) / (r2 - r1) amplifies the float32 rounding of
-      // r1, r2 by up to ~20 for endcap pairs
-      const double x1 = w.md_x[a], y1 = w.md_y[a], z1 = w.md_z[a];
-      const double x2 = w.md_x[b], y2 = w.md_y[b], z2 = w.md_z[b];
-      const double r1 = sqrt(x1 * x1 + y1 * y1), r2 = sqrt(x2 * x2 + y2 * y2);
-      w.ls_z0[d] = (float)((z1 * r2 - z2 * r1) / (r2 - r1));
-      w.ls_dphi[d] = w.lss_dphi[base + j];
-      atomicAdd(&w.lsin_cnt[a], 1);
-    }
+// dense LS ordered by (inner MD, outer MD); z0 is recomputed in float64 (its float32 form
+// amplifies radius rounding up to ~20x for endcap pairs)
+__global__ void k_ls_dense(Ws w) {
+  const int n = (int)lst_min64(w.ls_off[w.V], w.cap.ls_dense);
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
+    const int s = w.perm[d];
+    const int a = w.lss_in[s], b = w.lss_out[s];
+    w.ls_in[d] = a;
+    w.ls_out[d] = b;
+    const double x1 = w.md_x[a], y1 = w.md_y[a], z1 = w.md_z[a];
+    const double x2 = w.md_x[b], y2 = w.md_y[b], z2 = w.md_z[b];
+    const double r1 = sqrt(x1 * x1 + y1 * y1), r2 = sqrt(x2 * x2 + y2 * y2);
+    w.ls_z0[d] = (float)((z1 * r2 - z2 * r1) / (r2 - r1));
+    w.ls_dphi[d] = w.lss_dphi[s];
   }
 }
 
@@ -446,10 +471,12 @@ void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   k_md_recheck<<<grid_for(w.cap.q_md, 128, 152 * 4), 128, 0, L.stream>>>(w, g, c.d);
   LST_LAUNCH(L);
-  launch_effective(w, w.md_cnt, w.md_cap, w.md_base, w.cap.md_slots, w.md_off, ST_OVF_MD, ST_ARENA_MD, w.V, L);
-  scan_exclusive(w.md_off, w.md_off, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_MD_COMPACT);
-  k_md_compact<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, g, c.f);
+  GroupArgs ga{w.md_cnt, w.md_cap, w.md_base, w.cap.md_slots, ST_OVF_MD, ST_ARENA_MD, w.ms_lo, w.ms_up,
+               w.mdlo_cnt, w.mdlo_cur, w.mdlo_off, w.cap.H, w.cap.md_dense, ST_DENSE_MD,
+               w.md_off, w.sens_off, 2};
+  group_slots(w, ga, L);
+  k_md_dense<<<grid_for(w.cap.md_dense, 256), 256, 0, L.stream>>>(w, g, c.f);
   KT_END(L, K_MD_COMPACT);
   LST_LAUNCH(L);
 }
@@ -458,20 +485,27 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_ls_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, g);
   LST_LAUNCH(L);
   scan_exclusive(w.ls_base, w.ls_base, w.V, w.scan_tmp, L);
+  if (L.persistent) {
+    k_ls_work_scan<<<1, 32, 0, L.stream>>>(w);
+    k_ls_work_fill<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
+    *L.launches += 2;
+  }
   KT_BEGIN(L, K_LS);
-  k_ls<<<grid_for(w.V, 1, 152 * 16), L.block_ls, 0, L.stream>>>(w, g, c.f);
+  if (L.persistent) k_ls<<<L.n_sm * (2048 / L.block_ls), L.block_ls, 0, L.stream>>>(w, g, c.f, 1);
+  else k_ls<<<grid_for(w.V, 1, 152 * 16), L.block_ls, 0, L.stream>>>(w, g, c.f, 0);
   KT_END(L, K_LS);
   LST_LAUNCH(L);
   k_ls_recheck<<<grid_for(w.cap.q_ls, 128, 152 * 4), 128, 0, L.stream>>>(w, c.d);
   LST_LAUNCH(L);
-  launch_effective(w, w.ls_cnt, w.ls_cap, w.ls_base, w.cap.ls_slots, w.ls_off, ST_OVF_LS, ST_ARENA_LS, w.V, L);
-  scan_exclusive(w.ls_off, w.ls_off, w.V, w.scan_tmp, L);
+  // LS ordered by inner MD: the per-MD group offsets are the "LS by inner MD" adjacency
   KT_BEGIN(L, K_LS_COMPACT);
-  k_ls_compact<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w);
+  GroupArgs ga{w.ls_cnt, w.ls_cap, w.ls_base, w.cap.ls_slots, ST_OVF_LS, ST_ARENA_LS, w.lss_in, w.lss_out,
+               w.lsin_cnt, w.lsin_cur, w.lsin_off, w.cap.md_dense, w.cap.ls_dense, ST_DENSE_LS,
+               w.ls_off, w.md_off, 1};
+  group_slots(w, ga, L);
+  k_ls_dense<<<grid_for(w.cap.ls_dense, 256), 256, 0, L.stream>>>(w);
   KT_END(L, K_LS_COMPACT);
   LST_LAUNCH(L);
-  // LS are ordered by inner MD, so their per-MD offsets are a prefix sum of per-MD counts
-  scan_exclusive(w.lsin_cnt, w.lsin_off, w.cap.md_slots, w.scan_tmp, L);
 }
 
 }  // namespace lst

@@ -29,6 +29,7 @@ enum StatusWord : int {
   ST_Q_MD, ST_Q_LS, ST_Q_T3, ST_Q_T5, ST_Q_PT3, ST_Q_PT5,   // queue pushes attempted
   ST_REC_MD, ST_REC_LS,  // float64 re-decisions of MD / LS candidates
   ST_N_PT3, ST_N_PT5,    // appended pT3 / pT5 objects
+  ST_DENSE_MD, ST_DENSE_LS, ST_DENSE_T3, ST_DENSE_T5,   // dense totals beyond the dense capacity
   ST_TIMEOUT,            // blocks that ran out of their cycle budget
   ST_N_WORDS
 };
@@ -44,13 +45,18 @@ constexpr int kEvErr = 23;
 struct Caps {
   int64_t E = 0, H = 0, P = 0;
   int64_t md_slots = 0, ls_slots = 0, t3_slots = 0, t5_slots = 0, p3_slots = 0, p5_slots = 0;
+  int64_t md_dense = 0, ls_dense = 0, t3_dense = 0, t5_dense = 0;   // dense (compacted) objects
   int64_t q_md = 0, q_ls = 0, q_t3 = 0, q_t5 = 0, q_p3 = 0, q_p5 = 0;
   int64_t n_mods = 0;
 };
 
 // Per-batch workspace: every device array the chain uses. Passed to kernels by value.
 struct Ws {
-  int32_t E = 0, V = 0, S = 0, H = 0, P = 0;   // events, virtual modules / sensors, hits, seeds
+  // capacities of the launch shape (events, virtual modules / sensors, hits, seeds); the actual
+  // counts are on the device: event offsets are padded with empty events up to E
+  int32_t E = 0, V = 0, S = 0, H = 0, P = 0;
+  __device__ __forceinline__ int n_hits() const { return ev_hit_off[E]; }
+  __device__ __forceinline__ int n_pls() const { return ev_pls_off[E]; }
   Caps cap;
   float cap_scale = 1.0f;
   long long cycle_budget = 0;
@@ -70,6 +76,7 @@ struct Ws {
   int32_t *ms_lo = nullptr, *ms_up = nullptr;
   float *ms_dpc = nullptr, *ms_pte = nullptr;
   int32_t* md_off = nullptr;
+  int32_t *mdlo_cnt = nullptr, *mdlo_cur = nullptr, *mdlo_off = nullptr;   // MDs grouped by lower hit
   int32_t *md_lo = nullptr, *md_up = nullptr, *md_vm = nullptr;
   float *md_x = nullptr, *md_y = nullptr, *md_z = nullptr, *md_r = nullptr, *md_sthr = nullptr;
   float *md_dpc = nullptr, *md_pte = nullptr;
@@ -81,7 +88,7 @@ struct Ws {
   int32_t* ls_off = nullptr;
   int32_t *ls_in = nullptr, *ls_out = nullptr;
   float *ls_z0 = nullptr, *ls_dphi = nullptr;
-  int32_t *lsin_cnt = nullptr, *lsin_off = nullptr;   // LS by inner MD, [md_slots (+1)]
+  int32_t *lsin_cnt = nullptr, *lsin_cur = nullptr, *lsin_off = nullptr;   // LS grouped by inner MD
   // T3
   int32_t *t3_cap = nullptr, *t3_base = nullptr, *t3_cnt = nullptr, *t3_ovr = nullptr;
   int32_t *t3s_a = nullptr, *t3s_b = nullptr;
@@ -89,15 +96,21 @@ struct Ws {
   int32_t* t3_off = nullptr;
   int32_t *t3_a = nullptr, *t3_b = nullptr, *t3_md0 = nullptr, *t3_md1 = nullptr, *t3_md2 = nullptr;
   float *t3_R = nullptr, *t3_xc = nullptr, *t3_yc = nullptr, *t3_chi2 = nullptr, *t3_pte = nullptr;
-  int32_t *t3md_cnt = nullptr, *t3md_off = nullptr;   // T3 by first MD
+  int32_t* t3md_off = nullptr;   // T3 by first MD
+  int32_t *t3in_cnt = nullptr, *t3in_cur = nullptr, *t3in_off = nullptr;   // T3 grouped by inner LS
+  float4* t3_anc = nullptr;      // [3][t3_dense] anchor (x, y, z, r) of each member MD
+  uint8_t* t3_ecm = nullptr;     // endcap bit per anchor
   // T5
   int32_t *t5_cap = nullptr, *t5_base = nullptr, *t5_cnt = nullptr, *t5_ovr = nullptr;
   int32_t *t5s_a = nullptr, *t5s_b = nullptr;
   float* t5s_f = nullptr;   // [8][t5_slots]: kin, kout, kfit, chi2c, chi2rz, eta, phi, pt
   int32_t* t5_off = nullptr;
   int32_t *t5_a = nullptr, *t5_b = nullptr;
-  int32_t* t5_md = nullptr;  // [5][t5_slots]
-  float* t5_f = nullptr;     // [8][t5_slots]
+  int32_t* t5_md = nullptr;  // [5][t5_dense]
+  float* t5_f = nullptr;     // [8][t5_dense]
+  int32_t *t5in_cnt = nullptr, *t5in_cur = nullptr, *t5in_off = nullptr;   // T5 grouped by inner T3
+  float4* t5_anc = nullptr;      // [5][t5_dense]
+  uint8_t* t5_ecm = nullptr;
   // pixel seeds and pT3 / pT5: passing objects are appended, then grouped by seed
   int32_t* pls_bin = nullptr;
   int32_t *p3a_pls = nullptr, *p3a_obj = nullptr;
@@ -113,7 +126,7 @@ struct Ws {
   // track candidates
   int32_t *best5 = nullptr, *best3 = nullptr;   // [P]
   uint8_t *pls_member = nullptr, *acc3 = nullptr, *accl = nullptr;   // [P]
-  uint8_t *t5_kept = nullptr, *acc5t = nullptr;  // [t5_slots]
+  uint8_t *t5_kept = nullptr, *acc5t = nullptr;  // [t5_dense]
   int32_t *h5_cnt = nullptr, *h5_off = nullptr, *h5_cur = nullptr, *h5_idx = nullptr;  // hit -> T5
   int32_t *cell_cnt = nullptr, *cell_off = nullptr, *cell_cur = nullptr, *cell_item = nullptr;
   int32_t n_cells = 0;   // per event
@@ -135,10 +148,17 @@ struct Ws {
   int2 *q_t3 = nullptr, *q_t5 = nullptr, *q_p3 = nullptr, *q_p5 = nullptr;
   // scan scratch and status
   int32_t* scan_tmp = nullptr;
+  int32_t* eff = nullptr;    // [V] valid slots per module of the stage being compacted
+  int32_t* perm = nullptr;   // [max dense] slot of each dense object of the stage being compacted
   int32_t* status = nullptr;   // [ST_N_WORDS]
   int32_t* ev_stat = nullptr;  // [E][kEvWords]
-  int32_t* work = nullptr;     // persistent-kernel work lists and counters
-  int32_t* work_ctr = nullptr;
+  // persistent LS kernel: modules ordered by descending predicted cost (log2 buckets)
+  int32_t* work = nullptr;        // [V] module list
+  int32_t* work_bucket = nullptr; // [V] cost bucket of each module (-1: no candidates)
+  int32_t* work_cnt = nullptr;    // [32] modules per bucket
+  int32_t* work_cur = nullptr;    // [32]
+  int32_t* work_off = nullptr;    // [33]
+  int32_t* work_ctr = nullptr;    // [1] next item
 };
 
 // Launch settings (from lst_config).
@@ -157,14 +177,34 @@ enum KernelId : int {
   K_BIN = 0, K_MD, K_MD_COMPACT, K_LS, K_LS_COMPACT, K_T3_PRE, K_T3_DECIDE, K_T3_COMPACT, K_T5_PRE,
   K_T5_DECIDE, K_PT3_PRE, K_PT5_PRE, K_PT3_DECIDE, K_PT5_DECIDE, K_TC_CLEAN, K_TC_ASSEMBLE, K_N_TIMED
 };
+// (recorded as external events so that, inside a captured CUDA graph, they become real event-record
+// nodes that can be timed)
 #define KT_BEGIN(L, id) \
-  if ((L).kev) cudaEventRecord((L).kev[2 * (id)], (L).stream)
+  if ((L).kev) cudaEventRecordWithFlags((L).kev[2 * (id)], (L).stream, cudaEventRecordExternal)
 #define KT_END(L, id) \
-  if ((L).kev) cudaEventRecord((L).kev[2 * (id) + 1], (L).stream)
+  if ((L).kev) cudaEventRecordWithFlags((L).kev[2 * (id) + 1], (L).stream, cudaEventRecordExternal)
 
 // scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);
 int64_t scan_tmp_elems(int64_t n);
+
+// compaction of one stage's slots into ordered dense arrays (lst_group.cu)
+struct GroupArgs {
+  const int32_t *cnt, *cap, *base;   // per-module counts, capacities, slot bases (base[V] = total)
+  int64_t slots;
+  int ovf_word, arena_word;
+  const int32_t *key1, *key2;        // first / second member of each slot
+  int32_t *grp_cnt, *grp_cur, *grp_off;
+  int64_t n_keys;                    // key1 range (grp_off has n_keys + 1 entries)
+  int64_t dense_cap;
+  int dense_word;
+  int32_t* mod_off;                  // [V + 1] out: per-module dense offsets
+  const int32_t* mod_first;          // first key of each module, at [vm * stride]
+  int mod_first_stride;
+};
+void group_slots(const Ws& w, const GroupArgs& a, const Launch& L);
+void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* grp_off, int64_t cap,
+                     const Launch& L);
 
 // effective per-module object count = min(count, capacity, room left in the slot arena), with the
 // excess added to status[ovf_word] and the needed arena size to status[arena_word]

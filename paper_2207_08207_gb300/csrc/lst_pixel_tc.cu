@@ -30,7 +30,8 @@ __device__ __forceinline__ int find_seg(const int32_t* off, int n, int i) {
 // operations any implementation of the definition performs.
 // ---------------------------------------------------------------------------------------------
 __global__ void k_pls_prep(Ws w, Geo g) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const lst_pls s = w.pls[p];
     const bool ok = isfinite(s.pt) && isfinite(s.eta) && isfinite(s.phi) && isfinite(s.x0) &&
                     isfinite(s.y0) && isfinite(s.z0) && s.pt > 0.f && (s.charge == 1 || s.charge == -1);
@@ -101,22 +102,26 @@ __device__ __forceinline__ void seed_terms(const Seed<T>& s, const Cst<T>& c, T 
   rz_term = (z - zp) * (z - zp) / (sz * sz + th * th);
 }
 
-struct ObjMd {
-  const int32_t* md[5];   // first..last MD of each object (T3: 3, T5: 5)
-  int64_t stride;         // unused for T3; T5 md arrays are [5][S]
+// member anchors of T3 / T5 objects: anc[k * stride + i] = (x, y, z, r) of anchor k of object i,
+// ecm[i] bit k = anchor k is on an endcap module
+struct ObjAnc {
+  const float4* anc;
+  const uint8_t* ecm;
+  int64_t stride;
 };
 
 // Candidate pre-filter: one warp per seed; the candidates (objects in every module of the seed's
 // pixel-map row) are flattened across the warp with a shuffle-based search over the per-module
 // object counts.
 template <int N>
-__global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjMd om, int2* queue,
+__global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjAnc oa, int2* queue,
                          int q_word, int64_t q_cap, float cut_xy, float cut_rz) {
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const float lim_xy = cut_xy * (1.0f + kGuardChi2) + kGuardChi2Abs;
   const float lim_rz = cut_rz * (1.0f + kGuardChi2) + kGuardChi2Abs;
-  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < w.P; p += nwarps) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += nwarps) {
     const int bin = w.pls_bin[p];
     if (bin < 0) continue;
     const int e = find_seg(w.ev_pls_off, w.E, p);
@@ -156,29 +161,26 @@ __global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjM
           obj = st + (cidx - ex0);
           float xy = 0.f, rz = 0.f;
           keep = true;
-          int md[N];
-#pragma unroll
-          for (int a = 0; a < N; ++a) md[a] = om.md[a][obj];
+          // xy residuals first (they reject most candidates), anchors loaded as needed
 #pragma unroll
           for (int a = 0; a < N; ++a) {
-            const int d = md[a];
-            const float x = w.md_x[d], y = w.md_y[d], r = w.md_r[d];
-            const float dd = seed_dist(s, x, y);
-            const float e1 = r * c.pls_dir_err;
-            const float e2 = c.pls_pt_err * r * r * 0.5f * s.akap;
+            const float4 h = oa.anc[a * oa.stride + obj];
+            const float dd = seed_dist(s, h.x, h.y);
+            const float e1 = h.w * c.pls_dir_err;
+            const float e2 = c.pls_pt_err * h.w * h.w * 0.5f * s.akap;
             xy += dd * dd / (c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2);
             if (xy > lim_xy) { keep = false; break; }
           }
           if (keep) {
+            const uint8_t ecm = oa.ecm[obj];
 #pragma unroll
             for (int a = 0; a < N; ++a) {
-              const int d = md[a];
-              const float r = w.md_r[d], z = w.md_z[d];
-              const float sa = arc_len(s.akap, r);
+              const float4 h = oa.anc[a * oa.stride + obj];
+              const float sa = arc_len(s.akap, h.w);
               const float zp = s.z0 + sa * s.cot;
-              const float sz = w.md_ec[d] ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
+              const float sz = ((ecm >> a) & 1) ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
               const float th = sa * (1.0f + s.cot * s.cot) * c.pls_dir_err;
-              rz += (z - zp) * (z - zp) / (sz * sz + th * th);
+              rz += (h.z - zp) * (h.z - zp) / (sz * sz + th * th);
               if (rz > lim_rz) { keep = false; break; }
             }
           }
@@ -191,7 +193,7 @@ __global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjM
 }
 
 template <int N>
-__global__ void k_pt_decide(Ws w, Cst<double> c, ObjMd om, const int2* queue, int q_word, int64_t q_cap,
+__global__ void k_pt_decide(Ws w, Cst<double> c, ObjAnc oa, const int2* queue, int q_word, int64_t q_cap,
                             double cut_xy, double cut_rz, int32_t* a_pls, int32_t* a_obj, float* a_xy,
                             float* a_rz, float* a_sc, int n_word, int64_t a_cap, int32_t* per_pls) {
   const int n = min((int64_t)w.status[q_word], q_cap);
@@ -201,11 +203,11 @@ __global__ void k_pt_decide(Ws w, Cst<double> c, ObjMd om, const int2* queue, in
     double xy = 0.0, rz = 0.0;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      const int d = om.md[a][q.y];
-      const double x = w.md_x[d], y = w.md_y[d], z = w.md_z[d];
+      const float4 h = oa.anc[a * oa.stride + q.y];
+      const double x = h.x, y = h.y, z = h.z;
       const double r = sqrt(x * x + y * y);
       double t1, t2;
-      seed_terms<double>(s, c, x, y, z, r, w.md_ec[d] != 0, t1, t2);
+      seed_terms<double>(s, c, x, y, z, r, ((oa.ecm[q.y] >> a) & 1) != 0, t1, t2);
       xy += t1;
       rz += t2;
     }
@@ -235,7 +237,8 @@ __global__ void k_pt_group(Ws w, int n_word, int64_t a_cap, const int32_t* a_pls
 __global__ void k_pt_order(Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls,
                            const int32_t* a_obj, const float* a_xy, const float* a_rz, const float* a_sc,
                            int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const int a = off[p], b = off[p + 1];
     for (int i = a + 1; i < b; ++i) {
       const int v = tmp_idx[i];
@@ -271,7 +274,7 @@ __device__ __forceinline__ int md_hits(const Ws& w, int d, int* h) {
   return 2;
 }
 __device__ int t5_hits(const Ws& w, int i, int* h) {
-  const int64_t S = w.cap.t5_slots;
+  const int64_t S = w.cap.t5_dense;
   int n = 0;
   for (int k = 0; k < 5; ++k) n += md_hits(w, w.t5_md[k * S + i], h + n);
   return n;
@@ -324,7 +327,8 @@ __device__ bool key_less(const Ws& w, int type, int a, int b) {
 }
 
 __global__ void k_tc_best(Ws w) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     int b5 = -1;
     for (int i = w.pt5_off[p]; i < w.pt5_off[p + 1]; ++i)
       if (b5 < 0 || w.pt5_sc[i] < w.pt5_sc[b5] || (w.pt5_sc[i] == w.pt5_sc[b5] && key_less(w, TC_PT5, i, b5)))
@@ -342,7 +346,7 @@ __global__ void k_tc_best(Ws w) {
 // hit -> T5 adjacency (binned hit indices)
 __global__ void k_h5_count(Ws w, int fill) {
   const int n = w.t5_off[w.V];
-  const int64_t S = w.cap.t5_slots;
+  const int64_t S = w.cap.t5_dense;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     for (int k = 0; k < 5; ++k) {
       const int d = w.t5_md[k * S + i];
@@ -357,7 +361,7 @@ __global__ void k_h5_count(Ws w, int fill) {
 
 __global__ void k_t5_clean(Ws w, int overlap) {
   const int n = w.t5_off[w.V];
-  const int64_t S = w.cap.t5_slots;
+  const int64_t S = w.cap.t5_dense;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
     int ha[10];
     for (int k = 0; k < 5; ++k) {
@@ -420,7 +424,7 @@ __device__ __forceinline__ void item_of(const Ws& w, int code, float& eta, float
   type = code >> 29;
   idx = code & ((1 << 29) - 1);
   if (type == TC_T5) {
-    const int64_t S = w.cap.t5_slots;
+    const int64_t S = w.cap.t5_dense;
     eta = w.t5_f[5 * S + idx];
     phi = w.t5_f[6 * S + idx];
   } else {
@@ -432,18 +436,19 @@ __device__ __forceinline__ void item_of(const Ws& w, int code, float& eta, float
 // pass 0: count, pass 1: fill; items: accepted pT5 seeds (type 0), pT3 candidates (1), kept T5 (2)
 __global__ void k_grid_items(Ws w, Geo g, int fill) {
   const int n_t5 = w.t5_off[w.V];
-  const int total = w.P + n_t5;
+  const int P = w.n_pls();
+  const int total = P + n_t5;
   const int NC = kCellsEta * kCellsPhi;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     int code, e;
-    if (k < w.P) {
+    if (k < P) {
       const int p = k;
       if (w.best5[p] >= 0) code = (TC_PT5 << 29) | p;
       else if (w.best3[p] >= 0) code = (TC_PT3 << 29) | p;
       else continue;
       e = find_seg(w.ev_pls_off, w.E, p);
     } else {
-      const int i = k - w.P;
+      const int i = k - P;
       if (!w.t5_kept[i]) continue;
       code = (TC_T5 << 29) | i;
       e = w.md_vm[w.t5_md[i]] / g.n_mods;
@@ -482,7 +487,8 @@ __device__ bool near_accepted(const Ws& w, double dr2, int e, float eta, float p
 }
 
 __global__ void k_clean_pt3(Ws w, double dr2) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     uint8_t acc = 0;
     if (w.best5[p] < 0 && w.best3[p] >= 0) {
       const int e = find_seg(w.ev_pls_off, w.E, p);
@@ -494,7 +500,7 @@ __global__ void k_clean_pt3(Ws w, double dr2) {
 
 __global__ void k_clean_t5(Ws w, Geo g, double dr2) {
   const int n = w.t5_off[w.V];
-  const int64_t S = w.cap.t5_slots;
+  const int64_t S = w.cap.t5_dense;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint8_t acc = 0;
     if (w.t5_kept[i]) {
@@ -506,7 +512,8 @@ __global__ void k_clean_t5(Ws w, Geo g, double dr2) {
 }
 
 __global__ void k_clean_pls(Ws w, double dr2) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < w.P; p += gridDim.x * blockDim.x) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     uint8_t acc = 0;
     if (!w.pls_member[p]) {
       const int e = find_seg(w.ev_pls_off, w.E, p);
@@ -641,7 +648,7 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
     } else if (type == TC_T5) {
       nh = code_hits(w, type, idx, h);
       obj = idx - t0;
-      const int64_t S = w.cap.t5_slots;
+      const int64_t S = w.cap.t5_dense;
       pt = w.t5_f[7 * S + idx]; eta = w.t5_f[5 * S + idx]; phi = w.t5_f[6 * S + idx];
     } else {
       nh = code_hits(w, type, idx, h);
@@ -656,6 +663,13 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
     w.tc_phi[row] = phi;
   }
   if (threadIdx.x == 0) w.tc_cnt[e] = n;
+  // per-type counts of the event (the per-event summary reads them)
+  __shared__ int ty[4];
+  if (threadIdx.x < 4) ty[threadIdx.x] = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) atomicAdd(&ty[code[k] >> 29], 1);
+  __syncthreads();
+  if (threadIdx.x < 4) w.ev_stat[e * kEvWords + 7 + threadIdx.x] = ty[threadIdx.x];
 }
 
 }  // namespace
@@ -665,9 +679,8 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   const int threads = 32 * L.warps_px;
   const int blocks = grid_for((int64_t)w.P * 32, threads, 152 * 16);
-  ObjMd om3{{w.t3_md0, w.t3_md1, w.t3_md2, nullptr, nullptr}, 0};
-  const int64_t S = w.cap.t5_slots;
-  ObjMd om5{{w.t5_md, w.t5_md + S, w.t5_md + 2 * S, w.t5_md + 3 * S, w.t5_md + 4 * S}, S};
+  ObjAnc om3{w.t3_anc, w.t3_ecm, w.cap.t3_dense};
+  ObjAnc om5{w.t5_anc, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
     KT_BEGIN(L, K_PT3_PRE);
   k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
@@ -710,19 +723,19 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
 void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   const double dr2 = c.d.dr_min * c.d.dr_min;
   k_tc_best<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w);
-  k_h5_count<<<grid_for(w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, 0);
+  k_h5_count<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, 0);
   *L.launches += 2;
   scan_exclusive(w.h5_cnt, w.h5_off, w.cap.H, w.scan_tmp, L);
-  k_h5_count<<<grid_for(w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, 1);
+  k_h5_count<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, 1);
   KT_BEGIN(L, K_TC_CLEAN);
-  k_t5_clean<<<grid_for(w.cap.t5_slots, 128), 128, 0, L.stream>>>(w, c.d.t5_overlap_hits);
+  k_t5_clean<<<grid_for(w.cap.t5_dense, 128), 128, 0, L.stream>>>(w, c.d.t5_overlap_hits);
   KT_END(L, K_TC_CLEAN);
-  k_grid_items<<<grid_for(w.P + w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, g, 0);
+  k_grid_items<<<grid_for(w.P + w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, g, 0);
   *L.launches += 3;
   scan_exclusive(w.cell_cnt, w.cell_off, (int64_t)w.E * w.n_cells, w.scan_tmp, L);
-  k_grid_items<<<grid_for(w.P + w.cap.t5_slots, 256), 256, 0, L.stream>>>(w, g, 1);
+  k_grid_items<<<grid_for(w.P + w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, g, 1);
   k_clean_pt3<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, dr2);
-  k_clean_t5<<<grid_for(w.cap.t5_slots, 128), 128, 0, L.stream>>>(w, g, dr2);
+  k_clean_t5<<<grid_for(w.cap.t5_dense, 128), 128, 0, L.stream>>>(w, g, dr2);
   k_clean_pls<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, dr2);
   const size_t smem = kTcSortMax * (sizeof(unsigned long long) + sizeof(int));
   KT_BEGIN(L, K_TC_ASSEMBLE);

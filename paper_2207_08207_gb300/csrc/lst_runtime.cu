@@ -38,10 +38,10 @@ struct EvPtr {
 };
 
 // concatenate device-resident events into the input arena
-__global__ void k_gather(const EvPtr* tab, Ws w) {
-  const int64_t n = (int64_t)w.H + w.P;
+__global__ void k_gather(const EvPtr* tab, Ws w, int H, int P) {
+  const int64_t n = (int64_t)H + P;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    if (k < w.H) {
+    if (k < H) {
       const int i = (int)k;
       const int e = find_seg_rt(w.ev_hit_off, w.E, i);
       const int l = i - w.ev_hit_off[e];
@@ -50,7 +50,7 @@ __global__ void k_gather(const EvPtr* tab, Ws w) {
       w.z[i] = tab[e].z[l];
       w.sensor[i] = tab[e].sensor[l];
     } else {
-      const int p = (int)(k - w.H);
+      const int p = (int)(k - H);
       const int e = find_seg_rt(w.ev_pls_off, w.E, p);
       w.pls[p] = tab[e].pls[p - w.ev_pls_off[e]];
     }
@@ -117,10 +117,7 @@ __global__ void k_ev_stat(Ws w, int n_mods) {
     st[5] = w.pt5_off[p1] - w.pt5_off[p0];
     const int ntc = w.tc_cnt[e];
     st[6] = ntc;
-    const int region = p0 + w.t5_off[a];
-    int ty[4] = {0, 0, 0, 0};
-    for (int r = 0; r < ntc; ++r) ty[w.tc_type[region + r] & 3]++;
-    for (int k = 0; k < 4; ++k) st[7 + k] = ty[k];
+    const int region = p0 + w.t5_off[a];   // st[7..10] (per-type counts) come from the assembly
     st[11] = w.md_off[a];
     st[12] = w.ls_off[a];
     st[13] = w.t3_off[a];
@@ -208,6 +205,12 @@ struct lst_ctx {
   int first_ovf[LST_N_STAGES] = {};
   // instrumentation
   long long launches = 0;
+  int n_sm = 152;
+  // CUDA graph of the whole chain for the current arenas (shape-independent within capacities)
+  cudaGraphExec_t graph_exec = nullptr;
+  long long graph_nodes = 0;
+  uint64_t arena_gen = 1, graph_gen = 0;
+  bool graph_timing = false;
   bool timing = false;
   cudaEvent_t ev_stage[10] = {};
   cudaEvent_t ev_kern[2 * K_N_TIMED] = {};
@@ -274,6 +277,7 @@ Launch make_launch(lst_ctx* ctx) {
   L.warps_px = ctx->cfg.warps_px;
   L.persistent = ctx->cfg.persistent != 0;
   L.launches = &ctx->launches;
+  L.n_sm = ctx->n_sm;
   L.kev = ctx->timing ? ctx->ev_kern : nullptr;
   return L;
 }
@@ -287,6 +291,10 @@ Caps default_caps(int64_t E, int64_t H, int64_t P, int64_t n_mods) {
   c.ls_slots = 40 * H + 16384;
   c.t3_slots = 16 * H + 8192;
   c.t5_slots = 2 * H + 4096;
+  c.md_dense = H + 4096;
+  c.ls_dense = 6 * H + 16384;
+  c.t3_dense = 2 * H + 8192;
+  c.t5_dense = H / 2 + 4096;
   c.p3_slots = H + 4096;
   c.p5_slots = H / 2 + 4096;
   c.q_md = H / 8 + 4096;
@@ -309,15 +317,17 @@ int plan_input(lst_ctx* ctx, int64_t E, int64_t H, int64_t P) {
   Ws& w = ctx->ws;
   pl.add(w.x, c.H); pl.add(w.y, c.H); pl.add(w.z, c.H); pl.add(w.sensor, c.H);
   pl.add(w.pls, c.P);
-  pl.add(w.ev_hit_off, c.E + 1); pl.add(w.ev_pls_off, c.E + 1);
+  pl.add(w.ev_hit_off, 2 * (c.E + 1));   // hit offsets, then seed offsets
   pl.add(w.md_ovr, V); pl.add(w.ls_ovr, V); pl.add(w.t3_ovr, V); pl.add(w.t5_ovr, V);
   const size_t bytes = pl.layout();
   if (ctx->in_mem) CK(cudaFreeAsync(ctx->in_mem, ctx->stream));
   ctx->in_mem = nullptr;
   CK(cudaMallocFromPoolAsync(&ctx->in_mem, bytes, ctx->pool, ctx->stream));
   pl.assign(ctx->in_mem);
+  w.ev_pls_off = w.ev_hit_off + (c.E + 1);
   ctx->in_bytes = bytes;
   ctx->in_caps = c;
+  ctx->arena_gen++;
   // overrides start at zero
   CK(cudaMemsetAsync(w.md_ovr, 0, V * sizeof(int32_t), ctx->stream));
   CK(cudaMemsetAsync(w.ls_ovr, 0, V * sizeof(int32_t), ctx->stream));
@@ -328,47 +338,57 @@ int plan_input(lst_ctx* ctx, int64_t E, int64_t H, int64_t P) {
 
 int plan_work(lst_ctx* ctx, const Caps& want) {
   Caps c = want;
+  c.E = ctx->in_caps.E;   // event offsets (padded to E) live in the input arena
   const int64_t V = c.E * ctx->geo.n_mods;
   const int64_t S = 2 * V;
   const int64_t NC = (int64_t)c.E * tc_cells_per_event();
-  const int64_t tc_cap = c.P + c.t5_slots;
+  const int64_t tc_cap = c.P + c.t5_dense;
   Ws& w = ctx->ws;
   Planner z, pl;   // z: cleared before every run
   z.add(w.status, ST_N_WORDS + c.E * kEvWords);   // status words, then the per-event words
   z.add(w.tc_cnt, c.E);
   z.add(w.sens_cnt, S); z.add(w.sens_cur, S);
   z.add(w.md_cnt, V); z.add(w.ls_cnt, V); z.add(w.t3_cnt, V); z.add(w.t5_cnt, V);
-  z.add(w.lsin_cnt, c.md_slots + 1); z.add(w.t3md_cnt, c.md_slots + 1);
+  z.add(w.mdlo_cnt, c.H + 1); z.add(w.mdlo_cur, c.H + 1);
+  z.add(w.lsin_cnt, c.md_dense + 1); z.add(w.lsin_cur, c.md_dense + 1);
+  z.add(w.t3in_cnt, c.ls_dense + 1); z.add(w.t3in_cur, c.ls_dense + 1);
+  z.add(w.t5in_cnt, c.t3_dense + 1); z.add(w.t5in_cur, c.t3_dense + 1);
   z.add(w.p3_cnt, c.P); z.add(w.p3_cur, c.P); z.add(w.p5_cnt, c.P); z.add(w.p5_cur, c.P);
   z.add(w.h5_cnt, c.H + 1); z.add(w.h5_cur, c.H + 1);
   z.add(w.cell_cnt, NC); z.add(w.cell_cur, NC);
+  z.add(w.work_cnt, 32); z.add(w.work_cur, 32); z.add(w.work_ctr, 1);
   // binning
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
   pl.add(w.bx, c.H); pl.add(w.by, c.H); pl.add(w.bz, c.H); pl.add(w.borig, c.H);
+  // compaction scratch, LS work list
+  pl.add(w.eff, V);
+  pl.add(w.work, V); pl.add(w.work_bucket, V); pl.add(w.work_off, 33);
+  pl.add(w.perm, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
   // MD
-  pl.add(w.md_cap, V); pl.add(w.md_base, V + 1); pl.add(w.md_off, V + 1);
+  pl.add(w.md_cap, V); pl.add(w.md_base, V + 1); pl.add(w.md_off, V + 1); pl.add(w.mdlo_off, c.H + 2);
   pl.add(w.ms_lo, c.md_slots); pl.add(w.ms_up, c.md_slots); pl.add(w.ms_dpc, c.md_slots); pl.add(w.ms_pte, c.md_slots);
-  pl.add(w.md_lo, c.md_slots); pl.add(w.md_up, c.md_slots); pl.add(w.md_vm, c.md_slots);
-  pl.add(w.md_x, c.md_slots); pl.add(w.md_y, c.md_slots); pl.add(w.md_z, c.md_slots); pl.add(w.md_r, c.md_slots);
-  pl.add(w.md_sthr, c.md_slots); pl.add(w.md_dpc, c.md_slots); pl.add(w.md_pte, c.md_slots); pl.add(w.md_ec, c.md_slots);
+  pl.add(w.md_lo, c.md_dense); pl.add(w.md_up, c.md_dense); pl.add(w.md_vm, c.md_dense);
+  pl.add(w.md_x, c.md_dense); pl.add(w.md_y, c.md_dense); pl.add(w.md_z, c.md_dense); pl.add(w.md_r, c.md_dense);
+  pl.add(w.md_sthr, c.md_dense); pl.add(w.md_dpc, c.md_dense); pl.add(w.md_pte, c.md_dense); pl.add(w.md_ec, c.md_dense);
   // LS
-  pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1);
+  pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1); pl.add(w.lsin_off, c.md_dense + 2);
   pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_z0, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
-  pl.add(w.ls_in, c.ls_slots); pl.add(w.ls_out, c.ls_slots); pl.add(w.ls_z0, c.ls_slots); pl.add(w.ls_dphi, c.ls_slots);
-  pl.add(w.lsin_off, c.md_slots + 2);
+  pl.add(w.ls_in, c.ls_dense); pl.add(w.ls_out, c.ls_dense); pl.add(w.ls_z0, c.ls_dense); pl.add(w.ls_dphi, c.ls_dense);
   // T3
-  pl.add(w.t3_cap, V); pl.add(w.t3_base, V + 1); pl.add(w.t3_off, V + 1);
+  pl.add(w.t3_cap, V); pl.add(w.t3_base, V + 1); pl.add(w.t3_off, V + 1); pl.add(w.t3in_off, c.ls_dense + 2);
   pl.add(w.t3s_a, c.t3_slots); pl.add(w.t3s_b, c.t3_slots); pl.add(w.t3s_R, c.t3_slots); pl.add(w.t3s_xc, c.t3_slots);
   pl.add(w.t3s_yc, c.t3_slots); pl.add(w.t3s_chi2, c.t3_slots); pl.add(w.t3s_pte, c.t3_slots);
-  pl.add(w.t3_a, c.t3_slots); pl.add(w.t3_b, c.t3_slots); pl.add(w.t3_md0, c.t3_slots); pl.add(w.t3_md1, c.t3_slots);
-  pl.add(w.t3_md2, c.t3_slots); pl.add(w.t3_R, c.t3_slots); pl.add(w.t3_xc, c.t3_slots); pl.add(w.t3_yc, c.t3_slots);
-  pl.add(w.t3_chi2, c.t3_slots); pl.add(w.t3_pte, c.t3_slots);
-  pl.add(w.t3md_off, c.md_slots + 2);
+  pl.add(w.t3_a, c.t3_dense); pl.add(w.t3_b, c.t3_dense); pl.add(w.t3_md0, c.t3_dense); pl.add(w.t3_md1, c.t3_dense);
+  pl.add(w.t3_md2, c.t3_dense); pl.add(w.t3_R, c.t3_dense); pl.add(w.t3_xc, c.t3_dense); pl.add(w.t3_yc, c.t3_dense);
+  pl.add(w.t3_chi2, c.t3_dense); pl.add(w.t3_pte, c.t3_dense);
+  pl.add(w.t3_anc, 3 * c.t3_dense); pl.add(w.t3_ecm, c.t3_dense);
+  pl.add(w.t3md_off, c.md_dense + 2);
   // T5
-  pl.add(w.t5_cap, V); pl.add(w.t5_base, V + 1); pl.add(w.t5_off, V + 1);
+  pl.add(w.t5_cap, V); pl.add(w.t5_base, V + 1); pl.add(w.t5_off, V + 1); pl.add(w.t5in_off, c.t3_dense + 2);
   pl.add(w.t5s_a, c.t5_slots); pl.add(w.t5s_b, c.t5_slots); pl.add(w.t5s_f, 8 * c.t5_slots);
-  pl.add(w.t5_a, c.t5_slots); pl.add(w.t5_b, c.t5_slots); pl.add(w.t5_md, 5 * c.t5_slots); pl.add(w.t5_f, 8 * c.t5_slots);
-  pl.add(w.t5_kept, c.t5_slots); pl.add(w.acc5t, c.t5_slots);
+  pl.add(w.t5_a, c.t5_dense); pl.add(w.t5_b, c.t5_dense); pl.add(w.t5_md, 5 * c.t5_dense); pl.add(w.t5_f, 8 * c.t5_dense);
+  pl.add(w.t5_anc, 5 * c.t5_dense); pl.add(w.t5_ecm, c.t5_dense);
+  pl.add(w.t5_kept, c.t5_dense); pl.add(w.acc5t, c.t5_dense);
   // pixel
   pl.add(w.pls_bin, c.P);
   pl.add(w.p3a_pls, c.p3_slots); pl.add(w.p3a_obj, c.p3_slots); pl.add(w.p3a_xy, c.p3_slots);
@@ -382,22 +402,22 @@ int plan_work(lst_ctx* ctx, const Caps& want) {
   pl.add(w.grp_tmp, std::max(c.p3_slots, c.p5_slots));
   // track candidates
   pl.add(w.best5, c.P); pl.add(w.best3, c.P); pl.add(w.pls_member, c.P); pl.add(w.acc3, c.P); pl.add(w.accl, c.P);
-  pl.add(w.h5_off, c.H + 2); pl.add(w.h5_idx, 10 * c.t5_slots);
-  pl.add(w.cell_off, NC + 1); pl.add(w.cell_item, c.P + c.t5_slots);
+  pl.add(w.h5_off, c.H + 2); pl.add(w.h5_idx, 10 * c.t5_dense);
+  pl.add(w.cell_off, NC + 1); pl.add(w.cell_item, c.P + c.t5_dense);
   pl.add(w.tc_code, tc_cap); pl.add(w.tc_key, tc_cap); pl.add(w.tc_hit_key, 14 * tc_cap);
   pl.add(w.tc_type, tc_cap); pl.add(w.tc_obj, tc_cap); pl.add(w.tc_hits, 14 * tc_cap);
   pl.add(w.tc_pt, tc_cap); pl.add(w.tc_eta, tc_cap); pl.add(w.tc_phi, tc_cap);
   // event-local outputs
-  pl.add(w.o_md_lo, c.md_slots); pl.add(w.o_md_up, c.md_slots); pl.add(w.o_md_mod, c.md_slots);
-  pl.add(w.o_ls_in, c.ls_slots); pl.add(w.o_ls_out, c.ls_slots);
-  pl.add(w.o_t3_a, c.t3_slots); pl.add(w.o_t3_b, c.t3_slots);
-  pl.add(w.o_t5_a, c.t5_slots); pl.add(w.o_t5_b, c.t5_slots);
+  pl.add(w.o_md_lo, c.md_dense); pl.add(w.o_md_up, c.md_dense); pl.add(w.o_md_mod, c.md_dense);
+  pl.add(w.o_ls_in, c.ls_dense); pl.add(w.o_ls_out, c.ls_dense);
+  pl.add(w.o_t3_a, c.t3_dense); pl.add(w.o_t3_b, c.t3_dense);
+  pl.add(w.o_t5_a, c.t5_dense); pl.add(w.o_t5_b, c.t5_dense);
   pl.add(w.o_pt3_pls, c.p3_slots); pl.add(w.o_pt3_obj, c.p3_slots);
   pl.add(w.o_pt5_pls, c.p5_slots); pl.add(w.o_pt5_obj, c.p5_slots);
   // queues
   pl.add(w.q_md, c.q_md); pl.add(w.q_ls, c.q_ls); pl.add(w.q_t3, c.q_t3); pl.add(w.q_t5, c.q_t5);
   pl.add(w.q_p3, c.q_p3); pl.add(w.q_p5, c.q_p5);
-  const int64_t scan_n = std::max({S + 1, V + 1, c.md_slots + 2, c.H + 2, NC + 1, c.P + 1});
+  const int64_t scan_n = std::max({S + 1, V + 1, c.H + 2, c.md_dense + 2, c.ls_dense + 2, c.t3_dense + 2, NC + 1, c.P + 1});
   pl.add(w.scan_tmp, scan_tmp_elems(scan_n) + 8);
   const size_t zb = z.layout();
   const size_t pb = pl.layout();
@@ -411,6 +431,7 @@ int plan_work(lst_ctx* ctx, const Caps& want) {
   ctx->zero_bytes = zb;
   ctx->work_bytes = zb + pb;
   ctx->caps = c;
+  ctx->arena_gen++;
   w.cap = c;
   w.n_cells = tc_cells_per_event();
   w.tc_capacity = tc_cap;
@@ -436,12 +457,15 @@ int ensure_pinned(lst_ctx* ctx, size_t bytes) {
   return LST_OK;
 }
 
-int launch_chain(lst_ctx* ctx) {
+// Enqueue the whole chain on ctx->stream. Every launch is shaped by the arena capacities, never by
+// the batch (kernels read the actual hit / seed counts from the padded event offsets), so the same
+// sequence serves every batch that fits and can be captured once as a CUDA graph.
+int enqueue_chain(lst_ctx* ctx) {
   Ws& w = ctx->ws;
-  w.E = ctx->E;
-  w.H = ctx->H;
-  w.P = ctx->P;
-  w.V = ctx->E * ctx->geo.n_mods;
+  w.E = (int32_t)ctx->caps.E;
+  w.H = (int32_t)ctx->caps.H;
+  w.P = (int32_t)ctx->caps.P;
+  w.V = w.E * ctx->geo.n_mods;
   w.S = 2 * w.V;
   w.cap_scale = ctx->cfg.cap_scale;
   w.cycle_budget = ctx->cfg.cycle_budget;
@@ -451,7 +475,7 @@ int launch_chain(lst_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->zero_begin, 0, ctx->zero_bytes, ctx->stream));
   int ei = 0;
   auto mark = [&]() {
-    if (ctx->timing) cudaEventRecord(ctx->ev_stage[ei++], ctx->stream);
+    if (ctx->timing) cudaEventRecordWithFlags(ctx->ev_stage[ei++], ctx->stream, cudaEventRecordExternal);
   };
   mark();
   run_binning(w, g, L);
@@ -467,13 +491,51 @@ int launch_chain(lst_ctx* ctx) {
   mark();
   run_tc(w, g, c, L);
   mark();
-  k_finalize<<<grid_for(std::max(ctx->caps.ls_slots, ctx->caps.md_slots), 256), 256, 0, ctx->stream>>>(w, g.n_mods);
+  k_finalize<<<grid_for(std::max({ctx->caps.ls_dense, ctx->caps.p3_slots, ctx->caps.md_dense}), 256), 256, 0,
+               ctx->stream>>>(w, g.n_mods);
   k_ev_stat<<<grid_for(w.E, 64), 64, 0, ctx->stream>>>(w, g.n_mods);
   ctx->launches += 2;
   mark();
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ctx->h_status, w.status, (ST_N_WORDS + (size_t)w.E * kEvWords) * sizeof(int32_t),
                      cudaMemcpyDeviceToHost, ctx->stream));
+  return LST_OK;
+}
+
+int launch_chain(lst_ctx* ctx) {
+  const bool graph = ctx->cfg.use_graph != 0;
+  if (!graph) {
+    int rc = enqueue_chain(ctx);
+    if (rc) return rc;
+  } else {
+    // the timing events, when enabled, are captured as event-record nodes of the graph
+    if (!ctx->graph_exec || ctx->graph_gen != ctx->arena_gen || ctx->graph_timing != ctx->timing) {
+      if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      const long long before = ctx->launches;
+      const int rc = enqueue_chain(ctx);
+      cudaGraph_t gr = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+      if (rc) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      if (e != cudaSuccess) return fail(ctx, LST_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ei != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        return fail(ctx, LST_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+      }
+      ctx->graph_nodes = ctx->launches - before;
+      ctx->launches = before;
+      ctx->graph_gen = ctx->arena_gen;
+      ctx->graph_timing = ctx->timing;
+    }
+    CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->launches += ctx->graph_nodes;
+  }
   CK(cudaEventRecord(ctx->ev_done, ctx->stream));
   return LST_OK;
 }
@@ -564,6 +626,8 @@ int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
   for (auto& ev : ctx->ev_stage) cudaEventCreate(&ev);
   for (auto& ev : ctx->ev_kern) cudaEventCreate(&ev);
   ctx->stream = ctx->own_stream;
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (ctx->n_sm <= 0) ctx->n_sm = 152;
   tc_configure();
   *out = ctx;
   return LST_OK;
@@ -579,6 +643,7 @@ void lst_destroy(lst_ctx* ctx) {
   if (ctx->d_tab) cudaFreeAsync(ctx->d_tab, ctx->own_stream);
   if (ctx->bin_mem) cudaFreeAsync(ctx->bin_mem, ctx->own_stream);
   if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->geo_mem) cudaFree(ctx->geo_mem);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
@@ -668,6 +733,7 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   ctx->in_mem = ctx->work_mem = nullptr;
   ctx->in_caps = Caps{};
   ctx->caps = Caps{};
+  ctx->arena_gen++;
   return LST_OK;
 }
 
@@ -709,7 +775,7 @@ int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event
   ctx->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->own_stream;
   int rc = plan_input(ctx, n_ev, H, P);
   if (rc) return rc;
-  if (!ctx->work_mem || n_ev > ctx->caps.E || H > ctx->caps.H || P > ctx->caps.P) {
+  if (!ctx->work_mem || ctx->caps.E != ctx->in_caps.E || H > ctx->caps.H || P > ctx->caps.P) {
     Caps want = default_caps(std::max<int64_t>(n_ev, ctx->caps.E), std::max<int64_t>(ctx->in_caps.H, ctx->caps.H),
                              std::max<int64_t>(ctx->in_caps.P, ctx->caps.P), ctx->geo.n_mods);
     want.E = std::max<int64_t>(ctx->in_caps.E, want.E);
@@ -721,27 +787,29 @@ int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event
   ctx->P = (int32_t)P;
   ctx->ev_hits.resize(n_ev);
   ctx->ev_pls.resize(n_ev);
-  std::vector<int32_t> hoff(n_ev + 1, 0), poff(n_ev + 1, 0);
+  // event offsets padded with empty events up to the arena's event capacity
+  const int32_t Ecap = (int32_t)ctx->in_caps.E;
+  std::vector<int32_t> hoff(Ecap + 1, 0), poff(Ecap + 1, 0);
+  for (int32_t e = 0; e < Ecap; ++e) {
+    hoff[e + 1] = hoff[e] + (e < n_ev ? ev[e].n_hits : 0);
+    poff[e + 1] = poff[e] + (e < n_ev ? ev[e].n_pls : 0);
+  }
   for (int32_t e = 0; e < n_ev; ++e) {
-    hoff[e + 1] = hoff[e] + ev[e].n_hits;
-    poff[e + 1] = poff[e] + ev[e].n_pls;
     ctx->ev_hits[e] = ev[e].n_hits;
     ctx->ev_pls[e] = ev[e].n_pls;
   }
   Ws& w = ctx->ws;
   // stage the inputs: host events are packed into pinned memory and copied with one transfer per
   // array; device events are gathered by one kernel
-  const size_t off_bytes = 2 * (n_ev + 1) * sizeof(int32_t);
+  const size_t off_bytes = 2 * ((size_t)Ecap + 1) * sizeof(int32_t);
   const size_t host_bytes = any_host ? (size_t)H * 16 + (size_t)P * sizeof(lst_pls) : 0;
   rc = ensure_pinned(ctx, off_bytes + host_bytes + (size_t)n_ev * sizeof(EvPtr) + 64);
   if (rc) return rc;
   CK(cudaStreamSynchronize(ctx->stream));   // the staging buffer may still feed the previous copy
   char* hp = static_cast<char*>(ctx->pinned);
-  std::memcpy(hp, hoff.data(), (n_ev + 1) * sizeof(int32_t));
-  std::memcpy(hp + (n_ev + 1) * sizeof(int32_t), poff.data(), (n_ev + 1) * sizeof(int32_t));
-  CK(cudaMemcpyAsync(w.ev_hit_off, hp, (n_ev + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(w.ev_pls_off, hp + (n_ev + 1) * sizeof(int32_t), (n_ev + 1) * sizeof(int32_t),
-                     cudaMemcpyHostToDevice, ctx->stream));
+  std::memcpy(hp, hoff.data(), ((size_t)Ecap + 1) * sizeof(int32_t));
+  std::memcpy(hp + ((size_t)Ecap + 1) * sizeof(int32_t), poff.data(), ((size_t)Ecap + 1) * sizeof(int32_t));
+  CK(cudaMemcpyAsync(w.ev_hit_off, hp, off_bytes, cudaMemcpyHostToDevice, ctx->stream));
   if (any_host) {
     float* hx = reinterpret_cast<float*>(hp + off_bytes);
     float* hy = hx + H;
@@ -775,14 +843,14 @@ int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event
     EvPtr* ht = reinterpret_cast<EvPtr*>(hp + off_bytes);
     for (int32_t e = 0; e < n_ev; ++e) ht[e] = EvPtr{ev[e].x, ev[e].y, ev[e].z, ev[e].sensor, ev[e].pls};
     CK(cudaMemcpyAsync(ctx->d_tab, ht, n_ev * sizeof(EvPtr), cudaMemcpyHostToDevice, ctx->stream));
-    w.E = n_ev; w.H = (int32_t)H; w.P = (int32_t)P;
+    w.E = Ecap;
     if (H + P > 0) {
-      k_gather<<<grid_for(H + P, 256), 256, 0, ctx->stream>>>(ctx->d_tab, w);
+      k_gather<<<grid_for(H + P, 256), 256, 0, ctx->stream>>>(ctx->d_tab, w, (int)H, (int)P);
       ctx->launches++;
     }
   }
   // capacity overrides belong to one batch
-  const int64_t V = (int64_t)n_ev * ctx->geo.n_mods;
+  const int64_t V = (int64_t)Ecap * ctx->geo.n_mods;
   CK(cudaMemsetAsync(w.md_ovr, 0, V * sizeof(int32_t), ctx->stream));
   CK(cudaMemsetAsync(w.ls_ovr, 0, V * sizeof(int32_t), ctx->stream));
   CK(cudaMemsetAsync(w.t3_ovr, 0, V * sizeof(int32_t), ctx->stream));
@@ -825,10 +893,12 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
       ctx->first_ovf[LST_STAGE_PT3] = std::max<int64_t>(0, (int64_t)st[ST_N_PT3] - ctx->caps.p3_slots);
       ctx->first_ovf[LST_STAGE_PT5] = std::max<int64_t>(0, (int64_t)st[ST_N_PT5] - ctx->caps.p5_slots);
       // slot arenas too small for the predicted capacities
-      const int64_t arena_need[4] = {st[ST_ARENA_MD], st[ST_ARENA_LS], st[ST_ARENA_T3], st[ST_ARENA_T5]};
-      const int64_t arena_cap[4] = {ctx->caps.md_slots, ctx->caps.ls_slots, ctx->caps.t3_slots, ctx->caps.t5_slots};
-      for (int k = 0; k < 4; ++k)
-        if (arena_need[k] > arena_cap[k]) ctx->first_ovf[k] += (int)(arena_need[k] - arena_cap[k]);
+      const int64_t arena_need[8] = {st[ST_ARENA_MD], st[ST_ARENA_LS], st[ST_ARENA_T3], st[ST_ARENA_T5],
+                                     st[ST_DENSE_MD], st[ST_DENSE_LS], st[ST_DENSE_T3], st[ST_DENSE_T5]};
+      const int64_t arena_cap[8] = {ctx->caps.md_slots, ctx->caps.ls_slots, ctx->caps.t3_slots, ctx->caps.t5_slots,
+                                    ctx->caps.md_dense, ctx->caps.ls_dense, ctx->caps.t3_dense, ctx->caps.t5_dense};
+      for (int k = 0; k < 8; ++k)
+        if (arena_need[k] > arena_cap[k]) ctx->first_ovf[k % 4] += (int)(arena_need[k] - arena_cap[k]);
       // float64 decision queues
       const int64_t qn[6] = {st[ST_Q_MD], st[ST_Q_LS], st[ST_Q_T3], st[ST_Q_T5], st[ST_Q_PT3], st[ST_Q_PT5]};
       const int64_t qc[6] = {ctx->caps.q_md, ctx->caps.q_ls, ctx->caps.q_t3, ctx->caps.q_t5, ctx->caps.q_p3, ctx->caps.q_p5};
@@ -845,6 +915,10 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     need(st[ST_ARENA_LS], c.ls_slots);
     need(st[ST_ARENA_T3], c.t3_slots);
     need(st[ST_ARENA_T5], c.t5_slots);
+    need(st[ST_DENSE_MD], c.md_dense);
+    need(st[ST_DENSE_LS], c.ls_dense);
+    need(st[ST_DENSE_T3], c.t3_dense);
+    need(st[ST_DENSE_T5], c.t5_dense);
     need(st[ST_N_PT3], c.p3_slots);
     need(st[ST_N_PT5], c.p5_slots);
     need(st[ST_Q_MD], c.q_md);
@@ -864,7 +938,7 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
       }
       ctx->retries++;
       if (raise) {
-        const int V = ctx->E * ctx->geo.n_mods;
+        const int V = (int)ctx->caps.E * ctx->geo.n_mods;
         const Ws& w = ctx->ws;
         if (st[ST_OVF_MD]) k_raise<<<grid_for(V, 256), 256, 0, ctx->stream>>>(w.md_cnt, w.md_ovr, V);
         if (st[ST_OVF_LS]) k_raise<<<grid_for(V, 256), 256, 0, ctx->stream>>>(w.ls_cnt, w.ls_ovr, V);
@@ -928,7 +1002,7 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     lst_event_out& o = ctx->outs[ev];
     o.counts = c;
     const int bmd = es[11], bls = es[12], bt3 = es[13], bt5 = es[14], bp3 = es[15], bp5 = es[16], btc = es[17];
-    const int64_t S5 = ctx->caps.t5_slots;
+    const int64_t S5 = ctx->caps.t5_dense;
     o.md_hit_lo = w.o_md_lo + bmd; o.md_hit_up = w.o_md_up + bmd; o.md_module = w.o_md_mod + bmd;
     o.md_dphichange = w.md_dpc + bmd; o.md_pt_est = w.md_pte + bmd;
     o.ls_md_in = w.o_ls_in + bls; o.ls_md_out = w.o_ls_out + bls; o.ls_z0 = w.ls_z0 + bls; o.ls_dphi = w.ls_dphi + bls;

@@ -76,7 +76,7 @@ __global__ void k_t3_pre(Ws w, Cst<float> c) {
   const int n_ls = w.ls_off[w.V];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ls; i += gridDim.x * blockDim.x) {
     const int m2 = w.ls_out[i];
-    const int j0 = w.lsin_off[m2], j1 = w.lsin_off[m2 + 1];
+    const int j0 = min(w.lsin_off[m2], n_ls), j1 = min(w.lsin_off[m2 + 1], n_ls);
     if (j0 == j1) continue;
     const Anchor<float> h1 = anchor<float>(w, w.ls_in[i]);
     const Anchor<float> h2 = anchor<float>(w, m2);
@@ -129,9 +129,10 @@ __device__ __forceinline__ int clamp_cap2(double pred, long long bound, int ovr)
 __global__ void k_t3_caps(Ws w) {
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     long long bound = 0;
+    const int n_ls = w.ls_off[w.V];
     for (int i = w.ls_off[vm]; i < w.ls_off[vm + 1]; ++i) {
       const int m2 = w.ls_out[i];
-      bound += w.lsin_off[m2 + 1] - w.lsin_off[m2];
+      bound += min(w.lsin_off[m2 + 1], n_ls) - min(w.lsin_off[m2], n_ls);
     }
     const int cc = clamp_cap2(w.cap_scale * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
     w.t3_cap[vm] = cc;
@@ -139,37 +140,31 @@ __global__ void k_t3_caps(Ws w) {
   }
 }
 
-__global__ void k_t3_compact(Ws w) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
-    const int o = w.t3_off[vm], n = w.t3_off[vm + 1] - o;
-    if (n == 0) continue;
-    const int base = w.t3_base[vm];
-    for (int j = lane; j < n; j += 32) {
-      const unsigned long long kj = ((unsigned long long)(unsigned)w.t3s_a[base + j] << 32) |
-                                    (unsigned)w.t3s_b[base + j];
-      int rank = 0;
-      for (int i = 0; i < n; ++i) {
-        const unsigned long long ki = ((unsigned long long)(unsigned)w.t3s_a[base + i] << 32) |
-                                      (unsigned)w.t3s_b[base + i];
-        rank += ki < kj;
-      }
-      const int d = o + rank, s = base + j;
-      const int a = w.t3s_a[s], b = w.t3s_b[s];
-      w.t3_a[d] = a;
-      w.t3_b[d] = b;
-      const int md0 = w.ls_in[a];
-      w.t3_md0[d] = md0;
-      w.t3_md1[d] = w.ls_out[a];
-      w.t3_md2[d] = w.ls_out[b];
-      w.t3_R[d] = w.t3s_R[s];
-      w.t3_xc[d] = w.t3s_xc[s];
-      w.t3_yc[d] = w.t3s_yc[s];
-      w.t3_chi2[d] = w.t3s_chi2[s];
-      w.t3_pte[d] = w.t3s_pte[s];
-      atomicAdd(&w.t3md_cnt[md0], 1);
+// dense T3 ordered by (inner LS, outer LS), with member MDs and an anchor cache for the pT3 stage
+__global__ void k_t3_dense(Ws w) {
+  const int n = (int)lst_min64(w.t3_off[w.V], w.cap.t3_dense);
+  const int64_t T = w.cap.t3_dense;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
+    const int s = w.perm[d];
+    const int a = w.t3s_a[s], b = w.t3s_b[s];
+    w.t3_a[d] = a;
+    w.t3_b[d] = b;
+    const int md[3] = {w.ls_in[a], w.ls_out[a], w.ls_out[b]};
+    w.t3_md0[d] = md[0];
+    w.t3_md1[d] = md[1];
+    w.t3_md2[d] = md[2];
+    w.t3_R[d] = w.t3s_R[s];
+    w.t3_xc[d] = w.t3s_xc[s];
+    w.t3_yc[d] = w.t3s_yc[s];
+    w.t3_chi2[d] = w.t3s_chi2[s];
+    w.t3_pte[d] = w.t3s_pte[s];
+    uint8_t ecm = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      w.t3_anc[k * T + d] = make_float4(w.md_x[md[k]], w.md_y[md[k]], w.md_z[md[k]], w.md_r[md[k]]);
+      ecm |= (uint8_t)(w.md_ec[md[k]] << k);
     }
+    w.t3_ecm[d] = ecm;
   }
 }
 
@@ -178,38 +173,56 @@ __global__ void k_t3_compact(Ws w) {
 // Circle: 1/2 rho (x^2 + y^2) - (1 + rho d)(x sin phi - y cos phi) + 1/2 rho d^2 + d = 0;
 // phi is the direction at the point of closest approach to the origin, oriented first -> last.
 // ---------------------------------------------------------------------------------------------
-template <int N>
-__device__ __forceinline__ void karimaki(const double* x, const double* y, double& rho, double& phi,
-                                         double& d) {
-  double mx = 0, my = 0, mxx = 0, mxy = 0, myy = 0, mr2 = 0, mxr = 0, myr = 0, mrr = 0;
+template <class T, int N>
+__device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi, T& d) {
+  T mx = 0, my = 0, mxx = 0, mxy = 0, myy = 0, mr2 = 0, mxr = 0, myr = 0, mrr = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const double r2 = x[i] * x[i] + y[i] * y[i];
+    const T r2 = x[i] * x[i] + y[i] * y[i];
     mx += x[i]; my += y[i];
     mxx += x[i] * x[i]; mxy += x[i] * y[i]; myy += y[i] * y[i];
     mr2 += r2; mxr += x[i] * r2; myr += y[i] * r2; mrr += r2 * r2;
   }
-  const double inv = 1.0 / N;
+  const T inv = T(1) / T(N);
   mx *= inv; my *= inv; mxx *= inv; mxy *= inv; myy *= inv; mr2 *= inv; mxr *= inv; myr *= inv; mrr *= inv;
-  const double Cxx = mxx - mx * mx, Cxy = mxy - mx * my, Cyy = myy - my * my;
-  const double Cxr = mxr - mx * mr2, Cyr = myr - my * mr2, Crr = mrr - mr2 * mr2;
-  const double q1 = Crr * Cxy - Cxr * Cyr;
-  const double q2 = Crr * (Cxx - Cyy) - Cxr * Cxr + Cyr * Cyr;
-  phi = 0.5 * atan2(2.0 * q1, q2);
-  double sp, cp;
-  sincos(phi, &sp, &cp);
-  if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < 0.0) {
-    phi += kPiD;
+  const T Cxx = mxx - mx * mx, Cxy = mxy - mx * my, Cyy = myy - my * my;
+  const T Cxr = mxr - mx * mr2, Cyr = myr - my * mr2, Crr = mrr - mr2 * mr2;
+  const T q1 = Crr * Cxy - Cxr * Cyr;
+  const T q2 = Crr * (Cxx - Cyy) - Cxr * Cxr + Cyr * Cyr;
+  phi = T(0.5) * m_atan2(T(2) * q1, q2);
+  T sp, cp;
+  if constexpr (sizeof(T) == 4) sincosf(phi, &sp, &cp);
+  else sincos(phi, &sp, &cp);
+  if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
+    phi += T(kPiD);
     sp = -sp;
     cp = -cp;
   }
-  if (phi > kPiD) phi -= kTwoPiD;
-  if (phi <= -kPiD) phi += kTwoPiD;
-  const double kap = (sp * Cxr - cp * Cyr) / Crr;
-  const double del = -kap * mr2 + sp * mx - cp * my;
-  const double root = sqrt(1.0 - 4.0 * del * kap);
-  rho = 2.0 * kap / root;
-  d = 2.0 * del / (1.0 + root);
+  if (phi > T(kPiD)) phi -= T(kTwoPiD);
+  if (phi <= -T(kPiD)) phi += T(kTwoPiD);
+  const T kap = (sp * Cxr - cp * Cyr) / Crr;
+  const T del = -kap * mr2 + sp * mx - cp * my;
+  const T root = m_sqrt(T(1) - T(4) * del * kap);
+  rho = T(2) * kap / root;
+  d = T(2) * del / (T(1) + root);
+}
+
+// sum over the anchors of ((|p - c| - R) / sigma)^2 at the circle (rho, phi, d), each residual in
+// the exact cancellation-free form 2 eps / (1 + sqrt(1 + 2 rho eps))
+template <class T, int N>
+__device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T phi, T d, T sigma) {
+  T sp, cp;
+  if constexpr (sizeof(T) == 4) sincosf(phi, &sp, &cp);
+  else sincos(phi, &sp, &cp);
+  T chi2 = 0;
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const T eps = T(0.5) * rho * (x[a] * x[a] + y[a] * y[a]) - (T(1) + rho * d) * (x[a] * sp - y[a] * cp) +
+                  T(0.5) * rho * d * d + d;
+    const T res = T(2) * eps / (T(1) + m_sqrt(T(1) + T(2) * rho * eps)) / sigma;
+    chi2 += res * res;
+  }
+  return chi2;
 }
 
 __global__ void k_t5_caps(Ws w) {
@@ -227,17 +240,50 @@ __global__ void k_t5_caps(Ws w) {
 
 __device__ __forceinline__ float kappa_of(float R) { return isinf(R) ? 0.0f : 1.0f / R; }
 
+// T5 candidates: the curvature-compatibility window in float32 with the window guard, then
+// Karimaki's fit and the r-z fit in float32 as a pre-filter (rejects only chi2 > 1.25 cut + 1: the
+// float32 fit parameters enter chi2 at second order and the residual rounding at ~0.3 %)
 __global__ void k_t5_pre(Ws w, Cst<float> c) {
   const int n_t3 = w.t3_off[w.V];
+  const int64_t T = w.cap.t3_dense;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_t3; i += gridDim.x * blockDim.x) {
     const int m3 = w.t3_md2[i];
     const int j0 = w.t3md_off[m3], j1 = w.t3md_off[m3 + 1];
+    if (j0 == j1) continue;
     const float kin = kappa_of(w.t3_R[i]);
+    float x[5], y[5], z[5], r[5];
+    bool ec[5];
+    const uint8_t ecm_i = w.t3_ecm[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 a4 = w.t3_anc[k * T + i];
+      x[k] = a4.x; y[k] = a4.y; z[k] = a4.z; r[k] = a4.w;
+      ec[k] = (ecm_i >> k) & 1;
+    }
     for (int j = j0; j < j1; ++j) {
       const float kout = kappa_of(w.t3_R[j]);
       Acc32 acc(kGuardWindow);
       acc.cut(c.c_rel * fmaxf(kin, kout) + c.c_abs, fabsf(kin - kout));
-      const int q = warp_agg_slot(!acc.fail, &w.status[ST_Q_T5]);
+      bool keep = !acc.fail;
+      if (keep) {
+        const uint8_t ecm_j = w.t3_ecm[j];
+#pragma unroll
+        for (int k = 1; k < 3; ++k) {
+          const float4 a4 = w.t3_anc[k * T + j];
+          x[k + 2] = a4.x; y[k + 2] = a4.y; z[k + 2] = a4.z; r[k + 2] = a4.w;
+          ec[k + 2] = (ecm_j >> k) & 1;
+        }
+        float rho, phi, d;
+        karimaki<float, 5>(x, y, rho, phi, d);
+        const float chi2c = circle_chi2<float, 5>(x, y, rho, phi, d, c.sigma_rphi);
+        if (chi2c > 1.25f * c.chi2_t5_c + 1.0f) keep = false;
+        if (keep) {
+          float chi2rz, slope;
+          if (rz_fit<float, 5>(c, fabsf(rho), r, z, ec, chi2rz, slope) && chi2rz > 1.25f * c.chi2_t5_rz + 1.0f)
+            keep = false;
+        }
+      }
+      const int q = warp_agg_slot(keep, &w.status[ST_Q_T5]);
       if (q >= 0 && q < w.cap.q_t5) w.q_t5[q] = make_int2(i, j);
     }
   }
@@ -266,18 +312,8 @@ __global__ void k_t5_decide(Ws w, Cst<double> c) {
       ec[a] = w.md_ec[md[a]] != 0;
     }
     double rho, phi, d;
-    karimaki<5>(x, y, rho, phi, d);
-    double sp, cp;
-    sincos(phi, &sp, &cp);
-    double chi2c = 0;
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-      // geometric residual |p - c| - R, as 2 eps / (1 + sqrt(1 + 2 rho eps)) (exact, stable)
-      const double eps = 0.5 * rho * (x[a] * x[a] + y[a] * y[a]) - (1.0 + rho * d) * (x[a] * sp - y[a] * cp) +
-                         0.5 * rho * d * d + d;
-      const double res = 2.0 * eps / (1.0 + sqrt(1.0 + 2.0 * rho * eps)) / c.sigma_rphi;
-      chi2c += res * res;
-    }
+    karimaki<double, 5>(x, y, rho, phi, d);
+    const double chi2c = circle_chi2<double, 5>(x, y, rho, phi, d, c.sigma_rphi);
     acc.cut(c.chi2_t5_c, chi2c);
     double chi2rz, slope;
     if (!rz_fit<double, 5>(c, fabs(rho), r, z, ec, chi2rz, slope)) {
@@ -306,35 +342,26 @@ __global__ void k_t5_decide(Ws w, Cst<double> c) {
   }
 }
 
-__global__ void k_t5_compact(Ws w) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int64_t S = w.cap.t5_slots;
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
-    const int o = w.t5_off[vm], n = w.t5_off[vm + 1] - o;
-    if (n == 0) continue;
-    const int base = w.t5_base[vm];
-    for (int j = lane; j < n; j += 32) {
-      const unsigned long long kj = ((unsigned long long)(unsigned)w.t5s_a[base + j] << 32) |
-                                    (unsigned)w.t5s_b[base + j];
-      int rank = 0;
-      for (int i = 0; i < n; ++i) {
-        const unsigned long long ki = ((unsigned long long)(unsigned)w.t5s_a[base + i] << 32) |
-                                      (unsigned)w.t5s_b[base + i];
-        rank += ki < kj;
-      }
-      const int d = o + rank, s = base + j;
-      const int a = w.t5s_a[s], b = w.t5s_b[s];
-      w.t5_a[d] = a;
-      w.t5_b[d] = b;
-      w.t5_md[0 * S + d] = w.t3_md0[a];
-      w.t5_md[1 * S + d] = w.t3_md1[a];
-      w.t5_md[2 * S + d] = w.t3_md2[a];
-      w.t5_md[3 * S + d] = w.t3_md1[b];
-      w.t5_md[4 * S + d] = w.t3_md2[b];
+// dense T5 ordered by (inner T3, outer T3), with member MDs, fit results and an anchor cache
+__global__ void k_t5_dense(Ws w) {
+  const int n = (int)lst_min64(w.t5_off[w.V], w.cap.t5_dense);
+  const int64_t S = w.cap.t5_slots, D = w.cap.t5_dense;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
+    const int s = w.perm[d];
+    const int a = w.t5s_a[s], b = w.t5s_b[s];
+    w.t5_a[d] = a;
+    w.t5_b[d] = b;
+    const int md[5] = {w.t3_md0[a], w.t3_md1[a], w.t3_md2[a], w.t3_md1[b], w.t3_md2[b]};
+    uint8_t ecm = 0;
 #pragma unroll
-      for (int f = 0; f < 8; ++f) w.t5_f[f * S + d] = w.t5s_f[f * S + s];
+    for (int k = 0; k < 5; ++k) {
+      w.t5_md[k * D + d] = md[k];
+      w.t5_anc[k * D + d] = make_float4(w.md_x[md[k]], w.md_y[md[k]], w.md_z[md[k]], w.md_r[md[k]]);
+      ecm |= (uint8_t)(w.md_ec[md[k]] << k);
     }
+    w.t5_ecm[d] = ecm;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) w.t5_f[f * D + d] = w.t5s_f[f * S + s];
   }
 }
 
@@ -353,13 +380,16 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_t3_decide<<<grid_for(w.cap.q_t3, 128, 152 * 8), 128, 0, L.stream>>>(w, c.d);
   KT_END(L, K_T3_DECIDE);
   LST_LAUNCH(L);
-  launch_effective(w, w.t3_cnt, w.t3_cap, w.t3_base, w.cap.t3_slots, w.t3_off, ST_OVF_T3, ST_ARENA_T3, w.V, L);
-  scan_exclusive(w.t3_off, w.t3_off, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T3_COMPACT);
-  k_t3_compact<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w);
-  KT_END(L, K_T3_COMPACT);
+  GroupArgs ga{w.t3_cnt, w.t3_cap, w.t3_base, w.cap.t3_slots, ST_OVF_T3, ST_ARENA_T3, w.t3s_a, w.t3s_b,
+               w.t3in_cnt, w.t3in_cur, w.t3in_off, w.cap.ls_dense, w.cap.t3_dense, ST_DENSE_T3,
+               w.t3_off, w.ls_off, 1};
+  group_slots(w, ga, L);
+  k_t3_dense<<<grid_for(w.cap.t3_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
-  scan_exclusive(w.t3md_cnt, w.t3md_off, w.cap.md_slots, w.scan_tmp, L);
+  // T3 by first MD: T3 are ordered by inner LS, and LS by inner MD
+  compose_offsets(w.t3md_off, (int)w.cap.md_dense, w.lsin_off, 1, w.t3in_off, w.cap.t3_dense, L);
+  KT_END(L, K_T3_COMPACT);
 }
 
 void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
@@ -368,16 +398,18 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.t5_base, w.t5_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T5_PRE);
-  k_t5_pre<<<152 * 4, 256, 0, L.stream>>>(w, c.f);
+  k_t5_pre<<<152 * 8, 256, 0, L.stream>>>(w, c.f);
   KT_END(L, K_T5_PRE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T5_DECIDE);
   k_t5_decide<<<grid_for(w.cap.q_t5, 128, 152 * 8), 128, 0, L.stream>>>(w, c.d);
   KT_END(L, K_T5_DECIDE);
   LST_LAUNCH(L);
-  launch_effective(w, w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, w.t5_off, ST_OVF_T5, ST_ARENA_T5, w.V, L);
-  scan_exclusive(w.t5_off, w.t5_off, w.V, w.scan_tmp, L);
-  k_t5_compact<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w);
+  GroupArgs ga{w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, ST_OVF_T5, ST_ARENA_T5, w.t5s_a, w.t5s_b,
+               w.t5in_cnt, w.t5in_cur, w.t5in_off, w.cap.t3_dense, w.cap.t5_dense, ST_DENSE_T5,
+               w.t5_off, w.t3_off, 1};
+  group_slots(w, ga, L);
+  k_t5_dense<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
 }
 

@@ -144,3 +144,31 @@ def test_pu300_low_threshold_config4():
     ctx.run([ev])
     _check(oracle.run(det, ev), ctx.results(0), ev)
     ctx.close()
+
+
+@pytest.mark.parametrize("persistent,graph", [(1, 0), (0, 1), (1, 1)])
+def test_executor_modes_identical(det_full, ctx_full, persistent, graph):
+    """The persistent work-queue LS kernel and the CUDA-graph replay give the same objects as the
+    plain launches, for a full batch and then a smaller batch replayed through the same graph."""
+    evs = [gen.config_event(3, e)[1] for e in range(3)]
+    ctx_full.run(evs)
+    ref = [ctx_full.results(e) for e in range(3)]
+    ctx = lst.Context(det_full, persistent=persistent, use_graph=graph)
+    ctx.reserve(3, max(e.n_hits for e in evs), max(e.n_pls for e in evs))
+    for _ in range(2):
+        ctx.run(evs)
+        for e in range(3):
+            got = ctx.results(e)
+            for k in got:
+                if k != "counts":
+                    assert np.array_equal(got[k], ref[e][k]), (e, k)
+    ctx.run(evs[1:2])   # fewer events than the graph's shape: padded with empty events
+    got = ctx.results(0)
+    for k in got:
+        if k != "counts":
+            assert np.array_equal(got[k], ref[1][k]), k
+    if graph:
+        n0 = ctx.launch_count()
+        ctx.run(evs)
+        assert ctx.launch_count() - n0 > 50   # graph replays count their kernel nodes
+    ctx.close()
