@@ -90,6 +90,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def to_device(ev, torch):
+    return {"x": torch.as_tensor(ev.x, device="cuda"), "y": torch.as_tensor(ev.y, device="cuda"),
+            "z": torch.as_tensor(ev.z, device="cuda"), "sensor": torch.as_tensor(ev.sensor, device="cuda"),
+            "pls": torch.as_tensor(ev.pls.view(np.uint8).copy(), device="cuda"), "n_pls": ev.n_pls}
+
+
+def serving_run(det, events, rate, n_requests, n_engines, max_batch, seed=0):
+    """Poisson stream of `n_requests` events (drawn cyclically from `events`) at `rate` per second."""
+    from paper_2207_08207_gb300.serving import Server, poisson_arrivals
+    srv = Server(det, n_engines=n_engines, max_batch=max_batch, max_hits=max(e.n_hits for e in events),
+                 max_pls=max(e.n_pls for e in events), budget=40e9, keep="tc", use_graph=1, persistent=1)
+    reqs = [events[i % len(events)] for i in range(n_requests)]
+    srv.warmup(events)   # graph capture and arena first touch on every engine
+    stats, _ = srv.serve(reqs, poisson_arrivals(rate, n_requests, seed))
+    srv.close()
+    d = stats.as_dict()
+    d["rate_hz"] = rate
+    return d
+
+
 def make_events(n, seed0=0):
     from paper_2207_08207_gb300 import gen
     det = gen.make_detector(barrel_only=False, pt_thr=0.8)
@@ -152,6 +172,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-rates", default="1000",
+                    help="comma-separated Poisson rates (events/s) of the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -169,19 +193,19 @@ def main():
     B = args.batch
     # every rank processes its own events (events are independent: no collective on the data path)
     det, evs = make_events(B, seed0=1000 * rank)
-    # batched executor: persistent LS kernel on a cost-ordered work list, chain replayed as a CUDA graph
-    ctx = lst.Context(det, device=local, persistent=1, use_graph=1)
-    ctx.reserve(B, max(e.n_hits for e in evs), max(e.n_pls for e in evs))
-
     # inputs resident in HBM
-    dev = []
-    for ev in evs:
-        dev.append({"x": torch.as_tensor(ev.x, device="cuda"), "y": torch.as_tensor(ev.y, device="cuda"),
-                    "z": torch.as_tensor(ev.z, device="cuda"), "sensor": torch.as_tensor(ev.sensor, device="cuda"),
-                    "pls": torch.as_tensor(ev.pls.view(np.uint8).copy(), device="cuda"), "n_pls": ev.n_pls})
+    dev = [to_device(ev, torch) for ev in evs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.Stream()   # the library's work and the timing events share this stream
     torch.cuda.set_stream(stream)
+
+    # batched executor: launch settings from the autotuner, chain replayed as a CUDA graph
+    tuned = {"block_ls": 128, "warps_px": 4, "persistent": 1, "cap_scale": 1.0}
+    if not args.no_tune:
+        from paper_2207_08207_gb300 import autotune
+        tuned = autotune.tune(det, dev, workload="pu200")
+    ctx = lst.Context(det, device=local, use_graph=1, **tuned)
+    ctx.reserve(B, max(e.n_hits for e in evs), max(e.n_pls for e in evs))
 
     def step():
         ctx.submit(dev, stream=stream)
@@ -264,19 +288,39 @@ def main():
     e2e_ms = [float("nan")]
     h2d = sum(e.n_hits * 16 + e.n_pls * 48 for e in evs) + 2 * (B + 1) * 4
     d2h = 0
-    for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5))):
+    # pinned host buffers for the results (one transfer per array for the whole batch)
+    cap_tc = sum(e.n_pls for e in evs) + 20000 * B
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    tc_buf = {"offsets": pin((B + 1,), torch.int32), "type": pin((cap_tc,), torch.int32),
+              "obj": pin((cap_tc,), torch.int32), "hits": pin((cap_tc, 14), torch.int32),
+              "pt": pin((cap_tc,), torch.float32), "eta": pin((cap_tc,), torch.float32),
+              "phi": pin((cap_tc,), torch.float32)}
+    for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5)) + 1):
         if len(e2e_ms) == 1 and e2e_ms[0] != e2e_ms[0]:
             e2e_ms = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.submit(evs, stream=stream)
         ctx.sync()
-        d2h = 0
-        for e in range(B):
-            tc = ctx.copy_tc(e)
-            d2h += sum(a.nbytes for a in tc.values())
+        tc = ctx.copy_tc_all(tc_buf)
+        n_tc = tc["n"]
+        d2h = n_tc * (4 * 5 + 14 * 4) + (B + 1) * 4
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    if len(e2e_ms) > 1:
+        e2e_ms = e2e_ms[1:]   # first pass: host staging buffers
     e2e_value = B / (statistics.mean(e2e_ms) / 1e3)
+
+    # serving: Poisson arrivals of PU ~ U[50, 300] events, continuous batching vs one at a time
+    serving = None
+    if not args.no_serving and rank == 0:
+        from paper_2207_08207_gb300 import gen
+        pool = [gen.config_event(5, e)[1] for e in range(24)]
+        serving = {"workload": "Poisson stream of PU ~ U[50, 300] events (24 generated, cycled), 40 GB budget",
+                   "batched": [], "one_at_a_time": []}
+        for rate in [float(r) for r in args.serving_rates.split(",")]:
+            n_req = int(min(4000, max(200, rate * 2.0)))
+            serving["batched"].append(serving_run(det, pool, rate, n_req, n_engines=3, max_batch=64))
+            serving["one_at_a_time"].append(serving_run(det, pool, rate, min(n_req, 600), n_engines=1, max_batch=1))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -296,6 +340,8 @@ def main():
             "latency_ms": {"batched_p50": float(np.percentile(step_ms, 50)),
                            "batched_p99": float(np.percentile(step_ms, 99))},
             "plain": plain,
+            "serving": serving,
+            "tuned": tuned,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -268,6 +268,17 @@ int lst_get_counts(const lst_ctx* ctx, int32_t ev, lst_counts* c);
 int lst_copy_tc(lst_ctx* ctx, int32_t ev, int32_t* type, int32_t* obj, int32_t* hits, float* pt,
                 float* eta, float* phi);
 
+/*
+ * Copy the track candidates of every event of the last completed run to host memory with one
+ * transfer per array (the "copy track candidates to the CPU" step of Sec. 4.2). Event e's rows are
+ * [offsets[e], offsets[e + 1]) (offsets has n_ev + 1 entries); type / obj / pt / eta / phi hold
+ * lst_tc_total(ctx) rows and hits 14 per row. Any array pointer may be NULL. Pinned host memory
+ * gives the fastest transfer. Waits for the copies.
+ */
+int64_t lst_tc_total(const lst_ctx* ctx);
+int lst_copy_tc_all(lst_ctx* ctx, int32_t* offsets, int32_t* type, int32_t* obj, int32_t* hits, float* pt,
+                    float* eta, float* phi);
+
 /* Device time of each stage of the last run, in ms (CUDA events on the run's stream), indexed by
  * LST_STAGE_*; stage_ms[LST_N_STAGES] receives the whole chain. Needs lst_set_timing(ctx, 1). */
 int lst_set_timing(lst_ctx* ctx, int enable);
@@ -281,6 +292,13 @@ int lst_get_stage_ms(const lst_ctx* ctx, float* stage_ms);
  * Writes min(n, count) values and returns the count (16), or a negative lst_status on error.
  */
 int lst_get_kernel_ms(const lst_ctx* ctx, float* ms, int32_t n);
+
+/*
+ * Device bytes the context's arenas need for a batch of n_events events with n_hits hits and n_pls
+ * seeds in total, at the default capacity predictions (what a serving loop admits work against).
+ * Needs a loaded geometry; allocates nothing. Returns a negative lst_status on error.
+ */
+int64_t lst_predict_bytes(const lst_ctx* ctx, int32_t n_events, int64_t n_hits, int64_t n_pls);
 
 /* Number of kernel launches issued by this context since creation (graph replays count each
  * kernel node). */

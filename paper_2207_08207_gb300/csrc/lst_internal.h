@@ -135,8 +135,11 @@ struct Ws {
   unsigned long long* tc_key = nullptr;   // [tc_capacity] sort keys
   int32_t* tc_hit_key = nullptr;          // [tc_capacity][14] sorted hit tuples
   int32_t* grp_tmp = nullptr;             // [max(p3_slots, p5_slots)] grouping scratch
-  int32_t *tc_type = nullptr, *tc_obj = nullptr, *tc_hits = nullptr;
+  int32_t *tc_type = nullptr, *tc_obj = nullptr, *tc_hits = nullptr;   // per-event regions
   float *tc_pt = nullptr, *tc_eta = nullptr, *tc_phi = nullptr;
+  int32_t* tcd_off = nullptr;   // [E + 1] first dense row of each event
+  int32_t *tcd_type = nullptr, *tcd_obj = nullptr, *tcd_hits = nullptr;   // dense over the batch
+  float *tcd_pt = nullptr, *tcd_eta = nullptr, *tcd_phi = nullptr;
   int64_t tc_capacity = 0;
   // event-local output copies
   int32_t *o_md_lo = nullptr, *o_md_up = nullptr, *o_md_mod = nullptr;

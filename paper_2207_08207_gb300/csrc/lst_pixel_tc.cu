@@ -672,6 +672,25 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
   if (threadIdx.x < 4) w.ev_stat[e * kEvWords + 7 + threadIdx.x] = ty[threadIdx.x];
 }
 
+// track candidates of all events packed densely (event e's rows start at tcd_off[e]), so that the
+// whole batch's candidates reach the host in one transfer per array
+__global__ void k_tc_dense(Ws w, Geo g) {
+  const int e = blockIdx.x;
+  if (e >= w.E) return;
+  const int n = w.tc_cnt[e];
+  const int src0 = w.ev_pls_off[e] + w.t5_off[e * g.n_mods];
+  const int dst0 = w.tcd_off[e];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int a = src0 + k, b = dst0 + k;
+    w.tcd_type[b] = w.tc_type[a];
+    w.tcd_obj[b] = w.tc_obj[a];
+    w.tcd_pt[b] = w.tc_pt[a];
+    w.tcd_eta[b] = w.tc_eta[a];
+    w.tcd_phi[b] = w.tc_phi[a];
+  }
+  for (int k = threadIdx.x; k < 14 * n; k += blockDim.x) w.tcd_hits[(int64_t)dst0 * 14 + k] = w.tc_hits[(int64_t)src0 * 14 + k];
+}
+
 }  // namespace
 
 void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
@@ -741,6 +760,9 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_BEGIN(L, K_TC_ASSEMBLE);
   k_tc_assemble<<<w.E, 1024, smem, L.stream>>>(w, g);
   KT_END(L, K_TC_ASSEMBLE);
+  scan_exclusive(w.tc_cnt, w.tcd_off, w.E, w.scan_tmp, L);
+  k_tc_dense<<<w.E, 256, 0, L.stream>>>(w, g);
+  LST_LAUNCH(L);
   *L.launches += 5;
 }
 

@@ -117,14 +117,14 @@ __global__ void k_ev_stat(Ws w, int n_mods) {
     st[5] = w.pt5_off[p1] - w.pt5_off[p0];
     const int ntc = w.tc_cnt[e];
     st[6] = ntc;
-    const int region = p0 + w.t5_off[a];   // st[7..10] (per-type counts) come from the assembly
+    // st[7..10] (per-type counts) come from the assembly
     st[11] = w.md_off[a];
     st[12] = w.ls_off[a];
     st[13] = w.t3_off[a];
     st[14] = w.t5_off[a];
     st[15] = w.pt3_off[p0];
     st[16] = w.pt5_off[p0];
-    st[17] = region;
+    st[17] = w.tcd_off[e];
   }
 }
 
@@ -336,14 +336,44 @@ int plan_input(lst_ctx* ctx, int64_t E, int64_t H, int64_t P) {
   return LST_OK;
 }
 
+// Lay out the work arena for capacities c (addresses assigned to ws when base is not null).
+// Returns its bytes (zeroed region first, size in *zero_bytes).
+size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_bytes);
+
 int plan_work(lst_ctx* ctx, const Caps& want) {
   Caps c = want;
   c.E = ctx->in_caps.E;   // event offsets (padded to E) live in the input arena
-  const int64_t V = c.E * ctx->geo.n_mods;
+  size_t zb = 0;
+  const size_t total = layout_work(ctx->ws, c, ctx->geo.n_mods, nullptr, &zb);
+  if (ctx->work_mem) CK(cudaFreeAsync(ctx->work_mem, ctx->stream));
+  ctx->work_mem = nullptr;
+  CK(cudaMallocFromPoolAsync(&ctx->work_mem, total, ctx->pool, ctx->stream));
+  layout_work(ctx->ws, c, ctx->geo.n_mods, ctx->work_mem, &zb);
+  Ws& w = ctx->ws;
+  ctx->zero_begin = ctx->work_mem;
+  ctx->zero_bytes = zb;
+  ctx->work_bytes = total;
+  ctx->caps = c;
+  ctx->arena_gen++;
+  w.cap = c;
+  w.n_cells = tc_cells_per_event();
+  w.tc_capacity = c.P + c.t5_dense;
+  // pinned status words
+  const size_t words = ST_N_WORDS + (size_t)c.E * kEvWords;
+  if (words > ctx->h_status_words) {
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    ctx->h_status = nullptr;
+    CK(cudaMallocHost(&ctx->h_status, words * sizeof(int32_t)));
+    ctx->h_status_words = words;
+  }
+  return LST_OK;
+}
+
+size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_bytes) {
+  const int64_t V = c.E * n_mods;
   const int64_t S = 2 * V;
   const int64_t NC = (int64_t)c.E * tc_cells_per_event();
   const int64_t tc_cap = c.P + c.t5_dense;
-  Ws& w = ctx->ws;
   Planner z, pl;   // z: cleared before every run
   z.add(w.status, ST_N_WORDS + c.E * kEvWords);   // status words, then the per-event words
   z.add(w.tc_cnt, c.E);
@@ -407,6 +437,9 @@ int plan_work(lst_ctx* ctx, const Caps& want) {
   pl.add(w.tc_code, tc_cap); pl.add(w.tc_key, tc_cap); pl.add(w.tc_hit_key, 14 * tc_cap);
   pl.add(w.tc_type, tc_cap); pl.add(w.tc_obj, tc_cap); pl.add(w.tc_hits, 14 * tc_cap);
   pl.add(w.tc_pt, tc_cap); pl.add(w.tc_eta, tc_cap); pl.add(w.tc_phi, tc_cap);
+  pl.add(w.tcd_off, c.E + 1);
+  pl.add(w.tcd_type, tc_cap); pl.add(w.tcd_obj, tc_cap); pl.add(w.tcd_hits, 14 * tc_cap);
+  pl.add(w.tcd_pt, tc_cap); pl.add(w.tcd_eta, tc_cap); pl.add(w.tcd_phi, tc_cap);
   // event-local outputs
   pl.add(w.o_md_lo, c.md_dense); pl.add(w.o_md_up, c.md_dense); pl.add(w.o_md_mod, c.md_dense);
   pl.add(w.o_ls_in, c.ls_dense); pl.add(w.o_ls_out, c.ls_dense);
@@ -421,29 +454,13 @@ int plan_work(lst_ctx* ctx, const Caps& want) {
   pl.add(w.scan_tmp, scan_tmp_elems(scan_n) + 8);
   const size_t zb = z.layout();
   const size_t pb = pl.layout();
-  if (ctx->work_mem) CK(cudaFreeAsync(ctx->work_mem, ctx->stream));
-  ctx->work_mem = nullptr;
-  CK(cudaMallocFromPoolAsync(&ctx->work_mem, zb + pb, ctx->pool, ctx->stream));
-  z.assign(ctx->work_mem);
-  pl.assign(static_cast<char*>(ctx->work_mem) + zb);
-  w.ev_stat = w.status + ST_N_WORDS;
-  ctx->zero_begin = ctx->work_mem;
-  ctx->zero_bytes = zb;
-  ctx->work_bytes = zb + pb;
-  ctx->caps = c;
-  ctx->arena_gen++;
-  w.cap = c;
-  w.n_cells = tc_cells_per_event();
-  w.tc_capacity = tc_cap;
-  // pinned status words
-  const size_t words = ST_N_WORDS + (size_t)c.E * kEvWords;
-  if (words > ctx->h_status_words) {
-    if (ctx->h_status) cudaFreeHost(ctx->h_status);
-    ctx->h_status = nullptr;
-    CK(cudaMallocHost(&ctx->h_status, words * sizeof(int32_t)));
-    ctx->h_status_words = words;
+  if (base) {
+    z.assign(base);
+    pl.assign(static_cast<char*>(base) + zb);
+    w.ev_stat = w.status + ST_N_WORDS;
   }
-  return LST_OK;
+  *zero_bytes = zb;
+  return zb + pb;
 }
 
 int ensure_pinned(lst_ctx* ctx, size_t bytes) {
@@ -1015,8 +1032,8 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     o.t5_phi = w.t5_f + 6 * S5 + bt5; o.t5_pt = w.t5_f + 7 * S5 + bt5;
     o.pt3_pls = w.o_pt3_pls + bp3; o.pt3_t3 = w.o_pt3_obj + bp3; o.pt3_chi2_xy = w.pt3_xy + bp3; o.pt3_chi2_rz = w.pt3_rz + bp3;
     o.pt5_pls = w.o_pt5_pls + bp5; o.pt5_t5 = w.o_pt5_obj + bp5; o.pt5_chi2_xy = w.pt5_xy + bp5; o.pt5_chi2_rz = w.pt5_rz + bp5;
-    o.tc_type = w.tc_type + btc; o.tc_obj = w.tc_obj + btc; o.tc_hits = w.tc_hits + (int64_t)btc * 14;
-    o.tc_pt = w.tc_pt + btc; o.tc_eta = w.tc_eta + btc; o.tc_phi = w.tc_phi + btc;
+    o.tc_type = w.tcd_type + btc; o.tc_obj = w.tcd_obj + btc; o.tc_hits = w.tcd_hits + (int64_t)btc * 14;
+    o.tc_pt = w.tcd_pt + btc; o.tc_eta = w.tcd_eta + btc; o.tc_phi = w.tcd_phi + btc;
     if (ctx->user_out) ctx->user_out[ev] = o;
   }
   return first_err;
@@ -1078,6 +1095,41 @@ int lst_copy_tc(lst_ctx* ctx, int32_t ev, int32_t* type, int32_t* obj, int32_t* 
   return LST_OK;
 }
 
+int64_t lst_tc_total(const lst_ctx* ctx) {
+  if (!ctx) return -LST_EINVAL;
+  int64_t n = 0;
+  for (const lst_counts& c : ctx->counts) n += c.n_tc;
+  return n;
+}
+
+int lst_copy_tc_all(lst_ctx* ctx, int32_t* offsets, int32_t* type, int32_t* obj, int32_t* hits, float* pt,
+                    float* eta, float* phi) {
+  if (!ctx) return LST_EINVAL;
+  if (ctx->outs.empty()) return fail(ctx, LST_ESTATE, "lst_copy_tc_all: no completed run");
+  CK(cudaSetDevice(ctx->device));
+  const int32_t E = (int32_t)ctx->outs.size();
+  const int64_t n = lst_tc_total(ctx);
+  if (offsets) {
+    int64_t acc = 0;
+    for (int32_t e = 0; e < E; ++e) {
+      offsets[e] = (int32_t)acc;
+      acc += ctx->counts[e].n_tc;
+    }
+    offsets[E] = (int32_t)acc;
+  }
+  if (n == 0) return LST_OK;
+  const Ws& w = ctx->ws;
+  // rows of events 0..E-1 are contiguous from row 0 of the dense arrays
+  if (type) CK(cudaMemcpyAsync(type, w.tcd_type, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (obj) CK(cudaMemcpyAsync(obj, w.tcd_obj, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (hits) CK(cudaMemcpyAsync(hits, w.tcd_hits, n * 14 * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (pt) CK(cudaMemcpyAsync(pt, w.tcd_pt, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (eta) CK(cudaMemcpyAsync(eta, w.tcd_eta, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (phi) CK(cudaMemcpyAsync(phi, w.tcd_phi, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LST_OK;
+}
+
 int lst_set_timing(lst_ctx* ctx, int enable) {
   if (!ctx) return LST_EINVAL;
   ctx->timing = enable != 0;
@@ -1094,6 +1146,17 @@ int lst_get_kernel_ms(const lst_ctx* ctx, float* ms, int32_t n) {
   if (!ctx || !ms || n < 0) return LST_EINVAL;
   for (int k = 0; k < n && k < K_N_TIMED; ++k) ms[k] = ctx->kern_ms[k];
   return K_N_TIMED;
+}
+
+int64_t lst_predict_bytes(const lst_ctx* ctx, int32_t n_events, int64_t n_hits, int64_t n_pls) {
+  if (!ctx || !ctx->geo_loaded || n_events <= 0 || n_hits < 0 || n_pls < 0) return -LST_EINVAL;
+  Caps c = default_caps(n_events, n_hits, n_pls, ctx->geo.n_mods);
+  Ws tmp{};
+  size_t zb = 0;
+  const size_t work = layout_work(tmp, c, ctx->geo.n_mods, nullptr, &zb);
+  const size_t in = (size_t)n_hits * 16 + (size_t)n_pls * sizeof(lst_pls) + 8 * (size_t)(n_events + 1) +
+                    16 * (size_t)n_events * ctx->geo.n_mods;
+  return (int64_t)(work + in);
 }
 
 int64_t lst_launch_count(const lst_ctx* ctx) { return ctx ? ctx->launches : 0; }

@@ -118,6 +118,11 @@ def lib():
         L.lst_copy_tc.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 6
         L.lst_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.lst_get_stage_ms.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.lst_tc_total.argtypes = [ctypes.c_void_p]
+        L.lst_tc_total.restype = ctypes.c_int64
+        L.lst_copy_tc_all.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 7
+        L.lst_predict_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]
+        L.lst_predict_bytes.restype = ctypes.c_int64
         L.lst_get_kernel_ms.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
         L.lst_launch_count.argtypes = [ctypes.c_void_p]
         L.lst_launch_count.restype = ctypes.c_int64
@@ -291,6 +296,19 @@ class Context:
                                         _ptr(out["pt"]), _ptr(out["eta"]), _ptr(out["phi"])))
         return out
 
+    def copy_tc_all(self, out=None) -> dict:
+        """Every track candidate of the last run, one transfer per array. `out`: optional dict of
+        preallocated (e.g. pinned) numpy arrays large enough for the batch."""
+        n = int(self._L.lst_tc_total(self._h))
+        if out is None:
+            out = {"offsets": np.zeros(self._n_ev + 1, np.int32), "type": np.zeros(n, np.int32),
+                   "obj": np.zeros(n, np.int32), "hits": np.zeros((n, 14), np.int32), "pt": np.zeros(n, np.float32),
+                   "eta": np.zeros(n, np.float32), "phi": np.zeros(n, np.float32)}
+        self._check(self._L.lst_copy_tc_all(self._h, _ptr(out["offsets"]), _ptr(out["type"]), _ptr(out["obj"]),
+                                            _ptr(out["hits"]), _ptr(out["pt"]), _ptr(out["eta"]), _ptr(out["phi"])))
+        out["n"] = n
+        return out
+
     def set_timing(self, on=True):
         self._check(self._L.lst_set_timing(self._h, 1 if on else 0))
 
@@ -309,6 +327,12 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._L.lst_launch_count(self._h))
+
+    def predict_bytes(self, n_events, n_hits, n_pls) -> int:
+        v = int(self._L.lst_predict_bytes(self._h, int(n_events), int(n_hits), int(n_pls)))
+        if v < 0:
+            raise LSTError(-v, "lst_predict_bytes")
+        return v
 
     def kernel_ms(self) -> dict:
         a = np.zeros(len(KERNELS), dtype=np.float32)

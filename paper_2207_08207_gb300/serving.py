@@ -1,0 +1,232 @@
+"""Serving loop for the LST chain: events arrive over time, are admitted by their predicted
+object-buffer memory against a fixed budget, and are processed by continuous batching.
+
+Several resident engines (library contexts, each with its own CUDA stream and arenas, all sharing
+the device-resident geometry's layout) run batches concurrently: whenever an engine is free, every
+event that has arrived and fits the memory budget is taken into its next batch, so requests that
+arrive while others are on the GPU are admitted as soon as an engine and memory free up, and their
+work overlaps on the device with batches already running. Latency is measured from an event's
+arrival to the host's observation of its batch's completion.
+
+The scheduling (``Scheduler``) is independent of the engine so that it can be exercised on the host
+with a fake engine; ``LSTEngine`` drives the CUDA library.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrival: float          # seconds since the start of the run
+    event: object
+    n_hits: int
+    n_pls: int
+    pred_bytes: int = 0
+    t_done: float = math.nan
+    result: object = None
+
+
+@dataclass
+class ServeStats:
+    n: int
+    wall_s: float
+    throughput: float
+    p50_ms: float
+    p99_ms: float
+    p999_ms: float
+    mean_batch: float
+    max_inflight_bytes: int
+    batches: int
+    latencies_ms: list = field(default_factory=list)
+
+    def as_dict(self):
+        d = dict(self.__dict__)
+        d.pop("latencies_ms")
+        return d
+
+
+class Engine:
+    """Interface of one batch executor. `max_batch`: the most events it takes per batch."""
+
+    max_batch = 64
+
+    def submit(self, events):           # enqueue a batch; must not block on the GPU
+        raise NotImplementedError
+
+    def done(self) -> bool:             # has the last batch finished?
+        raise NotImplementedError
+
+    def collect(self, n):               # results of the last batch (after done()), list of n
+        raise NotImplementedError
+
+
+class Scheduler:
+    """Continuous batching over several engines with memory-based admission.
+
+    predict(n_hits, n_pls) -> bytes: the object-buffer memory one event is predicted to need.
+    An event is admitted only while the predicted bytes of all events on the engines stay within
+    `budget`; events are admitted in arrival order (no overtaking) up to `max_batch` per batch.
+    """
+
+    def __init__(self, engines, predict, budget=40e9, max_batch=64, clock=time.perf_counter, idle_sleep=0.0):
+        self.engines = list(engines)
+        self.predict = predict
+        self.budget = float(budget)
+        self.max_batch = int(max_batch)
+        self.clock = clock
+        self.idle_sleep = idle_sleep
+
+    def run(self, requests):
+        reqs = sorted(requests, key=lambda r: r.t_arrival)
+        for r in reqs:
+            r.pred_bytes = int(self.predict(r.n_hits, r.n_pls))
+            if r.pred_bytes > self.budget:
+                raise ValueError(f"request {r.rid} alone exceeds the memory budget")
+        pending = collections.deque(reqs)
+        waiting = collections.deque()
+        busy = {}                     # engine index -> list of requests
+        inflight = 0
+        max_inflight = 0
+        batches = 0
+        batch_sizes = []
+        t0 = self.clock()
+        while pending or waiting or busy:
+            now = self.clock() - t0
+            while pending and pending[0].t_arrival <= now:
+                waiting.append(pending.popleft())
+            # completions
+            for k in list(busy):
+                if self.engines[k].done():
+                    batch = busy.pop(k)
+                    res = self.engines[k].collect(len(batch))
+                    t_done = self.clock() - t0
+                    for r, out in zip(batch, res):
+                        r.t_done = t_done
+                        r.result = out
+                    inflight -= sum(r.pred_bytes for r in batch)
+            # admission onto free engines: the smallest free engine that takes everything waiting
+            # (else the largest free one), so small bursts run on small launch shapes
+            while waiting:
+                free = [k for k in range(len(self.engines)) if k not in busy]
+                if not free:
+                    break
+                cap = lambda k: min(self.max_batch, getattr(self.engines[k], "max_batch", self.max_batch))
+                fits = [k for k in free if cap(k) >= len(waiting)]
+                k = min(fits, key=cap) if fits else max(free, key=cap)
+                batch = []
+                while waiting and len(batch) < cap(k) and \
+                        inflight + waiting[0].pred_bytes <= self.budget:
+                    r = waiting.popleft()
+                    inflight += r.pred_bytes
+                    batch.append(r)
+                if not batch:
+                    break
+                max_inflight = max(max_inflight, inflight)
+                self.engines[k].submit([r.event for r in batch])
+                busy[k] = batch
+                batches += 1
+                batch_sizes.append(len(batch))
+            if not busy and not waiting and pending:
+                # idle until the next arrival
+                wait = pending[0].t_arrival - (self.clock() - t0)
+                if wait > 0 and self.idle_sleep > 0:
+                    time.sleep(min(wait, self.idle_sleep))
+        wall = self.clock() - t0
+        lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in reqs])
+        return ServeStats(
+            n=len(reqs), wall_s=wall, throughput=len(reqs) / wall if wall > 0 else math.inf,
+            p50_ms=float(np.percentile(lat, 50)) if lat.size else math.nan,
+            p99_ms=float(np.percentile(lat, 99)) if lat.size else math.nan,
+            p999_ms=float(np.percentile(lat, 99.9)) if lat.size else math.nan,
+            mean_batch=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+            max_inflight_bytes=int(max_inflight), batches=batches, latencies_ms=lat.tolist())
+
+
+def poisson_arrivals(rate_hz, n, seed=0):
+    """Arrival times (s) of a Poisson stream with the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_hz, n))
+
+
+class LSTEngine(Engine):
+    """One library context with its own stream; batches of resident (device) or host events."""
+
+    def __init__(self, det, max_batch, max_hits, max_pls, device=0, stream=None, keep="tc", **cfg):
+        import torch
+        from . import lst
+        self.max_batch = int(max_batch)
+        self.ctx = lst.Context(det, device=device, **cfg)
+        self.ctx.reserve(max_batch, max_hits, max_pls)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self.keep = keep
+        self._n = 0
+
+    def predict(self, n_hits, n_pls):
+        return self.ctx.predict_bytes(1, n_hits, n_pls)
+
+    def submit(self, events):
+        self.ctx.submit(events, stream=self.stream)
+        self._n = len(events)
+
+    def done(self):
+        return self.ctx.query()
+
+    def collect(self, n):
+        self.ctx.sync()
+        if self.keep == "tc":   # the batch's track candidates, one transfer per array
+            tc = self.ctx.copy_tc_all()
+            o = tc["offsets"]
+            return [{k: tc[k][o[e]:o[e + 1]] for k in ("type", "obj", "hits", "pt", "eta", "phi")}
+                    for e in range(n)]
+        if self.keep == "all":
+            return [self.ctx.results(e) for e in range(n)]
+        return [self.ctx.counts(e) for e in range(n)]
+
+    def close(self):
+        self.ctx.close()
+
+
+class Server:
+    """LST serving: resident contexts of different batch capacities (`batch_sizes`, default one
+    single-event context plus `n_engines - 1` of `max_batch`), continuous batching, memory admission."""
+
+    def __init__(self, det, n_engines=3, max_batch=64, max_hits=150_000, max_pls=12_000, budget=40e9, device=0,
+                 keep="tc", batch_sizes=None, **cfg):
+        if batch_sizes is None:
+            batch_sizes = [max_batch] if n_engines == 1 else [1] + [max_batch] * (n_engines - 1)
+        self.engines = [LSTEngine(det, b, max_hits, max_pls, device=device, keep=keep, **cfg) for b in batch_sizes]
+        self.scheduler = Scheduler(self.engines, self.engines[0].predict, budget=budget, max_batch=max(batch_sizes))
+
+    def warmup(self, events):
+        """One batch on every engine (graph capture, arena first touch) before a measurement."""
+        for e in self.engines:
+            e.submit(list(events[: e.max_batch]))
+            e.collect(min(len(events), e.max_batch))
+
+    def serve(self, events, arrivals):
+        reqs = [Request(i, float(t), ev, _n_hits(ev), _n_pls(ev)) for i, (t, ev) in enumerate(zip(arrivals, events))]
+        stats = self.scheduler.run(reqs)
+        return stats, reqs
+
+    def close(self):
+        for e in self.engines:
+            e.close()
+
+
+def _n_hits(ev):
+    if isinstance(ev, dict):
+        return int(ev["x"].shape[0])
+    return ev.n_hits
+
+
+def _n_pls(ev):
+    if isinstance(ev, dict):
+        return int(ev.get("n_pls", 0))
+    return ev.n_pls
