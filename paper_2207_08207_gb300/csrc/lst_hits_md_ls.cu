@@ -185,12 +185,23 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
     w.md_dpc[d] = w.ms_dpc[s];
     w.md_pte[d] = w.ms_pte[s];
     const float x = w.bx[lo], y = w.by[lo];
-    const float r = sqrtf(x * x + y * y);
+    // x^2 + y^2 as an unevaluated float pair (products exact by FMA), its float32 square root, and
+    // the low part of the radius: r = r_hi + (q - r_hi^2) / (2 r_hi) to float-float accuracy
+    const float xx = x * x, exx = fmaf(x, x, -xx);
+    const float yy = y * y, eyy = fmaf(y, y, -yy);
+    const float q = xx + yy;
+    const float qb = q - xx;                                  // TwoSum: q + qs == xx + yy exactly
+    const float qs = (xx - (q - qb)) + (yy - qb);
+    const float qe = qs + exx + eyy;
+    const float r = sqrtf(q);
+    const float rlo = (fmaf(-r, r, q) + qe) / (2.0f * r);
     w.md_x[d] = x;
     w.md_y[d] = y;
     w.md_z[d] = w.bz[lo];
     w.md_r[d] = r;
+    w.md_rlo[d] = r > 0.f ? rlo : 0.f;
     w.md_sthr[d] = c.two_rthr * asinf(fminf(r / c.two_rthr, 1.0f));
+    w.md_alpha[d] = asinf(fminf(r * c.k2p, c.sin_max));
     w.md_ec[d] = g.endcap[vm % g.n_mods];
   }
 }
@@ -257,10 +268,10 @@ __global__ void k_ls_work_fill(Ws w) {
 // is sized to the GPU and blocks pull modules from the cost-ordered work list; otherwise a
 // grid-stride loop over all modules.
 __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persistent) {
-  __shared__ float ax[kLsA], ay[kLsA], az[kLsA], ar[kLsA], as_[kLsA];
+  __shared__ float ax[kLsA], ay[kLsA], az[kLsA], ar[kLsA], as_[kLsA], aal[kLsA];
   __shared__ int aid[kLsA];
   __shared__ uint8_t aec[kLsA];
-  __shared__ float bx[kLsB], by[kLsB], bz[kLsB], br[kLsB], bs[kLsB];
+  __shared__ float bx[kLsB], by[kLsB], bz[kLsB], br[kLsB], bs[kLsB], bal[kLsB];
   __shared__ int bid[kLsB];
   __shared__ uint8_t bec[kLsB];
   __shared__ int tpre[kMaxTargets + 1];
@@ -306,6 +317,7 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
         const int d = a_begin + a0 + tid;
         ax[tid] = w.md_x[d]; ay[tid] = w.md_y[d]; az[tid] = w.md_z[d];
         ar[tid] = w.md_r[d]; as_[tid] = w.md_sthr[d]; aec[tid] = w.md_ec[d]; aid[tid] = d;
+        aal[tid] = w.md_alpha[d];
       }
       for (int b0 = 0; b0 < totB; b0 += kLsB) {
         const int nB = min(kLsB, totB - b0);
@@ -319,6 +331,7 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
           const int d = tbase[lo] + (gj - tpre[lo]);
           bx[j] = w.md_x[d]; by[j] = w.md_y[d]; bz[j] = w.md_z[d];
           br[j] = w.md_r[d]; bs[j] = w.md_sthr[d]; bec[j] = w.md_ec[d]; bid[j] = d;
+          bal[j] = w.md_alpha[d];
         }
         __syncthreads();
         const int np = nA * nB;
@@ -329,8 +342,16 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
           if (p < np) {
             ia = p / nB;
             ib = p - ia * nB;
-            v = ls_eval<float>(c, ax[ia], ay[ia], az[ia], ar[ia], as_[ia], aec[ia] != 0, bx[ib], by[ib],
-                               bz[ib], br[ib], bs[ib], bec[ib] != 0, kGuardWindow, z0, dphi);
+            // azimuth quick reject: |dphi| >= |sin dphi| = |p1 x p2| / (r1 r2), against an upper
+            // bound of the window (alpha difference + resolution and d0 terms with 1/r1 + 1/r2)
+            const float cr = ax[ia] * by[ib] - ay[ia] * bx[ib];
+            const float r1 = ar[ia], r2 = br[ib];
+            const float inv = 1.0f / r1 + 1.0f / r2;
+            const float bup = (bal[ib] - aal[ia]) + c.n_sigma * c.sigma_rphi * inv + c.d0_max * inv + 1e-5f;
+            if (fabsf(cr) > r1 * r2 * bup * 1.0001f + 1e-6f) v = kReject;
+            else
+              v = ls_eval<float>(c, ax[ia], ay[ia], az[ia], r1, as_[ia], aec[ia] != 0, bx[ib], by[ib], bz[ib], r2,
+                                 bs[ib], bec[ib] != 0, kGuardWindow, z0, dphi);
           }
           const int slot = warp_agg_slot(v == kAccept, &w.ls_cnt[vm]);
           if (slot >= 0 && slot < cap && (int64_t)base + slot < w.cap.ls_slots) {
@@ -388,10 +409,13 @@ __global__ void k_ls_dense(Ws w) {
     const int a = w.lss_in[s], b = w.lss_out[s];
     w.ls_in[d] = a;
     w.ls_out[d] = b;
-    const double x1 = w.md_x[a], y1 = w.md_y[a], z1 = w.md_z[a];
-    const double x2 = w.md_x[b], y2 = w.md_y[b], z2 = w.md_z[b];
-    const double r1 = sqrt(x1 * x1 + y1 * y1), r2 = sqrt(x2 * x2 + y2 * y2);
-    w.ls_z0[d] = (float)((z1 * r2 - z2 * r1) / (r2 - r1));
+    // z0 = (z1 r2 - z2 r1) / (r2 - r1) with the radii in float-float: the float32 rounding of the
+    // radii would be amplified up to ~20x for endcap pairs
+    const float z1 = w.md_z[a], z2 = w.md_z[b];
+    const float r1 = w.md_r[a], r1l = w.md_rlo[a], r2 = w.md_r[b], r2l = w.md_rlo[b];
+    const float num = diff_prod(z1, r2, z2, r1) + (z1 * r2l - z2 * r1l);
+    const float den = (r2 - r1) + (r2l - r1l);
+    w.ls_z0[d] = num / den;
     w.ls_dphi[d] = w.lss_dphi[s];
   }
 }

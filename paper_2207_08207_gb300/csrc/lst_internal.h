@@ -79,6 +79,8 @@ struct Ws {
   int32_t *mdlo_cnt = nullptr, *mdlo_cur = nullptr, *mdlo_off = nullptr;   // MDs grouped by lower hit
   int32_t *md_lo = nullptr, *md_up = nullptr, *md_vm = nullptr;
   float *md_x = nullptr, *md_y = nullptr, *md_z = nullptr, *md_r = nullptr, *md_sthr = nullptr;
+  float *md_rlo = nullptr;     // r = md_r + md_rlo to ~1e-14 relative (float-float)
+  float *md_alpha = nullptr;   // alpha_thr(r) = asin(min(r k / (2 pT_thr), sin_max)), float32
   float *md_dpc = nullptr, *md_pte = nullptr;
   uint8_t* md_ec = nullptr;
   // LS

@@ -161,14 +161,22 @@ __global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjA
           obj = st + (cidx - ex0);
           float xy = 0.f, rz = 0.f;
           keep = true;
-          // xy residuals first (they reject most candidates), anchors loaded as needed
+          // xy residuals first (they reject most candidates), anchors loaded as needed. With
+          // A = rho/2 |u|^2 - u.n the residual is 2A / (1 + sqrt(1 + 2 rho A)), whose size is at
+          // least |A| / (1 + |rho A| / 2): a term that exceeds the limit on that bound alone is
+          // rejected without a square root or a division.
 #pragma unroll
           for (int a = 0; a < N; ++a) {
             const float4 h = oa.anc[a * oa.stride + obj];
-            const float dd = seed_dist(s, h.x, h.y);
+            const float ux = h.x - s.x0, uy = h.y - s.y0;
+            const float A = 0.5f * s.rho * (ux * ux + uy * uy) - (ux * s.sp - uy * s.cp);
             const float e1 = h.w * c.pls_dir_err;
             const float e2 = c.pls_pt_err * h.w * h.w * 0.5f * s.akap;
-            xy += dd * dd / (c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2);
+            const float sig2 = c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2;
+            const float g = 1.0f + 0.5f * fabsf(s.rho * A);
+            if (A * A > (lim_xy - xy) * sig2 * g * g) { keep = false; break; }
+            const float dd = 2.0f * A / (1.0f + sqrtf(1.0f + 2.0f * s.rho * A));
+            xy += dd * dd / sig2;
             if (xy > lim_xy) { keep = false; break; }
           }
           if (keep) {
@@ -539,33 +547,64 @@ __device__ __forceinline__ int hit_key_cmp(const int* a, const int* b) {
   return 0;
 }
 
+// accepted candidates of each event and type (block per event)
+__global__ void k_tc_count(Ws w, Geo g) {
+  __shared__ int ty[4];
+  const int e = blockIdx.x;
+  if (threadIdx.x < 4) ty[threadIdx.x] = 0;
+  __syncthreads();
+  const int p0 = w.ev_pls_off[e], p1 = w.ev_pls_off[e + 1];
+  const int t0 = w.t5_off[e * g.n_mods], t1 = w.t5_off[(e + 1) * g.n_mods];
+  int c[4] = {0, 0, 0, 0};
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    c[TC_PT5] += w.best5[p] >= 0;
+    c[TC_PT3] += w.acc3[p];
+    c[TC_PLS] += w.accl[p];
+  }
+  for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x) c[TC_T5] += w.acc5t[i];
+  for (int t = 0; t < 4; ++t)
+    if (c[t]) atomicAdd(&ty[t], c[t]);
+  __syncthreads();
+  if (threadIdx.x < 4) w.ev_stat[e * kEvWords + 7 + threadIdx.x] = ty[threadIdx.x];
+  if (threadIdx.x == 0) w.tc_cnt[e] = ty[0] + ty[1] + ty[2] + ty[3];
+}
+
+// Assembly of one (event, type): collect the accepted candidates, sort them by their sorted hit
+// tuple, write the rows. The sort is a bitonic sort of 64-bit prefix keys (smallest hit) in shared
+// memory followed by an exact ordering of equal-prefix runs; rows of type t start after the event's
+// rows of the types before it.
 __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
   extern __shared__ unsigned char smem_raw[];
   unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem_raw);
   int* sidx = reinterpret_cast<int*>(skey + kTcSortMax);
   __shared__ int n_sh;
-  const int e = blockIdx.x;
+  const int e = blockIdx.x, type = blockIdx.y;
   if (e >= w.E) return;
   const int p0 = w.ev_pls_off[e], p1 = w.ev_pls_off[e + 1];
   const int t0 = w.t5_off[e * g.n_mods], t1 = w.t5_off[(e + 1) * g.n_mods];
-  const int region = p0 + t0;
+  int before = 0;
+  for (int t = 0; t < type; ++t) before += w.ev_stat[e * kEvWords + 7 + t];
+  const int region = p0 + t0 + before;
   int* code = w.tc_code + region;
   unsigned long long* key = w.tc_key + region;
   int* hk = w.tc_hit_key + (int64_t)region * 14;
   if (threadIdx.x == 0) n_sh = 0;
   __syncthreads();
-  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    if (w.best5[p] >= 0) code[atomicAdd(&n_sh, 1)] = (TC_PT5 << 29) | p;
-    if (w.acc3[p]) code[atomicAdd(&n_sh, 1)] = (TC_PT3 << 29) | p;
-    if (w.accl[p]) code[atomicAdd(&n_sh, 1)] = (TC_PLS << 29) | p;
+  if (type == TC_T5) {
+    for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x)
+      if (w.acc5t[i]) code[atomicAdd(&n_sh, 1)] = (TC_T5 << 29) | i;
+  } else {
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const bool take = type == TC_PT5 ? w.best5[p] >= 0 : (type == TC_PT3 ? w.acc3[p] != 0 : w.accl[p] != 0);
+      if (take) code[atomicAdd(&n_sh, 1)] = (type << 29) | p;
+    }
   }
-  for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x)
-    if (w.acc5t[i]) code[atomicAdd(&n_sh, 1)] = (TC_T5 << 29) | i;
   __syncthreads();
   const int n = n_sh;
+  if (n == 0) return;
   // sorted hit tuples (padded with INT_MAX) and 64-bit prefix keys
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const int type = code[k] >> 29, idx = code[k] & ((1 << 29) - 1);
+    const int idx = code[k] & ((1 << 29) - 1);
     int h[14];
     const int obj = (type == TC_PT5) ? w.best5[idx] : (type == TC_PT3 ? w.best3[idx] : idx);
     const int nh = code_hits(w, type, obj, h);
@@ -619,7 +658,7 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
     }
     __syncthreads();
   }
-  // write rows in order (ranks computed directly when the event does not fit the shared sort)
+  // write rows in order (ranks computed directly when the set does not fit the shared sort)
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     int src, rank;
     if (in_smem) {
@@ -628,14 +667,9 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
     } else {
       src = k;
       rank = 0;
-      const int ts = code[k] >> 29;
-      for (int j = 0; j < n; ++j) {
-        const int tj = code[j] >> 29;
-        const int c = (tj != ts) ? (tj < ts ? -1 : 1) : hit_key_cmp(hk + (int64_t)j * 14, hk + (int64_t)k * 14);
-        rank += c < 0;
-      }
+      for (int j = 0; j < n; ++j) rank += hit_key_cmp(hk + (int64_t)j * 14, hk + (int64_t)k * 14) < 0;
     }
-    const int type = code[src] >> 29, idx = code[src] & ((1 << 29) - 1);
+    const int idx = code[src] & ((1 << 29) - 1);
     const int row = region + rank;
     int h[14];
     int obj, nh;
@@ -662,14 +696,6 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
     w.tc_eta[row] = eta;
     w.tc_phi[row] = phi;
   }
-  if (threadIdx.x == 0) w.tc_cnt[e] = n;
-  // per-type counts of the event (the per-event summary reads them)
-  __shared__ int ty[4];
-  if (threadIdx.x < 4) ty[threadIdx.x] = 0;
-  __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) atomicAdd(&ty[code[k] >> 29], 1);
-  __syncthreads();
-  if (threadIdx.x < 4) w.ev_stat[e * kEvWords + 7 + threadIdx.x] = ty[threadIdx.x];
 }
 
 // track candidates of all events packed densely (event e's rows start at tcd_off[e]), so that the
@@ -758,7 +784,9 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_clean_pls<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, dr2);
   const size_t smem = kTcSortMax * (sizeof(unsigned long long) + sizeof(int));
   KT_BEGIN(L, K_TC_ASSEMBLE);
-  k_tc_assemble<<<w.E, 1024, smem, L.stream>>>(w, g);
+  k_tc_count<<<w.E, 256, 0, L.stream>>>(w, g);
+  LST_LAUNCH(L);
+  k_tc_assemble<<<dim3(w.E, 4), 1024, smem, L.stream>>>(w, g);
   KT_END(L, K_TC_ASSEMBLE);
   scan_exclusive(w.tc_cnt, w.tcd_off, w.E, w.scan_tmp, L);
   k_tc_dense<<<w.E, 256, 0, L.stream>>>(w, g);

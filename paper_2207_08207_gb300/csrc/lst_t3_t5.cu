@@ -72,21 +72,60 @@ __device__ __forceinline__ int t3_eval(const Cst<T>& c, const Anchor<T>& h1, con
   }
 }
 
+// T3 candidates, flattened across each warp: the warp takes 32 inner LS, a warp scan of their
+// outer-LS list lengths turns the (inner, outer) pairs into one index range, and each lane finds
+// its pair's inner LS by a shuffle search. The pT cut is tested first without a square root:
+// k R >= f pT_thr  <=>  4 (u x v)^2 <= kappa_max^2 |u|^2 |v|^2 |v - u|^2.
 __global__ void k_t3_pre(Ws w, Cst<float> c) {
   const int n_ls = w.ls_off[w.V];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ls; i += gridDim.x * blockDim.x) {
-    const int m2 = w.ls_out[i];
-    const int j0 = min(w.lsin_off[m2], n_ls), j1 = min(w.lsin_off[m2 + 1], n_ls);
-    if (j0 == j1) continue;
-    const Anchor<float> h1 = anchor<float>(w, w.ls_in[i]);
-    const Anchor<float> h2 = anchor<float>(w, m2);
-    for (int j = j0; j < j1; ++j) {
-      const Anchor<float> h3 = anchor<float>(w, w.ls_out[j]);
-      Circle3<float> circ;
-      float chi2;
-      const int v = t3_eval<float>(c, h1, h2, h3, circ, chi2);
-      const int q = warp_agg_slot(v != kReject, &w.status[ST_Q_T3]);
-      if (q >= 0 && q < w.cap.q_t3) w.q_t3[q] = make_int2(i, j);
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const float kmax = c.k / (c.f_t3 * c.pt_thr);
+  const float kmax2 = kmax * kmax * (1.0f + 4.0f * kGuardWindow);
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n_ls; base += nwarps * 32) {
+    const int i = base + lane;
+    int j0 = 0, size = 0;
+    if (i < n_ls) {
+      const int m2 = w.ls_out[i];
+      j0 = min(w.lsin_off[m2], n_ls);
+      size = min(w.lsin_off[m2 + 1], n_ls) - j0;
+    }
+    int incl = size;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - size;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int b = 0; b < total; b += 32) {
+      const int cidx = b + lane;
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = lo + step;
+        if (__shfl_sync(0xffffffffu, excl, cand) <= cidx) lo = cand;
+      }
+      const int jj = __shfl_sync(0xffffffffu, j0, lo) + (cidx - __shfl_sync(0xffffffffu, excl, lo));
+      const int ii = base + lo;
+      bool keep = false;
+      if (cidx < total) {
+        const int d1 = w.ls_in[ii], d2 = w.ls_out[ii], d3 = w.ls_out[jj];
+        const float x1 = w.md_x[d1], y1 = w.md_y[d1];
+        const float ux = w.md_x[d2] - x1, uy = w.md_y[d2] - y1;
+        const float vx = w.md_x[d3] - x1, vy = w.md_y[d3] - y1;
+        const float cr = diff_prod(ux, vy, uy, vx);
+        const float wx = vx - ux, wy = vy - uy;
+        const float prod = (ux * ux + uy * uy) * (vx * vx + vy * vy) * (wx * wx + wy * wy);
+        if (!(4.0f * cr * cr > kmax2 * prod)) {
+          Circle3<float> circ;
+          float chi2;
+          keep = t3_eval<float>(c, anchor<float>(w, d1), anchor<float>(w, d2), anchor<float>(w, d3), circ, chi2) !=
+                 kReject;
+        }
+      }
+      const int q = warp_agg_slot(keep, &w.status[ST_Q_T3]);
+      if (q >= 0 && q < w.cap.q_t3) w.q_t3[q] = make_int2(ii, jj);
     }
   }
 }
@@ -373,7 +412,7 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.t3_base, w.t3_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T3_PRE);
-  k_t3_pre<<<152 * 8, 256, 0, L.stream>>>(w, c.f);
+  k_t3_pre<<<L.n_sm * 8, 256, 0, L.stream>>>(w, c.f);
   KT_END(L, K_T3_PRE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T3_DECIDE);
