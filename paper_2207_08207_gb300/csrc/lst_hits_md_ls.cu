@@ -209,8 +209,6 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
 // ---------------------------------------------------------------------------------------------
 // Line Segments
 // ---------------------------------------------------------------------------------------------
-constexpr int kLsA = 32;           // inner MDs staged per chunk
-constexpr int kLsB = 384;          // outer MDs staged per chunk
 constexpr int kMaxTargets = 256;   // module-map degree limit (checked when loading the geometry)
 
 __device__ __forceinline__ int md_count(const Ws& w, int vm) { return w.md_off[vm + 1] - w.md_off[vm]; }
@@ -263,112 +261,221 @@ __global__ void k_ls_work_fill(Ws w) {
   }
 }
 
-// One block per module at a time: stage the module's MDs (A) and all MDs of its connected modules
-// (B) in shared memory, then evaluate every (a, b) pair across the block. Persistent mode: the grid
-// is sized to the GPU and blocks pull modules from the cost-ordered work list; otherwise a
-// grid-stride loop over all modules.
-__global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persistent) {
-  __shared__ float ax[kLsA], ay[kLsA], az[kLsA], ar[kLsA], as_[kLsA], aal[kLsA];
-  __shared__ int aid[kLsA];
-  __shared__ uint8_t aec[kLsA];
-  __shared__ float bx[kLsB], by[kLsB], bz[kLsB], br[kLsB], bs[kLsB], bal[kLsB];
-  __shared__ int bid[kLsB];
-  __shared__ uint8_t bec[kLsB];
-  __shared__ int tpre[kMaxTargets + 1];
-  __shared__ int tbase[kMaxTargets];
-  __shared__ int s_item;
-  const int tid = threadIdx.x;
-  const int n_items = persistent ? w.work_off[32] : w.V;
-  for (int it = blockIdx.x;; it += gridDim.x) {
-    int vm;
-    if (persistent) {
-      if (tid == 0) s_item = atomicAdd(w.work_ctr, 1);
-      __syncthreads();
-      const int item = s_item;
-      __syncthreads();
-      if (item >= n_items) break;
-      vm = w.work[item];
-    } else {
-      if (it >= n_items) break;
-      vm = it;
+// One warp per module at a time. Each lane holds one MD of the connected modules (B) in registers
+// and sweeps the module's own MDs (A, staged in shared memory): a conservative division-free test
+// (below) rejects most pairs, and the survivors go to a per-warp queue that carries over from module
+// to module; whenever it holds 32 pairs, every lane takes one of them through the full evaluation, so
+// the expensive path runs with a full warp. Persistent mode: the grid holds every resident warp and
+// the warps take the cost-ordered work list in a boustrophedon order (heaviest modules first, one
+// pass forward and the next backward, which evens out the sums); otherwise warps stride over all
+// modules in index order.
+constexpr int kLsAW = 32;   // inner MDs staged per chunk
+constexpr int kLsQ = 64;    // survivor queue per warp (at most 31 carried + 32 new)
+
+struct LsWarpSmem {
+  int tpre[kMaxTargets + 1];   // prefix of the MD counts of the connected modules
+  int tbase[kMaxTargets];      // their first dense MD
+  uint8_t tec[kMaxTargets];    // their endcap flag
+  float4 a_xyzr[kLsAW];
+  float2 a_sal[kLsAW];         // (arc length at threshold, alpha)
+  int a_id[kLsAW];
+  int q_vm[kLsQ], q_a[kLsQ], q_b[kLsQ];
+};
+
+// Quick rejection of an (a, b) pair, exact-safe: it returns true only when the float64 evaluation
+// is certain to reject, with margins far above the float32 rounding of the anchors and of this
+// arithmetic.
+//  azimuth: |dphi| >= |sin dphi| = |p1 x p2| / (r1 r2), against r1 r2 times an upper bound of the
+//    window, (alpha2 - alpha1) + (n_sigma sigma_rphi + d0_max)(1/r1 + 1/r2), multiplied out;
+//  r-z: with D = r2 - r1, z0r = (z1 r2 - z2 r1) / D and z0s the same with the arc lengths s, the
+//    window L = z_lum + n_sigma sqrt(q1^2 + .. + q4^2) has D^2 L <= D^2 z_lum + n_sigma (|D| (r2 sz1
+//    + r1 sz2) + |z1 - z2| (r2 sr1 + r1 sr2)), since |q3| D^2 = r2 |z1 - z2| sr1 and |q4| D^2 =
+//    r1 |z1 - z2| sr2; both z0r and z0s beyond that bound on the same side rejects. Applied only when
+//    |D| >= 1 and |s2 - s1| >= |D| (always so for r below 2 R_thr), where float32 z0 is accurate.
+__device__ __forceinline__ bool ls_quick_reject(const Cst<float>& c, float4 a, float2 as, float sz1, float sr1,
+                                                float x2, float y2, float z2, float r2, float s2, float al2,
+                                                float sz2, float sr2) {
+  const float r1 = a.w;
+  const float cr = fmaf(a.x, y2, -a.y * x2);
+  const float win = fmaf(r1 * r2, (al2 - as.y) + 1e-5f, (c.n_sigma * c.sigma_rphi + c.d0_max) * (r1 + r2));
+  if (fabsf(cr) > fmaf(win, 1.0003f, 1e-6f)) return true;
+  const float D = r2 - r1, Ds = s2 - as.x;
+  const float aD = fabsf(D);
+  if (!(aD >= 1.0f && fabsf(Ds) >= aD)) return false;
+  const float dz = fabsf(a.z - z2);
+  const float ld2 = fmaf(D * D, c.z_lum,
+                         c.n_sigma * fmaf(aD, fmaf(r2, sz1, r1 * sz2), dz * fmaf(r2, sr1, r1 * sr2)));
+  const float E = (fabsf(a.z) + fabsf(z2)) * (as.x + s2);        // bounds |z1 r2| + |z2 r1| (s >= r)
+  const float M = fmaf(ld2, 1.0f + 1.0f / 1024.0f, E * aD * (1.0f / 262144.0f));
+  const float P = fmaf(a.z, r2, -z2 * r1) * D;                   // z0r D^2
+  const float Ps = fmaf(a.z, s2, -z2 * as.x) * Ds * (D * D);     // z0s Ds^2 D^2
+  const float Ms = M * (Ds * Ds);
+  return (P > M && Ps > Ms) || (P < -M && Ps < -Ms);
+}
+
+// warp-aggregated slot reservation where lanes may target different counters (counters[key])
+__device__ __forceinline__ int warp_agg_slot_keyed(bool pred, int key, int* counters) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  int slot = -1;
+  if (pred) {
+    const unsigned grp = __match_any_sync(m, key);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane_id() == leader) base = atomicAdd(&counters[key], __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    slot = base + __popc(grp & ((1u << lane_id()) - 1u));
+  }
+  return slot;
+}
+
+// full float32 evaluation of the first n (<= 32) queued pairs, one per lane; called by the whole warp
+__device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const LsWarpSmem& S, int n) {
+  const int lane = lane_id();
+  int v = kReject, vm = 0, a = 0, b = 0;
+  float z0 = 0.f, dphi = 0.f;
+  if (lane < n) {
+    vm = S.q_vm[lane];
+    a = S.q_a[lane];
+    b = S.q_b[lane];
+    v = ls_eval<float>(c, w.md_x[a], w.md_y[a], w.md_z[a], w.md_r[a], w.md_sthr[a], w.md_ec[a] != 0, w.md_x[b],
+                       w.md_y[b], w.md_z[b], w.md_r[b], w.md_sthr[b], w.md_ec[b] != 0, kGuardWindow, z0, dphi);
+  }
+  const int slot = warp_agg_slot_keyed(v == kAccept, vm, w.ls_cnt);
+  if (slot >= 0) {
+    const int cap = w.ls_cap[vm], base = w.ls_base[vm];
+    if (slot < cap && (int64_t)base + slot < w.cap.ls_slots) {
+      w.lss_in[base + slot] = a;
+      w.lss_out[base + slot] = b;
+      w.lss_z0[base + slot] = z0;
+      w.lss_dphi[base + slot] = dphi;
     }
+  }
+  const int q = warp_agg_slot(v == kUnsure, &w.status[ST_Q_LS]);
+  if (q >= 0 && q < w.cap.q_ls) w.q_ls[q] = make_int4(vm, a, b, 0);
+}
+
+__global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persistent) {
+  extern __shared__ __align__(16) unsigned char ls_smem[];
+  LsWarpSmem& S = reinterpret_cast<LsWarpSmem*>(ls_smem)[threadIdx.x >> 5];
+  const int lane = lane_id();
+  const int n_warps = gridDim.x * (blockDim.x >> 5);
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int n_items = persistent ? w.work_off[32] : w.V;
+  int qn = 0;   // pairs waiting in this warp's queue
+  for (int round = 0; (int64_t)round * n_warps < n_items; ++round) {
+    const int item = round * n_warps + ((round & 1) ? n_warps - 1 - gw : gw);
+    if (item >= n_items) continue;
+    const int vm = persistent ? w.work[item] : item;
     const int na = md_count(w, vm);
     if (na == 0) continue;
     const int m = vm % g.n_mods, e0 = vm - m;
     const int t0 = g.conn_off[m];
     const int nt = min(g.conn_off[m + 1] - t0, kMaxTargets);
-    for (int t = tid; t < nt; t += blockDim.x) {
-      const int vb = e0 + g.conn_tgt[t0 + t];
-      tbase[t] = w.md_off[vb];
-      tpre[t + 1] = md_count(w, vb);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      tpre[0] = 0;
-      for (int t = 0; t < nt; ++t) tpre[t + 1] += tpre[t];
-    }
-    __syncthreads();
-    const int totB = tpre[nt];
-    const int cap = w.ls_cap[vm], base = w.ls_base[vm];
-    const int a_begin = w.md_off[vm];
-    for (int a0 = 0; totB > 0 && a0 < na; a0 += kLsA) {
-      const int nA = min(kLsA, na - a0);
-      if (tid < nA) {
-        const int d = a_begin + a0 + tid;
-        ax[tid] = w.md_x[d]; ay[tid] = w.md_y[d]; az[tid] = w.md_z[d];
-        ar[tid] = w.md_r[d]; as_[tid] = w.md_sthr[d]; aec[tid] = w.md_ec[d]; aid[tid] = d;
-        aal[tid] = w.md_alpha[d];
+    // target prefix by a warp scan, 32 targets at a time
+    int run = 0;
+    for (int t = lane; t - lane < nt; t += 32) {
+      int cnt = 0;
+      if (t < nt) {
+        const int tm = g.conn_tgt[t0 + t];
+        const int vb = e0 + tm;
+        cnt = md_count(w, vb);
+        S.tbase[t] = w.md_off[vb];
+        S.tec[t] = g.endcap[tm];
       }
-      for (int b0 = 0; b0 < totB; b0 += kLsB) {
-        const int nB = min(kLsB, totB - b0);
-        for (int j = tid; j < nB; j += blockDim.x) {
-          const int gj = b0 + j;
-          int lo = 0, hi = nt;   // target k with tpre[k] <= gj < tpre[k+1]
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (t < nt) S.tpre[t + 1] = run + incl;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) S.tpre[0] = 0;
+    const int totB = run;
+    if (totB == 0) {
+      __syncwarp();
+      continue;
+    }
+    const bool aec = g.endcap[m] != 0;
+    const float sz1 = aec ? 0.f : c.sigma_z, sr1 = aec ? c.sigma_r : 0.f;
+    const int a_begin = w.md_off[vm];
+    for (int a0 = 0; a0 < na; a0 += kLsAW) {
+      const int nA = min(kLsAW, na - a0);
+      __syncwarp();
+      if (lane < nA) {
+        const int d = a_begin + a0 + lane;
+        S.a_xyzr[lane] = make_float4(w.md_x[d], w.md_y[d], w.md_z[d], w.md_r[d]);
+        S.a_sal[lane] = make_float2(w.md_sthr[d], w.md_alpha[d]);
+        S.a_id[lane] = d;
+      }
+      __syncwarp();
+      for (int j0 = 0; j0 < totB; j0 += 32) {
+        const int j = j0 + lane;
+        const bool has_b = j < totB;
+        float x2 = 0.f, y2 = 0.f, z2 = 0.f, r2 = 1.f, s2 = 1.f, al2 = 0.f, sz2 = 0.f, sr2 = 0.f;
+        int bid = 0;
+        if (has_b) {
+          int lo = 0, hi = nt;   // target k with tpre[k] <= j < tpre[k + 1]
           while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (tpre[mid] <= gj) lo = mid; else hi = mid;
+            if (S.tpre[mid] <= j) lo = mid; else hi = mid;
           }
-          const int d = tbase[lo] + (gj - tpre[lo]);
-          bx[j] = w.md_x[d]; by[j] = w.md_y[d]; bz[j] = w.md_z[d];
-          br[j] = w.md_r[d]; bs[j] = w.md_sthr[d]; bec[j] = w.md_ec[d]; bid[j] = d;
-          bal[j] = w.md_alpha[d];
+          bid = S.tbase[lo] + (j - S.tpre[lo]);
+          x2 = w.md_x[bid]; y2 = w.md_y[bid]; z2 = w.md_z[bid]; r2 = w.md_r[bid];
+          s2 = w.md_sthr[bid]; al2 = w.md_alpha[bid];
+          const bool bec = S.tec[lo] != 0;
+          sz2 = bec ? 0.f : c.sigma_z;
+          sr2 = bec ? c.sigma_r : 0.f;
         }
-        __syncthreads();
-        const int np = nA * nB;
-        for (int p0 = 0; p0 < np; p0 += blockDim.x) {
-          const int p = p0 + tid;
-          int v = kReject, ia = 0, ib = 0;
-          float z0 = 0.f, dphi = 0.f;
-          if (p < np) {
-            ia = p / nB;
-            ib = p - ia * nB;
-            // azimuth quick reject: |dphi| >= |sin dphi| = |p1 x p2| / (r1 r2), against an upper
-            // bound of the window (alpha difference + resolution and d0 terms with 1/r1 + 1/r2)
-            const float cr = ax[ia] * by[ib] - ay[ia] * bx[ib];
-            const float r1 = ar[ia], r2 = br[ib];
-            const float inv = 1.0f / r1 + 1.0f / r2;
-            const float bup = (bal[ib] - aal[ia]) + c.n_sigma * c.sigma_rphi * inv + c.d0_max * inv + 1e-5f;
-            if (fabsf(cr) > r1 * r2 * bup * 1.0001f + 1e-6f) v = kReject;
-            else
-              v = ls_eval<float>(c, ax[ia], ay[ia], az[ia], r1, as_[ia], aec[ia] != 0, bx[ib], by[ib], bz[ib], r2,
-                                 bs[ib], bec[ib] != 0, kGuardWindow, z0, dphi);
+        for (int ia = 0; ia < nA; ++ia) {
+          const bool keep = has_b && !ls_quick_reject(c, S.a_xyzr[ia], S.a_sal[ia], sz1, sr1, x2, y2, z2, r2,
+                                                      s2, al2, sz2, sr2);
+          const unsigned km = __ballot_sync(0xffffffffu, keep);
+          if (km == 0) continue;
+          if (keep) {
+            const int pos = qn + __popc(km & ((1u << lane) - 1u));
+            S.q_vm[pos] = vm;
+            S.q_a[pos] = S.a_id[ia];
+            S.q_b[pos] = bid;
           }
-          const int slot = warp_agg_slot(v == kAccept, &w.ls_cnt[vm]);
-          if (slot >= 0 && slot < cap && (int64_t)base + slot < w.cap.ls_slots) {
-            w.lss_in[base + slot] = aid[ia];
-            w.lss_out[base + slot] = bid[ib];
-            w.lss_z0[base + slot] = z0;
-            w.lss_dphi[base + slot] = dphi;
+          qn += __popc(km);
+          if (qn >= 32) {
+            __syncwarp();
+            ls_flush(w, c, S, 32);
+            __syncwarp();
+            qn -= 32;
+            if (lane < qn) {   // move the rest (at most 31) to the front
+              const int t_vm = S.q_vm[32 + lane], t_a = S.q_a[32 + lane], t_b = S.q_b[32 + lane];
+              S.q_vm[lane] = t_vm;
+              S.q_a[lane] = t_a;
+              S.q_b[lane] = t_b;
+            }
+            __syncwarp();
           }
-          const int q = warp_agg_slot(v == kUnsure, &w.status[ST_Q_LS]);
-          if (q >= 0 && q < w.cap.q_ls) w.q_ls[q] = make_int4(vm, aid[ia], bid[ib], 0);
         }
-        __syncthreads();
       }
     }
-    __syncthreads();   // tpre / tbase are rewritten for the next module
   }
+  __syncwarp();
+  if (qn > 0) ls_flush(w, c, S, qn);
 }
+
+// dynamic shared memory of k_ls for a block of `block` threads
+inline size_t ls_smem_bytes(int block) { return sizeof(LsWarpSmem) * (size_t)(block / 32); }
+
+}  // namespace
+
+int ls_resident_blocks(int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ls, block, ls_smem_bytes(block)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+namespace {
 
 __device__ __forceinline__ void md_anchor64(const Ws& w, const Cst<double>& c, int d, double& x,
                                             double& y, double& z, double& r, double& s) {
@@ -515,8 +622,17 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
     *L.launches += 2;
   }
   KT_BEGIN(L, K_LS);
-  if (L.persistent) k_ls<<<L.n_sm * (2048 / L.block_ls), L.block_ls, 0, L.stream>>>(w, g, c.f, 1);
-  else k_ls<<<grid_for(w.V, 1, 152 * 16), L.block_ls, 0, L.stream>>>(w, g, c.f, 0);
+  {
+    const size_t smem = ls_smem_bytes(L.block_ls);
+    const int warps = L.block_ls / 32;
+    if (L.persistent) {
+      // every resident warp, no more: the boustrophedon assignment is static
+      const int bps = L.ls_blocks_per_sm > 0 ? L.ls_blocks_per_sm : 1;
+      k_ls<<<L.n_sm * bps, L.block_ls, smem, L.stream>>>(w, g, c.f, 1);
+    } else {
+      k_ls<<<grid_for((w.V + warps - 1) / warps, 1, 152 * 16), L.block_ls, smem, L.stream>>>(w, g, c.f, 0);
+    }
+  }
   KT_END(L, K_LS);
   LST_LAUNCH(L);
   k_ls_recheck<<<grid_for(w.cap.q_ls, 128, 152 * 4), 128, 0, L.stream>>>(w, c.d);

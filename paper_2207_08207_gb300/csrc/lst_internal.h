@@ -113,6 +113,9 @@ struct Ws {
   int32_t *t5in_cnt = nullptr, *t5in_cur = nullptr, *t5in_off = nullptr;   // T5 grouped by inner T3
   float4* t5_anc = nullptr;      // [5][t5_dense]
   uint8_t* t5_ecm = nullptr;
+  // per module: lo[vm], hi[V + vm] = bounding box (x, y, z, r) of the first anchors of its T3 / T5
+  float4* box3 = nullptr;
+  float4* box5 = nullptr;
   // pixel seeds and pT3 / pT5: passing objects are appended, then grouped by seed
   int32_t* pls_bin = nullptr;
   int32_t *p3a_pls = nullptr, *p3a_obj = nullptr;
@@ -173,6 +176,7 @@ struct Launch {
   int warps_px = 4;
   bool persistent = false;
   int n_sm = 152;
+  int ls_blocks_per_sm = 0;        // resident blocks of the Line-Segment kernel (0: not queried)
   long long* launches = nullptr;   // host counter
   cudaEvent_t* kev = nullptr;      // when set: [2 * kernel id] start / end events of timed kernels
 };
@@ -188,6 +192,9 @@ enum KernelId : int {
   if ((L).kev) cudaEventRecordWithFlags((L).kev[2 * (id)], (L).stream, cudaEventRecordExternal)
 #define KT_END(L, id) \
   if ((L).kev) cudaEventRecordWithFlags((L).kev[2 * (id) + 1], (L).stream, cudaEventRecordExternal)
+
+// resident blocks per SM of the Line-Segment kernel at `block` threads (0 when the query fails)
+int ls_resident_blocks(int block);
 
 // scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);

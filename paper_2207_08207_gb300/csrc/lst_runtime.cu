@@ -206,6 +206,7 @@ struct lst_ctx {
   // instrumentation
   long long launches = 0;
   int n_sm = 152;
+  int ls_bps = 0;
   // CUDA graph of the whole chain for the current arenas (shape-independent within capacities)
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_nodes = 0;
@@ -278,6 +279,7 @@ Launch make_launch(lst_ctx* ctx) {
   L.persistent = ctx->cfg.persistent != 0;
   L.launches = &ctx->launches;
   L.n_sm = ctx->n_sm;
+  L.ls_blocks_per_sm = ctx->ls_bps;
   L.kev = ctx->timing ? ctx->ev_kern : nullptr;
   return L;
 }
@@ -420,6 +422,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.t5_a, c.t5_dense); pl.add(w.t5_b, c.t5_dense); pl.add(w.t5_md, 5 * c.t5_dense); pl.add(w.t5_f, 8 * c.t5_dense);
   pl.add(w.t5_anc, 5 * c.t5_dense); pl.add(w.t5_ecm, c.t5_dense);
   pl.add(w.t5_kept, c.t5_dense); pl.add(w.acc5t, c.t5_dense);
+  pl.add(w.box3, 2 * V); pl.add(w.box5, 2 * V);
   // pixel
   pl.add(w.pls_bin, c.P);
   pl.add(w.p3a_pls, c.p3_slots); pl.add(w.p3a_obj, c.p3_slots); pl.add(w.p3a_xy, c.p3_slots);
@@ -646,6 +649,7 @@ int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
   ctx->stream = ctx->own_stream;
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
   if (ctx->n_sm <= 0) ctx->n_sm = 152;
+  ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls);
   tc_configure();
   *out = ctx;
   return LST_OK;
