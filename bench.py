@@ -110,6 +110,27 @@ def serving_run(det, events, rate, n_requests, n_engines, max_batch, seed=0):
     return d
 
 
+def rank_seed0(rank):
+    """First event seed of a rank: ranks draw disjoint events (seeds 1000 rank + e, e < 1000)."""
+    return 1000 * rank
+
+
+def max_over_ranks(t_local, world, device):
+    """The slowest rank's timed-region length (seconds): all-reduce MAX, then a barrier."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    return float(t.item())
+
+
+def whole_job_rate(events_per_step, steps, world, t_max):
+    """Whole-job throughput: the events all ranks processed over the slowest rank's time."""
+    return events_per_step * steps * world / t_max
+
+
 def make_events(n, seed0=0):
     from paper_2207_08207_gb300 import gen
     det = gen.make_detector(barrel_only=False, pt_thr=0.8)
@@ -192,7 +213,7 @@ def main():
 
     B = args.batch
     # every rank processes its own events (events are independent: no collective on the data path)
-    det, evs = make_events(B, seed0=1000 * rank)
+    det, evs = make_events(B, seed0=rank_seed0(rank))
     # inputs resident in HBM
     dev = [to_device(ev, torch) for ev in evs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -238,12 +259,8 @@ def main():
     launches = ctx.launch_count() - launches0
     ctx.set_timing(False)
     t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    t_max = float(t.item())
-    value = B * args.steps * world / t_max
+    t_max = max_over_ranks(t_local, world, "cuda")
+    value = whole_job_rate(B, args.steps, world, t_max)
     counts = [ctx.counts(e) for e in range(B)]
 
     # roofline of the dominant kernel (algorithmic bytes per launch / average duration)

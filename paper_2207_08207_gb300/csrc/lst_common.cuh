@@ -8,14 +8,16 @@
 // hit-coordinate differences, an asin-difference identity). Candidates inside the band are queued
 // and decided again in float64. The chi2 cuts (T3, T5, pT3, pT5), whose residuals are tiny
 // differences of coordinates of order 100 cm, use float32 only as a conservative pre-filter; every
-// candidate that survives it is decided, and its stored floats computed, in float64. The float64
-// decisions agree with an exact evaluation of the cut definitions except within ~1e-12 relative
-// of a threshold.
+// candidate that survives it is decided, and its stored floats computed, in double-float
+// arithmetic (pairs of floats, ~48 bits, lst_ff.cuh), which runs on the float32 pipes: on GB300
+// float64 issues at a small fraction of the float32 rate. The decisions agree with an exact
+// evaluation of the cut definitions except within ~1e-12 relative of a threshold.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "lst.h"
+#include "lst_ff.cuh"
 
 namespace lst {
 
@@ -44,6 +46,7 @@ struct Cst {
 struct Consts {
   Cst<float> f;
   Cst<double> d;
+  Cst<ff> x;   // the float64 values as double-float pairs
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -121,9 +124,23 @@ struct Acc64 {
   __device__ __forceinline__ int verdict() const { return fail ? kReject : kAccept; }
 };
 
+// double-float evaluation: the decision, as in float64 (NaN fails)
+struct AccFF {
+  bool fail = false;
+  __device__ explicit AccFF(ff = ff(0.0f)) {}
+  __device__ __forceinline__ void cut(ff bound, ff value) {
+    if (!(value <= bound)) fail = true;
+  }
+  __device__ __forceinline__ void cut_ge(ff bound, ff value) { cut(-bound, -value); }
+  __device__ __forceinline__ void force_unsure() {}
+  __device__ __forceinline__ void reject() { fail = true; }
+  __device__ __forceinline__ int verdict() const { return fail ? kReject : kAccept; }
+};
+
 template <class T> struct AccOf;
 template <> struct AccOf<float> { using type = Acc32; };
 template <> struct AccOf<double> { using type = Acc64; };
+template <> struct AccOf<ff> { using type = AccFF; };
 
 // ---------------------------------------------------------------------------------------------
 // Mini-Doublet selection (Sec. 2.2). Lower hit l, upper hit u of one module with sensor spacing

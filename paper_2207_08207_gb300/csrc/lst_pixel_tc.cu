@@ -10,6 +10,8 @@
 // (chi2, hit tuple) is dropped); pT3 kept only if no accepted pT5 uses its seed or lies within
 // dR < dr_min; T5 only if no accepted pT5 / pT3 is within dR; pLS only if it is in no pT3 / pT5 and
 // no accepted candidate is within dR. Output ordered by type, then sorted hit tuple.
+#include <type_traits>
+
 #include "lst_internal.h"
 
 namespace lst {
@@ -72,6 +74,9 @@ __device__ __forceinline__ Seed<T> make_seed(const lst_pls& s, const Cst<T>& c) 
   if constexpr (sizeof(T) == 4) {
     sincosf(s.phi, &o.sp, &o.cp);
     o.cot = sinhf(s.eta);
+  } else if constexpr (std::is_same<T, ff>::value) {
+    ff_sincos(s.phi, o.sp, o.cp);
+    o.cot = ff_sinh(s.eta);
   } else {
     sincos((double)s.phi, &o.sp, &o.cp);
     o.cot = sinh((double)s.eta);
@@ -110,12 +115,80 @@ struct ObjAnc {
   int64_t stride;
 };
 
+// bounding box of the first anchors of each module's objects (a warp per module)
+__global__ void k_obj_box(Ws w, const int32_t* obj_off, const float4* anc0, float4* box) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+    const int a = obj_off[vm], b = obj_off[vm + 1];
+    if (a == b) continue;
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+    for (int i = a + lane; i < b; i += 32) {
+      const float4 h = anc0[i];
+      lo.x = fminf(lo.x, h.x); lo.y = fminf(lo.y, h.y); lo.z = fminf(lo.z, h.z); lo.w = fminf(lo.w, h.w);
+      hi.x = fmaxf(hi.x, h.x); hi.y = fmaxf(hi.y, h.y); hi.z = fmaxf(hi.z, h.z); hi.w = fmaxf(hi.w, h.w);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+      lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+      lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+      lo.w = fminf(lo.w, __shfl_xor_sync(0xffffffffu, lo.w, o));
+      hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+      hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+      hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+      hi.w = fmaxf(hi.w, __shfl_xor_sync(0xffffffffu, hi.w, o));
+    }
+    if (lane == 0) {
+      box[vm] = lo;
+      box[w.V + vm] = hi;
+    }
+  }
+}
+
+// Whole-module rejection for a seed, exact-safe: true only when every object of the module has a
+// first-anchor term (alone) above the pre-filter limit, so the chi-square sums are too.
+//  x-y: the signed distance to the seed circle, |p - c| - R, is 1-Lipschitz, so over the anchors'
+//    box it is at least its value at the box centre minus the half diagonal; the resolution term
+//    grows with r and is taken at the box's largest r.
+//  r-z: the predicted z at radius r, z0 + s(r) cot, is monotonic in r, so over the box's r range
+//    it spans the interval between its values at the ends; the gap between that interval and the
+//    box's z range bounds |z - z_pred|, and the variance is taken at its largest (largest s).
+// Margins (1e-3 cm, relative 1e-4, 1/16 on the squared limits) lie far above float32 rounding.
+__device__ __forceinline__ bool seed_box_reject(const Seed<float>& s, const Cst<float>& c, float4 lo, float4 hi,
+                                                bool ec, float lim_xy, float lim_rz) {
+  const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y);
+  const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y);
+  const float h = sqrtf(hx * hx + hy * hy);
+  const float ux = cx - s.x0, uy = cy - s.y0;
+  const float dc = fabsf(seed_dist(s, cx, cy));
+  const float lb = dc - h * 1.0001f - 1e-3f - 1e-4f * (fabsf(ux) + fabsf(uy));
+  if (lb > 0.f) {
+    const float e1 = hi.w * c.pls_dir_err;
+    const float e2 = c.pls_pt_err * hi.w * hi.w * 0.5f * s.akap;
+    const float sig2 = c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2;
+    if (lb * lb > lim_xy * sig2 * 1.0625f) return true;
+  }
+  const float sl = arc_len(s.akap, lo.w), sh = arc_len(s.akap, hi.w);
+  const float za = s.z0 + sl * s.cot, zb = s.z0 + sh * s.cot;
+  const float zmin = fminf(za, zb), zmax = fmaxf(za, zb);
+  const float gap = fmaxf(lo.z - zmax, zmin - hi.z) - 1e-3f -
+                    1e-4f * (fabsf(zmin) + fabsf(zmax) + fabsf(lo.z) + fabsf(hi.z));
+  if (gap > 0.f) {
+    const float sz = ec ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
+    const float th = sh * (1.0f + s.cot * s.cot) * c.pls_dir_err;
+    if (gap * gap > lim_rz * (sz * sz + th * th) * 1.0625f) return true;
+  }
+  return false;
+}
+
 // Candidate pre-filter: one warp per seed; the candidates (objects in every module of the seed's
 // pixel-map row) are flattened across the warp with a shuffle-based search over the per-module
 // object counts.
 template <int N>
-__global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjAnc oa, int2* queue,
-                         int q_word, int64_t q_cap, float cut_xy, float cut_rz) {
+__global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, const float4* box, ObjAnc oa,
+                         int2* queue, int q_word, int64_t q_cap, float cut_xy, float cut_rz) {
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const float lim_xy = cut_xy * (1.0f + kGuardChi2) + kGuardChi2Abs;
@@ -132,9 +205,12 @@ __global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjA
       const int k = t0 + lane;
       int start = 0, size = 0;
       if (k < nt) {
-        const int vmk = e0 + g.pix_tgt[tb + k];
+        const int mk = g.pix_tgt[tb + k];
+        const int vmk = e0 + mk;
         start = obj_off[vmk];
         size = obj_off[vmk + 1] - start;
+        if (size > 0 && seed_box_reject(s, c, box[vmk], box[w.V + vmk], g.endcap[mk] != 0, lim_xy, lim_rz))
+          size = 0;
       }
       int incl = size;
 #pragma unroll
@@ -200,26 +276,28 @@ __global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, ObjA
   }
 }
 
+// decision of the pre-filter's survivors (chi2 sums of the seed's circle and r-z line over the
+// object's anchors), evaluated in double-float: float64-exact outside ~1e-12 of a threshold
 template <int N>
-__global__ void k_pt_decide(Ws w, Cst<double> c, ObjAnc oa, const int2* queue, int q_word, int64_t q_cap,
-                            double cut_xy, double cut_rz, int32_t* a_pls, int32_t* a_obj, float* a_xy,
+__global__ void k_pt_decide(Ws w, Cst<ff> c, ObjAnc oa, const int2* queue, int q_word, int64_t q_cap,
+                            ff cut_xy, ff cut_rz, int32_t* a_pls, int32_t* a_obj, float* a_xy,
                             float* a_rz, float* a_sc, int n_word, int64_t a_cap, int32_t* per_pls) {
   const int n = min((int64_t)w.status[q_word], q_cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int2 q = queue[k];
-    const Seed<double> s = make_seed<double>(w.pls[q.x], c);
-    double xy = 0.0, rz = 0.0;
+    const Seed<ff> s = make_seed<ff>(w.pls[q.x], c);
+    ff xy = ff(0.0f), rz = ff(0.0f);
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       const float4 h = oa.anc[a * oa.stride + q.y];
-      const double x = h.x, y = h.y, z = h.z;
-      const double r = sqrt(x * x + y * y);
-      double t1, t2;
-      seed_terms<double>(s, c, x, y, z, r, ((oa.ecm[q.y] >> a) & 1) != 0, t1, t2);
+      const ff x(h.x), y(h.y), z(h.z);
+      const ff r = m_sqrt(x * x + y * y);
+      ff t1, t2;
+      seed_terms<ff>(s, c, x, y, z, r, ((oa.ecm[q.y] >> a) & 1) != 0, t1, t2);
       xy += t1;
       rz += t2;
     }
-    if (!(cut_xy - xy >= 0.0) || !(cut_rz - rz >= 0.0)) continue;
+    if (!(xy <= cut_xy) || !(rz <= cut_rz)) continue;
     const int slot = atomicAdd(&w.status[n_word], 1);
     if (slot >= a_cap) continue;
     a_pls[slot] = q.x;
@@ -727,26 +805,29 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   ObjAnc om3{w.t3_anc, w.t3_ecm, w.cap.t3_dense};
   ObjAnc om5{w.t5_anc, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
+    k_obj_box<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, w.t3_off, w.t3_anc, w.box3);
+    k_obj_box<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, w.t5_off, w.t5_anc, w.box5);
+    *L.launches += 2;
     KT_BEGIN(L, K_PT3_PRE);
-  k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
+  k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, w.box3, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
                                                    c.f.chi2_pt3_xy, c.f.chi2_pt3_rz);
   KT_END(L, K_PT3_PRE);
     LST_LAUNCH(L);
     KT_BEGIN(L, K_PT5_PRE);
-  k_pt_pre<5><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t5_off, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5,
+  k_pt_pre<5><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t5_off, w.box5, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5,
                                                    c.f.chi2_pt5_xy, c.f.chi2_pt5_rz);
   KT_END(L, K_PT5_PRE);
     LST_LAUNCH(L);
   }
   KT_BEGIN(L, K_PT3_DECIDE);
   k_pt_decide<3><<<grid_for(w.cap.q_p3, 128, 152 * 8), 128, 0, L.stream>>>(
-      w, c.d, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3, c.d.chi2_pt3_xy, c.d.chi2_pt3_rz, w.p3a_pls, w.p3a_obj,
+      w, c.x, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3, c.x.chi2_pt3_xy, c.x.chi2_pt3_rz, w.p3a_pls, w.p3a_obj,
       w.p3a_xy, w.p3a_rz, w.p3a_sc, ST_N_PT3, w.cap.p3_slots, w.p3_cnt);
   KT_END(L, K_PT3_DECIDE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_PT5_DECIDE);
   k_pt_decide<5><<<grid_for(w.cap.q_p5, 128, 152 * 8), 128, 0, L.stream>>>(
-      w, c.d, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5, c.d.chi2_pt5_xy, c.d.chi2_pt5_rz, w.p5a_pls, w.p5a_obj,
+      w, c.x, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5, c.x.chi2_pt5_xy, c.x.chi2_pt5_rz, w.p5a_pls, w.p5a_obj,
       w.p5a_xy, w.p5a_rz, w.p5a_sc, ST_N_PT5, w.cap.p5_slots, w.p5_cnt);
   KT_END(L, K_PT5_DECIDE);
   LST_LAUNCH(L);

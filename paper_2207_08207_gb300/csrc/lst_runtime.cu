@@ -268,6 +268,16 @@ Consts make_consts(const lst_config& c) {
   f.c_rel = (float)d.c_rel; f.c_abs = (float)d.c_abs; f.dr_min = (float)d.dr_min;
   f.pt_cap = (float)d.pt_cap; f.pls_dir_err = (float)d.pls_dir_err; f.pls_pt_err = (float)d.pls_pt_err;
   f.sigma_floor = (float)d.sigma_floor; f.t5_overlap_hits = d.t5_overlap_hits;
+  Cst<ff>& x = k.x;
+  x.k = ff(d.k); x.pt_thr = ff(d.pt_thr); x.sin_max = ff(d.sin_max); x.z_lum = ff(d.z_lum);
+  x.d0_max = ff(d.d0_max); x.n_sigma = ff(d.n_sigma); x.sigma_rphi = ff(d.sigma_rphi);
+  x.sigma_z = ff(d.sigma_z); x.sigma_r = ff(d.sigma_r); x.k2p = ff(d.k2p); x.two_rthr = ff(d.two_rthr);
+  x.tol_rphi = ff(d.tol_rphi); x.tol_z = ff(d.tol_z); x.tol_r = ff(d.tol_r); x.chi2_t3 = ff(d.chi2_t3);
+  x.chi2_t5_c = ff(d.chi2_t5_c); x.chi2_t5_rz = ff(d.chi2_t5_rz); x.chi2_pt3_xy = ff(d.chi2_pt3_xy);
+  x.chi2_pt3_rz = ff(d.chi2_pt3_rz); x.chi2_pt5_xy = ff(d.chi2_pt5_xy); x.chi2_pt5_rz = ff(d.chi2_pt5_rz);
+  x.f_t3 = ff(d.f_t3); x.d0_t3 = ff(d.d0_t3); x.c_rel = ff(d.c_rel); x.c_abs = ff(d.c_abs);
+  x.dr_min = ff(d.dr_min); x.pt_cap = ff(d.pt_cap); x.pls_dir_err = ff(d.pls_dir_err);
+  x.pls_pt_err = ff(d.pls_pt_err); x.sigma_floor = ff(d.sigma_floor); x.t5_overlap_hits = d.t5_overlap_hits;
   return k;
 }
 

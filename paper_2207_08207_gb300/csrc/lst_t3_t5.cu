@@ -8,7 +8,10 @@
 // fit give chi2_c <= chi2_t5_c and chi2_rz <= chi2_t5_rz.
 //
 // Candidates are enumerated in float32 with a conservative pre-filter; the survivors are decided
-// (and their stored floats computed) in float64 from the float32 hit coordinates.
+// (and their stored floats computed) in double-float arithmetic (float64-exact outside ~1e-12 of a
+// threshold) from the float32 hit coordinates.
+#include <type_traits>
+
 #include "lst_internal.h"
 
 namespace lst {
@@ -32,7 +35,7 @@ __device__ __forceinline__ Anchor<T> anchor(const Ws& w, int d) {
   a.y = (T)w.md_y[d];
   a.z = (T)w.md_z[d];
   if constexpr (sizeof(T) == 4) a.r = w.md_r[d];
-  else a.r = sqrt(a.x * a.x + a.y * a.y);
+  else a.r = m_sqrt(a.x * a.x + a.y * a.y);
   a.ec = w.md_ec[d] != 0;
   return a;
 }
@@ -56,7 +59,7 @@ __device__ __forceinline__ int t3_eval(const Cst<T>& c, const Anchor<T>& h1, con
     if (!rz_fit<T, 3>(c, ak, r, z, ec, chi2, slope)) return kAccept;  // decided in float64
     return chi2_clear_fail(chi2, c.chi2_t3) ? kReject : kAccept;
   } else {
-    Acc64 acc;
+    typename AccOf<T>::type acc;
     acc.cut_ge(c.f_t3 * c.pt_thr, c.k * circ.R);
     acc.cut(c.d0_t3, circ.d0);
     const T r[3] = {h1.r, h2.r, h3.r}, z[3] = {h1.z, h2.z, h3.z};
@@ -72,23 +75,67 @@ __device__ __forceinline__ int t3_eval(const Cst<T>& c, const Anchor<T>& h1, con
   }
 }
 
+// Quick rejection of a T3 candidate from its three anchors, exact-safe (true only when the float64
+// selection is certain to reject; margins far above float32 rounding). With u = p2 - p1,
+// v = p3 - p1 and cr = u x v:
+//  pT: k R >= f pT_thr  <=>  4 cr^2 <= kappa_max^2 |u|^2 |v|^2 |v - u|^2 (no square root);
+//  d0: the circle through 0, u, v (frame at p1) has centre c' = N / (2 cr), N = (|u|^2 v_y - |v|^2 u_y,
+//    |v|^2 u_x - |u|^2 v_x), so with c = p1 + c' and R = |c'|, Q = cr (|c|^2 - R^2) = |p1|^2 cr + p1.N
+//    and d0 = ||c| - R| = |Q| / (|cr| (|c| + R)); since |cr| (|c| + R) <= |p1| |cr| + |N|, a |Q| above
+//    d0_t3 (|p1|_1 |cr| + |N|_1) rejects, without a division or a square root.
+__device__ __forceinline__ bool t3_quick_reject(const Cst<float>& c, float kmax2, float x1, float y1, float x2,
+                                                float y2, float x3, float y3) {
+  const float ux = x2 - x1, uy = y2 - y1, vx = x3 - x1, vy = y3 - y1;
+  const float cr = diff_prod(ux, vy, uy, vx);
+  const float uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
+  const float wx = vx - ux, wy = vy - uy;
+  if (4.0f * cr * cr > kmax2 * (uu * vv * (wx * wx + wy * wy))) return true;
+  const float Nx = uu * vy - vv * uy, Ny = vv * ux - uu * vx;
+  const float Q = fmaf(x1 * x1 + y1 * y1, cr, fmaf(x1, Nx, y1 * Ny));
+  const float p1 = fabsf(x1) + fabsf(y1);
+  const float bound = c.d0_t3 * fmaf(p1, fabsf(cr), fabsf(Nx) + fabsf(Ny));
+  return fabsf(Q) > fmaf(bound, 1.001f, 1e-6f * p1 * fabsf(cr));
+}
+
 // T3 candidates, flattened across each warp: the warp takes 32 inner LS, a warp scan of their
 // outer-LS list lengths turns the (inner, outer) pairs into one index range, and each lane finds
-// its pair's inner LS by a shuffle search. The pT cut is tested first without a square root:
-// k R >= f pT_thr  <=>  4 (u x v)^2 <= kappa_max^2 |u|^2 |v|^2 |v - u|^2.
-__global__ void k_t3_pre(Ws w, Cst<float> c) {
+// its pair's inner LS by a shuffle search. Pairs that pass the quick test go to a per-warp queue;
+// whenever it holds 32, the full float32 pre-filter runs on them with every lane busy.
+constexpr int kT3Warps = 8;
+constexpr int kT3Q = 64;
+
+__device__ __forceinline__ void t3_flush(const Ws& w, const Cst<float>& c, const int2* qe, int n) {
+  const int lane = threadIdx.x & 31;
+  bool keep = false;
+  int2 e = make_int2(0, 0);
+  if (lane < n) {
+    e = qe[lane];
+    Circle3<float> circ;
+    float chi2;
+    keep = t3_eval<float>(c, anchor<float>(w, w.ls_in[e.x]), anchor<float>(w, w.ls_out[e.x]),
+                          anchor<float>(w, w.ls_out[e.y]), circ, chi2) != kReject;
+  }
+  const int q = warp_agg_slot(keep, &w.status[ST_Q_T3]);
+  if (q >= 0 && q < w.cap.q_t3) w.q_t3[q] = e;
+}
+
+__global__ void __launch_bounds__(32 * kT3Warps) k_t3_pre(Ws w, Cst<float> c) {
+  __shared__ int2 queue[kT3Warps][kT3Q];
+  int2* qe = queue[threadIdx.x >> 5];
   const int n_ls = w.ls_off[w.V];
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const float kmax = c.k / (c.f_t3 * c.pt_thr);
   const float kmax2 = kmax * kmax * (1.0f + 4.0f * kGuardWindow);
+  int qn = 0;
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n_ls; base += nwarps * 32) {
     const int i = base + lane;
-    int j0 = 0, size = 0;
+    int j0 = 0, size = 0, d1 = 0, d2 = 0;
     if (i < n_ls) {
-      const int m2 = w.ls_out[i];
-      j0 = min(w.lsin_off[m2], n_ls);
-      size = min(w.lsin_off[m2 + 1], n_ls) - j0;
+      d1 = w.ls_in[i];
+      d2 = w.ls_out[i];
+      j0 = min(w.lsin_off[d2], n_ls);
+      size = min(w.lsin_off[d2 + 1], n_ls) - j0;
     }
     int incl = size;
 #pragma unroll
@@ -107,38 +154,38 @@ __global__ void k_t3_pre(Ws w, Cst<float> c) {
         if (__shfl_sync(0xffffffffu, excl, cand) <= cidx) lo = cand;
       }
       const int jj = __shfl_sync(0xffffffffu, j0, lo) + (cidx - __shfl_sync(0xffffffffu, excl, lo));
-      const int ii = base + lo;
+      const int m1 = __shfl_sync(0xffffffffu, d1, lo), m2 = __shfl_sync(0xffffffffu, d2, lo);
       bool keep = false;
       if (cidx < total) {
-        const int d1 = w.ls_in[ii], d2 = w.ls_out[ii], d3 = w.ls_out[jj];
-        const float x1 = w.md_x[d1], y1 = w.md_y[d1];
-        const float ux = w.md_x[d2] - x1, uy = w.md_y[d2] - y1;
-        const float vx = w.md_x[d3] - x1, vy = w.md_y[d3] - y1;
-        const float cr = diff_prod(ux, vy, uy, vx);
-        const float wx = vx - ux, wy = vy - uy;
-        const float prod = (ux * ux + uy * uy) * (vx * vx + vy * vy) * (wx * wx + wy * wy);
-        if (!(4.0f * cr * cr > kmax2 * prod)) {
-          Circle3<float> circ;
-          float chi2;
-          keep = t3_eval<float>(c, anchor<float>(w, d1), anchor<float>(w, d2), anchor<float>(w, d3), circ, chi2) !=
-                 kReject;
-        }
+        const int m3 = w.ls_out[jj];
+        keep = !t3_quick_reject(c, kmax2, w.md_x[m1], w.md_y[m1], w.md_x[m2], w.md_y[m2], w.md_x[m3], w.md_y[m3]);
       }
-      const int q = warp_agg_slot(keep, &w.status[ST_Q_T3]);
-      if (q >= 0 && q < w.cap.q_t3) w.q_t3[q] = make_int2(ii, jj);
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      if (keep) qe[qn + __popc(km & ((1u << lane) - 1u))] = make_int2(base + lo, jj);
+      qn += __popc(km);
+      if (qn >= 32) {
+        __syncwarp();
+        t3_flush(w, c, qe, 32);
+        __syncwarp();
+        qn -= 32;
+        if (lane < qn) qe[lane] = qe[32 + lane];
+        __syncwarp();
+      }
     }
   }
+  __syncwarp();
+  if (qn > 0) t3_flush(w, c, qe, qn);
 }
 
-__global__ void k_t3_decide(Ws w, Cst<double> c) {
+// float64-exact decision of the pre-filter's survivors, evaluated in double-float
+__global__ void k_t3_decide(Ws w, Cst<ff> c) {
   const int n = min((int64_t)w.status[ST_Q_T3], w.cap.q_t3);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int2 q = w.q_t3[k];
     const int md0 = w.ls_in[q.x], md1 = w.ls_out[q.x], md2 = w.ls_out[q.y];
-    Circle3<double> circ;
-    double chi2;
-    const int v = t3_eval<double>(c, anchor<double>(w, md0), anchor<double>(w, md1),
-                                  anchor<double>(w, md2), circ, chi2);
+    Circle3<ff> circ;
+    ff chi2;
+    const int v = t3_eval<ff>(c, anchor<ff>(w, md0), anchor<ff>(w, md1), anchor<ff>(w, md2), circ, chi2);
     if (v != kAccept) continue;
     const int vm = w.md_vm[md0];
     const int slot = atomicAdd(&w.t3_cnt[vm], 1);
@@ -151,7 +198,7 @@ __global__ void k_t3_decide(Ws w, Cst<double> c) {
       w.t3s_xc[s] = (float)circ.xc;
       w.t3s_yc[s] = (float)circ.yc;
       w.t3s_chi2[s] = (float)chi2;
-      w.t3s_pte[s] = (float)fmin(c.k * circ.R, c.pt_cap);
+      w.t3s_pte[s] = (float)m_min(c.k * circ.R, c.pt_cap);
     }
   }
 }
@@ -208,12 +255,12 @@ __global__ void k_t3_dense(Ws w) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Karimaki's circle fit (V. Karimaki, NIM A305 (1991) 187) with equal weights, float64.
+// Karimaki's circle fit (V. Karimaki, NIM A305 (1991) 187) with equal weights.
 // Circle: 1/2 rho (x^2 + y^2) - (1 + rho d)(x sin phi - y cos phi) + 1/2 rho d^2 + d = 0;
 // phi is the direction at the point of closest approach to the origin, oriented first -> last.
 // ---------------------------------------------------------------------------------------------
 template <class T, int N>
-__device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi, T& d) {
+__device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi, T& d, T& sp, T& cp) {
   T mx = 0, my = 0, mxx = 0, mxy = 0, myy = 0, mr2 = 0, mxr = 0, myr = 0, mrr = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -228,17 +275,43 @@ __device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi,
   const T Cxr = mxr - mx * mr2, Cyr = myr - my * mr2, Crr = mrr - mr2 * mr2;
   const T q1 = Crr * Cxy - Cxr * Cyr;
   const T q2 = Crr * (Cxx - Cyy) - Cxr * Cxr + Cyr * Cyr;
-  phi = T(0.5) * m_atan2(T(2) * q1, q2);
-  T sp, cp;
-  if constexpr (sizeof(T) == 4) sincosf(phi, &sp, &cp);
-  else sincos(phi, &sp, &cp);
-  if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
-    phi += T(kPiD);
-    sp = -sp;
-    cp = -cp;
+  if constexpr (std::is_same<T, ff>::value) {
+    // phi = atan2(2 q1, q2) / 2 in (-pi/2, pi/2], so cos phi >= 0: its sine and cosine from the
+    // double angle's, (cos 2phi, sin 2phi) = (q2, 2 q1) / h, by the half-angle formulas, each in
+    // the form free of cancellation; the angle itself (an output only) in float32
+    const ff s2 = ff(2.0f) * q1;
+    const ff h = m_sqrt(s2 * s2 + q2 * q2);
+    if (h.hi == 0.0f) {
+      sp = ff(0.0f);
+      cp = ff(1.0f);
+    } else {
+      const ff c2 = q2 / h, sn2 = s2 / h;
+      if (c2.hi >= 0.0f) {
+        cp = m_sqrt((ff(1.0f) + c2) * ff(0.5f));
+        sp = sn2 / (ff(2.0f) * cp);
+      } else {
+        sp = m_sqrt((ff(1.0f) - c2) * ff(0.5f));
+        if (signbit(sn2.hi)) sp = -sp;
+        cp = sn2 / (ff(2.0f) * sp);
+      }
+    }
+    if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
+      sp = -sp;
+      cp = -cp;
+    }
+    phi = ff(atan2f(sp.hi, cp.hi));
+  } else {
+    phi = T(0.5) * m_atan2(T(2) * q1, q2);
+    if constexpr (sizeof(T) == 4) sincosf(phi, &sp, &cp);
+    else sincos(phi, &sp, &cp);
+    if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
+      phi += T(kPiD);
+      sp = -sp;
+      cp = -cp;
+    }
+    if (phi > T(kPiD)) phi -= T(kTwoPiD);
+    if (phi <= -T(kPiD)) phi += T(kTwoPiD);
   }
-  if (phi > T(kPiD)) phi -= T(kTwoPiD);
-  if (phi <= -T(kPiD)) phi += T(kTwoPiD);
   const T kap = (sp * Cxr - cp * Cyr) / Crr;
   const T del = -kap * mr2 + sp * mx - cp * my;
   const T root = m_sqrt(T(1) - T(4) * del * kap);
@@ -246,13 +319,11 @@ __device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi,
   d = T(2) * del / (T(1) + root);
 }
 
-// sum over the anchors of ((|p - c| - R) / sigma)^2 at the circle (rho, phi, d), each residual in
+// sum over the anchors of ((|p - c| - R) / sigma)^2 at the circle (rho, phi, d) given by rho,
+// (sin phi, cos phi) and d, each residual in
 // the exact cancellation-free form 2 eps / (1 + sqrt(1 + 2 rho eps))
 template <class T, int N>
-__device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T phi, T d, T sigma) {
-  T sp, cp;
-  if constexpr (sizeof(T) == 4) sincosf(phi, &sp, &cp);
-  else sincos(phi, &sp, &cp);
+__device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T cp, T d, T sigma) {
   T chi2 = 0;
 #pragma unroll
   for (int a = 0; a < N; ++a) {
@@ -312,9 +383,9 @@ __global__ void k_t5_pre(Ws w, Cst<float> c) {
           x[k + 2] = a4.x; y[k + 2] = a4.y; z[k + 2] = a4.z; r[k + 2] = a4.w;
           ec[k + 2] = (ecm_j >> k) & 1;
         }
-        float rho, phi, d;
-        karimaki<float, 5>(x, y, rho, phi, d);
-        const float chi2c = circle_chi2<float, 5>(x, y, rho, phi, d, c.sigma_rphi);
+        float rho, phi, d, sp, cp;
+        karimaki<float, 5>(x, y, rho, phi, d, sp, cp);
+        const float chi2c = circle_chi2<float, 5>(x, y, rho, sp, cp, d, c.sigma_rphi);
         if (chi2c > 1.25f * c.chi2_t5_c + 1.0f) keep = false;
         if (keep) {
           float chi2rz, slope;
@@ -328,34 +399,35 @@ __global__ void k_t5_pre(Ws w, Cst<float> c) {
   }
 }
 
-__global__ void k_t5_decide(Ws w, Cst<double> c) {
+// float64-exact decision of the pre-filter's survivors, evaluated in double-float
+__global__ void k_t5_decide(Ws w, Cst<ff> c) {
   const int n = min((int64_t)w.status[ST_Q_T5], w.cap.q_t5);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int2 q = w.q_t5[k];
     const int i = q.x, j = q.y;
     const float Ri = w.t3_R[i], Rj = w.t3_R[j];
-    const double kin = isinf(Ri) ? 0.0 : 1.0 / (double)Ri;
-    const double kout = isinf(Rj) ? 0.0 : 1.0 / (double)Rj;
-    Acc64 acc;
-    acc.cut(c.c_rel * fmax(kin, kout) + c.c_abs, fabs(kin - kout));
+    const ff kin = isinf(Ri) ? ff(0.0f) : ff(1.0f) / ff(Ri);
+    const ff kout = isinf(Rj) ? ff(0.0f) : ff(1.0f) / ff(Rj);
+    AccFF acc;
+    acc.cut(c.c_rel * m_max(kin, kout) + c.c_abs, m_abs(kin - kout));
     if (acc.fail) continue;
     const int md[5] = {w.t3_md0[i], w.t3_md1[i], w.t3_md2[i], w.t3_md1[j], w.t3_md2[j]};
-    double x[5], y[5], z[5], r[5];
+    ff x[5], y[5], z[5], r[5];
     bool ec[5];
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
-      x[a] = w.md_x[md[a]];
-      y[a] = w.md_y[md[a]];
-      z[a] = w.md_z[md[a]];
-      r[a] = sqrt(x[a] * x[a] + y[a] * y[a]);
+      x[a] = ff(w.md_x[md[a]]);
+      y[a] = ff(w.md_y[md[a]]);
+      z[a] = ff(w.md_z[md[a]]);
+      r[a] = m_sqrt(x[a] * x[a] + y[a] * y[a]);
       ec[a] = w.md_ec[md[a]] != 0;
     }
-    double rho, phi, d;
-    karimaki<double, 5>(x, y, rho, phi, d);
-    const double chi2c = circle_chi2<double, 5>(x, y, rho, phi, d, c.sigma_rphi);
+    ff rho, phi, d, sp, cp;
+    karimaki<ff, 5>(x, y, rho, phi, d, sp, cp);
+    const ff chi2c = circle_chi2<ff, 5>(x, y, rho, sp, cp, d, c.sigma_rphi);
     acc.cut(c.chi2_t5_c, chi2c);
-    double chi2rz, slope;
-    if (!rz_fit<double, 5>(c, fabs(rho), r, z, ec, chi2rz, slope)) {
+    ff chi2rz, slope;
+    if (!rz_fit<ff, 5>(c, m_abs(rho), r, z, ec, chi2rz, slope)) {
       acc.reject();
     } else {
       acc.cut(c.chi2_t5_rz, chi2rz);
@@ -374,9 +446,9 @@ __global__ void k_t5_decide(Ws w, Cst<double> c) {
       w.t5s_f[2 * S + s] = (float)rho;
       w.t5s_f[3 * S + s] = (float)chi2c;
       w.t5s_f[4 * S + s] = (float)chi2rz;
-      w.t5s_f[5 * S + s] = (float)asinh(slope);
+      w.t5s_f[5 * S + s] = asinhf((float)slope);
       w.t5s_f[6 * S + s] = (float)phi;
-      w.t5s_f[7 * S + s] = (float)(rho == 0.0 ? c.pt_cap : fmin(c.k / fabs(rho), c.pt_cap));
+      w.t5s_f[7 * S + s] = rho.hi == 0.0f ? (float)c.pt_cap : (float)m_min(c.k / m_abs(rho), c.pt_cap);
     }
   }
 }
@@ -412,11 +484,11 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.t3_base, w.t3_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T3_PRE);
-  k_t3_pre<<<L.n_sm * 8, 256, 0, L.stream>>>(w, c.f);
+  k_t3_pre<<<L.n_sm * 8, 32 * kT3Warps, 0, L.stream>>>(w, c.f);
   KT_END(L, K_T3_PRE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T3_DECIDE);
-  k_t3_decide<<<grid_for(w.cap.q_t3, 128, 152 * 8), 128, 0, L.stream>>>(w, c.d);
+  k_t3_decide<<<grid_for(w.cap.q_t3, 128, 152 * 8), 128, 0, L.stream>>>(w, c.x);
   KT_END(L, K_T3_DECIDE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T3_COMPACT);
@@ -441,7 +513,7 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_END(L, K_T5_PRE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T5_DECIDE);
-  k_t5_decide<<<grid_for(w.cap.q_t5, 128, 152 * 8), 128, 0, L.stream>>>(w, c.d);
+  k_t5_decide<<<grid_for(w.cap.q_t5, 128, 152 * 8), 128, 0, L.stream>>>(w, c.x);
   KT_END(L, K_T5_DECIDE);
   LST_LAUNCH(L);
   GroupArgs ga{w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, ST_OVF_T5, ST_ARENA_T5, w.t5s_a, w.t5s_b,
