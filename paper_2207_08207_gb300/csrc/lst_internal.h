@@ -118,6 +118,7 @@ struct Ws {
   float4* box5 = nullptr;
   // pixel seeds and pT3 / pT5: passing objects are appended, then grouped by seed
   int32_t* pls_bin = nullptr;
+  float4* pls_seed = nullptr;    // [2][P] float32 seed helix: (x0, y0, z0, rho), (|kappa|, sin phi, cos phi, cot theta)
   int32_t *p3a_pls = nullptr, *p3a_obj = nullptr;
   float *p3a_xy = nullptr, *p3a_rz = nullptr, *p3a_sc = nullptr;
   int32_t *p3_cnt = nullptr, *p3_cur = nullptr, *pt3_off = nullptr;   // [P], [P], [P + 1]
@@ -133,6 +134,7 @@ struct Ws {
   uint8_t *pls_member = nullptr, *acc3 = nullptr, *accl = nullptr;   // [P]
   uint8_t *t5_kept = nullptr, *acc5t = nullptr;  // [t5_dense]
   int32_t *h5_cnt = nullptr, *h5_off = nullptr, *h5_cur = nullptr, *h5_idx = nullptr;  // hit -> T5
+  int32_t* t5_hit = nullptr;     // [t5_dense][10] hits of each T5 (lower, upper of each member MD)
   int32_t *cell_cnt = nullptr, *cell_off = nullptr, *cell_cur = nullptr, *cell_item = nullptr;
   int32_t n_cells = 0;   // per event
   int32_t* tc_cnt = nullptr;   // [E]

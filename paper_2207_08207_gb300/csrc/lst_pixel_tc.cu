@@ -183,23 +183,109 @@ __device__ __forceinline__ bool seed_box_reject(const Seed<float>& s, const Cst<
   return false;
 }
 
-// Candidate pre-filter: one warp per seed; the candidates (objects in every module of the seed's
-// pixel-map row) are flattened across the warp with a shuffle-based search over the per-module
-// object counts.
+// float32 seed helices, once per seed, for the candidate pre-filters
+__global__ void k_seed_cache(Ws w, Cst<float> c) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    if (w.pls_bin[p] < 0) continue;
+    const Seed<float> s = make_seed<float>(w.pls[p], c);
+    w.pls_seed[p] = make_float4(s.x0, s.y0, s.z0, s.rho);
+    w.pls_seed[w.P + p] = make_float4(s.akap, s.sp, s.cp, s.cot);
+  }
+}
+
+__device__ __forceinline__ Seed<float> cached_seed(const Ws& w, int p) {
+  const float4 a = w.pls_seed[p], b = w.pls_seed[w.P + p];
+  Seed<float> s;
+  s.x0 = a.x; s.y0 = a.y; s.z0 = a.z; s.rho = a.w;
+  s.akap = b.x; s.sp = b.y; s.cp = b.z; s.cot = b.w;
+  s.R = 1.0f / b.x;
+  return s;
+}
+
+// xy term of one anchor against the remaining room lim - acc, exact-safe: with A = rho/2 |u|^2 - u.n
+// the residual is 2A / (1 + sqrt(1 + 2 rho A)), whose size is at least |A| / (1 + |rho A| / 2), so a
+// term that exceeds the room on that bound alone is rejected without a square root or a division
+__device__ __forceinline__ bool seed_xy_term(const Seed<float>& s, const Cst<float>& c, float4 h, float room,
+                                             float& term) {
+  const float ux = h.x - s.x0, uy = h.y - s.y0;
+  const float A = 0.5f * s.rho * (ux * ux + uy * uy) - (ux * s.sp - uy * s.cp);
+  const float e1 = h.w * c.pls_dir_err;
+  const float e2 = c.pls_pt_err * h.w * h.w * 0.5f * s.akap;
+  const float sig2 = c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2;
+  const float g = 1.0f + 0.5f * fabsf(s.rho * A);
+  if (A * A > room * sig2 * g * g) return false;
+  const float dd = 2.0f * A / (1.0f + sqrtf(1.0f + 2.0f * s.rho * A));
+  term = dd * dd / sig2;
+  return true;
+}
+
+// full float32 pre-filter of the first n (<= 32) queued (seed, object) pairs, one per lane
 template <int N>
-__global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, const float4* box, ObjAnc oa,
-                         int2* queue, int q_word, int64_t q_cap, float cut_xy, float cut_rz) {
+__device__ __forceinline__ void pt_flush(const Ws& w, const Cst<float>& c, const ObjAnc& oa, const int2* qe,
+                                         int n, float lim_xy, float lim_rz, int2* queue, int q_word,
+                                         int64_t q_cap) {
+  const int lane = threadIdx.x & 31;
+  bool keep = false;
+  int2 e = make_int2(0, 0);
+  if (lane < n) {
+    e = qe[lane];
+    const Seed<float> s = cached_seed(w, e.x);
+    const int obj = e.y;
+    float xy = 0.f, rz = 0.f;
+    keep = true;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      float t;
+      if (!seed_xy_term(s, c, oa.anc[a * oa.stride + obj], lim_xy - xy, t)) { keep = false; break; }
+      xy += t;
+      if (xy > lim_xy) { keep = false; break; }
+    }
+    if (keep) {
+      const uint8_t ecm = oa.ecm[obj];
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const float4 h = oa.anc[a * oa.stride + obj];
+        const float sa = arc_len(s.akap, h.w);
+        const float zp = s.z0 + sa * s.cot;
+        const float sz = ((ecm >> a) & 1) ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
+        const float th = sa * (1.0f + s.cot * s.cot) * c.pls_dir_err;
+        rz += (h.z - zp) * (h.z - zp) / (sz * sz + th * th);
+        if (rz > lim_rz) { keep = false; break; }
+      }
+    }
+  }
+  const int q = warp_agg_slot(keep, &w.status[q_word]);
+  if (q >= 0 && q < q_cap) queue[q] = e;
+}
+
+// Candidate pre-filter: one warp per seed. The seed's pixel-map row is scanned 32 modules at a time;
+// modules that cannot hold a passing object are dropped whole (seed_box_reject); the objects of the
+// rest are flattened across the warp by a shuffle search over the per-module counts. Each candidate
+// gets the first anchor's x-y test; survivors go to a per-warp queue that carries over from seed to
+// seed, and whenever it holds 32 the full float32 pre-filter runs on them with every lane busy.
+constexpr int kPxMaxWarps = 16;
+constexpr int kPxQ = 64;
+
+template <int N>
+__global__ void __launch_bounds__(32 * kPxMaxWarps) k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off,
+                                                             const float4* box, ObjAnc oa, int2* queue,
+                                                             int q_word, int64_t q_cap, float cut_xy,
+                                                             float cut_rz) {
+  __shared__ int2 qbuf[kPxMaxWarps][kPxQ];
+  int2* qe = qbuf[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const float lim_xy = cut_xy * (1.0f + kGuardChi2) + kGuardChi2Abs;
   const float lim_rz = cut_rz * (1.0f + kGuardChi2) + kGuardChi2Abs;
   const int P = w.n_pls();
+  int qn = 0;
   for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += nwarps) {
     const int bin = w.pls_bin[p];
     if (bin < 0) continue;
     const int e = find_seg(w.ev_pls_off, w.E, p);
     const int e0 = e * g.n_mods;
-    const Seed<float> s = make_seed<float>(w.pls[p], c);
+    const Seed<float> s = cached_seed(w, p);
     const int tb = g.pix_off[bin], nt = g.pix_off[bin + 1] - tb;
     for (int t0 = 0; t0 < nt; t0 += 32) {
       const int k = t0 + lane;
@@ -231,49 +317,25 @@ __global__ void k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off, cons
         }
         const int st = __shfl_sync(0xffffffffu, start, lo);
         const int ex0 = __shfl_sync(0xffffffffu, excl, lo);
-        bool keep = false;
-        int obj = 0;
-        if (cidx < total) {
-          obj = st + (cidx - ex0);
-          float xy = 0.f, rz = 0.f;
-          keep = true;
-          // xy residuals first (they reject most candidates), anchors loaded as needed. With
-          // A = rho/2 |u|^2 - u.n the residual is 2A / (1 + sqrt(1 + 2 rho A)), whose size is at
-          // least |A| / (1 + |rho A| / 2): a term that exceeds the limit on that bound alone is
-          // rejected without a square root or a division.
-#pragma unroll
-          for (int a = 0; a < N; ++a) {
-            const float4 h = oa.anc[a * oa.stride + obj];
-            const float ux = h.x - s.x0, uy = h.y - s.y0;
-            const float A = 0.5f * s.rho * (ux * ux + uy * uy) - (ux * s.sp - uy * s.cp);
-            const float e1 = h.w * c.pls_dir_err;
-            const float e2 = c.pls_pt_err * h.w * h.w * 0.5f * s.akap;
-            const float sig2 = c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2;
-            const float g = 1.0f + 0.5f * fabsf(s.rho * A);
-            if (A * A > (lim_xy - xy) * sig2 * g * g) { keep = false; break; }
-            const float dd = 2.0f * A / (1.0f + sqrtf(1.0f + 2.0f * s.rho * A));
-            xy += dd * dd / sig2;
-            if (xy > lim_xy) { keep = false; break; }
-          }
-          if (keep) {
-            const uint8_t ecm = oa.ecm[obj];
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-              const float4 h = oa.anc[a * oa.stride + obj];
-              const float sa = arc_len(s.akap, h.w);
-              const float zp = s.z0 + sa * s.cot;
-              const float sz = ((ecm >> a) & 1) ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
-              const float th = sa * (1.0f + s.cot * s.cot) * c.pls_dir_err;
-              rz += (h.z - zp) * (h.z - zp) / (sz * sz + th * th);
-              if (rz > lim_rz) { keep = false; break; }
-            }
-          }
+        const int obj = st + (cidx - ex0);
+        float t;
+        const bool keep = cidx < total && seed_xy_term(s, c, oa.anc[obj], lim_xy, t) && t <= lim_xy;
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) qe[qn + __popc(km & ((1u << lane) - 1u))] = make_int2(p, obj);
+        qn += __popc(km);
+        if (qn >= 32) {
+          __syncwarp();
+          pt_flush<N>(w, c, oa, qe, 32, lim_xy, lim_rz, queue, q_word, q_cap);
+          __syncwarp();
+          qn -= 32;
+          if (lane < qn) qe[lane] = qe[32 + lane];
+          __syncwarp();
         }
-        const int q = warp_agg_slot(keep, &w.status[q_word]);
-        if (q >= 0 && q < q_cap) queue[q] = make_int2(p, obj);
       }
     }
   }
+  __syncwarp();
+  if (qn > 0) pt_flush<N>(w, c, oa, qe, qn, lim_xy, lim_rz, queue, q_word, q_cap);
 }
 
 // decision of the pre-filter's survivors (chi2 sums of the seed's circle and r-z line over the
@@ -320,30 +382,50 @@ __global__ void k_pt_group(Ws w, int n_word, int64_t a_cap, const int32_t* a_pls
   (void)a_obj;
 }
 
-__global__ void k_pt_order(Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls,
-                           const int32_t* a_obj, const float* a_xy, const float* a_rz, const float* a_sc,
-                           int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc) {
+// order each seed's objects by object index (unique within a seed): a warp per seed; each element's
+// output position is its rank, the number of the seed's keys below its own (keys staged in shared
+// memory for groups up to kPtOrderSmem)
+constexpr int kPtOrderWarps = 4;
+constexpr int kPtOrderSmem = 256;
+
+__global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
+    Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls, const int32_t* a_obj, const float* a_xy,
+    const float* a_rz, const float* a_sc, int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc) {
+  __shared__ int keys[kPtOrderWarps][kPtOrderSmem];
+  int* K = keys[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const int P = w.n_pls();
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    const int a = off[p], b = off[p + 1];
-    for (int i = a + 1; i < b; ++i) {
-      const int v = tmp_idx[i];
-      const int key = a_obj[v];
-      int j = i - 1;
-      while (j >= a && a_obj[tmp_idx[j]] > key) {
-        tmp_idx[j + 1] = tmp_idx[j];
-        --j;
+  const int nwarps = gridDim.x * kPtOrderWarps;
+  for (int p = blockIdx.x * kPtOrderWarps + (threadIdx.x >> 5); p < P; p += nwarps) {
+    const int a = off[p], n = off[p + 1] - a;
+    if (n == 0) continue;
+    if (n <= 32) {
+      int v = 0, key = 0x7fffffff;
+      if (lane < n) {
+        v = tmp_idx[a + lane];
+        key = a_obj[v];
       }
-      tmp_idx[j + 1] = v;
+      int rank = 0;
+      for (int j = 0; j < n; ++j) rank += __shfl_sync(0xffffffffu, key, j) < key;
+      if (lane < n) {
+        const int o = a + rank;
+        d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+      }
+      continue;
     }
-    for (int i = a; i < b; ++i) {
-      const int v = tmp_idx[i];
-      d_pls[i] = a_pls[v];
-      d_obj[i] = a_obj[v];
-      d_xy[i] = a_xy[v];
-      d_rz[i] = a_rz[v];
-      d_sc[i] = a_sc[v];
+    const bool staged = n <= kPtOrderSmem;
+    if (staged)
+      for (int j = lane; j < n; j += 32) K[j] = a_obj[tmp_idx[a + j]];
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const int v = tmp_idx[a + i];
+      const int key = a_obj[v];
+      int rank = 0;
+      for (int j = 0; j < n; ++j) rank += (staged ? K[j] : a_obj[tmp_idx[a + j]]) < key;
+      const int o = a + rank;
+      d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
     }
+    __syncwarp();
   }
 }
 
@@ -430,6 +512,8 @@ __global__ void k_tc_best(Ws w) {
 }
 
 // hit -> T5 adjacency (binned hit indices)
+// hit -> T5 lists (counting pass, then fill pass); the counting pass also caches each T5's ten
+// hits in one row
 __global__ void k_h5_count(Ws w, int fill) {
   const int n = w.t5_off[w.V];
   const int64_t S = w.cap.t5_dense;
@@ -438,35 +522,44 @@ __global__ void k_h5_count(Ws w, int fill) {
       const int d = w.t5_md[k * S + i];
       const int hs[2] = {w.md_lo[d], w.md_up[d]};
       for (int t = 0; t < 2; ++t) {
-        if (!fill) atomicAdd(&w.h5_cnt[hs[t]], 1);
-        else w.h5_idx[w.h5_off[hs[t]] + atomicAdd(&w.h5_cur[hs[t]], 1)] = i;
+        if (!fill) {
+          atomicAdd(&w.h5_cnt[hs[t]], 1);
+          w.t5_hit[(int64_t)i * 10 + 2 * k + t] = hs[t];
+        } else {
+          w.h5_idx[w.h5_off[hs[t]] + atomicAdd(&w.h5_cur[hs[t]], 1)] = i;
+        }
       }
     }
   }
 }
 
+// T5 duplicate removal: T5 a is dropped when another passing T5 shares at least `overlap` of its
+// ten hits and ranks lower (chi2_c as float32, then hit tuple). A T5 sharing `overlap` hits with a
+// contains at least one of a's first 11 - overlap hits (a misses at most 10 - overlap of them), so
+// only those hits' T5 lists are searched.
 __global__ void k_t5_clean(Ws w, int overlap) {
   const int n = w.t5_off[w.V];
   const int64_t S = w.cap.t5_dense;
+  const int n_probe = min(10, max(1, 11 - overlap));
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
     int ha[10];
-    for (int k = 0; k < 5; ++k) {
-      const int d = w.t5_md[k * S + a];
-      ha[2 * k] = w.md_lo[d];
-      ha[2 * k + 1] = w.md_up[d];
-    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) ha[k] = w.t5_hit[(int64_t)a * 10 + k];
     const float ca = w.t5_f[3 * S + a];
     bool drop = false;
-    for (int t = 0; t < 10 && !drop; ++t) {
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      if (t >= n_probe || drop) break;
       const int h = ha[t];
       for (int k = w.h5_off[h]; k < w.h5_off[h + 1] && !drop; ++k) {
         const int b = w.h5_idx[k];
         if (b == a) continue;
         int shared = 0;
-        for (int kb = 0; kb < 5; ++kb) {
-          const int d = w.t5_md[kb * S + b];
-          const int hb0 = w.md_lo[d], hb1 = w.md_up[d];
-          for (int u = 0; u < 10; ++u) shared += (ha[u] == hb0) + (ha[u] == hb1);
+#pragma unroll
+        for (int kb = 0; kb < 10; ++kb) {
+          const int hb = w.t5_hit[(int64_t)b * 10 + kb];
+#pragma unroll
+          for (int u = 0; u < 10; ++u) shared += ha[u] == hb;
         }
         if (shared < overlap) continue;
         const float cb = w.t5_f[3 * S + b];
@@ -805,9 +898,10 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   ObjAnc om3{w.t3_anc, w.t3_ecm, w.cap.t3_dense};
   ObjAnc om5{w.t5_anc, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
+    k_seed_cache<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, c.f);
     k_obj_box<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, w.t3_off, w.t3_anc, w.box3);
     k_obj_box<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, w.t5_off, w.t5_anc, w.box5);
-    *L.launches += 2;
+    *L.launches += 3;
     KT_BEGIN(L, K_PT3_PRE);
   k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, w.box3, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
                                                    c.f.chi2_pt3_xy, c.f.chi2_pt3_rz);
@@ -835,14 +929,14 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   scan_exclusive(w.p5_cnt, w.pt5_off, w.P, w.scan_tmp, L);
   k_pt_group<<<grid_for(w.cap.p3_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT3, w.cap.p3_slots, w.p3a_pls,
                                                                    w.p3a_obj, w.pt3_off, w.p3_cur, w.grp_tmp);
-  k_pt_order<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, w.pt3_off, w.grp_tmp, w.p3a_pls, w.p3a_obj,
-                                                      w.p3a_xy, w.p3a_rz, w.p3a_sc, w.pt3_pls, w.pt3_obj,
-                                                      w.pt3_xy, w.pt3_rz, w.pt3_sc);
+  k_pt_order<<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
+      w, w.pt3_off, w.grp_tmp, w.p3a_pls, w.p3a_obj, w.p3a_xy, w.p3a_rz, w.p3a_sc, w.pt3_pls, w.pt3_obj,
+      w.pt3_xy, w.pt3_rz, w.pt3_sc);
   k_pt_group<<<grid_for(w.cap.p5_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT5, w.cap.p5_slots, w.p5a_pls,
                                                                    w.p5a_obj, w.pt5_off, w.p5_cur, w.grp_tmp);
-  k_pt_order<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w, w.pt5_off, w.grp_tmp, w.p5a_pls, w.p5a_obj,
-                                                      w.p5a_xy, w.p5a_rz, w.p5a_sc, w.pt5_pls, w.pt5_obj,
-                                                      w.pt5_xy, w.pt5_rz, w.pt5_sc);
+  k_pt_order<<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
+      w, w.pt5_off, w.grp_tmp, w.p5a_pls, w.p5a_obj, w.p5a_xy, w.p5a_rz, w.p5a_sc, w.pt5_pls, w.pt5_obj,
+      w.pt5_xy, w.pt5_rz, w.pt5_sc);
   *L.launches += 4;
 }
 

@@ -434,7 +434,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.t5_kept, c.t5_dense); pl.add(w.acc5t, c.t5_dense);
   pl.add(w.box3, 2 * V); pl.add(w.box5, 2 * V);
   // pixel
-  pl.add(w.pls_bin, c.P);
+  pl.add(w.pls_bin, c.P); pl.add(w.pls_seed, 2 * c.P);
   pl.add(w.p3a_pls, c.p3_slots); pl.add(w.p3a_obj, c.p3_slots); pl.add(w.p3a_xy, c.p3_slots);
   pl.add(w.p3a_rz, c.p3_slots); pl.add(w.p3a_sc, c.p3_slots); pl.add(w.pt3_off, c.P + 1);
   pl.add(w.pt3_pls, c.p3_slots); pl.add(w.pt3_obj, c.p3_slots); pl.add(w.pt3_xy, c.p3_slots);
@@ -447,6 +447,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   // track candidates
   pl.add(w.best5, c.P); pl.add(w.best3, c.P); pl.add(w.pls_member, c.P); pl.add(w.acc3, c.P); pl.add(w.accl, c.P);
   pl.add(w.h5_off, c.H + 2); pl.add(w.h5_idx, 10 * c.t5_dense);
+  pl.add(w.t5_hit, 10 * c.t5_dense);
   pl.add(w.cell_off, NC + 1); pl.add(w.cell_item, c.P + c.t5_dense);
   pl.add(w.tc_code, tc_cap); pl.add(w.tc_key, tc_cap); pl.add(w.tc_hit_key, 14 * tc_cap);
   pl.add(w.tc_type, tc_cap); pl.add(w.tc_obj, tc_cap); pl.add(w.tc_hits, 14 * tc_cap);
