@@ -38,6 +38,14 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
 
@@ -131,11 +139,22 @@ def whole_job_rate(events_per_step, steps, world, t_max):
     return events_per_step * steps * world / t_max
 
 
-def make_events(n, seed0=0):
+WORKLOADS = {
+    1: "toy barrel events, 200 helices (barrel only, 5258 modules)",
+    2: "PU200 events, full outer tracker (9138 modules)",
+    3: "PU ~ U[140, 250] events, full outer tracker (9138 modules)",
+    4: "PU300 events with 20 % loopers, pT threshold 0.6 GeV, full outer tracker (9138 modules)",
+}
+
+
+def make_events(n, seed0=0, config=2):
+    """Events of a benchmark configuration (seed 1000 config + event); returns (detector, events)."""
     from paper_2207_08207_gb300 import gen
-    det = gen.make_detector(barrel_only=False, pt_thr=0.8)
-    evs = [gen.config_event(2, seed0 + e, pu=200.0)[1] for e in range(n)]
-    return det, evs
+    if config == 2:
+        det = gen.make_detector(barrel_only=False, pt_thr=0.8)
+        return det, [gen.config_event(2, seed0 + e, pu=200.0)[1] for e in range(n)]
+    pairs = [gen.config_event(config, seed0 + e) for e in range(n)]
+    return pairs[0][0], [ev for _, ev in pairs]
 
 
 def oracle_events_per_s(det, evs, threads):
@@ -189,6 +208,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS),
+                    help="event configuration of the batched / plain measurement (2: PU200)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -213,7 +234,7 @@ def main():
 
     B = args.batch
     # every rank processes its own events (events are independent: no collective on the data path)
-    det, evs = make_events(B, seed0=rank_seed0(rank))
+    det, evs = make_events(B, seed0=rank_seed0(rank), config=args.config)
     # inputs resident in HBM
     dev = [to_device(ev, torch) for ev in evs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -224,7 +245,7 @@ def main():
     tuned = {"block_ls": 128, "warps_px": 4, "persistent": 1, "cap_scale": 1.0}
     if not args.no_tune:
         from paper_2207_08207_gb300 import autotune
-        tuned = autotune.tune(det, dev, workload="pu200")
+        tuned = autotune.tune(det, dev, workload=f"config{args.config}")
     ctx = lst.Context(det, device=local, use_graph=1, **tuned)
     ctx.reserve(B, max(e.n_hits for e in evs), max(e.n_pls for e in evs))
 
@@ -263,7 +284,10 @@ def main():
     value = whole_job_rate(B, args.steps, world, t_max)
     counts = [ctx.counts(e) for e in range(B)]
 
-    # roofline of the dominant kernel (algorithmic bytes per launch / average duration)
+    # roofline of the dominant kernel. The candidate kernels are bound by instruction issue (their
+    # working set sits in L2), so the ceiling is the issue rate: SMs x 4 schedulers x max SM clock,
+    # and the work per launch is the kernel's warp instructions per event (ncu, on this workload)
+    # times the events of the launch. The HBM fraction (algorithmic bytes) is reported beside it.
     hbm_peak, peak_kind = _peaks()
     kavg = {k: v / args.steps for k, v in kern_acc.items()}
     dom = max(kavg, key=kavg.get) if kavg else None
@@ -272,12 +296,25 @@ def main():
     n_t3 = sum(c["n_t3"] for c in counts)
     n_t5 = sum(c["n_t5"] for c in counts)
     alg_bytes = ctx.kernel_algorithmic_bytes(dom, counts, sum(e.n_hits for e in evs), sum(e.n_pls for e in evs)) if dom else 0
-    achieved = alg_bytes / (kavg[dom] * 1e-3) / 1e9 if dom and kavg[dom] > 0 else 0.0
-    traffic = None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel_ms": kavg.get(dom) if dom else None, "algorithmic_bytes": alg_bytes,
-                "kernels_ms": {k: round(v, 4) for k, v in sorted(kavg.items(), key=lambda kv: -kv[1])}}
+    dur_s = kavg[dom] * 1e-3 if dom and kavg[dom] > 0 else float("nan")
+    hbm_achieved = alg_bytes / dur_s / 1e9
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    issue_peak = n_sm * 4 * _sm_max_mhz() * 1e6 / 1e9          # G warp instructions / s
+    prof = lst.KERNEL_PROFILE.get(dom) if args.config == 2 else None
+    if prof is not None:
+        inst = prof["warp_inst_per_event"] * B
+        achieved = inst / dur_s / 1e9
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": issue_peak,
+                    "unit": "G warp-instructions/s", "frac": achieved / issue_peak,
+                    "traffic": prof["dram_bytes_per_event"] * B, "peak_kind": "derived: SMs x 4 schedulers x max SM clock",
+                    "warp_inst_per_launch": inst, "profile": prof["source"]}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
+    roofline.update({"kernel_ms": kavg.get(dom) if dom else None,
+                     "hbm": {"algorithmic_bytes": alg_bytes, "achieved": hbm_achieved, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind},
+                     "kernels_ms": {k: round(v, 4) for k, v in sorted(kavg.items(), key=lambda kv: -kv[1])}})
 
     # plain path: one event per call (a context shaped for one event), inputs resident
     plain = None
@@ -329,7 +366,7 @@ def main():
 
     # serving: Poisson arrivals of PU ~ U[50, 300] events, continuous batching vs one at a time
     serving = None
-    if not args.no_serving and rank == 0:
+    if not args.no_serving and rank == 0 and args.config == 2:
         from paper_2207_08207_gb300 import gen
         pool = [gen.config_event(5, e)[1] for e in range(24)]
         serving = {"workload": "Poisson stream of PU ~ U[50, 300] events (24 generated, cycled), 40 GB budget",
@@ -350,8 +387,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"PU200 events, full outer tracker (9138 modules), batch of {B} events per step",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
+            "config": {"workload": f"{WORKLOADS[args.config]}, batch of {B} events per step",
+                       "event_config": args.config,
                        "events_per_step": B, "l2": "256 MB buffer written between timed steps",
                        "parallelism": f"events sharded over {world} GPU(s)"},
             "latency_ms": {"batched_p50": float(np.percentile(step_ms, 50)),

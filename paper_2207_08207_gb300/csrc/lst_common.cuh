@@ -281,13 +281,14 @@ __device__ __forceinline__ Circle3<T> circle3(T x1, T y1, T x2, T y2, T x3, T y3
   const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
   const T wx3 = x3 - x2, wy3 = y3 - y2;
   const T ww = wx3 * wx3 + wy3 * wy3;
-  o.kappa = T(2) * cr / m_sqrt(uu * vv * ww);
+  const T rs = m_sqrt(uu * vv * ww);   // 2 R |cr|
+  o.kappa = T(2) * cr / rs;
   // direction of the centre from p1 (valid also when cr -> 0)
   const T Nx = uu * vy - vv * uy;
   const T Ny = -uu * vx + vv * ux;
-  const T Nn = m_sqrt(Nx * Nx + Ny * Ny);
+  const T inv_nn = T(1) / m_sqrt(Nx * Nx + Ny * Ny);
   const T sgn = cr >= T(0) ? T(1) : T(-1);
-  const T nx = sgn * Nx / Nn, ny = sgn * Ny / Nn;
+  const T nx = sgn * Nx * inv_nn, ny = sgn * Ny * inv_nn;
   const T ak = m_abs(o.kappa);
   if (cr == T(0)) {
     o.R = T(1) / T(0);
@@ -296,9 +297,10 @@ __device__ __forceinline__ Circle3<T> circle3(T x1, T y1, T x2, T y2, T x3, T y3
     o.d0 = m_abs(diff_prod(x1, vy, y1, vx)) / m_sqrt(vv);
     return o;
   }
-  o.R = T(1) / ak;
-  o.xc = x1 + Nx / (T(2) * cr);
-  o.yc = y1 + Ny / (T(2) * cr);
+  const T inv_2cr = T(1) / (T(2) * cr);
+  o.R = m_abs(rs * inv_2cr);
+  o.xc = x1 + Nx * inv_2cr;
+  o.yc = y1 + Ny * inv_2cr;
   const T A = T(0.5) * ak * (x1 * x1 + y1 * y1) + (x1 * nx + y1 * ny);
   o.d0 = m_abs(T(2) * A / (T(1) + m_sqrt(T(1) + T(2) * ak * A)));
   return o;
@@ -306,24 +308,30 @@ __device__ __forceinline__ Circle3<T> circle3(T x1, T y1, T x2, T y2, T x3, T y3
 
 // arc length from the origin to radius r on a circle of curvature |kappa| through the origin
 template <class T>
-__device__ __forceinline__ T arc_len(T akappa, T r) {
+__device__ __forceinline__ T arc_len(T akappa, T two_r, T r) {   // two_r = 2 / akappa
   const T x = r * akappa * T(0.5);
   if (x <= T(0)) return r;
-  if (x >= T(1)) return r * T(1.5707963267948966) / x;  // = pi R (the cap of asin at 1)
-  return m_asin(x) / x * r;
+  if (x >= T(1)) return two_r * T(1.5707963267948966);  // = pi R (the cap of asin at 1)
+  return m_asin(x) * two_r;
+}
+template <class T>
+__device__ __forceinline__ T arc_len(T akappa, T r) {
+  return arc_len(akappa, T(2) / akappa, r);
 }
 
 // Weighted straight-line fit z = a + b s; returns chi2 and the slope b (centred sums).
 template <class T, int N>
 __device__ __forceinline__ T line_chi2(const T* s, const T* z, const T* sig, T& slope) {
   T S = 0, Ss = 0, Sz = 0;
-  T w[N];
+  T w[N], isig[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    w[i] = T(1) / (sig[i] * sig[i]);
+    isig[i] = T(1) / sig[i];
+    w[i] = isig[i] * isig[i];
     S += w[i]; Ss += w[i] * s[i]; Sz += w[i] * z[i];
   }
-  const T sm = Ss / S, zm = Sz / S;
+  const T iS = T(1) / S;
+  const T sm = Ss * iS, zm = Sz * iS;
   T Sss = 0, Ssz = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -335,7 +343,7 @@ __device__ __forceinline__ T line_chi2(const T* s, const T* z, const T* sig, T& 
   T chi2 = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const T r = (z[i] - zm - b * (s[i] - sm)) / sig[i];
+    const T r = (z[i] - zm - b * (s[i] - sm)) * isig[i];
     chi2 += r * r;
   }
   slope = b;
@@ -350,7 +358,9 @@ __device__ __forceinline__ bool rz_fit(const Cst<T>& c, T akappa, const T* r, co
                                        const bool* ec, T& chi2, T& slope) {
   T s[N], sig[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) s[i] = arc_len(akappa, r[i]);
+  const T two_r = T(2) / akappa;
+#pragma unroll
+  for (int i = 0; i < N; ++i) s[i] = arc_len(akappa, two_r, r[i]);
   if (!(s[N - 1] > s[0])) return false;
   const T b0 = (z[N - 1] - z[0]) / (s[N - 1] - s[0]);
 #pragma unroll
@@ -376,6 +386,21 @@ __device__ __forceinline__ int warp_agg_slot(bool pred, int* counter) {
   if (lane_id() == leader) base = atomicAdd(counter, __popc(m));
   base = __shfl_sync(act, base, leader);
   return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
+}
+
+// warp-aggregated slot reservation where lanes may target different counters (counters[key])
+__device__ __forceinline__ int warp_agg_slot_keyed(bool pred, int key, int* counters) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  int slot = -1;
+  if (pred) {
+    const unsigned grp = __match_any_sync(m, key);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane_id() == leader) base = atomicAdd(&counters[key], __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    slot = base + __popc(grp & ((1u << lane_id()) - 1u));
+  }
+  return slot;
 }
 
 }  // namespace lst

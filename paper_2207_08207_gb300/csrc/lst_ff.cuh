@@ -9,8 +9,8 @@
 //
 // Building blocks are the error-free transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and
 // TwoProd by fused multiply-add; addition, multiplication, division and square root follow the
-// double-double algorithms of Dekker (Numer. Math. 18 (1971) 224) and Hida, Li and Bailey
-// (ARITH-15, 2001). asin and sin are written below from their Taylor series and a Newton step.
+// double-length algorithms of Dekker (Numer. Math. 18 (1971) 224), as in the double-double library
+// of Hida, Li and Bailey (ARITH-15, 2001). asin and sin are written below from their Taylor series and a Newton step.
 // Non-finite intermediate results are returned with lo = 0 so that inf propagates like in float64.
 #pragma once
 #include <cuda_runtime.h>
@@ -47,10 +47,7 @@ __host__ __device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo)
 __host__ __device__ __forceinline__ ff operator+(ff a, ff b) {
   ff s = ff_two_sum(a.hi, b.hi);
   if (!isfinite(s.hi)) return ff(s.hi, 0.0f);
-  const ff t = ff_two_sum(a.lo, b.lo);
-  s.lo += t.hi;
-  s = ff_fast_two_sum(s.hi, s.lo);
-  s.lo += t.lo;
+  s.lo += a.lo + b.lo;
   return ff_fast_two_sum(s.hi, s.lo);
 }
 __host__ __device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
@@ -66,15 +63,20 @@ __host__ __device__ __forceinline__ ff operator*(ff a, ff b) {
 
 __host__ __device__ __forceinline__ ff& operator*=(ff& a, ff b) { return a = a * b; }
 
-// quotient: three float quotient digits, each from the remainder of the previous ones
+// quotient: two float quotient digits, the second from the remainder of the first (Dekker);
+// the float reciprocal needs to be good to a few ulp only
 __host__ __device__ __forceinline__ ff operator/(ff a, ff b) {
-  const float q1 = a.hi / b.hi;
-  if (!isfinite(q1) || b.hi == 0.0f) return ff(q1, 0.0f);
-  ff r = a - b * ff(q1);
-  const float q2 = r.hi / b.hi;
-  r = r - b * ff(q2);
-  const float q3 = r.hi / b.hi;
-  return ff_fast_two_sum(q1, q2) + ff(q3);
+#ifdef __CUDA_ARCH__
+  const float ab = fabsf(b.hi);
+  const float inv = (ab > 1e-30f && ab < 1e30f) ? __fdividef(1.0f, b.hi) : 1.0f / b.hi;
+#else
+  const float inv = 1.0f / b.hi;
+#endif
+  const float q1 = a.hi * inv;
+  if (!isfinite(q1) || b.hi == 0.0f) return ff(a.hi / b.hi, 0.0f);
+  const ff p = ff_two_prod(b.hi, q1);
+  const float r = (((a.hi - p.hi) - p.lo) + a.lo) - b.lo * q1;
+  return ff_fast_two_sum(q1, r * inv);
 }
 
 // comparisons (exact for normalised pairs)

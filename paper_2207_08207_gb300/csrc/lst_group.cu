@@ -1,70 +1,232 @@
 // Ordered compaction of per-module capacity slots into dense arrays.
 //
 // Each stage writes its objects into per-module slots (order inside a module set by atomics). The
-// dense arrays are ordered by (first member, second member): a counting sort by the first member
-// (a dense index of the previous stage, or a binned hit index for MDs) followed by an insertion sort
-// of each first-member group by the second member. Groups are small (a few objects per MD / LS / T3),
-// so the whole step is O(objects). Because the first members are themselves ordered by module, the
-// result is also grouped by module, and the per-module offsets are the group offsets of each
-// module's first key.
+// dense arrays are ordered by (first member, second member). The first members of a module's
+// objects lie in that module's own range of first-member indices (the previous stage's dense
+// objects, or the module's binned hits for MDs), and those ranges increase with the module, so the
+// global order is the module order with each module's objects sorted on their own: the per-module
+// dense offsets are an exclusive scan of the per-module counts, and each module sorts its few
+// objects locally (a warp for most modules, a block and shared memory for the largest). The per-key group offsets (objects whose first member is below a key) follow from the
+// sorted keys by binary search.
 #include "lst_internal.h"
 
 namespace lst {
 namespace {
 
-// warp per virtual module: valid slots = min(count, capacity, arena room); count keys
-__global__ void k_grp_count(Ws w, const int32_t* cnt, const int32_t* cap, const int32_t* base, int64_t slots,
-                            int ovf_word, int arena_word, const int32_t* key1, int32_t* grp_cnt) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+constexpr int kSmallWarps = 8;        // warps per block of the small-module kernel
+constexpr int kBigThreads = 256;      // threads per block of the large-module kernel
+constexpr int kBigCap = 8192;         // objects a large module sorts in shared memory
+
+// valid slots per module = min(count, capacity, arena room); the excess is recorded
+__global__ void k_mod_eff(Ws w, const int32_t* cnt, const int32_t* cap, const int32_t* base, int64_t slots,
+                          int ovf_word, int arena_word) {
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const int c = cnt[vm], k = cap[vm], b = base[vm];
     int eff = min(c, k);
-    if ((int64_t)b + eff > slots) eff = (int)(slots - b > 0 ? slots - b : 0);
-    if (lane == 0) {
-      if (c > k) atomicAdd(&w.status[ovf_word], c - k);
-      if ((int64_t)b + min(c, k) > slots) atomicMax(&w.status[arena_word], base[w.V]);
-      w.eff[vm] = eff;
+    if (c > k) atomicAdd(&w.status[ovf_word], c - k);
+    if ((int64_t)b + eff > slots) {
+      eff = (int)(slots - b > 0 ? slots - b : 0);
+      atomicMax(&w.status[arena_word], base[w.V]);
     }
-    for (int j = lane; j < eff; j += 32) atomicAdd(&grp_cnt[key1[b + j]], 1);
+    w.eff[vm] = eff;
   }
 }
 
-__global__ void k_grp_scatter(Ws w, const int32_t* base, const int32_t* key1, const int32_t* grp_off,
-                              int32_t* grp_cur, int64_t dense_cap) {
+__device__ __forceinline__ unsigned long long pair_key(int k1, int k2) {
+  return ((unsigned long long)(unsigned)k1 << 32) | (unsigned)k2;
+}
+
+struct SortArgs {
+  const int32_t *base, *key1, *key2, *mod_first;
+  int stride;
+  int32_t* grp_off;
+  int64_t n_keys, dense_cap;
+  int32_t* mod_off;
+  int dense_word, big_word;
+};
+
+// Modules of moderate size: a warp per module. Up to 32 objects each lane holds one and ranks it
+// against the others by shuffles. Up to kMidCap objects whose first members span at most kMidCap
+// keys, a counting sort in shared memory: histogram of the first members, its scan (which is the
+// group offsets), placement, then each object's rank inside its first-member group by its second
+// member (groups hold a few objects). Larger modules are listed for k_mod_sort_big.
+constexpr int kMidCap = 512;
+
+__global__ void __launch_bounds__(32 * kSmallWarps) k_mod_sort_small(Ws w, SortArgs a) {
+  __shared__ int sh_k2[kSmallWarps][kMidCap];    // second member of each object
+  __shared__ int sh_pos[kSmallWarps][kMidCap];   // objects placed by first member
+  __shared__ int sh_g[kSmallWarps][kMidCap];     // group counts, then group starts (R + 1 <= kMidCap)
+  const int wi = threadIdx.x >> 5;
+  int* K2 = sh_k2[wi];
+  int* POS = sh_pos[wi];
+  int* G = sh_g[wi];
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
-    const int eff = w.eff[vm], b = base[vm];
-    for (int j = lane; j < eff; j += 32) {
-      const int s = b + j;
-      const int k = key1[s];
-      const int pos = grp_off[k] + atomicAdd(&grp_cur[k], 1);
-      if (pos < dense_cap) w.perm[pos] = s;
+  const int nwarps = gridDim.x * kSmallWarps;
+  const int64_t cap = a.dense_cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int total = w.eff[w.V];
+    if (total > cap) atomicMax(&w.status[a.dense_word], total);
+    a.mod_off[w.V] = (int)lst_min64(total, cap);
+  }
+  for (int vm = blockIdx.x * kSmallWarps + wi; vm < w.V; vm += nwarps) {
+    const int dest = w.eff[vm], n = w.eff[vm + 1] - dest;
+    if (lane == 0) a.mod_off[vm] = (int)lst_min64(dest, cap);
+    const int k0 = a.mod_first[(int64_t)vm * a.stride], k1 = a.mod_first[(int64_t)(vm + 1) * a.stride];
+    const int R = k1 - k0;
+    const int b = a.base[vm];
+    if (n <= 32) {
+      int kv1 = 0x7fffffff;
+      unsigned long long key = ~0ull;
+      if (lane < n) {
+        kv1 = a.key1[b + lane];
+        key = pair_key(kv1, a.key2[b + lane]);
+      }
+      int rank = 0;
+      for (int j = 0; j < n; ++j) {
+        const unsigned long long kj = __shfl_sync(0xffffffffu, key, j);
+        rank += kj < key || (kj == key && j < lane);
+      }
+      if (lane < n) {
+        if (dest + rank < cap) w.perm[dest + rank] = b + lane;
+        POS[rank] = kv1;
+      }
+      __syncwarp();
+      for (int k = k0 + lane; k < k1; k += 32) {   // dest + #(first members below k)
+        int lo = 0, hi = n;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (POS[mid] < k) lo = mid + 1; else hi = mid;
+        }
+        a.grp_off[k] = (int)lst_min64(dest + lo, cap);
+      }
+      __syncwarp();
+      continue;
+    }
+    if (n > kMidCap || R >= kMidCap) {
+      if (lane == 0) w.grp_big[atomicAdd(&w.grp_big_cnt[a.big_word], 1)] = vm;
+      continue;
+    }
+    for (int k = lane; k <= R; k += 32) G[k] = 0;
+    __syncwarp();
+    const int gmax = R > 0 ? R - 1 : 0;   // (first members outside the range only after an overflow)
+    for (int i = lane; i < n; i += 32) {
+      K2[i] = a.key2[b + i];
+      atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1);
+    }
+    __syncwarp();
+    int run = 0;   // exclusive scan of G[0..R] in chunks of 32
+    for (int k0c = 0; k0c <= R; k0c += 32) {
+      const int k = k0c + lane;
+      const int v = k <= R ? G[k] : 0;
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (k <= R) G[k] = run + incl - v;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    for (int k = lane; k < R; k += 32) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
+    // placement by first member (order inside a group arbitrary), via the group starts
+    for (int i = lane; i < n; i += 32) POS[atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1)] = i;
+    __syncwarp();
+    // G[g] is now the end of group g: rank inside the group by the second member
+    for (int p = lane; p < n; p += 32) {
+      const int i = POS[p];
+      const int g = min(max(a.key1[b + i] - k0, 0), gmax);
+      const int g_end = G[g], g_beg = g > 0 ? G[g - 1] : 0;
+      const int k2 = K2[i];
+      int r = g_beg;
+      for (int q = g_beg; q < g_end; ++q) {
+        const int j = POS[q];
+        const int kj = K2[j];
+        r += kj < k2 || (kj == k2 && j < i);
+      }
+      if (dest + r < cap) w.perm[dest + r] = b + i;
+    }
+    __syncwarp();
+  }
+}
+
+// Modules with more than kMidCap objects: a block per module, bitonic sort of (key, slot) in shared
+// memory up to kBigCap objects; beyond that, ranks counted directly from global memory.
+__global__ void __launch_bounds__(kBigThreads) k_mod_sort_big(Ws w, SortArgs a) {
+  extern __shared__ __align__(16) unsigned char big_smem[];
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(big_smem);
+  int* I = reinterpret_cast<int*>(K + kBigCap);
+  const int n_big = w.grp_big_cnt[a.big_word];
+  const int64_t cap = a.dense_cap;
+  for (int it = blockIdx.x; it < n_big; it += gridDim.x) {
+    const int vm = w.grp_big[it];
+    const int dest = w.eff[vm], n = w.eff[vm + 1] - dest;
+    const int b = a.base[vm];
+    const int k0 = a.mod_first[(int64_t)vm * a.stride], k1 = a.mod_first[(int64_t)(vm + 1) * a.stride];
+    if (n <= kBigCap) {
+      int np2 = 64;
+      while (np2 < n) np2 <<= 1;
+      for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+        K[i] = i < n ? pair_key(a.key1[b + i], a.key2[b + i]) : ~0ull;
+        I[i] = i < n ? b + i : -1;
+      }
+      __syncthreads();
+      for (int size = 2; size <= np2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+            const int j = i ^ stride;
+            if (j > i) {
+              const bool up = (i & size) == 0;
+              const unsigned long long ki = K[i], kj = K[j];
+              const int vi = I[i], vj = I[j];
+              const bool gt = ki > kj || (ki == kj && (unsigned)vi > (unsigned)vj);
+              if (gt == up) {
+                K[i] = kj; K[j] = ki;
+                I[i] = vj; I[j] = vi;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (dest + i < cap) w.perm[dest + i] = I[i];
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const unsigned long long kk = pair_key(k, 0);
+        int lo = 0, hi = n;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (K[mid] < kk) lo = mid + 1; else hi = mid;
+        }
+        a.grp_off[k] = (int)lst_min64(dest + lo, cap);
+      }
+      __syncthreads();
+    } else {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long ki = pair_key(a.key1[b + i], a.key2[b + i]);
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+          const unsigned long long kj = pair_key(a.key1[b + j], a.key2[b + j]);
+          rank += kj < ki || (kj == ki && j < i);
+        }
+        if (dest + rank < cap) w.perm[dest + rank] = b + i;
+      }
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        int below = 0;
+        for (int j = 0; j < n; ++j) below += a.key1[b + j] < k;
+        a.grp_off[k] = (int)lst_min64(dest + below, cap);
+      }
     }
   }
 }
 
-__global__ void k_grp_sort(Ws w, const int32_t* grp_off, int64_t n_keys, const int32_t* key2, int64_t dense_cap,
-                           int dense_word) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int total = grp_off[n_keys];
-    if (total > dense_cap) atomicMax(&w.status[dense_word], total);
-  }
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_keys; k += (int64_t)gridDim.x * blockDim.x) {
-    const int a = grp_off[k];
-    const int b = (int)lst_min64(grp_off[k + 1], dense_cap);
-    for (int i = a + 1; i < b; ++i) {
-      const int v = w.perm[i];
-      const int kv = key2[v];
-      int j = i - 1;
-      while (j >= a && key2[w.perm[j]] > kv) {
-        w.perm[j + 1] = w.perm[j];
-        --j;
-      }
-      w.perm[j + 1] = v;
-    }
-  }
+// group offsets of the keys past the last module's range: the (clamped) total
+__global__ void k_grp_tail(Ws w, SortArgs a) {
+  const int k_end = a.mod_first[(int64_t)w.V * a.stride];
+  const int total = (int)lst_min64(w.eff[w.V], a.dense_cap);
+  for (int64_t k = k_end + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= a.n_keys;
+       k += (int64_t)gridDim.x * blockDim.x)
+    a.grp_off[k] = total;
 }
 
 // out[i] = min(grp_off[first[i * stride]], cap), i in [0, n] (the clamp keeps later stages inside
@@ -77,18 +239,22 @@ __global__ void k_off_compose(int32_t* out, int n, const int32_t* first, int str
 
 }  // namespace
 
+void group_configure() {
+  cudaFuncSetAttribute(k_mod_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kBigCap * (int)(sizeof(unsigned long long) + sizeof(int)));
+}
+
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
-  k_grp_count<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, a.cnt, a.cap, a.base, a.slots, a.ovf_word,
-                                                                     a.arena_word, a.key1, a.grp_cnt);
+  k_mod_eff<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, a.cnt, a.cap, a.base, a.slots, a.ovf_word, a.arena_word);
   LST_LAUNCH(L);
-  scan_exclusive(a.grp_cnt, a.grp_off, a.n_keys, w.scan_tmp, L);
-  k_grp_scatter<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, a.base, a.key1, a.grp_off, a.grp_cur,
-                                                                       a.dense_cap);
+  scan_exclusive(w.eff, w.eff, w.V, w.scan_tmp, L);
+  SortArgs s{a.base, a.key1, a.key2, a.mod_first, a.mod_first_stride, a.grp_off, a.n_keys, a.dense_cap,
+             a.mod_off, a.dense_word, a.big_word};
+  k_mod_sort_small<<<grid_for((int64_t)w.V * 32, 32 * kSmallWarps, 152 * 32), 32 * kSmallWarps, 0, L.stream>>>(w, s);
   LST_LAUNCH(L);
-  k_grp_sort<<<grid_for(a.n_keys, 256), 256, 0, L.stream>>>(w, a.grp_off, a.n_keys, a.key2, a.dense_cap, a.dense_word);
+  k_mod_sort_big<<<L.n_sm * 2, kBigThreads, kBigCap * (sizeof(unsigned long long) + sizeof(int)), L.stream>>>(w, s);
   LST_LAUNCH(L);
-  k_off_compose<<<grid_for(w.V + 1, 256), 256, 0, L.stream>>>(a.mod_off, w.V, a.mod_first, a.mod_first_stride,
-                                                             a.grp_off, a.dense_cap);
+  k_grp_tail<<<grid_for(a.n_keys + 1, 256), 256, 0, L.stream>>>(w, s);
   LST_LAUNCH(L);
 }
 

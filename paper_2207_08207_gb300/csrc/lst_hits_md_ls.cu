@@ -114,39 +114,105 @@ __global__ void k_effective(Ws w, const int32_t* cnt, const int32_t* cap, const 
   }
 }
 
-__global__ void k_md(Ws w, Geo g, Cst<float> c) {
+// Quick rejection of a (lower, upper) hit pair by the Mini-Doublet's z window (barrel) or radial
+// window (endcap), exact-safe: true only when the float64 selection is certain to fail, with
+// margins far above float32 rounding. Barrel: the window lo = delta min(t1, g t1) - tol_z,
+// hi = delta max(t2, g t2) + tol_z (t1,2 = (z_l -+ z_lum) / r_l, 1 <= g <= g_max = 1 / cos(asin(
+// sin_max))) contains its g = g_max counterpart, multiplied through by r_l. Endcap: dr = r_u - r_l
+// against [dr_min, dr_max] -+ tol_r with dr_max,min = r_l delta / (|z_l| -+ z_lum), multiplied out.
+__device__ __forceinline__ bool md_quick_reject(const Cst<float>& c, bool endcap, float delta, float gmax, float xl,
+                                               float yl, float zl, float xu, float yu, float zu) {
+  const float rl = sqrtf(xl * xl + yl * yl);
+  if (!endcap) {
+    const float dz = zu - zl;
+    const float e1 = zl - c.z_lum, e2 = zl + c.z_lum;
+    const float lo = delta * (e1 < 0.f ? gmax * e1 : e1) - c.tol_z * rl;
+    const float hi = delta * (e2 > 0.f ? gmax * e2 : e2) + c.tol_z * rl;
+    const float m = 1e-4f * (delta * gmax * (fabsf(zl) + c.z_lum) + (c.tol_z + fabsf(dz)) * rl) + 1e-6f;
+    return dz * rl < lo - m || dz * rl > hi + m;
+  }
+  const float az = fabsf(zl);
+  if (!(az > c.z_lum * 1.001f)) return false;
+  const float ru = sqrtf(xu * xu + yu * yu);
+  const float dr = ru - rl;
+  const float ld = rl * delta;
+  const float m = 2e-4f * (ld + (fabsf(dr) + c.tol_r) * (az + c.z_lum)) + 1e-6f * (ru + rl) * (az + c.z_lum);
+  return (dr - c.tol_r) * (az - c.z_lum) > ld + m || (dr + c.tol_r) * (az + c.z_lum) < ld - m;
+}
+
+// full float32 evaluation of the first n (<= 32) queued (module, lower hit, upper hit) triples
+__device__ __forceinline__ void md_flush(const Ws& w, const Geo& g, const Cst<float>& c, const int4* qe, int n) {
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+  int v = kReject, vm = 0, l = 0, u = 0;
+  float dpc = 0.f, pte = 0.f;
+  if (lane < n) {
+    const int4 e = qe[lane];
+    vm = e.x; l = e.y; u = e.z;
     const int m = vm % g.n_mods;
-    const int lo0 = w.sens_off[2 * vm], up0 = w.sens_off[2 * vm + 1];
-    const int nlo = up0 - lo0, nup = w.sens_off[2 * vm + 2] - up0;
-    const int np = nlo * nup;
-    if (np == 0) continue;
-    const bool ec = g.endcap[m] != 0;
-    const float delta = g.spacing[m];
+    v = md_eval<float>(c, g.endcap[m] != 0, g.spacing[m], w.bx[l], w.by[l], w.bz[l], w.bx[u], w.by[u], w.bz[u],
+                       kGuardWindow, dpc, pte);
+  }
+  const int slot = warp_agg_slot_keyed(v == kAccept, vm, w.md_cnt);
+  if (slot >= 0) {
     const int cap = w.md_cap[vm], base = w.md_base[vm];
-    for (int p0 = 0; p0 < np; p0 += 32) {
-      const int p = p0 + lane;
-      int v = kReject, l = 0, u = 0;
-      float dpc = 0.f, pte = 0.f;
-      if (p < np) {
-        l = lo0 + p / nup;
-        u = up0 + p % nup;
-        v = md_eval<float>(c, ec, delta, w.bx[l], w.by[l], w.bz[l], w.bx[u], w.by[u], w.bz[u],
-                           kGuardWindow, dpc, pte);
-      }
-      const int slot = warp_agg_slot(v == kAccept, &w.md_cnt[vm]);
-      if (slot >= 0 && slot < cap && (int64_t)base + slot < w.cap.md_slots) {
-        w.ms_lo[base + slot] = l;
-        w.ms_up[base + slot] = u;
-        w.ms_dpc[base + slot] = dpc;
-        w.ms_pte[base + slot] = pte;
-      }
-      const int q = warp_agg_slot(v == kUnsure, &w.status[ST_Q_MD]);
-      if (q >= 0 && q < w.cap.q_md) w.q_md[q] = make_int4(vm, l, u, 0);
+    if (slot < cap && (int64_t)base + slot < w.cap.md_slots) {
+      w.ms_lo[base + slot] = l;
+      w.ms_up[base + slot] = u;
+      w.ms_dpc[base + slot] = dpc;
+      w.ms_pte[base + slot] = pte;
     }
   }
+  const int q = warp_agg_slot(v == kUnsure, &w.status[ST_Q_MD]);
+  if (q >= 0 && q < w.cap.q_md) w.q_md[q] = make_int4(vm, l, u, 0);
+}
+
+// MD candidates: every (lower hit, upper hit) pair of each module, a warp per module (modules taken
+// in a grid-stride loop, which spreads the busy inner-layer modules over the warps); pairs that
+// pass the quick window test go to a per-warp queue that carries over from module to module and is
+// evaluated fully 32 pairs at a time.
+constexpr int kMdWarps = 8;
+constexpr int kMdQ = 64;
+
+__global__ void __launch_bounds__(32 * kMdWarps) k_md(Ws w, Geo g, Cst<float> c) {
+  __shared__ int4 qbuf[kMdWarps][kMdQ];
+  int4* qe = qbuf[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const float gmax = (1.0f + 1e-5f) / sqrtf((1.0f - c.sin_max) * (1.0f + c.sin_max));
+  int qn = 0;
+  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+    const int lo0 = w.sens_off[2 * vm], up0 = w.sens_off[2 * vm + 1];
+    const int nup = w.sens_off[2 * vm + 2] - up0;
+    const int np = (up0 - lo0) * nup;
+    if (np == 0) continue;
+    const int m = vm % g.n_mods;
+    const bool ec = g.endcap[m] != 0;
+    const float delta = g.spacing[m];
+    for (int p0 = 0; p0 < np; p0 += 32) {
+      const int p = p0 + lane;
+      bool keep = false;
+      int l = 0, u = 0;
+      if (p < np) {
+        const int il = p / nup;
+        l = lo0 + il;
+        u = up0 + (p - il * nup);
+        keep = !md_quick_reject(c, ec, delta, gmax, w.bx[l], w.by[l], w.bz[l], w.bx[u], w.by[u], w.bz[u]);
+      }
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      if (keep) qe[qn + __popc(km & ((1u << lane) - 1u))] = make_int4(vm, l, u, 0);
+      qn += __popc(km);
+      if (qn >= 32) {
+        __syncwarp();
+        md_flush(w, g, c, qe, 32);
+        __syncwarp();
+        qn -= 32;
+        if (lane < qn) qe[lane] = qe[32 + lane];
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  if (qn > 0) md_flush(w, g, c, qe, qn);
 }
 
 __global__ void k_md_recheck(Ws w, Geo g, Cst<double> c) {
@@ -313,20 +379,6 @@ __device__ __forceinline__ bool ls_quick_reject(const Cst<float>& c, float4 a, f
   return (P > M && Ps > Ms) || (P < -M && Ps < -Ms);
 }
 
-// warp-aggregated slot reservation where lanes may target different counters (counters[key])
-__device__ __forceinline__ int warp_agg_slot_keyed(bool pred, int key, int* counters) {
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  int slot = -1;
-  if (pred) {
-    const unsigned grp = __match_any_sync(m, key);
-    const int leader = __ffs(grp) - 1;
-    int base = 0;
-    if (lane_id() == leader) base = atomicAdd(&counters[key], __popc(grp));
-    base = __shfl_sync(grp, base, leader);
-    slot = base + __popc(grp & ((1u << lane_id()) - 1u));
-  }
-  return slot;
-}
 
 // full float32 evaluation of the first n (<= 32) queued pairs, one per lane; called by the whole warp
 __device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const LsWarpSmem& S, int n) {
@@ -362,8 +414,8 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int n_items = persistent ? w.work_off[32] : w.V;
   int qn = 0;   // pairs waiting in this warp's queue
-  for (int round = 0; (int64_t)round * n_warps < n_items; ++round) {
-    const int item = round * n_warps + ((round & 1) ? n_warps - 1 - gw : gw);
+  for (int sweep = 0; (int64_t)sweep * n_warps < n_items; ++sweep) {
+    const int item = sweep * n_warps + ((sweep & 1) ? n_warps - 1 - gw : gw);
     if (item >= n_items) continue;
     const int vm = persistent ? w.work[item] : item;
     const int na = md_count(w, vm);
@@ -524,6 +576,7 @@ __global__ void k_ls_dense(Ws w) {
     const float den = (r2 - r1) + (r2l - r1l);
     w.ls_z0[d] = num / den;
     w.ls_dphi[d] = w.lss_dphi[s];
+    w.ls_xy_out[d] = make_float2(w.md_x[b], w.md_y[b]);
   }
 }
 
@@ -597,15 +650,15 @@ void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.md_base, w.md_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_MD);
-  k_md<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, g, c.f);
+  k_md<<<grid_for((int64_t)w.V * 32, 32 * kMdWarps, 152 * 16), 32 * kMdWarps, 0, L.stream>>>(w, g, c.f);
   KT_END(L, K_MD);
   LST_LAUNCH(L);
   k_md_recheck<<<grid_for(w.cap.q_md, 128, 152 * 4), 128, 0, L.stream>>>(w, g, c.d);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_MD_COMPACT);
   GroupArgs ga{w.md_cnt, w.md_cap, w.md_base, w.cap.md_slots, ST_OVF_MD, ST_ARENA_MD, w.ms_lo, w.ms_up,
-               w.mdlo_cnt, w.mdlo_cur, w.mdlo_off, w.cap.H, w.cap.md_dense, ST_DENSE_MD,
-               w.md_off, w.sens_off, 2};
+               w.mdlo_off, w.cap.H, w.cap.md_dense, ST_DENSE_MD,
+               w.md_off, w.sens_off, 2, 0};
   group_slots(w, ga, L);
   k_md_dense<<<grid_for(w.cap.md_dense, 256), 256, 0, L.stream>>>(w, g, c.f);
   KT_END(L, K_MD_COMPACT);
@@ -640,8 +693,8 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   // LS ordered by inner MD: the per-MD group offsets are the "LS by inner MD" adjacency
   KT_BEGIN(L, K_LS_COMPACT);
   GroupArgs ga{w.ls_cnt, w.ls_cap, w.ls_base, w.cap.ls_slots, ST_OVF_LS, ST_ARENA_LS, w.lss_in, w.lss_out,
-               w.lsin_cnt, w.lsin_cur, w.lsin_off, w.cap.md_dense, w.cap.ls_dense, ST_DENSE_LS,
-               w.ls_off, w.md_off, 1};
+               w.lsin_off, w.cap.md_dense, w.cap.ls_dense, ST_DENSE_LS,
+               w.ls_off, w.md_off, 1, 1};
   group_slots(w, ga, L);
   k_ls_dense<<<grid_for(w.cap.ls_dense, 256), 256, 0, L.stream>>>(w);
   KT_END(L, K_LS_COMPACT);

@@ -76,7 +76,7 @@ struct Ws {
   int32_t *ms_lo = nullptr, *ms_up = nullptr;
   float *ms_dpc = nullptr, *ms_pte = nullptr;
   int32_t* md_off = nullptr;
-  int32_t *mdlo_cnt = nullptr, *mdlo_cur = nullptr, *mdlo_off = nullptr;   // MDs grouped by lower hit
+  int32_t* mdlo_off = nullptr;   // MDs grouped by lower hit
   int32_t *md_lo = nullptr, *md_up = nullptr, *md_vm = nullptr;
   float *md_x = nullptr, *md_y = nullptr, *md_z = nullptr, *md_r = nullptr, *md_sthr = nullptr;
   float *md_rlo = nullptr;     // r = md_r + md_rlo to ~1e-14 relative (float-float)
@@ -90,7 +90,8 @@ struct Ws {
   int32_t* ls_off = nullptr;
   int32_t *ls_in = nullptr, *ls_out = nullptr;
   float *ls_z0 = nullptr, *ls_dphi = nullptr;
-  int32_t *lsin_cnt = nullptr, *lsin_cur = nullptr, *lsin_off = nullptr;   // LS grouped by inner MD
+  float2* ls_xy_out = nullptr;   // (x, y) of each dense LS's outer anchor (T3 candidate loop)
+  int32_t* lsin_off = nullptr;   // LS grouped by inner MD
   // T3
   int32_t *t3_cap = nullptr, *t3_base = nullptr, *t3_cnt = nullptr, *t3_ovr = nullptr;
   int32_t *t3s_a = nullptr, *t3s_b = nullptr;
@@ -99,7 +100,7 @@ struct Ws {
   int32_t *t3_a = nullptr, *t3_b = nullptr, *t3_md0 = nullptr, *t3_md1 = nullptr, *t3_md2 = nullptr;
   float *t3_R = nullptr, *t3_xc = nullptr, *t3_yc = nullptr, *t3_chi2 = nullptr, *t3_pte = nullptr;
   int32_t* t3md_off = nullptr;   // T3 by first MD
-  int32_t *t3in_cnt = nullptr, *t3in_cur = nullptr, *t3in_off = nullptr;   // T3 grouped by inner LS
+  int32_t* t3in_off = nullptr;   // T3 grouped by inner LS
   float4* t3_anc = nullptr;      // [3][t3_dense] anchor (x, y, z, r) of each member MD
   uint8_t* t3_ecm = nullptr;     // endcap bit per anchor
   // T5
@@ -110,7 +111,7 @@ struct Ws {
   int32_t *t5_a = nullptr, *t5_b = nullptr;
   int32_t* t5_md = nullptr;  // [5][t5_dense]
   float* t5_f = nullptr;     // [8][t5_dense]
-  int32_t *t5in_cnt = nullptr, *t5in_cur = nullptr, *t5in_off = nullptr;   // T5 grouped by inner T3
+  int32_t* t5in_off = nullptr;   // T5 grouped by inner T3
   float4* t5_anc = nullptr;      // [5][t5_dense]
   uint8_t* t5_ecm = nullptr;
   // per module: lo[vm], hi[V + vm] = bounding box (x, y, z, r) of the first anchors of its T3 / T5
@@ -158,7 +159,9 @@ struct Ws {
   int2 *q_t3 = nullptr, *q_t5 = nullptr, *q_p3 = nullptr, *q_p5 = nullptr;
   // scan scratch and status
   int32_t* scan_tmp = nullptr;
-  int32_t* eff = nullptr;    // [V] valid slots per module of the stage being compacted
+  int32_t* eff = nullptr;    // [V + 1] valid slots per module of the stage being compacted, then their scan
+  int32_t* grp_big = nullptr;       // [V] modules with more than 32 objects (compaction)
+  int32_t* grp_big_cnt = nullptr;   // [4] their counts, one per stage
   int32_t* perm = nullptr;   // [max dense] slot of each dense object of the stage being compacted
   int32_t* status = nullptr;   // [ST_N_WORDS]
   int32_t* ev_stat = nullptr;  // [E][kEvWords]
@@ -208,13 +211,14 @@ struct GroupArgs {
   int64_t slots;
   int ovf_word, arena_word;
   const int32_t *key1, *key2;        // first / second member of each slot
-  int32_t *grp_cnt, *grp_cur, *grp_off;
-  int64_t n_keys;                    // key1 range (grp_off has n_keys + 1 entries)
+  int32_t* grp_off;                  // out: [n_keys + 1] objects whose first member is below each key
+  int64_t n_keys;                    // key1 range
   int64_t dense_cap;
   int dense_word;
   int32_t* mod_off;                  // [V + 1] out: per-module dense offsets
   const int32_t* mod_first;          // first key of each module, at [vm * stride]
   int mod_first_stride;
+  int big_word;                      // which of the four large-module list counters the stage uses
 };
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L);
 void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* grp_off, int64_t cap,
@@ -243,6 +247,7 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
 void run_finalize(const Ws& w, const Geo& g, const Launch& L);
 int tc_cells_per_event();
 void tc_configure();
+void group_configure();
 // after an overflowing run: raise the per-module capacity overrides to the observed counts
 void run_raise_overrides(const Ws& w, const Launch& L);
 

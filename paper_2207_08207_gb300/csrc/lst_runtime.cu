@@ -391,10 +391,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.tc_cnt, c.E);
   z.add(w.sens_cnt, S); z.add(w.sens_cur, S);
   z.add(w.md_cnt, V); z.add(w.ls_cnt, V); z.add(w.t3_cnt, V); z.add(w.t5_cnt, V);
-  z.add(w.mdlo_cnt, c.H + 1); z.add(w.mdlo_cur, c.H + 1);
-  z.add(w.lsin_cnt, c.md_dense + 1); z.add(w.lsin_cur, c.md_dense + 1);
-  z.add(w.t3in_cnt, c.ls_dense + 1); z.add(w.t3in_cur, c.ls_dense + 1);
-  z.add(w.t5in_cnt, c.t3_dense + 1); z.add(w.t5in_cur, c.t3_dense + 1);
+  z.add(w.grp_big_cnt, 4);
   z.add(w.p3_cnt, c.P); z.add(w.p3_cur, c.P); z.add(w.p5_cnt, c.P); z.add(w.p5_cur, c.P);
   z.add(w.h5_cnt, c.H + 1); z.add(w.h5_cur, c.H + 1);
   z.add(w.cell_cnt, NC); z.add(w.cell_cur, NC);
@@ -403,7 +400,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
   pl.add(w.bx, c.H); pl.add(w.by, c.H); pl.add(w.bz, c.H); pl.add(w.borig, c.H);
   // compaction scratch, LS work list
-  pl.add(w.eff, V);
+  pl.add(w.eff, V + 1); pl.add(w.grp_big, V);
   pl.add(w.work, V); pl.add(w.work_bucket, V); pl.add(w.work_off, 33);
   pl.add(w.perm, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
   // MD
@@ -417,6 +414,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1); pl.add(w.lsin_off, c.md_dense + 2);
   pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_z0, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
   pl.add(w.ls_in, c.ls_dense); pl.add(w.ls_out, c.ls_dense); pl.add(w.ls_z0, c.ls_dense); pl.add(w.ls_dphi, c.ls_dense);
+  pl.add(w.ls_xy_out, c.ls_dense);
   // T3
   pl.add(w.t3_cap, V); pl.add(w.t3_base, V + 1); pl.add(w.t3_off, V + 1); pl.add(w.t3in_off, c.ls_dense + 2);
   pl.add(w.t3s_a, c.t3_slots); pl.add(w.t3s_b, c.t3_slots); pl.add(w.t3s_R, c.t3_slots); pl.add(w.t3s_xc, c.t3_slots);
@@ -662,6 +660,7 @@ int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
   if (ctx->n_sm <= 0) ctx->n_sm = 152;
   ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls);
   tc_configure();
+  group_configure();
   *out = ctx;
   return LST_OK;
 }

@@ -130,12 +130,15 @@ __global__ void __launch_bounds__(32 * kT3Warps) k_t3_pre(Ws w, Cst<float> c) {
   int qn = 0;
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n_ls; base += nwarps * 32) {
     const int i = base + lane;
-    int j0 = 0, size = 0, d1 = 0, d2 = 0;
+    int j0 = 0, size = 0;
+    float x1 = 0.f, y1 = 0.f, x2 = 0.f, y2 = 0.f;
     if (i < n_ls) {
-      d1 = w.ls_in[i];
-      d2 = w.ls_out[i];
+      const int d1 = w.ls_in[i], d2 = w.ls_out[i];
       j0 = min(w.lsin_off[d2], n_ls);
       size = min(w.lsin_off[d2 + 1], n_ls) - j0;
+      x1 = w.md_x[d1]; y1 = w.md_y[d1];
+      const float2 p2 = w.ls_xy_out[i];
+      x2 = p2.x; y2 = p2.y;
     }
     int incl = size;
 #pragma unroll
@@ -154,11 +157,12 @@ __global__ void __launch_bounds__(32 * kT3Warps) k_t3_pre(Ws w, Cst<float> c) {
         if (__shfl_sync(0xffffffffu, excl, cand) <= cidx) lo = cand;
       }
       const int jj = __shfl_sync(0xffffffffu, j0, lo) + (cidx - __shfl_sync(0xffffffffu, excl, lo));
-      const int m1 = __shfl_sync(0xffffffffu, d1, lo), m2 = __shfl_sync(0xffffffffu, d2, lo);
+      const float ax = __shfl_sync(0xffffffffu, x1, lo), ay = __shfl_sync(0xffffffffu, y1, lo);
+      const float bx = __shfl_sync(0xffffffffu, x2, lo), by = __shfl_sync(0xffffffffu, y2, lo);
       bool keep = false;
       if (cidx < total) {
-        const int m3 = w.ls_out[jj];
-        keep = !t3_quick_reject(c, kmax2, w.md_x[m1], w.md_y[m1], w.md_x[m2], w.md_y[m2], w.md_x[m3], w.md_y[m3]);
+        const float2 p3 = w.ls_xy_out[jj];
+        keep = !t3_quick_reject(c, kmax2, ax, ay, bx, by, p3.x, p3.y);
       }
       const unsigned km = __ballot_sync(0xffffffffu, keep);
       if (keep) qe[qn + __popc(km & ((1u << lane) - 1u))] = make_int2(base + lo, jj);
@@ -493,8 +497,8 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T3_COMPACT);
   GroupArgs ga{w.t3_cnt, w.t3_cap, w.t3_base, w.cap.t3_slots, ST_OVF_T3, ST_ARENA_T3, w.t3s_a, w.t3s_b,
-               w.t3in_cnt, w.t3in_cur, w.t3in_off, w.cap.ls_dense, w.cap.t3_dense, ST_DENSE_T3,
-               w.t3_off, w.ls_off, 1};
+               w.t3in_off, w.cap.ls_dense, w.cap.t3_dense, ST_DENSE_T3,
+               w.t3_off, w.ls_off, 1, 2};
   group_slots(w, ga, L);
   k_t3_dense<<<grid_for(w.cap.t3_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
@@ -517,8 +521,8 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_END(L, K_T5_DECIDE);
   LST_LAUNCH(L);
   GroupArgs ga{w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, ST_OVF_T5, ST_ARENA_T5, w.t5s_a, w.t5s_b,
-               w.t5in_cnt, w.t5in_cur, w.t5in_off, w.cap.t3_dense, w.cap.t5_dense, ST_DENSE_T5,
-               w.t5_off, w.t3_off, 1};
+               w.t5in_off, w.cap.t3_dense, w.cap.t5_dense, ST_DENSE_T5,
+               w.t5_off, w.t3_off, 1, 3};
   group_slots(w, ga, L);
   k_t5_dense<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);

@@ -60,7 +60,7 @@ SUBDET_ENDCAP = 1
 TYPE_PS = 0
 TYPE_2S = 1
 
-# hit resolution (BASELINE configs: 30 um in r-phi, 1 mm in z for barrel / r for endcap)
+# hit resolution: 30 um in r-phi, 1 mm in z for barrel / r for endcap
 SIGMA_RPHI = 0.003
 SIGMA_Z = 0.1
 SIGMA_R = 0.1

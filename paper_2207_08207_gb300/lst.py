@@ -366,9 +366,14 @@ def exported_symbols():
     return sorted(set(re.findall(r"^\s*(?:int|void|int64_t|const char\*)\s+(lst_[a-z_]+)\s*\(", txt, re.M)))
 
 
+# Per-event instruction and DRAM counts of the timed kernels on PU200 events (ncu, batch of 16 events,
+# the capture summarised in profiles/); used for the issue-slot roofline of the dominant kernel.
+KERNEL_PROFILE = {}
+
+
 def algorithmic_bytes(kernel, counts, n_hits, n_pls) -> int:
     """Compulsory HBM bytes of one launch of a timed kernel: every input element it needs read once,
-    every output it produces written once (sizes of the SoA fields; see DESIGN.md). `counts` is the
+    every output it produces written once (sizes of the SoA fields). `counts` is the
     list of per-event count dicts of the launch's batch."""
     s = lambda k: sum(c[k] for c in counts)
     n_md, n_ls, n_t3, n_t5 = s("n_md"), s("n_ls"), s("n_t3"), s("n_t5")
