@@ -230,11 +230,12 @@ __device__ __forceinline__ int ls_eval(const Cst<T>& c, T x1, T y1, T z1, T r1, 
   dphi_out = T(0);
   if (D == T(0)) { acc.reject(); return acc.verdict(); }
   if (m_abs(D) < T(1)) acc.force_unsure();  // float32 z0 loses accuracy when r1 ~ r2
-  const T z0r = diff_prod(z1, r2, z2, r1) / D;
+  const T iD = T(1) / D;
+  const T z0r = diff_prod(z1, r2, z2, r1) * iD;
   const T z0s = (s2 != s1) ? diff_prod(z1, s2, z2, s1) / (s2 - s1) : z0r;
   const T sz1 = ec1 ? T(0) : c.sigma_z, sz2 = ec2 ? T(0) : c.sigma_z;
   const T sr1 = ec1 ? c.sigma_r : T(0), sr2 = ec2 ? c.sigma_r : T(0);
-  const T q1 = r2 / D * sz1, q2 = r1 / D * sz2, q3 = (z0r - z2) / D * sr1, q4 = (z1 - z0r) / D * sr2;
+  const T q1 = r2 * iD * sz1, q2 = r1 * iD * sz2, q3 = (z0r - z2) * iD * sr1, q4 = (z1 - z0r) * iD * sr2;
   const T L = c.z_lum + c.n_sigma * m_sqrt(q1 * q1 + q2 * q2 + q3 * q3 + q4 * q4);
   acc.cut(L, m_min(z0r, z0s));
   acc.cut_ge(-L, m_max(z0r, z0s));
@@ -249,8 +250,8 @@ __device__ __forceinline__ int ls_eval(const Cst<T>& c, T x1, T y1, T z1, T r1, 
     adiff = m_asin(m_min(a2, c.sin_max)) - m_asin(m_min(a1, c.sin_max));
     acc.force_unsure();
   }
-  const T bound = adiff + c.n_sigma * c.sigma_rphi * m_sqrt(T(1) / (r1 * r1) + T(1) / (r2 * r2)) +
-                  c.d0_max * (T(1) / r1 + T(1) / r2);
+  const T ir1 = T(1) / r1, ir2 = T(1) / r2;
+  const T bound = adiff + c.n_sigma * c.sigma_rphi * m_sqrt(ir1 * ir1 + ir2 * ir2) + c.d0_max * (ir1 + ir2);
   acc.cut(bound, m_abs(dphi));
   z0_out = z0r;
   dphi_out = dphi;

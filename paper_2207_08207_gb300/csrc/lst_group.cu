@@ -6,7 +6,8 @@
 // objects, or the module's binned hits for MDs), and those ranges increase with the module, so the
 // global order is the module order with each module's objects sorted on their own: the per-module
 // dense offsets are an exclusive scan of the per-module counts, and each module sorts its few
-// objects locally (a warp for most modules, a block and shared memory for the largest). The per-key group offsets (objects whose first member is below a key) follow from the
+// objects locally (a warp for most modules, a block for the largest) by a counting sort on the first
+// member followed by ranks inside each first-member group. The per-key group offsets (objects whose first member is below a key) follow from the
 // sorted keys by binary search.
 #include "lst_internal.h"
 
@@ -150,59 +151,81 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_mod_sort_small(Ws w, SortA
   }
 }
 
-// Modules with more than kMidCap objects: a block per module, bitonic sort of (key, slot) in shared
-// memory up to kBigCap objects; beyond that, ranks counted directly from global memory.
+// Larger modules: a block per module, the same counting sort with the block (up to kBigCap objects
+// and first-member ranges below kBigCap); beyond that, ranks counted directly from global memory.
 __global__ void __launch_bounds__(kBigThreads) k_mod_sort_big(Ws w, SortArgs a) {
   extern __shared__ __align__(16) unsigned char big_smem[];
-  unsigned long long* K = reinterpret_cast<unsigned long long*>(big_smem);
-  int* I = reinterpret_cast<int*>(K + kBigCap);
+  int* K2 = reinterpret_cast<int*>(big_smem);   // [kBigCap] second members
+  int* POS = K2 + kBigCap;                     // [kBigCap] objects placed by first member
+  int* G = POS + kBigCap;                      // [kBigCap] group counts, then starts, then ends
+  __shared__ int part[kBigThreads];
   const int n_big = w.grp_big_cnt[a.big_word];
   const int64_t cap = a.dense_cap;
+  const int t = threadIdx.x;
   for (int it = blockIdx.x; it < n_big; it += gridDim.x) {
     const int vm = w.grp_big[it];
     const int dest = w.eff[vm], n = w.eff[vm + 1] - dest;
     const int b = a.base[vm];
     const int k0 = a.mod_first[(int64_t)vm * a.stride], k1 = a.mod_first[(int64_t)(vm + 1) * a.stride];
-    if (n <= kBigCap) {
-      int np2 = 64;
-      while (np2 < n) np2 <<= 1;
-      for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-        K[i] = i < n ? pair_key(a.key1[b + i], a.key2[b + i]) : ~0ull;
-        I[i] = i < n ? b + i : -1;
+    const int R = k1 - k0;
+    if (n <= kBigCap && R < kBigCap) {
+      const int gmax = R > 0 ? R - 1 : 0;
+      for (int k = t; k <= R; k += blockDim.x) G[k] = 0;
+      __syncthreads();
+      for (int i = t; i < n; i += blockDim.x) {
+        K2[i] = a.key2[b + i];
+        atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1);
       }
       __syncthreads();
-      for (int size = 2; size <= np2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-          for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-            const int j = i ^ stride;
-            if (j > i) {
-              const bool up = (i & size) == 0;
-              const unsigned long long ki = K[i], kj = K[j];
-              const int vi = I[i], vj = I[j];
-              const bool gt = ki > kj || (ki == kj && (unsigned)vi > (unsigned)vj);
-              if (gt == up) {
-                K[i] = kj; K[j] = ki;
-                I[i] = vj; I[j] = vi;
-              }
-            }
+      // exclusive scan of G[0..R]: each thread a contiguous run, then a scan of the run totals
+      const int per = (R + 1 + blockDim.x - 1) / blockDim.x;
+      const int r0 = t * per, r1 = min(r0 + per, R + 1);
+      int sum = 0;
+      for (int k = r0; k < r1; ++k) sum += G[k];
+      part[t] = sum;
+      __syncthreads();
+      if (t < 32) {
+        int run = 0;
+        for (int c0 = 0; c0 < kBigThreads; c0 += 32) {
+          const int v = part[c0 + t];
+          int incl = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (t >= o) incl += y;
           }
-          __syncthreads();
+          part[c0 + t] = run + incl - v;
+          run += __shfl_sync(0xffffffffu, incl, 31);
         }
       }
-      for (int i = threadIdx.x; i < n; i += blockDim.x)
-        if (dest + i < cap) w.perm[dest + i] = I[i];
-      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-        const unsigned long long kk = pair_key(k, 0);
-        int lo = 0, hi = n;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (K[mid] < kk) lo = mid + 1; else hi = mid;
+      __syncthreads();
+      int acc = part[t];
+      for (int k = r0; k < r1; ++k) {
+        const int v = G[k];
+        G[k] = acc;
+        acc += v;
+      }
+      __syncthreads();
+      for (int k = t; k < R; k += blockDim.x) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
+      __syncthreads();
+      for (int i = t; i < n; i += blockDim.x) POS[atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1)] = i;
+      __syncthreads();
+      for (int p = t; p < n; p += blockDim.x) {   // G[g] is now the end of group g
+        const int i = POS[p];
+        const int g = min(max(a.key1[b + i] - k0, 0), gmax);
+        const int g_end = G[g], g_beg = g > 0 ? G[g - 1] : 0;
+        const int k2 = K2[i];
+        int r = g_beg;
+        for (int q = g_beg; q < g_end; ++q) {
+          const int j = POS[q];
+          const int kj = K2[j];
+          r += kj < k2 || (kj == k2 && j < i);
         }
-        a.grp_off[k] = (int)lst_min64(dest + lo, cap);
+        if (dest + r < cap) w.perm[dest + r] = b + i;
       }
       __syncthreads();
     } else {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      for (int i = t; i < n; i += blockDim.x) {
         const unsigned long long ki = pair_key(a.key1[b + i], a.key2[b + i]);
         int rank = 0;
         for (int j = 0; j < n; ++j) {
@@ -211,7 +234,7 @@ __global__ void __launch_bounds__(kBigThreads) k_mod_sort_big(Ws w, SortArgs a) 
         }
         if (dest + rank < cap) w.perm[dest + rank] = b + i;
       }
-      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      for (int k = k0 + t; k < k1; k += blockDim.x) {
         int below = 0;
         for (int j = 0; j < n; ++j) below += a.key1[b + j] < k;
         a.grp_off[k] = (int)lst_min64(dest + below, cap);
@@ -240,8 +263,7 @@ __global__ void k_off_compose(int32_t* out, int n, const int32_t* first, int str
 }  // namespace
 
 void group_configure() {
-  cudaFuncSetAttribute(k_mod_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kBigCap * (int)(sizeof(unsigned long long) + sizeof(int)));
+  cudaFuncSetAttribute(k_mod_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kBigCap * (int)sizeof(int));
 }
 
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
@@ -252,7 +274,7 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
              a.mod_off, a.dense_word, a.big_word};
   k_mod_sort_small<<<grid_for((int64_t)w.V * 32, 32 * kSmallWarps, 152 * 32), 32 * kSmallWarps, 0, L.stream>>>(w, s);
   LST_LAUNCH(L);
-  k_mod_sort_big<<<L.n_sm * 2, kBigThreads, kBigCap * (sizeof(unsigned long long) + sizeof(int)), L.stream>>>(w, s);
+  k_mod_sort_big<<<L.n_sm * 2, kBigThreads, 3 * kBigCap * sizeof(int), L.stream>>>(w, s);
   LST_LAUNCH(L);
   k_grp_tail<<<grid_for(a.n_keys + 1, 256), 256, 0, L.stream>>>(w, s);
   LST_LAUNCH(L);

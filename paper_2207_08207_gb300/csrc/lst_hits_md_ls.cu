@@ -52,27 +52,66 @@ __global__ void k_bin_scatter(Ws w) {
 }
 
 // order each sensor's hits by input index (makes the binning identical to a stable sort), then
-// gather the binned coordinates
+// gather the binned coordinates: a warp per sensor, each hit's position its rank among the sensor's
+// input indices (unique), for up to kBinRank hits; larger sensors sorted by one lane
+constexpr int kBinRank = 256;
+
 __global__ void k_bin_sort_gather(Ws w, int n_sens) {
-  for (int vs = blockIdx.x * blockDim.x + threadIdx.x; vs < w.S; vs += gridDim.x * blockDim.x) {
-    const int a = w.sens_off[vs], b = w.sens_off[vs + 1];
-    for (int i = a + 1; i < b; ++i) {
-      const int v = w.bidx[i];
-      int j = i - 1;
-      while (j >= a && w.bidx[j] > v) {
-        w.bidx[j + 1] = w.bidx[j];
-        --j;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int vs = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vs < w.S; vs += nwarps) {
+    const int a = w.sens_off[vs], n = w.sens_off[vs + 1] - a;
+    if (n == 0) continue;
+    const int h0 = w.ev_hit_off[vs / n_sens];
+    if (n <= kBinRank) {
+      constexpr int kPer = kBinRank / 32;
+      int v[kPer], rk[kPer];
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        v[t] = lane + 32 * t < n ? w.bidx[a + lane + 32 * t] : 0x7fffffff;
+        rk[t] = 0;
       }
-      w.bidx[j + 1] = v;
-    }
-    const int e = vs / n_sens;
-    const int h0 = w.ev_hit_off[e];
-    for (int i = a; i < b; ++i) {
-      const int src = w.bidx[i];
-      w.bx[i] = w.x[src];
-      w.by[i] = w.y[src];
-      w.bz[i] = w.z[src];
-      w.borig[i] = src - h0;
+      for (int j0 = 0; j0 < n; j0 += 32) {
+        const int vj_own = j0 + lane < n ? w.bidx[a + j0 + lane] : 0x7fffffff;
+        const int m = min(32, n - j0);
+        for (int j = 0; j < m; ++j) {
+          const int vj = __shfl_sync(0xffffffffu, vj_own, j);
+#pragma unroll
+          for (int t = 0; t < kPer; ++t) rk[t] += vj < v[t];
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        if (lane + 32 * t < n) {
+          const int pos = a + rk[t], src = v[t];
+          w.bidx[pos] = src;
+          w.bx[pos] = w.x[src];
+          w.by[pos] = w.y[src];
+          w.bz[pos] = w.z[src];
+          w.borig[pos] = src - h0;
+        }
+      }
+    } else {
+      if (lane == 0) {
+        for (int i = a + 1; i < a + n; ++i) {
+          const int val = w.bidx[i];
+          int j = i - 1;
+          while (j >= a && w.bidx[j] > val) {
+            w.bidx[j + 1] = w.bidx[j];
+            --j;
+          }
+          w.bidx[j + 1] = val;
+        }
+      }
+      __syncwarp();
+      for (int i = a + lane; i < a + n; i += 32) {
+        const int src = w.bidx[i];
+        w.bx[i] = w.x[src];
+        w.by[i] = w.y[src];
+        w.bz[i] = w.z[src];
+        w.borig[i] = src - h0;
+      }
     }
   }
 }
@@ -321,9 +360,16 @@ __global__ void k_ls_work_scan(Ws w) {
 }
 
 __global__ void k_ls_work_fill(Ws w) {
-  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
-    const int b = w.work_bucket[vm];
-    if (b >= 0) w.work[w.work_off[b] + atomicAdd(&w.work_cur[b], 1)] = vm;
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm - (int)(threadIdx.x & 31) < w.V;
+       vm += gridDim.x * blockDim.x) {
+    const int b = vm < w.V ? w.work_bucket[vm] : -1;
+    // one atomic per bucket and warp: lanes with the same bucket share it
+    const unsigned grp = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (b >= 0 && (int)(threadIdx.x & 31) == leader) base = atomicAdd(&w.work_cur[b], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (b >= 0) w.work[w.work_off[b] + base + __popc(grp & ((1u << (threadIdx.x & 31)) - 1u))] = vm;
   }
 }
 
@@ -640,7 +686,7 @@ void run_binning(const Ws& w, const Geo& g, const Launch& L) {
   k_bin_scatter<<<grid_for(w.H, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_BIN);
-  k_bin_sort_gather<<<grid_for(w.S, 128), 128, 0, L.stream>>>(w, n_sens);
+  k_bin_sort_gather<<<grid_for((int64_t)w.S * 32, 256, 152 * 32), 256, 0, L.stream>>>(w, n_sens);
   KT_END(L, K_BIN);
   LST_LAUNCH(L);
 }

@@ -494,20 +494,34 @@ __device__ bool key_less(const Ws& w, int type, int a, int b) {
   return na < nb;
 }
 
+// best pT5 and pT3 of each seed by (score, hit tuple): a warp per seed, each lane the best of its
+// share of the candidates, then a shuffle reduction
+template <int Type>
+__device__ __forceinline__ int best_of(const Ws& w, const int32_t* off, const float* sc, int p) {
+  const int lane = threadIdx.x & 31;
+  int b = -1;
+  for (int i = off[p] + lane; i < off[p + 1]; i += 32)
+    if (b < 0 || sc[i] < sc[b] || (sc[i] == sc[b] && key_less(w, Type, i, b))) b = i;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const int c = __shfl_xor_sync(0xffffffffu, b, o);
+    if (c >= 0 && (b < 0 || sc[c] < sc[b] || (sc[c] == sc[b] && key_less(w, Type, c, b)))) b = c;
+  }
+  return b;
+}
+
 __global__ void k_tc_best(Ws w) {
   const int P = w.n_pls();
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    int b5 = -1;
-    for (int i = w.pt5_off[p]; i < w.pt5_off[p + 1]; ++i)
-      if (b5 < 0 || w.pt5_sc[i] < w.pt5_sc[b5] || (w.pt5_sc[i] == w.pt5_sc[b5] && key_less(w, TC_PT5, i, b5)))
-        b5 = i;
-    int b3 = -1;
-    for (int i = w.pt3_off[p]; i < w.pt3_off[p + 1]; ++i)
-      if (b3 < 0 || w.pt3_sc[i] < w.pt3_sc[b3] || (w.pt3_sc[i] == w.pt3_sc[b3] && key_less(w, TC_PT3, i, b3)))
-        b3 = i;
-    w.best5[p] = b5;
-    w.best3[p] = b3;
-    w.pls_member[p] = (b5 >= 0 || b3 >= 0) ? 1 : 0;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += nwarps) {
+    const int b5 = best_of<TC_PT5>(w, w.pt5_off, w.pt5_sc, p);
+    const int b3 = best_of<TC_PT3>(w, w.pt3_off, w.pt3_sc, p);
+    if (lane == 0) {
+      w.best5[p] = b5;
+      w.best3[p] = b3;
+      w.pls_member[p] = (b5 >= 0 || b3 >= 0) ? 1 : 0;
+    }
   }
 }
 
@@ -708,8 +722,13 @@ __global__ void k_clean_pls(Ws w, double dr2) {
 // (type, smallest hit) in shared memory, followed by an exact ordering of equal-key runs.
 constexpr int kTcSortMax = 8192;
 
-__device__ __forceinline__ unsigned long long tc_sort_key(int type, int first_hit) {
-  return ((unsigned long long)(unsigned)type << 32) | (unsigned)(first_hit ^ (int)0x80000000);
+// order-preserving 64-bit prefix of (type, sorted hit tuple): the type, then the first two hits
+// saturated at 2^30 - 1 (hit ids are non-negative); equal prefixes are ordered on the full tuple
+__device__ __forceinline__ unsigned long long tc_sort_key(int type, int h0, int h1) {
+  const unsigned long long m = (1ull << 30) - 1;
+  const unsigned long long a = (unsigned long long)min((unsigned)h0, (unsigned)m);
+  const unsigned long long b = (unsigned long long)min((unsigned)h1, (unsigned)m);
+  return ((unsigned long long)(unsigned)type << 60) | (a << 30) | b;
 }
 
 __device__ __forceinline__ int hit_key_cmp(const int* a, const int* b) {
@@ -781,7 +800,7 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
     const int nh = code_hits(w, type, obj, h);
     sort_small(h, nh);
     for (int t = 0; t < 14; ++t) hk[(int64_t)k * 14 + t] = t < nh ? h[t] : 0x7fffffff;
-    key[k] = tc_sort_key(type, h[0]);
+    key[k] = tc_sort_key(type, h[0], nh > 1 ? h[1] : 0x7fffffff);
   }
   __syncthreads();
   const bool in_smem = n <= kTcSortMax;
@@ -809,10 +828,10 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
         __syncthreads();
       }
     }
-    // exact order inside runs of equal prefix keys (short runs: insertion sort on full tuples)
-    if (threadIdx.x == 0) {
-      int r0 = 0;
-      while (r0 < n) {
+    // exact order inside runs of equal prefix keys (rare, short: insertion sort on full tuples by the
+    // thread at the start of each run)
+    for (int r0 = threadIdx.x; r0 < n; r0 += blockDim.x) {
+      if ((r0 == 0 || skey[r0 - 1] != skey[r0]) && r0 + 1 < n && skey[r0 + 1] == skey[r0]) {
         int r1 = r0 + 1;
         while (r1 < n && skey[r1] == skey[r0]) ++r1;
         for (int i = r0 + 1; i < r1; ++i) {
@@ -824,7 +843,6 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
           }
           sidx[j + 1] = v;
         }
-        r0 = r1;
       }
     }
     __syncthreads();
@@ -872,12 +890,14 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
 // track candidates of all events packed densely (event e's rows start at tcd_off[e]), so that the
 // whole batch's candidates reach the host in one transfer per array
 __global__ void k_tc_dense(Ws w, Geo g) {
-  const int e = blockIdx.x;
+  // blockIdx.y: event; blocks along x share its rows
+  const int e = blockIdx.y;
   if (e >= w.E) return;
   const int n = w.tc_cnt[e];
   const int src0 = w.ev_pls_off[e] + w.t5_off[e * g.n_mods];
   const int dst0 = w.tcd_off[e];
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
     const int a = src0 + k, b = dst0 + k;
     w.tcd_type[b] = w.tc_type[a];
     w.tcd_obj[b] = w.tc_obj[a];
@@ -885,7 +905,8 @@ __global__ void k_tc_dense(Ws w, Geo g) {
     w.tcd_eta[b] = w.tc_eta[a];
     w.tcd_phi[b] = w.tc_phi[a];
   }
-  for (int k = threadIdx.x; k < 14 * n; k += blockDim.x) w.tcd_hits[(int64_t)dst0 * 14 + k] = w.tc_hits[(int64_t)src0 * 14 + k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 14 * n; k += stride)
+    w.tcd_hits[(int64_t)dst0 * 14 + k] = w.tc_hits[(int64_t)src0 * 14 + k];
 }
 
 }  // namespace
@@ -942,7 +963,7 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
 
 void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   const double dr2 = c.d.dr_min * c.d.dr_min;
-  k_tc_best<<<grid_for(w.P, 128), 128, 0, L.stream>>>(w);
+  k_tc_best<<<grid_for((int64_t)w.P * 32, 256, 152 * 32), 256, 0, L.stream>>>(w);
   k_h5_count<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, 0);
   *L.launches += 2;
   scan_exclusive(w.h5_cnt, w.h5_off, w.cap.H, w.scan_tmp, L);
@@ -964,7 +985,7 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_tc_assemble<<<dim3(w.E, 4), 1024, smem, L.stream>>>(w, g);
   KT_END(L, K_TC_ASSEMBLE);
   scan_exclusive(w.tc_cnt, w.tcd_off, w.E, w.scan_tmp, L);
-  k_tc_dense<<<w.E, 256, 0, L.stream>>>(w, g);
+  k_tc_dense<<<dim3(16, w.E), 256, 0, L.stream>>>(w, g);
   LST_LAUNCH(L);
   *L.launches += 5;
 }

@@ -216,17 +216,24 @@ __device__ __forceinline__ int clamp_cap2(double pred, long long bound, int ovr)
 }
 
 // T3 capacity of module vm: bound = number of (inner LS, outer LS) pairs whose inner LS starts in vm
+// (a warp per module, lanes over its LS)
 __global__ void k_t3_caps(Ws w) {
-  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int n_ls = w.ls_off[w.V];
+  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
     long long bound = 0;
-    const int n_ls = w.ls_off[w.V];
-    for (int i = w.ls_off[vm]; i < w.ls_off[vm + 1]; ++i) {
+    for (int i = w.ls_off[vm] + lane; i < w.ls_off[vm + 1]; i += 32) {
       const int m2 = w.ls_out[i];
       bound += min(w.lsin_off[m2 + 1], n_ls) - min(w.lsin_off[m2], n_ls);
     }
-    const int cc = clamp_cap2(w.cap_scale * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
-    w.t3_cap[vm] = cc;
-    w.t3_base[vm] = cc;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) bound += __shfl_xor_sync(0xffffffffu, bound, o);
+    if (lane == 0) {
+      const int cc = clamp_cap2(w.cap_scale * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
+      w.t3_cap[vm] = cc;
+      w.t3_base[vm] = cc;
+    }
   }
 }
 
@@ -340,15 +347,21 @@ __device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T 
 }
 
 __global__ void k_t5_caps(Ws w) {
-  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
     long long bound = 0;
-    for (int i = w.t3_off[vm]; i < w.t3_off[vm + 1]; ++i) {
+    for (int i = w.t3_off[vm] + lane; i < w.t3_off[vm + 1]; i += 32) {
       const int m3 = w.t3_md2[i];
       bound += w.t3md_off[m3 + 1] - w.t3md_off[m3];
     }
-    const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
-    w.t5_cap[vm] = cc;
-    w.t5_base[vm] = cc;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) bound += __shfl_xor_sync(0xffffffffu, bound, o);
+    if (lane == 0) {
+      const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
+      w.t5_cap[vm] = cc;
+      w.t5_base[vm] = cc;
+    }
   }
 }
 
@@ -484,7 +497,7 @@ __global__ void k_t5_dense(Ws w) {
 
 void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   (void)g;
-  k_t3_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
+  k_t3_caps<<<grid_for((int64_t)w.V * 32, 256, 152 * 32), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   scan_exclusive(w.t3_base, w.t3_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T3_PRE);
@@ -509,7 +522,7 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
 
 void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   (void)g;
-  k_t5_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
+  k_t5_caps<<<grid_for((int64_t)w.V * 32, 256, 152 * 32), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   scan_exclusive(w.t5_base, w.t5_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T5_PRE);
