@@ -86,10 +86,12 @@ typedef struct {
   int32_t persistent;       /* 1: persistent kernels pulling (event, module) work items */
   int32_t use_graph;        /* 1: capture the MD->TC chain in a CUDA graph and replay it */
   int32_t block_ls;         /* threads per LS block (64, 128, 256) */
-  int32_t warps_px;         /* warps per block in the pT3/pT5 candidate kernels */
+  int32_t warps_px;         /* warps per block in the pT3/pT5 candidate kernels (1..8; else 4) */
   float cap_scale;          /* multiplier on predicted per-module capacities (>= 0.25) */
   int32_t max_retries;      /* capacity-overflow retries before LST_EOVERFLOW_UNRESOLVED */
-  int64_t cycle_budget;     /* per-block clock64 budget of the candidate kernels; 0 = none */
+  int64_t cycle_budget;     /* per-warp clock64 budget of the candidate kernels (MD, LS, T3, pT3/pT5 loops);
+                               0 = none. A warp past it stops taking work and the run ends with
+                               LST_ETIMEOUT (results incomplete; the context stays usable) */
 } lst_config;
 
 /* One detector module (a pair of closely spaced sensors, "bi-layer pT module", Sec. 1). */

@@ -52,66 +52,106 @@ __global__ void k_bin_scatter(Ws w) {
 }
 
 // order each sensor's hits by input index (makes the binning identical to a stable sort), then
-// gather the binned coordinates: a warp per sensor, each hit's position its rank among the sensor's
-// input indices (unique), for up to kBinRank hits; larger sensors sorted by one lane
-constexpr int kBinRank = 256;
+// gather the binned coordinates. Groups of 8 lanes take one sensor each (4 per warp); a hit's
+// position is its rank among the sensor's input indices (unique). Sensors with more than 64 hits
+// are taken by the whole warp (ranks up to 256 hits, else one lane's insertion sort).
+constexpr int kBinG = 8;      // lanes per sensor
+constexpr int kBinPer = 8;    // hits per lane in the grouped path
+
+__device__ __forceinline__ void bin_gather(Ws& w, int pos, int src, int h0) {
+  w.bidx[pos] = src;
+  w.bx[pos] = w.x[src];
+  w.by[pos] = w.y[src];
+  w.bz[pos] = w.z[src];
+  w.borig[pos] = src - h0;
+}
 
 __global__ void k_bin_sort_gather(Ws w, int n_sens) {
   const int lane = threadIdx.x & 31;
+  const int tile = lane / kBinG, sub = lane % kBinG;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vs = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vs < w.S; vs += nwarps) {
-    const int a = w.sens_off[vs], n = w.sens_off[vs + 1] - a;
-    if (n == 0) continue;
-    const int h0 = w.ev_hit_off[vs / n_sens];
-    if (n <= kBinRank) {
-      constexpr int kPer = kBinRank / 32;
-      int v[kPer], rk[kPer];
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; base < w.S; base += nwarps * 4) {
+    const int vs = base + tile;
+    const bool valid = vs < w.S;
+    const int a = valid ? w.sens_off[vs] : 0;
+    const int n = valid ? w.sens_off[vs + 1] - a : 0;
+    int nmax = n;
 #pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        v[t] = lane + 32 * t < n ? w.bidx[a + lane + 32 * t] : 0x7fffffff;
+    for (int o = 16; o >= 1; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    if (nmax == 0) continue;
+    if (nmax <= kBinG * kBinPer) {
+      const int h0 = valid ? w.ev_hit_off[vs / n_sens] : 0;
+      const int T = (nmax + kBinG - 1) / kBinG;
+      int v[kBinPer], rk[kBinPer];
+#pragma unroll
+      for (int t = 0; t < kBinPer; ++t) {
+        const int idx = sub + kBinG * t;
+        v[t] = idx < n ? w.bidx[a + idx] : 0x7fffffff;
         rk[t] = 0;
       }
-      for (int j0 = 0; j0 < n; j0 += 32) {
-        const int vj_own = j0 + lane < n ? w.bidx[a + j0 + lane] : 0x7fffffff;
-        const int m = min(32, n - j0);
-        for (int j = 0; j < m; ++j) {
-          const int vj = __shfl_sync(0xffffffffu, vj_own, j);
 #pragma unroll
-          for (int t = 0; t < kPer; ++t) rk[t] += vj < v[t];
-        }
-      }
-      __syncwarp();
+      for (int t2 = 0; t2 < kBinPer; ++t2) {
+        if (t2 < T) {
 #pragma unroll
-      for (int t = 0; t < kPer; ++t) {
-        if (lane + 32 * t < n) {
-          const int pos = a + rk[t], src = v[t];
-          w.bidx[pos] = src;
-          w.bx[pos] = w.x[src];
-          w.by[pos] = w.y[src];
-          w.bz[pos] = w.z[src];
-          w.borig[pos] = src - h0;
-        }
-      }
-    } else {
-      if (lane == 0) {
-        for (int i = a + 1; i < a + n; ++i) {
-          const int val = w.bidx[i];
-          int j = i - 1;
-          while (j >= a && w.bidx[j] > val) {
-            w.bidx[j + 1] = w.bidx[j];
-            --j;
+          for (int s2 = 0; s2 < kBinG; ++s2) {
+            const int vj = __shfl_sync(0xffffffffu, v[t2], s2, kBinG);
+#pragma unroll
+            for (int t = 0; t < kBinPer; ++t)
+              if (t < T) rk[t] += vj < v[t];
           }
-          w.bidx[j + 1] = val;
         }
       }
       __syncwarp();
-      for (int i = a + lane; i < a + n; i += 32) {
-        const int src = w.bidx[i];
-        w.bx[i] = w.x[src];
-        w.by[i] = w.y[src];
-        w.bz[i] = w.z[src];
-        w.borig[i] = src - h0;
+#pragma unroll
+      for (int t = 0; t < kBinPer; ++t) {
+        const int idx = sub + kBinG * t;
+        if (idx < n) bin_gather(w, a + rk[t], v[t], h0);
       }
+      continue;
+    }
+    // a sensor with more than 64 hits in this warp: the whole warp takes the four sensors in turn
+    for (int q = 0; q < 4; ++q) {
+      const int vq = base + q;
+      if (vq >= w.S) break;
+      const int aq = w.sens_off[vq], nq = w.sens_off[vq + 1] - aq;
+      if (nq == 0) continue;
+      const int h0 = w.ev_hit_off[vq / n_sens];
+      if (nq <= 256) {
+        int vv[8], rr[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          vv[t] = lane + 32 * t < nq ? w.bidx[aq + lane + 32 * t] : 0x7fffffff;
+          rr[t] = 0;
+        }
+        for (int j0 = 0; j0 < nq; j0 += 32) {
+          const int own = j0 + lane < nq ? w.bidx[aq + j0 + lane] : 0x7fffffff;
+          const int m = min(32, nq - j0);
+          for (int j = 0; j < m; ++j) {
+            const int vj = __shfl_sync(0xffffffffu, own, j);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) rr[t] += vj < vv[t];
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (lane + 32 * t < nq) bin_gather(w, aq + rr[t], vv[t], h0);
+      } else {
+        if (lane == 0) {
+          for (int i = aq + 1; i < aq + nq; ++i) {
+            const int val = w.bidx[i];
+            int j = i - 1;
+            while (j >= aq && w.bidx[j] > val) {
+              w.bidx[j + 1] = w.bidx[j];
+              --j;
+            }
+            w.bidx[j + 1] = val;
+          }
+        }
+        __syncwarp();
+        for (int i = aq + lane; i < aq + nq; i += 32) bin_gather(w, i, w.bidx[i], h0);
+      }
+      __syncwarp();
     }
   }
 }
@@ -219,7 +259,9 @@ __global__ void __launch_bounds__(32 * kMdWarps) k_md(Ws w, Geo g, Cst<float> c)
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const float gmax = (1.0f + 1e-5f) / sqrtf((1.0f - c.sin_max) * (1.0f + c.sin_max));
   int qn = 0;
+  const long long t0 = clock64();
   for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+    if (warp_over_budget(w, t0)) break;
     const int lo0 = w.sens_off[2 * vm], up0 = w.sens_off[2 * vm + 1];
     const int nup = w.sens_off[2 * vm + 2] - up0;
     const int np = (up0 - lo0) * nup;
@@ -460,7 +502,9 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int n_items = persistent ? w.work_off[32] : w.V;
   int qn = 0;   // pairs waiting in this warp's queue
+  const long long t0 = clock64();
   for (int sweep = 0; (int64_t)sweep * n_warps < n_items; ++sweep) {
+    if (warp_over_budget(w, t0)) break;
     const int item = sweep * n_warps + ((sweep & 1) ? n_warps - 1 - gw : gw);
     if (item >= n_items) continue;
     const int vm = persistent ? w.work[item] : item;
@@ -686,7 +730,7 @@ void run_binning(const Ws& w, const Geo& g, const Launch& L) {
   k_bin_scatter<<<grid_for(w.H, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_BIN);
-  k_bin_sort_gather<<<grid_for((int64_t)w.S * 32, 256, 152 * 32), 256, 0, L.stream>>>(w, n_sens);
+  k_bin_sort_gather<<<grid_for((int64_t)w.S * 8, 256, 152 * 32), 256, 0, L.stream>>>(w, n_sens);
   KT_END(L, K_BIN);
   LST_LAUNCH(L);
 }

@@ -251,6 +251,18 @@ void group_configure();
 // after an overflowing run: raise the per-module capacity overrides to the observed counts
 void run_raise_overrides(const Ws& w, const Launch& L);
 
+// Cycle budget of the candidate kernels (lst_config.cycle_budget, 0 = none): checked by whole warps at
+// the head of each work item; a warp past its budget counts itself in ST_TIMEOUT and stops taking
+// work, so a pathological batch ends with LST_ETIMEOUT instead of occupying the GPU.
+__device__ __forceinline__ bool warp_over_budget(const Ws& w, long long t0) {
+  const bool over = w.cycle_budget > 0 && clock64() - t0 > w.cycle_budget;
+  if (__any_sync(0xffffffffu, over)) {
+    if ((threadIdx.x & 31) == 0) atomicAdd(&w.status[ST_TIMEOUT], 1);
+    return true;
+  }
+  return false;
+}
+
 inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {
   int64_t b = (n + block - 1) / block;
   if (b < 1) b = 1;

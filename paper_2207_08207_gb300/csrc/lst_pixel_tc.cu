@@ -264,11 +264,11 @@ __device__ __forceinline__ void pt_flush(const Ws& w, const Cst<float>& c, const
 // rest are flattened across the warp by a shuffle search over the per-module counts. Each candidate
 // gets the first anchor's x-y test; survivors go to a per-warp queue that carries over from seed to
 // seed, and whenever it holds 32 the full float32 pre-filter runs on them with every lane busy.
-constexpr int kPxMaxWarps = 16;
+constexpr int kPxMaxWarps = 8;
 constexpr int kPxQ = 64;
 
 template <int N>
-__global__ void __launch_bounds__(32 * kPxMaxWarps) k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off,
+__global__ void __launch_bounds__(32 * kPxMaxWarps, 4) k_pt_pre(Ws w, Geo g, Cst<float> c, const int32_t* obj_off,
                                                              const float4* box, ObjAnc oa, int2* queue,
                                                              int q_word, int64_t q_cap, float cut_xy,
                                                              float cut_rz) {
@@ -280,7 +280,9 @@ __global__ void __launch_bounds__(32 * kPxMaxWarps) k_pt_pre(Ws w, Geo g, Cst<fl
   const float lim_rz = cut_rz * (1.0f + kGuardChi2) + kGuardChi2Abs;
   const int P = w.n_pls();
   int qn = 0;
+  const long long t0 = clock64();
   for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += nwarps) {
+    if (warp_over_budget(w, t0)) break;
     const int bin = w.pls_bin[p];
     if (bin < 0) continue;
     const int e = find_seg(w.ev_pls_off, w.E, p);
@@ -550,37 +552,55 @@ __global__ void k_h5_count(Ws w, int fill) {
 // T5 duplicate removal: T5 a is dropped when another passing T5 shares at least `overlap` of its
 // ten hits and ranks lower (chi2_c as float32, then hit tuple). A T5 sharing `overlap` hits with a
 // contains at least one of a's first 11 - overlap hits (a misses at most 10 - overlap of them), so
-// only those hits' T5 lists are searched.
+// only those hits' T5 lists are searched. A warp per T5: the candidates of the searched lists are
+// spread over the lanes, and any lane's hit drops it.
 __global__ void k_t5_clean(Ws w, int overlap) {
   const int n = w.t5_off[w.V];
   const int64_t S = w.cap.t5_dense;
   const int n_probe = min(10, max(1, 11 - overlap));
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); a < n; a += nwarps) {
     int ha[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) ha[k] = w.t5_hit[(int64_t)a * 10 + k];
     const float ca = w.t5_f[3 * S + a];
-    bool drop = false;
+    // the probed lists, concatenated: list t covers [beg[t], beg[t] + len[t])
+    int beg[10], end_[10];
+    int total = 0;
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
-      if (t >= n_probe || drop) break;
-      const int h = ha[t];
-      for (int k = w.h5_off[h]; k < w.h5_off[h + 1] && !drop; ++k) {
-        const int b = w.h5_idx[k];
-        if (b == a) continue;
-        int shared = 0;
-#pragma unroll
-        for (int kb = 0; kb < 10; ++kb) {
-          const int hb = w.t5_hit[(int64_t)b * 10 + kb];
-#pragma unroll
-          for (int u = 0; u < 10; ++u) shared += ha[u] == hb;
-        }
-        if (shared < overlap) continue;
-        const float cb = w.t5_f[3 * S + b];
-        if (cb < ca || (cb == ca && key_less(w, TC_T5, b, a))) drop = true;
-      }
+      beg[t] = t < n_probe ? w.h5_off[ha[t]] : 0;
+      const int len = t < n_probe ? w.h5_off[ha[t] + 1] - beg[t] : 0;
+      total += len;
+      end_[t] = total;
     }
-    w.t5_kept[a] = drop ? 0 : 1;
+    bool drop = false;
+    for (int k = lane; k < total && !drop; k += 32) {
+      int t = 0;
+#pragma unroll
+      for (int u = 0; u < 9; ++u) t += k >= end_[u];
+      int start = 0;
+#pragma unroll
+      for (int u = 0; u < 10; ++u) if (u == t) start = u > 0 ? end_[u - 1] : 0;
+      int bt = 0;
+#pragma unroll
+      for (int u = 0; u < 10; ++u) if (u == t) bt = beg[u];
+      const int b = w.h5_idx[bt + (k - start)];
+      if (b == a) continue;
+      int shared = 0;
+#pragma unroll
+      for (int kb = 0; kb < 10; ++kb) {
+        const int hb = w.t5_hit[(int64_t)b * 10 + kb];
+#pragma unroll
+        for (int u = 0; u < 10; ++u) shared += ha[u] == hb;
+      }
+      if (shared < overlap) continue;
+      const float cb = w.t5_f[3 * S + b];
+      if (cb < ca || (cb == ca && key_less(w, TC_T5, b, a))) drop = true;
+    }
+    drop = __any_sync(0xffffffffu, drop);
+    if (lane == 0) w.t5_kept[a] = drop ? 0 : 1;
   }
 }
 
@@ -969,7 +989,7 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   scan_exclusive(w.h5_cnt, w.h5_off, w.cap.H, w.scan_tmp, L);
   k_h5_count<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, 1);
   KT_BEGIN(L, K_TC_CLEAN);
-  k_t5_clean<<<grid_for(w.cap.t5_dense, 128), 128, 0, L.stream>>>(w, c.d.t5_overlap_hits);
+  k_t5_clean<<<grid_for((int64_t)w.cap.t5_dense * 32, 256, 152 * 32), 256, 0, L.stream>>>(w, c.d.t5_overlap_hits);
   KT_END(L, K_TC_CLEAN);
   k_grid_items<<<grid_for(w.P + w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, g, 0);
   *L.launches += 3;

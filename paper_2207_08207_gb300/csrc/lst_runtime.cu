@@ -628,7 +628,7 @@ int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
   if (cfg) ctx->cfg = *cfg;
   else lst_config_default(&ctx->cfg);
   if (ctx->cfg.block_ls != 64 && ctx->cfg.block_ls != 128 && ctx->cfg.block_ls != 256) ctx->cfg.block_ls = 128;
-  if (ctx->cfg.warps_px < 1 || ctx->cfg.warps_px > 16) ctx->cfg.warps_px = 4;
+  if (ctx->cfg.warps_px < 1 || ctx->cfg.warps_px > 8) ctx->cfg.warps_px = 4;
   if (!(ctx->cfg.cap_scale >= 0.25f)) ctx->cfg.cap_scale = 1.0f;
   if (ctx->cfg.max_retries < 0) ctx->cfg.max_retries = 0;
   if (!(ctx->cfg.pt_thr > 0.f) || !(ctx->cfg.k > 0.f)) {
@@ -960,7 +960,7 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     need(st[ST_Q_PT3], c.q_p3);
     need(st[ST_Q_PT5], c.q_p5);
     raise = st[ST_OVF_MD] || st[ST_OVF_LS] || st[ST_OVF_T3] || st[ST_OVF_T5];
-    if (!(st[ST_ERROR]) && (grow || raise)) {
+    if (!(st[ST_ERROR]) && !st[ST_TIMEOUT] && (grow || raise)) {
       if (ctx->retries >= ctx->cfg.max_retries) {
         ctx->pending = false;
         for (int32_t ev = 0; ev < ctx->E; ++ev) {
@@ -1022,8 +1022,12 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     c.recheck[LST_STAGE_PT3] = st[ST_Q_PT3];
     c.recheck[LST_STAGE_PT5] = st[ST_Q_PT5];
     c.retries = ctx->retries;
-    c.status = es[kEvErr] ? LST_EINVAL : LST_OK;
-    if (c.status && !first_err) {
+    c.status = es[kEvErr] ? LST_EINVAL : (st[ST_TIMEOUT] ? LST_ETIMEOUT : LST_OK);
+    if (c.status == LST_ETIMEOUT && !first_err) {
+      first_err = c.status;
+      ctx->err = "lst_sync: " + std::to_string(st[ST_TIMEOUT]) +
+                 " warps of the candidate kernels ran out of their cycle budget; results are incomplete";
+    } else if (c.status && !first_err) {
       first_err = c.status;
       ctx->err = "lst_sync: invalid input in event " + std::to_string(ev) +
                  ((es[kEvErr] & ERR_BAD_SENSOR) ? " (sensor id out of range)" : "") +

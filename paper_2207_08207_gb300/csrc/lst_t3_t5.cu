@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(32 * kT3Warps) k_t3_pre(Ws w, Cst<float> c) {
   const float kmax = c.k / (c.f_t3 * c.pt_thr);
   const float kmax2 = kmax * kmax * (1.0f + 4.0f * kGuardWindow);
   int qn = 0;
+  const long long t0 = clock64();
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n_ls; base += nwarps * 32) {
+    if (warp_over_budget(w, t0)) break;
     const int i = base + lane;
     int j0 = 0, size = 0;
     float x1 = 0.f, y1 = 0.f, x2 = 0.f, y2 = 0.f;

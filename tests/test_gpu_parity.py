@@ -137,6 +137,25 @@ def test_forced_overflow_is_counted_and_recovered(det_full):
     ctx.close()
 
 
+def test_cycle_budget_ends_run_with_timeout(det_full):
+    """A warp past its cycle budget stops taking work: the run ends with LST_ETIMEOUT (no fault, no
+    hang), the same context keeps answering, and a context without a budget gives full results."""
+    _, ev = gen.small_event(400, seed=9)
+    tight = lst.Context(det_full, cycle_budget=1)
+    with pytest.raises(lst.LSTError) as ei:
+        tight.run([ev])
+    assert ei.value.code == lst.LST_ETIMEOUT
+    assert tight.counts(0)["status"] == lst.LST_ETIMEOUT
+    with pytest.raises(lst.LSTError):   # still usable, still over budget
+        tight.run([ev])
+    tight.close()
+    free = lst.Context(det_full)
+    free.run([ev])
+    assert free.counts(0)["status"] == 0
+    _check(oracle.run(det_full, ev), free.results(0), ev)
+    free.close()
+
+
 @pytest.mark.slow
 def test_pu300_low_threshold_config4():
     det, ev = gen.config_event(4, 0)
