@@ -61,7 +61,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -70,9 +70,14 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def mark(self):
+        """Host time stamp (start / end of the timed region)."""
+        return time.perf_counter()
+
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken between t0 and t1 (all samples if none fall inside)."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         self.proc.terminate()
@@ -82,7 +87,8 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if t0 is None or (t0 <= t <= t1)]
+        for ln in inside or [ln for _, ln in self.lines]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -95,7 +101,7 @@ class ClockSampler:
                 if v.lower() in ("active", "1"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "in_timed_region": bool(inside)}
 
 
 def to_device(ev, torch):
@@ -205,7 +211,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS),
@@ -253,15 +259,18 @@ def main():
         ctx.submit(dev, stream=stream)
         ctx.sync()
 
+    # per-kernel timing events are part of the captured graph: enable them before the warm-up so
+    # that the graph used in the timed region is captured there
+    ctx.set_timing(True)
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(max(3, args.warmup)):
         step()
-    ctx.set_timing(True)
     launches0 = ctx.launch_count()
-    sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    t_begin = sampler.mark()
     step_ms, stage_acc, kern_acc = [], {}, {}
     for _ in range(args.steps):
         flush.zero_()
@@ -276,7 +285,8 @@ def main():
         for k, v in ctx.kernel_ms().items():
             kern_acc[k] = kern_acc.get(k, 0.0) + v
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    t_end = sampler.mark()
+    clocks = sampler.stop(t_begin, t_end)
     launches = ctx.launch_count() - launches0
     ctx.set_timing(False)
     t_local = sum(step_ms) / 1e3

@@ -104,16 +104,39 @@ __device__ __forceinline__ bool t3_quick_reject(const Cst<float>& c, float kmax2
 constexpr int kT3Warps = 8;
 constexpr int kT3Q = 64;
 
+// Float32 pre-filter of a T3 candidate that passed the quick test (whose pT and d0 bounds already
+// hold): the r-z chi2 of the three anchors in closed form. For three points the best straight line
+// leaves chi2 = (c.z)^2 / sum(c_i^2 sigma_i^2) with c = (s3 - s2, -(s3 - s1), s2 - s1), the one
+// combination of the z's that every line annuls, which equals the weighted least-squares fit's
+// chi2. Rejects only chi2 clearly above the cut (the float32 error is ~1e-3 relative).
+__device__ __forceinline__ bool t3_pre_keep(const Cst<float>& c, const Anchor<float>& h1, const Anchor<float>& h2,
+                                            const Anchor<float>& h3) {
+  const float ux = h2.x - h1.x, uy = h2.y - h1.y, vx = h3.x - h1.x, vy = h3.y - h1.y;
+  const float cr = diff_prod(ux, vy, uy, vx);
+  const float wx = h3.x - h2.x, wy = h3.y - h2.y;
+  const float rs = sqrtf((ux * ux + uy * uy) * (vx * vx + vy * vy) * (wx * wx + wy * wy));
+  const float ak = 2.0f * fabsf(cr) / rs;   // |curvature| of the circle through the anchors
+  const float two_r = 2.0f / ak;
+  const float s1 = arc_len(ak, two_r, h1.r), s2 = arc_len(ak, two_r, h2.r), s3 = arc_len(ak, two_r, h3.r);
+  if (!(s3 > s1)) return true;   // decided in double-float
+  const float b0 = (h3.z - h1.z) / (s3 - s1);
+  const float sg1 = fmaxf(h1.ec ? c.sigma_r * fabsf(b0) : c.sigma_z, c.sigma_floor);
+  const float sg2 = fmaxf(h2.ec ? c.sigma_r * fabsf(b0) : c.sigma_z, c.sigma_floor);
+  const float sg3 = fmaxf(h3.ec ? c.sigma_r * fabsf(b0) : c.sigma_z, c.sigma_floor);
+  const float c1 = s3 - s2, c2 = s1 - s3, c3 = s2 - s1;
+  const float num = c1 * h1.z + c2 * h2.z + c3 * h3.z;
+  const float den = c1 * c1 * sg1 * sg1 + c2 * c2 * sg2 * sg2 + c3 * c3 * sg3 * sg3;
+  return !(num * num > (c.chi2_t3 * (1.0f + kGuardChi2) + kGuardChi2Abs) * den);
+}
+
 __device__ __forceinline__ void t3_flush(const Ws& w, const Cst<float>& c, const int2* qe, int n) {
   const int lane = threadIdx.x & 31;
   bool keep = false;
   int2 e = make_int2(0, 0);
   if (lane < n) {
     e = qe[lane];
-    Circle3<float> circ;
-    float chi2;
-    keep = t3_eval<float>(c, anchor<float>(w, w.ls_in[e.x]), anchor<float>(w, w.ls_out[e.x]),
-                          anchor<float>(w, w.ls_out[e.y]), circ, chi2) != kReject;
+    keep = t3_pre_keep(c, anchor<float>(w, w.ls_in[e.x]), anchor<float>(w, w.ls_out[e.x]),
+                       anchor<float>(w, w.ls_out[e.y]));
   }
   const int q = warp_agg_slot(keep, &w.status[ST_Q_T3]);
   if (q >= 0 && q < w.cap.q_t3) w.q_t3[q] = e;
