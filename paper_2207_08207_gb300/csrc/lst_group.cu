@@ -69,11 +69,17 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_mod_sort_small(Ws w, SortA
     if (total > cap) atomicMax(&w.status[a.dense_word], total);
     a.mod_off[w.V] = (int)lst_min64(total, cap);
   }
+  const bool offsets = a.grp_off != nullptr;
   for (int vm = blockIdx.x * kSmallWarps + wi; vm < w.V; vm += nwarps) {
     const int dest = w.eff[vm], n = w.eff[vm + 1] - dest;
     if (lane == 0) a.mod_off[vm] = (int)lst_min64(dest, cap);
     const int k0 = a.mod_first[(int64_t)vm * a.stride], k1 = a.mod_first[(int64_t)(vm + 1) * a.stride];
     const int R = k1 - k0;
+    if (n > 32 && (n > kMidCap || R >= kMidCap)) {
+      if (lane == 0) w.grp_big[atomicAdd(&w.grp_big_cnt[a.big_word], 1)] = vm;
+      continue;
+    }
+    if (n == 0 && !(offsets && R > 0)) continue;
     const int b = a.base[vm];
     if (n <= 32) {
       int kv1 = 0x7fffffff;
@@ -92,19 +98,16 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_mod_sort_small(Ws w, SortA
         POS[rank] = kv1;
       }
       __syncwarp();
-      for (int k = k0 + lane; k < k1; k += 32) {   // dest + #(first members below k)
-        int lo = 0, hi = n;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (POS[mid] < k) lo = mid + 1; else hi = mid;
+      if (offsets)
+        for (int k = k0 + lane; k < k1; k += 32) {   // dest + #(first members below k)
+          int lo = 0, hi = n;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (POS[mid] < k) lo = mid + 1; else hi = mid;
+          }
+          a.grp_off[k] = (int)lst_min64(dest + lo, cap);
         }
-        a.grp_off[k] = (int)lst_min64(dest + lo, cap);
-      }
       __syncwarp();
-      continue;
-    }
-    if (n > kMidCap || R >= kMidCap) {
-      if (lane == 0) w.grp_big[atomicAdd(&w.grp_big_cnt[a.big_word], 1)] = vm;
       continue;
     }
     for (int k = lane; k <= R; k += 32) G[k] = 0;
@@ -129,7 +132,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_mod_sort_small(Ws w, SortA
       run += __shfl_sync(0xffffffffu, incl, 31);
     }
     __syncwarp();
-    for (int k = lane; k < R; k += 32) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
+    if (offsets)
+      for (int k = lane; k < R; k += 32) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
     // placement by first member (order inside a group arbitrary), via the group starts
     for (int i = lane; i < n; i += 32) POS[atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1)] = i;
     __syncwarp();
@@ -140,8 +144,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_mod_sort_small(Ws w, SortA
       const int g_end = G[g], g_beg = g > 0 ? G[g - 1] : 0;
       const int k2 = K2[i];
       int r = g_beg;
-      for (int q = g_beg; q < g_end; ++q) {
-        const int j = POS[q];
+      for (int qq = g_beg; qq < g_end; ++qq) {
+        const int j = POS[qq];
         const int kj = K2[j];
         r += kj < k2 || (kj == k2 && j < i);
       }
@@ -206,7 +210,8 @@ __global__ void __launch_bounds__(kBigThreads) k_mod_sort_big(Ws w, SortArgs a) 
         acc += v;
       }
       __syncthreads();
-      for (int k = t; k < R; k += blockDim.x) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
+      if (a.grp_off)
+        for (int k = t; k < R; k += blockDim.x) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
       __syncthreads();
       for (int i = t; i < n; i += blockDim.x) POS[atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1)] = i;
       __syncthreads();
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kBigThreads) k_mod_sort_big(Ws w, SortArgs a) 
         }
         if (dest + rank < cap) w.perm[dest + rank] = b + i;
       }
-      for (int k = k0 + t; k < k1; k += blockDim.x) {
+      for (int k = k0 + t; a.grp_off && k < k1; k += blockDim.x) {
         int below = 0;
         for (int j = 0; j < n; ++j) below += a.key1[b + j] < k;
         a.grp_off[k] = (int)lst_min64(dest + below, cap);
@@ -276,8 +281,10 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
   LST_LAUNCH(L);
   k_mod_sort_big<<<L.n_sm * 2, kBigThreads, 3 * kBigCap * sizeof(int), L.stream>>>(w, s);
   LST_LAUNCH(L);
-  k_grp_tail<<<grid_for(a.n_keys + 1, 256), 256, 0, L.stream>>>(w, s);
-  LST_LAUNCH(L);
+  if (a.grp_off) {
+    k_grp_tail<<<grid_for(a.n_keys + 1, 256), 256, 0, L.stream>>>(w, s);
+    LST_LAUNCH(L);
+  }
 }
 
 void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* grp_off, int64_t cap,

@@ -347,8 +347,12 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
     w.md_z[d] = w.bz[lo];
     w.md_r[d] = r;
     w.md_rlo[d] = r > 0.f ? rlo : 0.f;
-    w.md_sthr[d] = c.two_rthr * asinf(fminf(r / c.two_rthr, 1.0f));
-    w.md_alpha[d] = asinf(fminf(r * c.k2p, c.sin_max));
+    const float sthr = c.two_rthr * asinf(fminf(r / c.two_rthr, 1.0f));
+    const float alpha = asinf(fminf(r * c.k2p, c.sin_max));
+    w.md_sthr[d] = sthr;
+    w.md_alpha[d] = alpha;
+    w.md_xyzr[d] = make_float4(x, y, w.bz[lo], r);
+    w.md_sa[d] = make_float2(sthr, alpha);
     w.md_ec[d] = g.endcap[vm % g.n_mods];
   }
 }
@@ -477,8 +481,9 @@ __device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const
     vm = S.q_vm[lane];
     a = S.q_a[lane];
     b = S.q_b[lane];
-    v = ls_eval<float>(c, w.md_x[a], w.md_y[a], w.md_z[a], w.md_r[a], w.md_sthr[a], w.md_ec[a] != 0, w.md_x[b],
-                       w.md_y[b], w.md_z[b], w.md_r[b], w.md_sthr[b], w.md_ec[b] != 0, kGuardWindow, z0, dphi);
+    const float4 pa = w.md_xyzr[a], pb = w.md_xyzr[b];
+    v = ls_eval<float>(c, pa.x, pa.y, pa.z, pa.w, w.md_sa[a].x, w.md_ec[a] != 0, pb.x, pb.y, pb.z, pb.w,
+                       w.md_sa[b].x, w.md_ec[b] != 0, kGuardWindow, z0, dphi);
   }
   const int slot = warp_agg_slot_keyed(v == kAccept, vm, w.ls_cnt);
   if (slot >= 0) {
@@ -547,8 +552,8 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
       __syncwarp();
       if (lane < nA) {
         const int d = a_begin + a0 + lane;
-        S.a_xyzr[lane] = make_float4(w.md_x[d], w.md_y[d], w.md_z[d], w.md_r[d]);
-        S.a_sal[lane] = make_float2(w.md_sthr[d], w.md_alpha[d]);
+        S.a_xyzr[lane] = w.md_xyzr[d];
+        S.a_sal[lane] = w.md_sa[d];
         S.a_id[lane] = d;
       }
       __syncwarp();
@@ -564,8 +569,10 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
             if (S.tpre[mid] <= j) lo = mid; else hi = mid;
           }
           bid = S.tbase[lo] + (j - S.tpre[lo]);
-          x2 = w.md_x[bid]; y2 = w.md_y[bid]; z2 = w.md_z[bid]; r2 = w.md_r[bid];
-          s2 = w.md_sthr[bid]; al2 = w.md_alpha[bid];
+          const float4 pb = w.md_xyzr[bid];
+          const float2 sb = w.md_sa[bid];
+          x2 = pb.x; y2 = pb.y; z2 = pb.z; r2 = pb.w;
+          s2 = sb.x; al2 = sb.y;
           const bool bec = S.tec[lo] != 0;
           sz2 = bec ? 0.f : c.sigma_z;
           sr2 = bec ? c.sigma_r : 0.f;
@@ -747,7 +754,7 @@ void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   KT_BEGIN(L, K_MD_COMPACT);
   GroupArgs ga{w.md_cnt, w.md_cap, w.md_base, w.cap.md_slots, ST_OVF_MD, ST_ARENA_MD, w.ms_lo, w.ms_up,
-               w.mdlo_off, w.cap.H, w.cap.md_dense, ST_DENSE_MD,
+               nullptr, w.cap.H, w.cap.md_dense, ST_DENSE_MD,
                w.md_off, w.sens_off, 2, 0};
   group_slots(w, ga, L);
   k_md_dense<<<grid_for(w.cap.md_dense, 256), 256, 0, L.stream>>>(w, g, c.f);

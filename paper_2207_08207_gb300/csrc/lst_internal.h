@@ -76,11 +76,12 @@ struct Ws {
   int32_t *ms_lo = nullptr, *ms_up = nullptr;
   float *ms_dpc = nullptr, *ms_pte = nullptr;
   int32_t* md_off = nullptr;
-  int32_t* mdlo_off = nullptr;   // MDs grouped by lower hit
   int32_t *md_lo = nullptr, *md_up = nullptr, *md_vm = nullptr;
   float *md_x = nullptr, *md_y = nullptr, *md_z = nullptr, *md_r = nullptr, *md_sthr = nullptr;
   float *md_rlo = nullptr;     // r = md_r + md_rlo to ~1e-14 relative (float-float)
   float *md_alpha = nullptr;   // alpha_thr(r) = asin(min(r k / (2 pT_thr), sin_max)), float32
+  float4* md_xyzr = nullptr;     // [md_dense] (x, y, z, r) of each MD anchor, one load (LS kernel)
+  float2* md_sa = nullptr;       // [md_dense] (arc length at R_thr, alpha_thr)
   float *md_dpc = nullptr, *md_pte = nullptr;
   uint8_t* md_ec = nullptr;
   // LS
@@ -111,7 +112,6 @@ struct Ws {
   int32_t *t5_a = nullptr, *t5_b = nullptr;
   int32_t* t5_md = nullptr;  // [5][t5_dense]
   float* t5_f = nullptr;     // [8][t5_dense]
-  int32_t* t5in_off = nullptr;   // T5 grouped by inner T3
   float4* t5_anc = nullptr;      // [5][t5_dense]
   uint8_t* t5_ecm = nullptr;
   // per module: lo[vm], hi[V + vm] = bounding box (x, y, z, r) of the first anchors of its T3 / T5
@@ -212,6 +212,7 @@ struct GroupArgs {
   int ovf_word, arena_word;
   const int32_t *key1, *key2;        // first / second member of each slot
   int32_t* grp_off;                  // out: [n_keys + 1] objects whose first member is below each key
+                                     // (nullptr: not needed by a later stage, not computed)
   int64_t n_keys;                    // key1 range
   int64_t dense_cap;
   int dense_word;

@@ -404,12 +404,13 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.work, V); pl.add(w.work_bucket, V); pl.add(w.work_off, 33);
   pl.add(w.perm, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
   // MD
-  pl.add(w.md_cap, V); pl.add(w.md_base, V + 1); pl.add(w.md_off, V + 1); pl.add(w.mdlo_off, c.H + 2);
+  pl.add(w.md_cap, V); pl.add(w.md_base, V + 1); pl.add(w.md_off, V + 1);
   pl.add(w.ms_lo, c.md_slots); pl.add(w.ms_up, c.md_slots); pl.add(w.ms_dpc, c.md_slots); pl.add(w.ms_pte, c.md_slots);
   pl.add(w.md_lo, c.md_dense); pl.add(w.md_up, c.md_dense); pl.add(w.md_vm, c.md_dense);
   pl.add(w.md_x, c.md_dense); pl.add(w.md_y, c.md_dense); pl.add(w.md_z, c.md_dense); pl.add(w.md_r, c.md_dense);
   pl.add(w.md_sthr, c.md_dense); pl.add(w.md_rlo, c.md_dense); pl.add(w.md_alpha, c.md_dense);
   pl.add(w.md_dpc, c.md_dense); pl.add(w.md_pte, c.md_dense); pl.add(w.md_ec, c.md_dense);
+  pl.add(w.md_xyzr, c.md_dense); pl.add(w.md_sa, c.md_dense);
   // LS
   pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1); pl.add(w.lsin_off, c.md_dense + 2);
   pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_z0, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
@@ -425,7 +426,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.t3_anc, 3 * c.t3_dense); pl.add(w.t3_ecm, c.t3_dense);
   pl.add(w.t3md_off, c.md_dense + 2);
   // T5
-  pl.add(w.t5_cap, V); pl.add(w.t5_base, V + 1); pl.add(w.t5_off, V + 1); pl.add(w.t5in_off, c.t3_dense + 2);
+  pl.add(w.t5_cap, V); pl.add(w.t5_base, V + 1); pl.add(w.t5_off, V + 1);
   pl.add(w.t5s_a, c.t5_slots); pl.add(w.t5s_b, c.t5_slots); pl.add(w.t5s_f, 8 * c.t5_slots);
   pl.add(w.t5_a, c.t5_dense); pl.add(w.t5_b, c.t5_dense); pl.add(w.t5_md, 5 * c.t5_dense); pl.add(w.t5_f, 8 * c.t5_dense);
   pl.add(w.t5_anc, 5 * c.t5_dense); pl.add(w.t5_ecm, c.t5_dense);

@@ -31,10 +31,11 @@ struct Anchor {
 template <class T>
 __device__ __forceinline__ Anchor<T> anchor(const Ws& w, int d) {
   Anchor<T> a;
-  a.x = (T)w.md_x[d];
-  a.y = (T)w.md_y[d];
-  a.z = (T)w.md_z[d];
-  if constexpr (sizeof(T) == 4) a.r = w.md_r[d];
+  const float4 p = w.md_xyzr[d];
+  a.x = (T)p.x;
+  a.y = (T)p.y;
+  a.z = (T)p.z;
+  if constexpr (sizeof(T) == 4) a.r = p.w;
   else a.r = m_sqrt(a.x * a.x + a.y * a.y);
   a.ec = w.md_ec[d] != 0;
   return a;
@@ -559,7 +560,7 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_END(L, K_T5_DECIDE);
   LST_LAUNCH(L);
   GroupArgs ga{w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, ST_OVF_T5, ST_ARENA_T5, w.t5s_a, w.t5s_b,
-               w.t5in_off, w.cap.t3_dense, w.cap.t5_dense, ST_DENSE_T5,
+               nullptr, w.cap.t3_dense, w.cap.t5_dense, ST_DENSE_T5,
                w.t5_off, w.t3_off, 1, 3};
   group_slots(w, ga, L);
   k_t5_dense<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w);
