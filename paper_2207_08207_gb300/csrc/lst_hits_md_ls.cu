@@ -178,21 +178,6 @@ __global__ void k_md_caps(Ws w) {
   }
 }
 
-// effective count = min(count, capacity, room left in the arena); excess is recorded
-__global__ void k_effective(Ws w, const int32_t* cnt, const int32_t* cap, const int32_t* base,
-                            int64_t slots, int32_t* eff_out, int ovf_word, int arena_word, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int c = cnt[i], k = cap[i], b = base[i];
-    int eff = min(c, k);
-    if (c > k) atomicAdd(&w.status[ovf_word], c - k);
-    if ((int64_t)b + eff > slots) {
-      eff = (int)(slots - b > 0 ? slots - b : 0);
-      atomicMax(&w.status[arena_word], base[n]);
-    }
-    eff_out[i] = eff;
-  }
-}
-
 // Quick rejection of a (lower, upper) hit pair by the Mini-Doublet's z window (barrel) or radial
 // window (endcap), exact-safe: true only when the float64 selection is certain to fail, with
 // margins far above float32 rounding. Barrel: the window lo = delta min(t1, g t1) - tol_z,
@@ -720,12 +705,6 @@ void run_bin_raw(const int32_t* sensor, int n, int n_sens, int32_t* order, int32
   k_braw_scatter<<<grid_for(n, 256), 256, 0, L.stream>>>(sensor, n, n_sens, offsets, cur, order);
   LST_LAUNCH(L);
   k_braw_sort<<<grid_for(n_sens, 128), 128, 0, L.stream>>>(offsets, n_sens, order);
-  LST_LAUNCH(L);
-}
-
-void launch_effective(const Ws& w, const int32_t* cnt, const int32_t* cap, const int32_t* base,
-                      int64_t slots, int32_t* eff, int ovf_word, int arena_word, int n, const Launch& L) {
-  k_effective<<<grid_for(n, 256), 256, 0, L.stream>>>(w, cnt, cap, base, slots, eff, ovf_word, arena_word, n);
   LST_LAUNCH(L);
 }
 

@@ -171,7 +171,6 @@ struct Ws {
   int32_t* work_cnt = nullptr;    // [32] modules per bucket
   int32_t* work_cur = nullptr;    // [32]
   int32_t* work_off = nullptr;    // [33]
-  int32_t* work_ctr = nullptr;    // [1] next item
 };
 
 // Launch settings (from lst_config).
@@ -224,11 +223,6 @@ struct GroupArgs {
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L);
 void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* grp_off, int64_t cap,
                      const Launch& L);
-
-// effective per-module object count = min(count, capacity, room left in the slot arena), with the
-// excess added to status[ovf_word] and the needed arena size to status[arena_word]
-void launch_effective(const Ws& w, const int32_t* cnt, const int32_t* cap, const int32_t* base,
-                      int64_t slots, int32_t* eff, int ovf_word, int arena_word, int n, const Launch& L);
 
 // message returned by lst_last_error(NULL) (calls that have no context)
 void set_global_error(const char* msg);

@@ -395,7 +395,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.p3_cnt, c.P); z.add(w.p3_cur, c.P); z.add(w.p5_cnt, c.P); z.add(w.p5_cur, c.P);
   z.add(w.h5_cnt, c.H + 1); z.add(w.h5_cur, c.H + 1);
   z.add(w.cell_cnt, NC); z.add(w.cell_cur, NC);
-  z.add(w.work_cnt, 32); z.add(w.work_cur, 32); z.add(w.work_ctr, 1);
+  z.add(w.work_cnt, 32); z.add(w.work_cur, 32);
   // binning
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
   pl.add(w.bx, c.H); pl.add(w.by, c.H); pl.add(w.bz, c.H); pl.add(w.borig, c.H);
