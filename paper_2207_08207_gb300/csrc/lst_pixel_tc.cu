@@ -100,7 +100,7 @@ __device__ __forceinline__ void seed_terms(const Seed<T>& s, const Cst<T>& c, T 
   const T e1 = r * c.pls_dir_err;
   const T e2 = c.pls_pt_err * r * r * T(0.5) * s.akap;
   xy_term = d * d / (c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2);
-  const T sa = arc_len(s.akap, r);
+  const T sa = arc_len(s.akap, T(2) * s.R, r);
   const T zp = s.z0 + sa * s.cot;
   const T sz = ec ? c.sigma_r * m_abs(s.cot) : c.sigma_z;
   const T th = sa * (T(1) + s.cot * s.cot) * c.pls_dir_err;
@@ -162,15 +162,21 @@ __device__ __forceinline__ bool seed_box_reject(const Seed<float>& s, const Cst<
   const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y);
   const float h = sqrtf(hx * hx + hy * hy);
   const float ux = cx - s.x0, uy = cy - s.y0;
-  const float dc = fabsf(seed_dist(s, cx, cy));
-  const float lb = dc - h * 1.0001f - 1e-3f - 1e-4f * (fabsf(ux) + fabsf(uy));
-  if (lb > 0.f) {
+  // distance at the centre: at least |A| / g with A = rho/2 |u|^2 - u.n and g = 1 + |rho A| / 2
+  // (the exact 2A / (1 + sqrt(1 + 2 rho A)) without its square root and division); the test
+  // lb = |A| / g - margin > 0, lb^2 > limit is multiplied through by g
+  const float A = 0.5f * s.rho * (ux * ux + uy * uy) - (ux * s.sp - uy * s.cp);
+  const float g = 1.0f + 0.5f * fabsf(s.rho * A);
+  const float m = h * 1.0001f + 1e-3f + 1e-4f * (fabsf(ux) + fabsf(uy));
+  const float lbg = fabsf(A) - m * g;
+  if (lbg > 0.f) {
     const float e1 = hi.w * c.pls_dir_err;
     const float e2 = c.pls_pt_err * hi.w * hi.w * 0.5f * s.akap;
     const float sig2 = c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2;
-    if (lb * lb > lim_xy * sig2 * 1.0625f) return true;
+    if (lbg * lbg > lim_xy * sig2 * 1.0625f * g * g) return true;
   }
-  const float sl = arc_len(s.akap, lo.w), sh = arc_len(s.akap, hi.w);
+  const float two_r = 2.0f * s.R;
+  const float sl = arc_len(s.akap, two_r, lo.w), sh = arc_len(s.akap, two_r, hi.w);
   const float za = s.z0 + sl * s.cot, zb = s.z0 + sh * s.cot;
   const float zmin = fminf(za, zb), zmax = fmaxf(za, zb);
   const float gap = fmaxf(lo.z - zmax, zmin - hi.z) - 1e-3f -
@@ -246,7 +252,7 @@ __device__ __forceinline__ void pt_flush(const Ws& w, const Cst<float>& c, const
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         const float4 h = oa.anc[a * oa.stride + obj];
-        const float sa = arc_len(s.akap, h.w);
+        const float sa = arc_len(s.akap, 2.0f * s.R, h.w);
         const float zp = s.z0 + sa * s.cot;
         const float sz = ((ecm >> a) & 1) ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
         const float th = sa * (1.0f + s.cot * s.cot) * c.pls_dir_err;

@@ -63,13 +63,23 @@ __device__ __forceinline__ int t3_eval(const Cst<T>& c, const Anchor<T>& h1, con
     typename AccOf<T>::type acc;
     acc.cut_ge(c.f_t3 * c.pt_thr, c.k * circ.R);
     acc.cut(c.d0_t3, circ.d0);
-    const T r[3] = {h1.r, h2.r, h3.r}, z[3] = {h1.z, h2.z, h3.z};
-    const bool ec[3] = {h1.ec, h2.ec, h3.ec};
-    T slope;
-    if (!rz_fit<T, 3>(c, ak, r, z, ec, chi2, slope)) {
+    // the straight-line fit in (s, z) of three anchors, in closed form: chi2 = (c.z)^2 / sum(c_i^2
+    // sigma_i^2) with c = (s3 - s2, s1 - s3, s2 - s1), the combination of the z's that every line
+    // annuls (identical to the weighted least-squares fit's chi2)
+    const T two_r = T(2) / ak;
+    const T s1 = arc_len(ak, two_r, h1.r), s2 = arc_len(ak, two_r, h2.r), s3 = arc_len(ak, two_r, h3.r);
+    if (!(s3 > s1)) {
       acc.reject();
       chi2 = T(1) / T(0);
     } else {
+      const T b0 = m_abs((h3.z - h1.z) / (s3 - s1));
+      const T sg1 = m_max(h1.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
+      const T sg2 = m_max(h2.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
+      const T sg3 = m_max(h3.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
+      const T c1 = s3 - s2, c2 = s1 - s3, c3 = s2 - s1;
+      const T num = c1 * h1.z + c2 * h2.z + c3 * h3.z;
+      const T den = c1 * c1 * sg1 * sg1 + c2 * c2 * sg2 * sg2 + c3 * c3 * sg3 * sg3;
+      chi2 = num * num / den;
       acc.cut(c.chi2_t3, chi2);
     }
     return acc.verdict();
