@@ -643,22 +643,32 @@ __global__ void k_ls_recheck(Ws w, Cst<double> c) {
 
 // dense LS ordered by (inner MD, outer MD); z0 is recomputed in float64 (its float32 form
 // amplifies radius rounding up to ~20x for endcap pairs)
+// dense LS ordered by (inner MD, outer MD), with z0, dphi, the outer anchor cache, and each LS's
+// count of outer partners (the T3 candidates it starts) summed per module for the T3 capacities
 __global__ void k_ls_dense(Ws w) {
   const int n = (int)lst_min64(w.ls_off[w.V], w.cap.ls_dense);
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
-    const int s = w.perm[d];
-    const int a = w.lss_in[s], b = w.lss_out[s];
-    w.ls_in[d] = a;
-    w.ls_out[d] = b;
-    // z0 = (z1 r2 - z2 r1) / (r2 - r1) with the radii in float-float: the float32 rounding of the
-    // radii would be amplified up to ~20x for endcap pairs
-    const float z1 = w.md_z[a], z2 = w.md_z[b];
-    const float r1 = w.md_r[a], r1l = w.md_rlo[a], r2 = w.md_r[b], r2l = w.md_rlo[b];
-    const float num = diff_prod(z1, r2, z2, r1) + (z1 * r2l - z2 * r1l);
-    const float den = (r2 - r1) + (r2l - r1l);
-    w.ls_z0[d] = num / den;
-    w.ls_dphi[d] = w.lss_dphi[s];
-    w.ls_xy_out[d] = make_float2(w.md_x[b], w.md_y[b]);
+  for (int d0 = blockIdx.x * blockDim.x; d0 < n; d0 += gridDim.x * blockDim.x) {
+    const int d = d0 + threadIdx.x;
+    int vm = 0;
+    unsigned outs = 0;
+    if (d < n) {
+      const int s = w.perm[d];
+      const int a = w.lss_in[s], b = w.lss_out[s];
+      w.ls_in[d] = a;
+      w.ls_out[d] = b;
+      // z0 = (z1 r2 - z2 r1) / (r2 - r1) with the radii in float-float: the float32 rounding of the
+      // radii would be amplified up to ~20x for endcap pairs
+      const float z1 = w.md_z[a], z2 = w.md_z[b];
+      const float r1 = w.md_r[a], r1l = w.md_rlo[a], r2 = w.md_r[b], r2l = w.md_rlo[b];
+      const float num = diff_prod(z1, r2, z2, r1) + (z1 * r2l - z2 * r1l);
+      const float den = (r2 - r1) + (r2l - r1l);
+      w.ls_z0[d] = num / den;
+      w.ls_dphi[d] = w.lss_dphi[s];
+      w.ls_xy_out[d] = make_float2(w.md_x[b], w.md_y[b]);
+      vm = w.md_vm[a];
+      outs = (unsigned)(min(w.lsin_off[b + 1], n) - min(w.lsin_off[b], n));
+    }
+    warp_add_keyed(w.t3_bound, vm, outs);
   }
 }
 

@@ -162,6 +162,8 @@ struct Ws {
   int32_t* eff = nullptr;    // [V + 1] valid slots per module of the stage being compacted, then their scan
   int32_t* grp_big = nullptr;       // [V] modules with more than 32 objects (compaction)
   int32_t* grp_big_cnt = nullptr;   // [4] their counts, one per stage
+  unsigned long long* t3_bound = nullptr;   // [V] T3 candidates per module (summed over its dense LS)
+  unsigned long long* t5_bound = nullptr;   // [V] T5 candidates per module (summed over its dense T3)
   int32_t* perm = nullptr;   // [max dense] slot of each dense object of the stage being compacted
   int32_t* status = nullptr;   // [ST_N_WORDS]
   int32_t* ev_stat = nullptr;  // [E][kEvWords]
@@ -256,6 +258,14 @@ __device__ __forceinline__ bool warp_over_budget(const Ws& w, long long t0) {
     return true;
   }
   return false;
+}
+
+// counters[key] += v over the lanes of a warp (all lanes call it; inactive lanes pass v = 0):
+// lanes with the same key are summed first, one atomic per distinct key
+__device__ __forceinline__ void warp_add_keyed(unsigned long long* counters, int key, unsigned v) {
+  const unsigned grp = __match_any_sync(0xffffffffu, key);
+  const unsigned sum = __reduce_add_sync(grp, v);
+  if ((threadIdx.x & 31) == __ffs(grp) - 1 && sum) atomicAdd(&counters[key], (unsigned long long)sum);
 }
 
 inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {

@@ -390,52 +390,6 @@ __global__ void k_pt_group(Ws w, int n_word, int64_t a_cap, const int32_t* a_pls
   (void)a_obj;
 }
 
-// order each seed's objects by object index (unique within a seed): a warp per seed; each element's
-// output position is its rank, the number of the seed's keys below its own (keys staged in shared
-// memory for groups up to kPtOrderSmem)
-constexpr int kPtOrderWarps = 4;
-constexpr int kPtOrderSmem = 256;
-
-__global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
-    Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls, const int32_t* a_obj, const float* a_xy,
-    const float* a_rz, const float* a_sc, int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc) {
-  __shared__ int keys[kPtOrderWarps][kPtOrderSmem];
-  int* K = keys[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  const int P = w.n_pls();
-  const int nwarps = gridDim.x * kPtOrderWarps;
-  for (int p = blockIdx.x * kPtOrderWarps + (threadIdx.x >> 5); p < P; p += nwarps) {
-    const int a = off[p], n = off[p + 1] - a;
-    if (n == 0) continue;
-    if (n <= 32) {
-      int v = 0, key = 0x7fffffff;
-      if (lane < n) {
-        v = tmp_idx[a + lane];
-        key = a_obj[v];
-      }
-      int rank = 0;
-      for (int j = 0; j < n; ++j) rank += __shfl_sync(0xffffffffu, key, j) < key;
-      if (lane < n) {
-        const int o = a + rank;
-        d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
-      }
-      continue;
-    }
-    const bool staged = n <= kPtOrderSmem;
-    if (staged)
-      for (int j = lane; j < n; j += 32) K[j] = a_obj[tmp_idx[a + j]];
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      const int v = tmp_idx[a + i];
-      const int key = a_obj[v];
-      int rank = 0;
-      for (int j = 0; j < n; ++j) rank += (staged ? K[j] : a_obj[tmp_idx[a + j]]) < key;
-      const int o = a + rank;
-      d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
-    }
-    __syncwarp();
-  }
-}
 
 // ---------------------------------------------------------------------------------------------
 // track candidates
@@ -518,17 +472,64 @@ __device__ __forceinline__ int best_of(const Ws& w, const int32_t* off, const fl
   return b;
 }
 
-__global__ void k_tc_best(Ws w) {
-  const int P = w.n_pls();
+// order each seed's objects by object index (unique within a seed): a warp per seed; each element's
+// output position is its rank, the number of the seed's keys below its own (keys staged in shared
+// memory for groups up to kPtOrderSmem). The same warp then picks the seed's best candidate by
+// (score, hit tuple) for the track-candidate stage; the pT5 pass (the second) also records whether
+// the seed is in any pT3 / pT5.
+constexpr int kPtOrderWarps = 4;
+constexpr int kPtOrderSmem = 256;
+
+template <int Type>
+__global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
+    Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls, const int32_t* a_obj, const float* a_xy,
+    const float* a_rz, const float* a_sc, int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc,
+    int32_t* best) {
+  __shared__ int keys[kPtOrderWarps][kPtOrderSmem];
+  int* K = keys[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += nwarps) {
-    const int b5 = best_of<TC_PT5>(w, w.pt5_off, w.pt5_sc, p);
-    const int b3 = best_of<TC_PT3>(w, w.pt3_off, w.pt3_sc, p);
+  const int P = w.n_pls();
+  const int nwarps = gridDim.x * kPtOrderWarps;
+  for (int p = blockIdx.x * kPtOrderWarps + (threadIdx.x >> 5); p < P; p += nwarps) {
+    const int a = off[p], n = off[p + 1] - a;
+    if (n == 0) {
+      if (lane == 0) {
+        best[p] = -1;
+        if (Type == TC_PT5) w.pls_member[p] = w.best3[p] >= 0 ? 1 : 0;
+      }
+      continue;
+    }
+    if (n <= 32) {
+      int v = 0, key = 0x7fffffff;
+      if (lane < n) {
+        v = tmp_idx[a + lane];
+        key = a_obj[v];
+      }
+      int rank = 0;
+      for (int j = 0; j < n; ++j) rank += __shfl_sync(0xffffffffu, key, j) < key;
+      if (lane < n) {
+        const int o = a + rank;
+        d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+      }
+    } else {
+    const bool staged = n <= kPtOrderSmem;
+    if (staged)
+      for (int j = lane; j < n; j += 32) K[j] = a_obj[tmp_idx[a + j]];
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const int v = tmp_idx[a + i];
+      const int key = a_obj[v];
+      int rank = 0;
+      for (int j = 0; j < n; ++j) rank += (staged ? K[j] : a_obj[tmp_idx[a + j]]) < key;
+      const int o = a + rank;
+      d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+    }
+    }
+    __syncwarp();   // the ordered rows are read back by the other lanes below
+    const int b = best_of<Type>(w, off, d_sc, p);
     if (lane == 0) {
-      w.best5[p] = b5;
-      w.best3[p] = b3;
-      w.pls_member[p] = (b5 >= 0 || b3 >= 0) ? 1 : 0;
+      best[p] = b;
+      if (Type == TC_PT5) w.pls_member[p] = (b >= 0 || w.best3[p] >= 0) ? 1 : 0;
     }
   }
 }
@@ -976,22 +977,21 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   scan_exclusive(w.p5_cnt, w.pt5_off, w.P, w.scan_tmp, L);
   k_pt_group<<<grid_for(w.cap.p3_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT3, w.cap.p3_slots, w.p3a_pls,
                                                                    w.p3a_obj, w.pt3_off, w.p3_cur, w.grp_tmp);
-  k_pt_order<<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
+  k_pt_order<TC_PT3><<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt3_off, w.grp_tmp, w.p3a_pls, w.p3a_obj, w.p3a_xy, w.p3a_rz, w.p3a_sc, w.pt3_pls, w.pt3_obj,
-      w.pt3_xy, w.pt3_rz, w.pt3_sc);
+      w.pt3_xy, w.pt3_rz, w.pt3_sc, w.best3);
   k_pt_group<<<grid_for(w.cap.p5_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT5, w.cap.p5_slots, w.p5a_pls,
                                                                    w.p5a_obj, w.pt5_off, w.p5_cur, w.grp_tmp);
-  k_pt_order<<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
+  k_pt_order<TC_PT5><<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt5_off, w.grp_tmp, w.p5a_pls, w.p5a_obj, w.p5a_xy, w.p5a_rz, w.p5a_sc, w.pt5_pls, w.pt5_obj,
-      w.pt5_xy, w.pt5_rz, w.pt5_sc);
+      w.pt5_xy, w.pt5_rz, w.pt5_sc, w.best5);
   *L.launches += 4;
 }
 
 void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   const double dr2 = c.d.dr_min * c.d.dr_min;
-  k_tc_best<<<grid_for((int64_t)w.P * 32, 256, 152 * 32), 256, 0, L.stream>>>(w);
   k_h5_count<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, 0);
-  *L.launches += 2;
+  *L.launches += 1;
   scan_exclusive(w.h5_cnt, w.h5_off, w.cap.H, w.scan_tmp, L);
   k_h5_count<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, 1);
   KT_BEGIN(L, K_TC_CLEAN);

@@ -392,6 +392,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.sens_cnt, S); z.add(w.sens_cur, S);
   z.add(w.md_cnt, V); z.add(w.ls_cnt, V); z.add(w.t3_cnt, V); z.add(w.t5_cnt, V);
   z.add(w.grp_big_cnt, 4);
+  z.add(w.t3_bound, V); z.add(w.t5_bound, V);
   z.add(w.p3_cnt, c.P); z.add(w.p3_cur, c.P); z.add(w.p5_cnt, c.P); z.add(w.p5_cur, c.P);
   z.add(w.h5_cnt, c.H + 1); z.add(w.h5_cur, c.H + 1);
   z.add(w.cell_cnt, NC); z.add(w.cell_cur, NC);

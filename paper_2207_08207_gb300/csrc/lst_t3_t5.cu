@@ -251,53 +251,51 @@ __device__ __forceinline__ int clamp_cap2(double pred, long long bound, int ovr)
   return (int)p;
 }
 
-// T3 capacity of module vm: bound = number of (inner LS, outer LS) pairs whose inner LS starts in vm
-// (a warp per module, lanes over its LS)
+// T3 capacity of module vm from its bound (the number of (inner LS, outer LS) pairs whose inner LS
+// starts in vm, summed while the LS were compacted)
 __global__ void k_t3_caps(Ws w) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int n_ls = w.ls_off[w.V];
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
-    long long bound = 0;
-    for (int i = w.ls_off[vm] + lane; i < w.ls_off[vm + 1]; i += 32) {
-      const int m2 = w.ls_out[i];
-      bound += min(w.lsin_off[m2 + 1], n_ls) - min(w.lsin_off[m2], n_ls);
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) bound += __shfl_xor_sync(0xffffffffu, bound, o);
-    if (lane == 0) {
-      const int cc = clamp_cap2(w.cap_scale * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
-      w.t3_cap[vm] = cc;
-      w.t3_base[vm] = cc;
-    }
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
+    const long long bound = (long long)w.t3_bound[vm];
+    const int cc = clamp_cap2(w.cap_scale * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
+    w.t3_cap[vm] = cc;
+    w.t3_base[vm] = cc;
   }
 }
 
-// dense T3 ordered by (inner LS, outer LS), with member MDs and an anchor cache for the pT3 stage
+// dense T3 ordered by (inner LS, outer LS), with member MDs, an anchor cache for the pT3 stage, and
+// each T3's count of outer partners (the T5 candidates it starts) summed per module
 __global__ void k_t3_dense(Ws w) {
   const int n = (int)lst_min64(w.t3_off[w.V], w.cap.t3_dense);
   const int64_t T = w.cap.t3_dense;
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
-    const int s = w.perm[d];
-    const int a = w.t3s_a[s], b = w.t3s_b[s];
-    w.t3_a[d] = a;
-    w.t3_b[d] = b;
-    const int md[3] = {w.ls_in[a], w.ls_out[a], w.ls_out[b]};
-    w.t3_md0[d] = md[0];
-    w.t3_md1[d] = md[1];
-    w.t3_md2[d] = md[2];
-    w.t3_R[d] = w.t3s_R[s];
-    w.t3_xc[d] = w.t3s_xc[s];
-    w.t3_yc[d] = w.t3s_yc[s];
-    w.t3_chi2[d] = w.t3s_chi2[s];
-    w.t3_pte[d] = w.t3s_pte[s];
-    uint8_t ecm = 0;
+  for (int d0 = blockIdx.x * blockDim.x; d0 < n; d0 += gridDim.x * blockDim.x) {
+    const int d = d0 + threadIdx.x;
+    int vm = 0;
+    unsigned outs = 0;
+    if (d < n) {
+      const int s = w.perm[d];
+      const int a = w.t3s_a[s], b = w.t3s_b[s];
+      w.t3_a[d] = a;
+      w.t3_b[d] = b;
+      const int md[3] = {w.ls_in[a], w.ls_out[a], w.ls_out[b]};
+      w.t3_md0[d] = md[0];
+      w.t3_md1[d] = md[1];
+      w.t3_md2[d] = md[2];
+      w.t3_R[d] = w.t3s_R[s];
+      w.t3_xc[d] = w.t3s_xc[s];
+      w.t3_yc[d] = w.t3s_yc[s];
+      w.t3_chi2[d] = w.t3s_chi2[s];
+      w.t3_pte[d] = w.t3s_pte[s];
+      uint8_t ecm = 0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      w.t3_anc[k * T + d] = make_float4(w.md_x[md[k]], w.md_y[md[k]], w.md_z[md[k]], w.md_r[md[k]]);
-      ecm |= (uint8_t)(w.md_ec[md[k]] << k);
+      for (int k = 0; k < 3; ++k) {
+        w.t3_anc[k * T + d] = w.md_xyzr[md[k]];
+        ecm |= (uint8_t)(w.md_ec[md[k]] << k);
+      }
+      w.t3_ecm[d] = ecm;
+      vm = w.md_vm[md[0]];
+      outs = (unsigned)(min(w.t3md_off[md[2] + 1], n) - min(w.t3md_off[md[2]], n));
     }
-    w.t3_ecm[d] = ecm;
+    warp_add_keyed(w.t5_bound, vm, outs);
   }
 }
 
@@ -382,22 +380,14 @@ __device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T 
   return chi2;
 }
 
+// T5 capacity of module vm from its bound (the number of (inner T3, outer T3) pairs whose inner T3
+// starts in vm, summed while the T3 were compacted)
 __global__ void k_t5_caps(Ws w) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
-    long long bound = 0;
-    for (int i = w.t3_off[vm] + lane; i < w.t3_off[vm + 1]; i += 32) {
-      const int m3 = w.t3_md2[i];
-      bound += w.t3md_off[m3 + 1] - w.t3md_off[m3];
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) bound += __shfl_xor_sync(0xffffffffu, bound, o);
-    if (lane == 0) {
-      const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
-      w.t5_cap[vm] = cc;
-      w.t5_base[vm] = cc;
-    }
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
+    const long long bound = (long long)w.t5_bound[vm];
+    const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
+    w.t5_cap[vm] = cc;
+    w.t5_base[vm] = cc;
   }
 }
 
@@ -533,7 +523,7 @@ __global__ void k_t5_dense(Ws w) {
 
 void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   (void)g;
-  k_t3_caps<<<grid_for((int64_t)w.V * 32, 256, 152 * 32), 256, 0, L.stream>>>(w);
+  k_t3_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   scan_exclusive(w.t3_base, w.t3_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T3_PRE);
@@ -549,16 +539,16 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
                w.t3in_off, w.cap.ls_dense, w.cap.t3_dense, ST_DENSE_T3,
                w.t3_off, w.ls_off, 1, 2};
   group_slots(w, ga, L);
-  k_t3_dense<<<grid_for(w.cap.t3_dense, 256), 256, 0, L.stream>>>(w);
-  LST_LAUNCH(L);
   // T3 by first MD: T3 are ordered by inner LS, and LS by inner MD
   compose_offsets(w.t3md_off, (int)w.cap.md_dense, w.lsin_off, 1, w.t3in_off, w.cap.t3_dense, L);
+  k_t3_dense<<<grid_for(w.cap.t3_dense, 256), 256, 0, L.stream>>>(w);
+  LST_LAUNCH(L);
   KT_END(L, K_T3_COMPACT);
 }
 
 void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   (void)g;
-  k_t5_caps<<<grid_for((int64_t)w.V * 32, 256, 152 * 32), 256, 0, L.stream>>>(w);
+  k_t5_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   scan_exclusive(w.t5_base, w.t5_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T5_PRE);
