@@ -110,10 +110,11 @@ def to_device(ev, torch):
             "pls": torch.as_tensor(ev.pls.view(np.uint8).copy(), device="cuda"), "n_pls": ev.n_pls}
 
 
-def serving_run(det, events, rate, n_requests, n_engines, max_batch, seed=0):
-    """Poisson stream of `n_requests` events (drawn cyclically from `events`) at `rate` per second."""
+def serving_run(det, events, rate, n_requests, batch_sizes, seed=0):
+    """Poisson stream of `n_requests` events (drawn cyclically from `events`) at `rate` per second,
+    served by resident engines of the given batch capacities."""
     from paper_2207_08207_gb300.serving import Server, poisson_arrivals
-    srv = Server(det, n_engines=n_engines, max_batch=max_batch, max_hits=max(e.n_hits for e in events),
+    srv = Server(det, batch_sizes=batch_sizes, max_hits=max(e.n_hits for e in events),
                  max_pls=max(e.n_pls for e in events), budget=40e9, keep="tc", use_graph=1, persistent=1)
     reqs = [events[i % len(events)] for i in range(n_requests)]
     srv.warmup(events)   # graph capture and arena first touch on every engine
@@ -379,12 +380,13 @@ def main():
     if not args.no_serving and rank == 0 and args.config == 2:
         from paper_2207_08207_gb300 import gen
         pool = [gen.config_event(5, e)[1] for e in range(24)]
-        serving = {"workload": "Poisson stream of PU ~ U[50, 300] events (24 generated, cycled), 40 GB budget",
+        serving = {"workload": "Poisson stream of PU ~ U[50, 300] events (24 generated, cycled), 40 GB budget; "
+                               "continuous batching over engines of 1, 4, 16 and 64 events vs one engine of 1",
                    "batched": [], "one_at_a_time": []}
         for rate in [float(r) for r in args.serving_rates.split(",")]:
             n_req = int(min(4000, max(200, rate * 2.0)))
-            serving["batched"].append(serving_run(det, pool, rate, n_req, n_engines=3, max_batch=64))
-            serving["one_at_a_time"].append(serving_run(det, pool, rate, min(n_req, 600), n_engines=1, max_batch=1))
+            serving["batched"].append(serving_run(det, pool, rate, n_req, batch_sizes=[1, 4, 16, 64]))
+            serving["one_at_a_time"].append(serving_run(det, pool, rate, min(n_req, 600), batch_sizes=[1]))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

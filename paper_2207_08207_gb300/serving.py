@@ -194,13 +194,15 @@ class LSTEngine(Engine):
 
 
 class Server:
-    """LST serving: resident contexts of different batch capacities (`batch_sizes`, default one
-    single-event context plus `n_engines - 1` of `max_batch`), continuous batching, memory admission."""
+    """LST serving: resident contexts of different batch capacities (`batch_sizes`, default capacities
+    growing by 4x up to `max_batch`), continuous batching, memory admission."""
 
-    def __init__(self, det, n_engines=3, max_batch=64, max_hits=150_000, max_pls=12_000, budget=40e9, device=0,
+    def __init__(self, det, n_engines=4, max_batch=64, max_hits=150_000, max_pls=12_000, budget=40e9, device=0,
                  keep="tc", batch_sizes=None, **cfg):
         if batch_sizes is None:
-            batch_sizes = [max_batch] if n_engines == 1 else [1] + [max_batch] * (n_engines - 1)
+            # capacities growing by 4x up to max_batch (1, 4, 16, 64 for four engines): a burst goes
+            # to the smallest free engine that takes it, whose capacity-shaped launches cost the least
+            batch_sizes = [max(1, max_batch // 4 ** k) for k in range(n_engines)][::-1]
         self.engines = [LSTEngine(det, b, max_hits, max_pls, device=device, keep=keep, **cfg) for b in batch_sizes]
         self.scheduler = Scheduler(self.engines, self.engines[0].predict, budget=budget, max_batch=max(batch_sizes))
 
