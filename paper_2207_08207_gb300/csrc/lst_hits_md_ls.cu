@@ -171,7 +171,7 @@ __global__ void k_md_caps(Ws w) {
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long nlo = w.sens_off[2 * vm + 1] - w.sens_off[2 * vm];
     const long long nup = w.sens_off[2 * vm + 2] - w.sens_off[2 * vm + 1];
-    const double pred = w.cap_scale * (3.0 * (double)max(nlo, nup) + 4.0);
+    const double pred = w.cap_scale * w.stage_scale[0] * (3.0 * (double)max(nlo, nup) + 4.0);
     const int c = clamp_cap(pred, nlo * nup, w.md_ovr[vm]);
     w.md_cap[vm] = c;
     w.md_base[vm] = c;
@@ -362,7 +362,7 @@ __global__ void k_ls_caps(Ws w, Geo g) {
     if (na > 0)
       for (int k = g.conn_off[m]; k < g.conn_off[m + 1]; ++k) nb += md_count(w, e0 + g.conn_tgt[k]);
     const long long bound = na * nb;
-    const double pred = w.cap_scale * (32.0 + 0.5 * (double)bound);
+    const double pred = w.cap_scale * w.stage_scale[1] * (32.0 + 0.5 * (double)bound);
     const int cc = clamp_cap(pred, bound, w.ls_ovr[vm]);
     w.ls_cap[vm] = cc;
     w.ls_base[vm] = cc;

@@ -59,6 +59,7 @@ struct Ws {
   __device__ __forceinline__ int n_pls() const { return ev_pls_off[E]; }
   Caps cap;
   float cap_scale = 1.0f;
+  const float* stage_scale = nullptr;   // [4] device: adaptive capacity multipliers (MD, LS, T3, T5)
   long long cycle_budget = 0;
   // inputs (concatenated events)
   float *x = nullptr, *y = nullptr, *z = nullptr;

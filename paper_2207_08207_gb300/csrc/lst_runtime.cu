@@ -189,6 +189,9 @@ struct lst_ctx {
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
   int32_t* h_status = nullptr;   // pinned: [ST_N_WORDS + E * kEvWords]
+  // capacity multipliers per stage (MD, LS, T3, T5), raised after a stage overflowed so that later
+  // batches of the same context rarely need a retry; copied to the device before each run
+  float stage_scale[4] = {1.0f, 1.0f, 1.0f, 1.0f};
   size_t h_status_words = 0;
   EvPtr* d_tab = nullptr;
   int tab_cap = 0;
@@ -331,12 +334,15 @@ int plan_input(lst_ctx* ctx, int64_t E, int64_t H, int64_t P) {
   pl.add(w.pls, c.P);
   pl.add(w.ev_hit_off, 2 * (c.E + 1));   // hit offsets, then seed offsets
   pl.add(w.md_ovr, V); pl.add(w.ls_ovr, V); pl.add(w.t3_ovr, V); pl.add(w.t5_ovr, V);
+  float* stage_scale = nullptr;
+  pl.add(stage_scale, 4);
   const size_t bytes = pl.layout();
   if (ctx->in_mem) CK(cudaFreeAsync(ctx->in_mem, ctx->stream));
   ctx->in_mem = nullptr;
   CK(cudaMallocFromPoolAsync(&ctx->in_mem, bytes, ctx->pool, ctx->stream));
   pl.assign(ctx->in_mem);
   w.ev_pls_off = w.ev_hit_off + (c.E + 1);
+  w.stage_scale = stage_scale;
   ctx->in_bytes = bytes;
   ctx->in_caps = c;
   ctx->arena_gen++;
@@ -892,6 +898,8 @@ int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event
   ctx->retries = 0;
   std::memset(ctx->first_ovf, 0, sizeof(ctx->first_ovf));
   ctx->user_out = out;
+  CK(cudaMemcpyAsync(const_cast<float*>(w.stage_scale), ctx->stage_scale, sizeof(ctx->stage_scale),
+                     cudaMemcpyHostToDevice, ctx->stream));
   rc = launch_chain(ctx);
   if (rc) return rc;
   ctx->pending = true;
@@ -971,6 +979,9 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
         return fail(ctx, LST_EOVERFLOW_UNRESOLVED, "lst_sync: object capacity still exceeded after retries");
       }
       ctx->retries++;
+      const int ovf_word[4] = {ST_OVF_MD, ST_OVF_LS, ST_OVF_T3, ST_OVF_T5};
+      for (int k = 0; k < 4; ++k)
+        if (st[ovf_word[k]]) ctx->stage_scale[k] = std::min(ctx->stage_scale[k] * 1.5f, 8.0f);
       if (raise) {
         const int V = (int)ctx->caps.E * ctx->geo.n_mods;
         const Ws& w = ctx->ws;

@@ -256,7 +256,7 @@ __device__ __forceinline__ int clamp_cap2(double pred, long long bound, int ovr)
 __global__ void k_t3_caps(Ws w) {
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long bound = (long long)w.t3_bound[vm];
-    const int cc = clamp_cap2(w.cap_scale * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
+    const int cc = clamp_cap2(w.cap_scale * w.stage_scale[2] * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
     w.t3_cap[vm] = cc;
     w.t3_base[vm] = cc;
   }
@@ -385,7 +385,7 @@ __device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T 
 __global__ void k_t5_caps(Ws w) {
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long bound = (long long)w.t5_bound[vm];
-    const int cc = clamp_cap2(w.cap_scale * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
+    const int cc = clamp_cap2(w.cap_scale * w.stage_scale[3] * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
     w.t5_cap[vm] = cc;
     w.t5_base[vm] = cc;
   }
