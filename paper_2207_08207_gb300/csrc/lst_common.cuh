@@ -358,7 +358,6 @@ template <class T, int N>
 __device__ __forceinline__ bool rz_fit(const Cst<T>& c, T akappa, const T* r, const T* z,
                                        const bool* ec, T& chi2, T& slope) {
   T s[N], sig[N];
-#pragma unroll
   const T two_r = T(2) / akappa;
 #pragma unroll
   for (int i = 0; i < N; ++i) s[i] = arc_len(akappa, two_r, r[i]);

@@ -476,7 +476,6 @@ __device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const
     if (slot < cap && (int64_t)base + slot < w.cap.ls_slots) {
       w.lss_in[base + slot] = a;
       w.lss_out[base + slot] = b;
-      w.lss_z0[base + slot] = z0;
       w.lss_dphi[base + slot] = dphi;
     }
   }
@@ -635,7 +634,6 @@ __global__ void k_ls_recheck(Ws w, Cst<double> c) {
     if (slot < cap && (int64_t)base + slot < w.cap.ls_slots) {
       w.lss_in[base + slot] = a;
       w.lss_out[base + slot] = b;
-      w.lss_z0[base + slot] = (float)z0;
       w.lss_dphi[base + slot] = (float)dphi;
     }
   }

@@ -88,7 +88,7 @@ struct Ws {
   // LS
   int32_t *ls_cap = nullptr, *ls_base = nullptr, *ls_cnt = nullptr, *ls_ovr = nullptr;
   int32_t *lss_in = nullptr, *lss_out = nullptr;
-  float *lss_z0 = nullptr, *lss_dphi = nullptr;
+  float* lss_dphi = nullptr;   // (z0 is computed again, in float-float, for the dense LS)
   int32_t* ls_off = nullptr;
   int32_t *ls_in = nullptr, *ls_out = nullptr;
   float *ls_z0 = nullptr, *ls_dphi = nullptr;
@@ -120,6 +120,7 @@ struct Ws {
   float4* box5 = nullptr;
   // pixel seeds and pT3 / pT5: passing objects are appended, then grouped by seed
   int32_t* pls_bin = nullptr;
+  int32_t* pls_ev = nullptr;     // [P] event of each seed
   float4* pls_seed = nullptr;    // [2][P] float32 seed helix: (x0, y0, z0, rho), (|kappa|, sin phi, cos phi, cot theta)
   int32_t *p3a_pls = nullptr, *p3a_obj = nullptr;
   float *p3a_xy = nullptr, *p3a_rz = nullptr, *p3a_sc = nullptr;
@@ -141,6 +142,8 @@ struct Ws {
   int32_t n_cells = 0;   // per event
   int32_t* tc_cnt = nullptr;   // [E]
   int32_t* tc_code = nullptr;  // [tc_capacity] candidate codes (type << 29 | index), per-event regions
+  int32_t* tc_perm = nullptr;  // [tc_capacity] source (collected index) of each ordered row
+  int32_t* tc_n = nullptr;     // [4 E] candidates collected per (event, type)
   unsigned long long* tc_key = nullptr;   // [tc_capacity] sort keys
   int32_t* tc_hit_key = nullptr;          // [tc_capacity][14] sorted hit tuples
   int32_t* grp_tmp = nullptr;             // [max(p3_slots, p5_slots)] grouping scratch

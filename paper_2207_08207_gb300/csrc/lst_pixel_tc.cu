@@ -38,8 +38,9 @@ __global__ void k_pls_prep(Ws w, Geo g) {
     const bool ok = isfinite(s.pt) && isfinite(s.eta) && isfinite(s.phi) && isfinite(s.x0) &&
                     isfinite(s.y0) && isfinite(s.z0) && s.pt > 0.f && (s.charge == 1 || s.charge == -1);
     int bin = -1;
+    const int e = find_seg(w.ev_pls_off, w.E, p);
+    w.pls_ev[p] = e;
     if (!ok) {
-      const int e = find_seg(w.ev_pls_off, w.E, p);
       atomicOr(&w.status[ST_ERROR], ERR_BAD_PLS);
       atomicOr(&w.ev_stat[e * kEvWords + kEvErr], ERR_BAD_PLS);
     } else if (g.n_pix_bins > 0) {
@@ -291,8 +292,7 @@ __global__ void __launch_bounds__(32 * kPxMaxWarps, 4) k_pt_pre(Ws w, Geo g, Cst
     if (warp_over_budget(w, t0)) break;
     const int bin = w.pls_bin[p];
     if (bin < 0) continue;
-    const int e = find_seg(w.ev_pls_off, w.E, p);
-    const int e0 = e * g.n_mods;
+    const int e0 = w.pls_ev[p] * g.n_mods;
     const Seed<float> s = cached_seed(w, p);
     const int tb = g.pix_off[bin], nt = g.pix_off[bin + 1] - tb;
     for (int t0 = 0; t0 < nt; t0 += 32) {
@@ -666,7 +666,7 @@ __global__ void k_grid_items(Ws w, Geo g, int fill) {
       if (w.best5[p] >= 0) code = (TC_PT5 << 29) | p;
       else if (w.best3[p] >= 0) code = (TC_PT3 << 29) | p;
       else continue;
-      e = find_seg(w.ev_pls_off, w.E, p);
+      e = w.pls_ev[p];
     } else {
       const int i = k - P;
       if (!w.t5_kept[i]) continue;
@@ -711,7 +711,7 @@ __global__ void k_clean_pt3(Ws w, double dr2) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     uint8_t acc = 0;
     if (w.best5[p] < 0 && w.best3[p] >= 0) {
-      const int e = find_seg(w.ev_pls_off, w.E, p);
+      const int e = w.pls_ev[p];
       acc = near_accepted(w, dr2, e, w.pls[p].eta, w.pls[p].phi, 1 << TC_PT5) ? 0 : 1;
     }
     w.acc3[p] = acc;
@@ -736,7 +736,7 @@ __global__ void k_clean_pls(Ws w, double dr2) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     uint8_t acc = 0;
     if (!w.pls_member[p]) {
-      const int e = find_seg(w.ev_pls_off, w.E, p);
+      const int e = w.pls_ev[p];
       acc = near_accepted(w, dr2, e, w.pls[p].eta, w.pls[p].phi,
                           (1 << TC_PT5) | (1 << TC_PT3) | (1 << TC_T5)) ? 0 : 1;
     }
@@ -786,25 +786,25 @@ __global__ void k_tc_count(Ws w, Geo g) {
   if (threadIdx.x == 0) w.tc_cnt[e] = ty[0] + ty[1] + ty[2] + ty[3];
 }
 
-// Assembly of one (event, type): collect the accepted candidates, sort them by their sorted hit
-// tuple, write the rows. The sort is a bitonic sort of 64-bit prefix keys (smallest hit) in shared
-// memory followed by an exact ordering of equal-prefix runs; rows of type t start after the event's
-// rows of the types before it.
-__global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem_raw);
-  int* sidx = reinterpret_cast<int*>(skey + kTcSortMax);
+// Assembly of the track candidates of each (event, type), ordered by their sorted hit tuple, in four
+// launches: collect the accepted candidates, build their keys (all candidates in parallel), sort
+// the keys (bitonic sort of 64-bit prefix keys in shared memory, then an exact ordering of
+// equal-prefix runs), write the rows (in parallel). Rows of type t start after the event's rows of
+// the types before it.
+__device__ __forceinline__ int tc_region(const Ws& w, const Geo& g, int e, int type) {
+  int before = 0;
+  for (int t = 0; t < type; ++t) before += w.ev_stat[e * kEvWords + 7 + t];
+  return w.ev_pls_off[e] + w.t5_off[e * g.n_mods] + before;
+}
+
+// (1) a block per (event, type) collects the accepted candidates' codes (type << 29 | index)
+__global__ void k_tc_collect(Ws w, Geo g) {
   __shared__ int n_sh;
   const int e = blockIdx.x, type = blockIdx.y;
   if (e >= w.E) return;
   const int p0 = w.ev_pls_off[e], p1 = w.ev_pls_off[e + 1];
   const int t0 = w.t5_off[e * g.n_mods], t1 = w.t5_off[(e + 1) * g.n_mods];
-  int before = 0;
-  for (int t = 0; t < type; ++t) before += w.ev_stat[e * kEvWords + 7 + t];
-  const int region = p0 + t0 + before;
-  int* code = w.tc_code + region;
-  unsigned long long* key = w.tc_key + region;
-  int* hk = w.tc_hit_key + (int64_t)region * 14;
+  int* code = w.tc_code + tc_region(w, g, e, type);
   if (threadIdx.x == 0) n_sh = 0;
   __syncthreads();
   if (type == TC_T5) {
@@ -817,76 +817,107 @@ __global__ void __launch_bounds__(1024) k_tc_assemble(Ws w, Geo g) {
     }
   }
   __syncthreads();
-  const int n = n_sh;
-  if (n == 0) return;
-  // sorted hit tuples (padded with INT_MAX) and 64-bit prefix keys
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  if (threadIdx.x == 0) w.tc_n[e * 4 + type] = n_sh;
+}
+
+// (2) the sorted hit tuple (padded with INT_MAX) and 64-bit prefix key of every collected candidate;
+// blockIdx.y = event * 4 + type, the x blocks share its candidates
+__global__ void k_tc_keys(Ws w, Geo g) {
+  const int e = blockIdx.y >> 2, type = blockIdx.y & 3;
+  if (e >= w.E) return;
+  const int n = w.tc_n[blockIdx.y];
+  const int region = tc_region(w, g, e, type);
+  const int* code = w.tc_code + region;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int idx = code[k] & ((1 << 29) - 1);
     int h[14];
     const int obj = (type == TC_PT5) ? w.best5[idx] : (type == TC_PT3 ? w.best3[idx] : idx);
     const int nh = code_hits(w, type, obj, h);
     sort_small(h, nh);
-    for (int t = 0; t < 14; ++t) hk[(int64_t)k * 14 + t] = t < nh ? h[t] : 0x7fffffff;
-    key[k] = tc_sort_key(type, h[0], nh > 1 ? h[1] : 0x7fffffff);
+    int* hk = w.tc_hit_key + (int64_t)(region + k) * 14;
+    for (int t = 0; t < 14; ++t) hk[t] = t < nh ? h[t] : 0x7fffffff;
+    w.tc_key[region + k] = tc_sort_key(type, h[0], nh > 1 ? h[1] : 0x7fffffff);
   }
-  __syncthreads();
-  const bool in_smem = n <= kTcSortMax;
+}
+
+// (3) a block per (event, type) sorts the keys (bitonic in shared memory; equal prefixes ordered on
+// the full tuples) and records each row's source: tc_perm[region + rank] = collected index
+__global__ void __launch_bounds__(1024) k_tc_sort(Ws w, Geo g) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem_raw);
+  int* sidx = reinterpret_cast<int*>(skey + kTcSortMax);
+  const int e = blockIdx.x, type = blockIdx.y;
+  if (e >= w.E) return;
+  const int n = w.tc_n[e * 4 + type];
+  if (n == 0) return;
+  const int region = tc_region(w, g, e, type);
+  const unsigned long long* key = w.tc_key + region;
+  const int* hk = w.tc_hit_key + (int64_t)region * 14;
+  int* perm = w.tc_perm + region;
+  if (n > kTcSortMax) {   // ranks counted directly
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      int rank = 0;
+      for (int j = 0; j < n; ++j) rank += hit_key_cmp(hk + (int64_t)j * 14, hk + (int64_t)k * 14) < 0;
+      perm[rank] = k;
+    }
+    return;
+  }
   int m = 1;
   while (m < n) m <<= 1;
-  if (in_smem) {
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-      skey[k] = k < n ? key[k] : ~0ull;
-      sidx[k] = k < n ? k : 0x7fffffff;
-    }
-    __syncthreads();
-    for (int size = 2; size <= m; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int t = threadIdx.x; t < m / 2; t += blockDim.x) {
-          const int lo = 2 * t - (t & (stride - 1));
-          const int hi = lo + stride;
-          const bool up = ((lo & size) == 0);
-          const unsigned long long a = skey[lo], b = skey[hi];
-          const bool gt = (a > b) || (a == b && sidx[lo] > sidx[hi]);
-          if (gt == up) {
-            skey[lo] = b; skey[hi] = a;
-            const int ti = sidx[lo]; sidx[lo] = sidx[hi]; sidx[hi] = ti;
-          }
-        }
-        __syncthreads();
-      }
-    }
-    // exact order inside runs of equal prefix keys (rare, short: insertion sort on full tuples by the
-    // thread at the start of each run)
-    for (int r0 = threadIdx.x; r0 < n; r0 += blockDim.x) {
-      if ((r0 == 0 || skey[r0 - 1] != skey[r0]) && r0 + 1 < n && skey[r0 + 1] == skey[r0]) {
-        int r1 = r0 + 1;
-        while (r1 < n && skey[r1] == skey[r0]) ++r1;
-        for (int i = r0 + 1; i < r1; ++i) {
-          const int v = sidx[i];
-          int j = i - 1;
-          while (j >= r0 && hit_key_cmp(hk + (int64_t)sidx[j] * 14, hk + (int64_t)v * 14) > 0) {
-            sidx[j + 1] = sidx[j];
-            --j;
-          }
-          sidx[j + 1] = v;
-        }
-      }
-    }
-    __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    skey[k] = k < n ? key[k] : ~0ull;
+    sidx[k] = k < n ? k : 0x7fffffff;
   }
-  // write rows in order (ranks computed directly when the set does not fit the shared sort)
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    int src, rank;
-    if (in_smem) {
-      src = sidx[k];
-      rank = k;
-    } else {
-      src = k;
-      rank = 0;
-      for (int j = 0; j < n; ++j) rank += hit_key_cmp(hk + (int64_t)j * 14, hk + (int64_t)k * 14) < 0;
+  __syncthreads();
+  for (int size = 2; size <= m; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < m / 2; t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = ((lo & size) == 0);
+        const unsigned long long a = skey[lo], b = skey[hi];
+        const bool gt = (a > b) || (a == b && sidx[lo] > sidx[hi]);
+        if (gt == up) {
+          skey[lo] = b; skey[hi] = a;
+          const int ti = sidx[lo]; sidx[lo] = sidx[hi]; sidx[hi] = ti;
+        }
+      }
+      __syncthreads();
     }
-    const int idx = code[src] & ((1 << 29) - 1);
-    const int row = region + rank;
+  }
+  // exact order inside runs of equal prefix keys (rare, short: insertion sort on full tuples by the
+  // thread at the start of each run)
+  for (int r0 = threadIdx.x; r0 < n; r0 += blockDim.x) {
+    if ((r0 == 0 || skey[r0 - 1] != skey[r0]) && r0 + 1 < n && skey[r0 + 1] == skey[r0]) {
+      int r1 = r0 + 1;
+      while (r1 < n && skey[r1] == skey[r0]) ++r1;
+      for (int i = r0 + 1; i < r1; ++i) {
+        const int v = sidx[i];
+        int j = i - 1;
+        while (j >= r0 && hit_key_cmp(hk + (int64_t)sidx[j] * 14, hk + (int64_t)v * 14) > 0) {
+          sidx[j + 1] = sidx[j];
+          --j;
+        }
+        sidx[j + 1] = v;
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) perm[k] = sidx[k];
+}
+
+// (4) the rows in order: blockIdx.y = event * 4 + type, the x blocks share its rows
+__global__ void k_tc_write(Ws w, Geo g) {
+  const int e = blockIdx.y >> 2, type = blockIdx.y & 3;
+  if (e >= w.E) return;
+  const int n = w.tc_n[blockIdx.y];
+  const int region = tc_region(w, g, e, type);
+  const int p0 = w.ev_pls_off[e];
+  const int t0 = w.t5_off[e * g.n_mods];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int src = w.tc_perm[region + r];
+    const int idx = w.tc_code[region + src] & ((1 << 29) - 1);
+    const int row = region + r;
     int h[14];
     int obj, nh;
     float pt, eta, phi;
@@ -1008,7 +1039,11 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_BEGIN(L, K_TC_ASSEMBLE);
   k_tc_count<<<w.E, 256, 0, L.stream>>>(w, g);
   LST_LAUNCH(L);
-  k_tc_assemble<<<dim3(w.E, 4), 1024, smem, L.stream>>>(w, g);
+  k_tc_collect<<<dim3(w.E, 4), 256, 0, L.stream>>>(w, g);
+  k_tc_keys<<<dim3(8, 4 * w.E), 256, 0, L.stream>>>(w, g);
+  k_tc_sort<<<dim3(w.E, 4), 1024, smem, L.stream>>>(w, g);
+  k_tc_write<<<dim3(8, 4 * w.E), 256, 0, L.stream>>>(w, g);
+  *L.launches += 3;
   KT_END(L, K_TC_ASSEMBLE);
   scan_exclusive(w.tc_cnt, w.tcd_off, w.E, w.scan_tmp, L);
   k_tc_dense<<<dim3(16, w.E), 256, 0, L.stream>>>(w, g);
@@ -1021,7 +1056,7 @@ int tc_cells_per_event() { return kCellsEta * kCellsPhi; }
 
 void tc_configure() {
   const size_t smem = kTcSortMax * (sizeof(unsigned long long) + sizeof(int));
-  cudaFuncSetAttribute(k_tc_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_tc_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace lst

@@ -420,7 +420,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.md_xyzr, c.md_dense); pl.add(w.md_sa, c.md_dense);
   // LS
   pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1); pl.add(w.lsin_off, c.md_dense + 2);
-  pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_z0, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
+  pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
   pl.add(w.ls_in, c.ls_dense); pl.add(w.ls_out, c.ls_dense); pl.add(w.ls_z0, c.ls_dense); pl.add(w.ls_dphi, c.ls_dense);
   pl.add(w.ls_xy_out, c.ls_dense);
   // T3
@@ -440,7 +440,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.t5_kept, c.t5_dense); pl.add(w.acc5t, c.t5_dense);
   pl.add(w.box3, 2 * V); pl.add(w.box5, 2 * V);
   // pixel
-  pl.add(w.pls_bin, c.P); pl.add(w.pls_seed, 2 * c.P);
+  pl.add(w.pls_bin, c.P); pl.add(w.pls_ev, c.P); pl.add(w.pls_seed, 2 * c.P);
   pl.add(w.p3a_pls, c.p3_slots); pl.add(w.p3a_obj, c.p3_slots); pl.add(w.p3a_xy, c.p3_slots);
   pl.add(w.p3a_rz, c.p3_slots); pl.add(w.p3a_sc, c.p3_slots); pl.add(w.pt3_off, c.P + 1);
   pl.add(w.pt3_pls, c.p3_slots); pl.add(w.pt3_obj, c.p3_slots); pl.add(w.pt3_xy, c.p3_slots);
@@ -455,7 +455,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.h5_off, c.H + 2); pl.add(w.h5_idx, 10 * c.t5_dense);
   pl.add(w.t5_hit, 10 * c.t5_dense);
   pl.add(w.cell_off, NC + 1); pl.add(w.cell_item, c.P + c.t5_dense);
-  pl.add(w.tc_code, tc_cap); pl.add(w.tc_key, tc_cap); pl.add(w.tc_hit_key, 14 * tc_cap);
+  pl.add(w.tc_code, tc_cap); pl.add(w.tc_perm, tc_cap); pl.add(w.tc_n, 4 * c.E); pl.add(w.tc_key, tc_cap); pl.add(w.tc_hit_key, 14 * tc_cap);
   pl.add(w.tc_type, tc_cap); pl.add(w.tc_obj, tc_cap); pl.add(w.tc_hits, 14 * tc_cap);
   pl.add(w.tc_pt, tc_cap); pl.add(w.tc_eta, tc_cap); pl.add(w.tc_phi, tc_cap);
   pl.add(w.tcd_off, c.E + 1);

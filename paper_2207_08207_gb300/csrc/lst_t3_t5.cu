@@ -17,11 +17,6 @@
 namespace lst {
 namespace {
 
-// chi2 pre-filter: reject only when clearly above the cut (float32 error is far below the guard)
-__device__ __forceinline__ bool chi2_clear_fail(float chi2, float cut) {
-  return chi2 > cut * (1.0f + kGuardChi2) + kGuardChi2Abs;
-}
-
 template <class T>
 struct Anchor {
   T x, y, z, r;
@@ -41,49 +36,35 @@ __device__ __forceinline__ Anchor<T> anchor(const Ws& w, int d) {
   return a;
 }
 
-// T3 selection on anchors (h1, h2, h3). Returns the verdict (float: pre-filter semantics, where
-// kAccept means "not clearly rejected").
+// T3 selection on anchors (h1, h2, h3), in the decision precision (double-float): circle through
+// the anchors with the pT and d0 cuts, and the straight-line fit in (s, z) of the three anchors in
+// closed form: chi2 = (c.z)^2 / sum(c_i^2 sigma_i^2) with c = (s3 - s2, s1 - s3, s2 - s1), the
+// combination of the z's that every line annuls (identical to the weighted least-squares fit's chi2).
 template <class T>
 __device__ __forceinline__ int t3_eval(const Cst<T>& c, const Anchor<T>& h1, const Anchor<T>& h2,
                                        const Anchor<T>& h3, Circle3<T>& circ, T& chi2) {
   circ = circle3<T>(h1.x, h1.y, h2.x, h2.y, h3.x, h3.y);
   const T ak = m_abs(circ.kappa);
-  chi2 = T(0);
-  if constexpr (sizeof(T) == 4) {
-    Acc32 acc(kGuardWindow * 4.0f);
-    acc.cut_ge(c.f_t3 * c.pt_thr, c.k / ak);
-    acc.cut(c.d0_t3, circ.d0);
-    if (acc.fail) return kReject;
-    const T r[3] = {h1.r, h2.r, h3.r}, z[3] = {h1.z, h2.z, h3.z};
-    const bool ec[3] = {h1.ec, h2.ec, h3.ec};
-    T slope;
-    if (!rz_fit<T, 3>(c, ak, r, z, ec, chi2, slope)) return kAccept;  // decided in float64
-    return chi2_clear_fail(chi2, c.chi2_t3) ? kReject : kAccept;
+  typename AccOf<T>::type acc;
+  acc.cut_ge(c.f_t3 * c.pt_thr, c.k * circ.R);
+  acc.cut(c.d0_t3, circ.d0);
+  const T two_r = T(2) / ak;
+  const T s1 = arc_len(ak, two_r, h1.r), s2 = arc_len(ak, two_r, h2.r), s3 = arc_len(ak, two_r, h3.r);
+  if (!(s3 > s1)) {
+    acc.reject();
+    chi2 = T(1) / T(0);
   } else {
-    typename AccOf<T>::type acc;
-    acc.cut_ge(c.f_t3 * c.pt_thr, c.k * circ.R);
-    acc.cut(c.d0_t3, circ.d0);
-    // the straight-line fit in (s, z) of three anchors, in closed form: chi2 = (c.z)^2 / sum(c_i^2
-    // sigma_i^2) with c = (s3 - s2, s1 - s3, s2 - s1), the combination of the z's that every line
-    // annuls (identical to the weighted least-squares fit's chi2)
-    const T two_r = T(2) / ak;
-    const T s1 = arc_len(ak, two_r, h1.r), s2 = arc_len(ak, two_r, h2.r), s3 = arc_len(ak, two_r, h3.r);
-    if (!(s3 > s1)) {
-      acc.reject();
-      chi2 = T(1) / T(0);
-    } else {
-      const T b0 = m_abs((h3.z - h1.z) / (s3 - s1));
-      const T sg1 = m_max(h1.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
-      const T sg2 = m_max(h2.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
-      const T sg3 = m_max(h3.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
-      const T c1 = s3 - s2, c2 = s1 - s3, c3 = s2 - s1;
-      const T num = c1 * h1.z + c2 * h2.z + c3 * h3.z;
-      const T den = c1 * c1 * sg1 * sg1 + c2 * c2 * sg2 * sg2 + c3 * c3 * sg3 * sg3;
-      chi2 = num * num / den;
-      acc.cut(c.chi2_t3, chi2);
-    }
-    return acc.verdict();
+    const T b0 = m_abs((h3.z - h1.z) / (s3 - s1));
+    const T sg1 = m_max(h1.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
+    const T sg2 = m_max(h2.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
+    const T sg3 = m_max(h3.ec ? c.sigma_r * b0 : c.sigma_z, c.sigma_floor);
+    const T c1 = s3 - s2, c2 = s1 - s3, c3 = s2 - s1;
+    const T num = c1 * h1.z + c2 * h2.z + c3 * h3.z;
+    const T den = c1 * c1 * sg1 * sg1 + c2 * c2 * sg2 * sg2 + c3 * c3 * sg3 * sg3;
+    chi2 = num * num / den;
+    acc.cut(c.chi2_t3, chi2);
   }
+  return acc.verdict();
 }
 
 // Quick rejection of a T3 candidate from its three anchors, exact-safe (true only when the float64
