@@ -13,6 +13,7 @@ the roofline of the dominant kernel, the CPU oracle baseline, and the SM clocks 
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -36,6 +37,14 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _pinned_copy(a):
+    """A copy of the 1-D numpy array `a` in pinned (page-locked) host memory."""
+    import torch
+    t = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+    t[:] = a.view(np.uint8).reshape(-1)
+    return t.view(a.dtype)
 
 
 def _sm_max_mhz():
@@ -360,12 +369,19 @@ def main():
               "obj": pin((cap_tc,), torch.int32), "hits": pin((cap_tc, 14), torch.int32),
               "pt": pin((cap_tc,), torch.float32), "eta": pin((cap_tc,), torch.float32),
               "phi": pin((cap_tc,), torch.float32)}
+    # the step's inputs in pinned host memory (the source of the host-to-device transfer)
+    def pinned_event(ev):
+        f32 = lambda a: _pinned_copy(np.ascontiguousarray(a, dtype=np.float32))
+        return dataclasses.replace(ev, x=f32(ev.x), y=f32(ev.y), z=f32(ev.z),
+                                   sensor=_pinned_copy(np.ascontiguousarray(ev.sensor, dtype=np.int32)),
+                                   pls=_pinned_copy(np.ascontiguousarray(ev.pls)))
+    evs_pin = [pinned_event(e) for e in evs] if not args.no_e2e else []
     for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5)) + 1):
         if len(e2e_ms) == 1 and e2e_ms[0] != e2e_ms[0]:
             e2e_ms = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.submit(evs, stream=stream)
+        ctx.submit(evs_pin, stream=stream, host_async=True)
         ctx.sync()
         tc = ctx.copy_tc_all(tc_buf)
         n_tc = tc["n"]
@@ -419,7 +435,7 @@ def main():
                                   "tc": sum(c["n_tc"] for c in counts) / B},
             "retries": max(c["retries"] for c in counts),
             "overflow_first_pass": counts[0]["overflow"],
-            "f64_decisions_per_batch": counts[0]["recheck"],
+            "exact_decisions_per_batch": counts[0]["recheck"],
         }
         print(json.dumps(line))
     ctx.close()

@@ -40,7 +40,12 @@ typedef enum {
   LST_ESTATE = 6                  /* call out of order (e.g. no geometry loaded) */
 } lst_status;
 
-enum { LST_MEM_HOST = 0, LST_MEM_DEVICE = 1 };
+/* Where an event's input arrays live. LST_MEM_HOST: host memory, copied before lst_run_events
+ * returns. LST_MEM_DEVICE: device memory of the context's device. LST_MEM_HOST_ASYNC: host memory
+ * that the caller keeps unchanged until lst_sync returns; where the GPU can read it in place (pinned
+ * memory, or pageable memory on a coherent host link such as NVLink-C2C) the device gathers it
+ * directly inside the run, else it is copied like LST_MEM_HOST. */
+enum { LST_MEM_HOST = 0, LST_MEM_DEVICE = 1, LST_MEM_HOST_ASYNC = 2 };
 
 /* Stage indices used by the per-stage arrays of lst_counts. */
 enum {
@@ -116,8 +121,9 @@ typedef struct {
   int32_t pad;
 } lst_pls;
 
-/* One event. sensor[i] = 2 * module + (0 lower sensor | 1 upper sensor). Inputs are read during
- * lst_run_events (copied into the context) and may be released when it returns. */
+/* One event. sensor[i] = 2 * module + (0 lower sensor | 1 upper sensor). LST_MEM_HOST and
+ * LST_MEM_DEVICE inputs are read during lst_run_events (copied into the context) and may be released
+ * when it returns; LST_MEM_HOST_ASYNC inputs must stay valid until lst_sync returns. */
 typedef struct {
   const float* x;
   const float* y;
@@ -126,16 +132,16 @@ typedef struct {
   int32_t n_hits;
   const lst_pls* pls;
   int32_t n_pls;
-  int32_t mem_space;   /* LST_MEM_HOST or LST_MEM_DEVICE, for all five arrays */
+  int32_t mem_space;   /* LST_MEM_HOST, LST_MEM_DEVICE or LST_MEM_HOST_ASYNC, for all five arrays */
 } lst_event_in;
 
 /* Per-event object counts and status. overflow[s] counts, for the whole batch the event was part
  * of, the objects that did not fit stage s's capacities on the first pass (per-module capacity or
- * the stage's slot arena; overflow[LST_STAGE_QUEUE]: entries beyond a float64-decision queue); they
+ * the stage's slot arena; overflow[LST_STAGE_QUEUE]: entries beyond an exact-decision queue); they
  * were recovered by a retry (retries > 0) unless status is LST_EOVERFLOW_UNRESOLVED.
- * recheck[s] (batch totals) counts candidates decided in float64: for MD and LS those whose float32
- * cut margins were too close to a threshold, for T3 / T5 / pT3 / pT5 every candidate that survived
- * the float32 pre-filter. */
+ * recheck[s] (batch totals) counts candidates decided in the exact path (float64 for MD and LS,
+ * double-float for T3 / T5 / pT3 / pT5): for MD and LS those whose float32 cut margins were too
+ * close to a threshold, for the others every candidate that survived the float32 pre-filter. */
 typedef struct {
   int32_t n_hits, n_pls;
   int32_t n_md, n_ls, n_t3, n_t5, n_pt3, n_pt5, n_tc;

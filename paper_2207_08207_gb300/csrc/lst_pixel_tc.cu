@@ -598,6 +598,7 @@ __global__ void k_t5_clean(Ws w, int overlap) {
       int shared = 0;
 #pragma unroll
       for (int kb = 0; kb < 10; ++kb) {
+        if (shared + (10 - kb) < overlap) break;   // the rest cannot reach the overlap
         const int hb = w.t5_hit[(int64_t)b * 10 + kb];
 #pragma unroll
         for (int u = 0; u < 10; ++u) shared += ha[u] == hb;

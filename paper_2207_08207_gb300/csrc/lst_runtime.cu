@@ -37,6 +37,17 @@ struct EvPtr {
   const lst_pls* pls;
 };
 
+// A device-readable address of host memory: pinned (page-locked) memory through its mapped device
+// pointer, pageable memory directly where the GPU reads it coherently; nullptr when neither.
+const void* device_view(const void* host, bool pageable_access) {
+  if (!host) return nullptr;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, host) == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer)
+    return attr.devicePointer;
+  cudaGetLastError();
+  return pageable_access ? host : nullptr;
+}
+
 // concatenate device-resident events into the input arena
 __global__ void k_gather(const EvPtr* tab, Ws w, int H, int P) {
   const int64_t n = (int64_t)H + P;
@@ -210,6 +221,7 @@ struct lst_ctx {
   long long launches = 0;
   int n_sm = 152;
   int ls_bps = 0;
+  bool pageable_access = false;   // the GPU reads pageable host memory coherently (e.g. NVLink-C2C)
   // CUDA graph of the whole chain for the current arenas (shape-independent within capacities)
   cudaGraphExec_t graph_exec = nullptr;
   long long graph_nodes = 0;
@@ -666,6 +678,9 @@ int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
   ctx->stream = ctx->own_stream;
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
   if (ctx->n_sm <= 0) ctx->n_sm = 152;
+  int pageable = 0;
+  cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+  ctx->pageable_access = pageable != 0;
   ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls);
   tc_configure();
   group_configure();
@@ -803,7 +818,8 @@ int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event
     if (ev[e].n_hits > 0 && (!ev[e].x || !ev[e].y || !ev[e].z || !ev[e].sensor))
       return fail(ctx, LST_EINVAL, "lst_run_events: NULL hit array");
     if (ev[e].n_pls > 0 && !ev[e].pls) return fail(ctx, LST_EINVAL, "lst_run_events: NULL seed array");
-    if (ev[e].mem_space != LST_MEM_HOST && ev[e].mem_space != LST_MEM_DEVICE)
+    if (ev[e].mem_space != LST_MEM_HOST && ev[e].mem_space != LST_MEM_DEVICE &&
+        ev[e].mem_space != LST_MEM_HOST_ASYNC)
       return fail(ctx, LST_EINVAL, "lst_run_events: bad mem_space");
     (ev[e].mem_space == LST_MEM_DEVICE ? any_dev : any_host) = true;
     H += ev[e].n_hits;
@@ -839,8 +855,31 @@ int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event
     ctx->ev_pls[e] = ev[e].n_pls;
   }
   Ws& w = ctx->ws;
-  // stage the inputs: host events are packed into pinned memory and copied with one transfer per
-  // array; device events are gathered by one kernel
+  // stage the inputs. Device events, and LST_MEM_HOST_ASYNC events the GPU can read where they are
+  // (pinned, or pageable with coherent access), are gathered by one kernel straight into the input
+  // arena; other host events are packed into the context's pinned buffer before this call returns and
+  // copied with one transfer per array.
+  std::vector<EvPtr> views(n_ev);
+  bool direct = true;
+  for (int32_t e = 0; e < n_ev; ++e) {
+    if (ev[e].mem_space == LST_MEM_DEVICE) {
+      views[e] = EvPtr{ev[e].x, ev[e].y, ev[e].z, ev[e].sensor, ev[e].pls};
+      continue;
+    }
+    if (ev[e].mem_space == LST_MEM_HOST) {
+      direct = false;
+      continue;
+    }
+    views[e] = EvPtr{static_cast<const float*>(device_view(ev[e].x, ctx->pageable_access)),
+                     static_cast<const float*>(device_view(ev[e].y, ctx->pageable_access)),
+                     static_cast<const float*>(device_view(ev[e].z, ctx->pageable_access)),
+                     static_cast<const int32_t*>(device_view(ev[e].sensor, ctx->pageable_access)),
+                     static_cast<const lst_pls*>(device_view(ev[e].pls, ctx->pageable_access))};
+    if ((ev[e].n_hits && (!views[e].x || !views[e].y || !views[e].z || !views[e].sensor)) ||
+        (ev[e].n_pls && !views[e].pls))
+      direct = false;
+  }
+  if (direct) any_host = false;
   const size_t off_bytes = 2 * ((size_t)Ecap + 1) * sizeof(int32_t);
   const size_t host_bytes = any_host ? (size_t)H * 16 + (size_t)P * sizeof(lst_pls) : 0;
   rc = ensure_pinned(ctx, off_bytes + host_bytes + (size_t)n_ev * sizeof(EvPtr) + 64);
@@ -881,7 +920,7 @@ int lst_run_events(lst_ctx* ctx, const lst_event_in* ev, int32_t n_ev, lst_event
       ctx->tab_cap = n_ev;
     }
     EvPtr* ht = reinterpret_cast<EvPtr*>(hp + off_bytes);
-    for (int32_t e = 0; e < n_ev; ++e) ht[e] = EvPtr{ev[e].x, ev[e].y, ev[e].z, ev[e].sensor, ev[e].pls};
+    for (int32_t e = 0; e < n_ev; ++e) ht[e] = views[e];
     CK(cudaMemcpyAsync(ctx->d_tab, ht, n_ev * sizeof(EvPtr), cudaMemcpyHostToDevice, ctx->stream));
     w.E = Ecap;
     if (H + P > 0) {

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblst.so")
 
 LST_OK, LST_EINVAL, LST_ENOMEM, LST_ECUDA, LST_ETIMEOUT, LST_EOVERFLOW_UNRESOLVED, LST_ESTATE = range(7)
-LST_MEM_HOST, LST_MEM_DEVICE = 0, 1
+LST_MEM_HOST, LST_MEM_DEVICE, LST_MEM_HOST_ASYNC = 0, 1, 2
 STAGES = ["md", "ls", "t3", "t5", "pt3", "pt5", "tc", "queue"]
 TC_TYPES = ["pT5", "pT3", "T5", "pLS"]
 
@@ -207,9 +207,11 @@ class Context:
         self._check(self._L.lst_reserve(self._h, n_events, max_hits, max_pls))
 
     # -- running ----------------------------------------------------------------------------
-    def submit(self, events, stream=None):
+    def submit(self, events, stream=None, host_async=False):
         """Enqueue a batch. `events`: gen.Event objects (host numpy) or dicts of torch CUDA tensors
-        with keys x, y, z, sensor, pls (uint8/int32 tensor viewing lst_pls records or None)."""
+        with keys x, y, z, sensor, pls (uint8/int32 tensor viewing lst_pls records or None).
+        host_async: pass host events as LST_MEM_HOST_ASYNC (the arrays are held until sync; pinned
+        arrays are then read by the device in place instead of being packed on the host)."""
         n = len(events)
         arr = (EventIn * n)()
         keep = []
@@ -225,7 +227,7 @@ class Context:
                 s = np.ascontiguousarray(ev.sensor, dtype=np.int32)
                 p = np.ascontiguousarray(ev.pls) if ev.n_pls else None
                 n_pls = ev.n_pls
-                mem = LST_MEM_HOST
+                mem = LST_MEM_HOST_ASYNC if host_async else LST_MEM_HOST
             keep += [x, y, z, s, p]
             nh = int(x.shape[0]) if hasattr(x, "shape") else len(x)
             arr[i] = EventIn(_ptr(x), _ptr(y), _ptr(z), _ptr(s), nh, _ptr(p) if n_pls else None, n_pls, mem)

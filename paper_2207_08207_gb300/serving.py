@@ -172,7 +172,7 @@ class LSTEngine(Engine):
         return self.ctx.predict_bytes(1, n_hits, n_pls)
 
     def submit(self, events):
-        self.ctx.submit(events, stream=self.stream)
+        self.ctx.submit(events, stream=self.stream, host_async=True)   # events are held until sync
         self._n = len(events)
 
     def done(self):

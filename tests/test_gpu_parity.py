@@ -96,6 +96,31 @@ def test_device_inputs_equal_host_inputs(det_full, ctx_full):
             assert np.array_equal(host[k], dev[k]), k
 
 
+def _pinned(a):
+    t = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+    t[:] = np.ascontiguousarray(a).view(np.uint8).reshape(-1)
+    return t.view(a.dtype)
+
+
+def test_async_host_inputs_equal_host_inputs(det_full, ctx_full):
+    """LST_MEM_HOST_ASYNC: pinned arrays are gathered by the device in place, pageable ones where the
+    host link is coherent (else packed); either way the results equal the LST_MEM_HOST run."""
+    import dataclasses
+    evs = [gen.small_event(700, seed=s)[1] for s in (21, 22)]
+    ctx_full.run(evs)
+    host = [ctx_full.results(e) for e in range(2)]
+    pinned = [dataclasses.replace(ev, x=_pinned(ev.x), y=_pinned(ev.y), z=_pinned(ev.z),
+                                  sensor=_pinned(ev.sensor), pls=_pinned(ev.pls)) for ev in evs]
+    for batch in (pinned, evs):
+        ctx_full.submit(batch, host_async=True)
+        ctx_full.sync()
+        for e in range(2):
+            got = ctx_full.results(e)
+            for k in host[e]:
+                if k != "counts":
+                    assert np.array_equal(host[e][k], got[k]), k
+
+
 def test_degenerate_events(det_full, ctx_full):
     empty = gen.Event(x=np.zeros(0, np.float32), y=np.zeros(0, np.float32), z=np.zeros(0, np.float32),
                       sensor=np.zeros(0, np.int32), pls=np.zeros(0, dtype=gen.PLS_DTYPE),
