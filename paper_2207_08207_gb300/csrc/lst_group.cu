@@ -3,293 +3,247 @@
 // Each stage writes its objects into per-module slots (order inside a module set by atomics). The
 // dense arrays are ordered by (first member, second member). The first members of a module's
 // objects lie in that module's own range of first-member indices (the previous stage's dense
-// objects, or the module's binned hits for MDs), and those ranges increase with the module, so the
-// global order is the module order with each module's objects sorted on their own: the per-module
-// dense offsets are an exclusive scan of the per-module counts, and each module sorts its few
-// objects locally (a warp for most modules, a block for the largest) by a counting sort on the first
-// member followed by ranks inside each first-member group. The per-key group offsets (objects whose first member is below a key) follow from the
-// sorted keys by binary search.
+// objects, or the module's binned hits for MDs), and those ranges increase with the module, so this
+// order is also the module order, and the objects sharing a first member form one contiguous group.
+// The compaction therefore works per object, with no per-module sort:
+//   1. count the objects of every first member (atomics on a key-indexed array);
+//   2. exclusive scan: the start of every group, which are also the per-key group offsets that the
+//      next stage uses as its adjacency ("objects whose first member is below k");
+//   3. place each object at its group's cursor (order inside a group arbitrary);
+//   4. rank each object inside its group by the second member (groups are small: a few objects,
+//      ranked against each other in shared memory).
+// The key-indexed arrays are zeroed and scanned up to the actual key count, read on the device, so
+// that the launches stay shaped by capacities (one CUDA graph serves every batch).
+// The per-module dense offsets are the group offsets of each module's first key.
 #include "lst_internal.h"
 
 namespace lst {
 namespace {
 
-constexpr int kSmallWarps = 8;        // warps per block of the small-module kernel
-constexpr int kBigThreads = 256;      // threads per block of the large-module kernel
-constexpr int kBigCap = 8192;         // objects a large module sorts in shared memory
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGrpWarps = 8;   // warps per block of the slot-visiting kernels
 
-// valid slots per module = min(count, capacity, arena room); the excess is recorded
-__global__ void k_mod_eff(Ws w, const int32_t* cnt, const int32_t* cap, const int32_t* base, int64_t slots,
-                          int ovf_word, int arena_word) {
+// Visit every valid slot of up to 32 modules with all lanes of the warp. eff and b are the
+// lane's module's valid-slot count and slot base (0 on lanes without a module); f(valid, s) is
+// called by all lanes together, once per valid slot s with valid = true.
+template <class F>
+__device__ __forceinline__ void visit_slots(int lane, int eff, int b, F&& f) {
+  int incl = eff;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  for (int i0 = 0; i0 < total; i0 += 32) {
+    const int i = i0 + lane;
+    // the lane whose slot range holds i: the number of lanes whose inclusive end is <= i
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int v = __shfl_sync(kFull, incl, j + step - 1);
+      if (v <= i) j += step;
+    }
+    const int start = __shfl_sync(kFull, incl, j) - __shfl_sync(kFull, eff, j);
+    const int s = __shfl_sync(kFull, b, j) + (i - start);
+    f(i < total, s);
+  }
+}
+
+// a first member inside [0, nk) (they all are, unless an earlier stage overflowed)
+__device__ __forceinline__ int clamp_key(int k, int nk) { return max(min(k, nk - 1), 0); }
+
+// per-module valid slots = min(count, capacity, arena room), the excess recorded
+__global__ void k_grp_eff(Ws w, GroupArgs a) {
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
-    const int c = cnt[vm], k = cap[vm], b = base[vm];
+    const int c = a.cnt[vm], k = a.cap[vm], b = a.base[vm];
     int eff = min(c, k);
-    if (c > k) atomicAdd(&w.status[ovf_word], c - k);
-    if ((int64_t)b + eff > slots) {
-      eff = (int)(slots - b > 0 ? slots - b : 0);
-      atomicMax(&w.status[arena_word], base[w.V]);
+    if (c > k) atomicAdd(&w.status[a.ovf_word], c - k);
+    if ((int64_t)b + eff > a.slots) {
+      eff = (int)(a.slots - b > 0 ? a.slots - b : 0);
+      atomicMax(&w.status[a.arena_word], a.base[w.V]);
     }
-    w.eff[vm] = eff;
+    w.eff[vm] = eff + 1;   // a module weighs its valid objects plus one (its visit)
   }
 }
 
-__device__ __forceinline__ unsigned long long pair_key(int k1, int k2) {
-  return ((unsigned long long)(unsigned)k1 << 32) | (unsigned)k2;
+// Work is split into tasks of about `chunk` units of weight (a module weighs its valid objects plus
+// one, so that long runs of empty modules are split too): task t holds the modules whose weighted
+// start (the scan of the weights, eff_off) lies in [t * chunk, (t + 1) * chunk). grp_task[t] is its
+// first module: the first vm with eff_off[vm] >= t * chunk.
+__global__ void k_grp_tasks(Ws w, int chunk) {
+  const int total = w.eff[w.V];
+  const int n_tasks = (total + chunk - 1) / chunk;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= n_tasks; t += gridDim.x * blockDim.x) {
+    const int64_t target = (int64_t)t * chunk;
+    int lo = 0, hi = w.V;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (w.eff[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    w.grp_task[t] = lo;
+  }
 }
 
-struct SortArgs {
-  const int32_t *base, *key1, *key2, *mod_first;
-  int stride;
-  int32_t* grp_off;
-  int64_t n_keys, dense_cap;
-  int32_t* mod_off;
-  int dense_word, big_word;
-};
+// all lanes of a warp visit the valid slots of task t's modules, 32 modules at a time
+template <class F>
+__device__ __forceinline__ void visit_task(const Ws& w, const GroupArgs& a, int t, int lane, F&& f) {
+  const int m_end = w.grp_task[t + 1];
+  for (int m0 = w.grp_task[t]; m0 < m_end; m0 += 32) {
+    const int vm = m0 + lane;
+    int eff = 0, b = 0;
+    if (vm < m_end) {
+      eff = w.eff[vm + 1] - w.eff[vm] - 1;
+      b = a.base[vm];
+    }
+    visit_slots(lane, eff, b, f);
+  }
+}
 
-// Modules of moderate size: a warp per module. Up to 32 objects each lane holds one and ranks it
-// against the others by shuffles. Up to kMidCap objects whose first members span at most kMidCap
-// keys, a counting sort in shared memory: histogram of the first members, its scan (which is the
-// group offsets), placement, then each object's rank inside its first-member group by its second
-// member (groups hold a few objects). Larger modules are listed for k_mod_sort_big.
-constexpr int kMidCap = 512;
-
-__global__ void __launch_bounds__(32 * kSmallWarps) k_mod_sort_small(Ws w, SortArgs a) {
-  __shared__ int sh_k2[kSmallWarps][kMidCap];    // second member of each object
-  __shared__ int sh_pos[kSmallWarps][kMidCap];   // objects placed by first member
-  __shared__ int sh_g[kSmallWarps][kMidCap];     // group counts, then group starts (R + 1 <= kMidCap)
-  const int wi = threadIdx.x >> 5;
-  int* K2 = sh_k2[wi];
-  int* POS = sh_pos[wi];
-  int* G = sh_g[wi];
+// Pass 1: one count per object at E[first member + 1] (lanes of one key summed first)
+__global__ void __launch_bounds__(32 * kGrpWarps) k_grp_count(Ws w, GroupArgs a, int32_t* E, int chunk) {
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * kSmallWarps;
-  const int64_t cap = a.dense_cap;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int total = w.eff[w.V];
-    if (total > cap) atomicMax(&w.status[a.dense_word], total);
-    a.mod_off[w.V] = (int)lst_min64(total, cap);
-  }
-  const bool offsets = a.grp_off != nullptr;
-  for (int vm = blockIdx.x * kSmallWarps + wi; vm < w.V; vm += nwarps) {
-    const int dest = w.eff[vm], n = w.eff[vm + 1] - dest;
-    if (lane == 0) a.mod_off[vm] = (int)lst_min64(dest, cap);
-    const int k0 = a.mod_first[(int64_t)vm * a.stride], k1 = a.mod_first[(int64_t)(vm + 1) * a.stride];
-    const int R = k1 - k0;
-    if (n > 32 && (n > kMidCap || R >= kMidCap)) {
-      if (lane == 0) w.grp_big[atomicAdd(&w.grp_big_cnt[a.big_word], 1)] = vm;
-      continue;
-    }
-    if (n == 0 && !(offsets && R > 0)) continue;
-    const int b = a.base[vm];
-    if (n <= 32) {
-      int kv1 = 0x7fffffff;
-      unsigned long long key = ~0ull;
-      if (lane < n) {
-        kv1 = a.key1[b + lane];
-        key = pair_key(kv1, a.key2[b + lane]);
-      }
-      int rank = 0;
-      for (int j = 0; j < n; ++j) {
-        const unsigned long long kj = __shfl_sync(0xffffffffu, key, j);
-        rank += kj < key || (kj == key && j < lane);
-      }
-      if (lane < n) {
-        if (dest + rank < cap) w.perm[dest + rank] = b + lane;
-        POS[rank] = kv1;
-      }
-      __syncwarp();
-      if (offsets)
-        for (int k = k0 + lane; k < k1; k += 32) {   // dest + #(first members below k)
-          int lo = 0, hi = n;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (POS[mid] < k) lo = mid + 1; else hi = mid;
-          }
-          a.grp_off[k] = (int)lst_min64(dest + lo, cap);
-        }
-      __syncwarp();
-      continue;
-    }
-    for (int k = lane; k <= R; k += 32) G[k] = 0;
-    __syncwarp();
-    const int gmax = R > 0 ? R - 1 : 0;   // (first members outside the range only after an overflow)
-    for (int i = lane; i < n; i += 32) {
-      K2[i] = a.key2[b + i];
-      atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1);
-    }
-    __syncwarp();
-    int run = 0;   // exclusive scan of G[0..R] in chunks of 32
-    for (int k0c = 0; k0c <= R; k0c += 32) {
-      const int k = k0c + lane;
-      const int v = k <= R ? G[k] : 0;
-      int incl = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (k <= R) G[k] = run + incl - v;
-      run += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    __syncwarp();
-    if (offsets)
-      for (int k = lane; k < R; k += 32) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
-    // placement by first member (order inside a group arbitrary), via the group starts
-    for (int i = lane; i < n; i += 32) POS[atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1)] = i;
-    __syncwarp();
-    // G[g] is now the end of group g: rank inside the group by the second member
-    for (int p = lane; p < n; p += 32) {
-      const int i = POS[p];
-      const int g = min(max(a.key1[b + i] - k0, 0), gmax);
-      const int g_end = G[g], g_beg = g > 0 ? G[g - 1] : 0;
-      const int k2 = K2[i];
-      int r = g_beg;
-      for (int qq = g_beg; qq < g_end; ++qq) {
-        const int j = POS[qq];
-        const int kj = K2[j];
-        r += kj < k2 || (kj == k2 && j < i);
-      }
-      if (dest + r < cap) w.perm[dest + r] = b + i;
-    }
-    __syncwarp();
-  }
+  const int nk = *a.n_keys_dev;
+  const int n_tasks = (w.eff[w.V] + chunk - 1) / chunk;   // (of the weights)
+  for (int t = blockIdx.x * kGrpWarps + (threadIdx.x >> 5); t < n_tasks; t += gridDim.x * kGrpWarps)
+    visit_task(w, a, t, lane, [&](bool v, int s) {
+      const int key = v ? clamp_key(a.key1[s], nk) + 1 : 0;
+      const unsigned grp = __match_any_sync(kFull, key);
+      const int cnt = __popc(grp & __ballot_sync(kFull, v));
+      if (v && lane == __ffs(grp) - 1) atomicAdd(&E[key], cnt);
+    });
 }
 
-// Larger modules: a block per module, the same counting sort with the block (up to kBigCap objects
-// and first-member ranges below kBigCap); beyond that, ranks counted directly from global memory.
-__global__ void __launch_bounds__(kBigThreads) k_mod_sort_big(Ws w, SortArgs a) {
-  extern __shared__ __align__(16) unsigned char big_smem[];
-  int* K2 = reinterpret_cast<int*>(big_smem);   // [kBigCap] second members
-  int* POS = K2 + kBigCap;                     // [kBigCap] objects placed by first member
-  int* G = POS + kBigCap;                      // [kBigCap] group counts, then starts, then ends
-  __shared__ int part[kBigThreads];
-  const int n_big = w.grp_big_cnt[a.big_word];
-  const int64_t cap = a.dense_cap;
-  const int t = threadIdx.x;
-  for (int it = blockIdx.x; it < n_big; it += gridDim.x) {
-    const int vm = w.grp_big[it];
-    const int dest = w.eff[vm], n = w.eff[vm + 1] - dest;
-    const int b = a.base[vm];
-    const int k0 = a.mod_first[(int64_t)vm * a.stride], k1 = a.mod_first[(int64_t)(vm + 1) * a.stride];
-    const int R = k1 - k0;
-    if (n <= kBigCap && R < kBigCap) {
-      const int gmax = R > 0 ? R - 1 : 0;
-      for (int k = t; k <= R; k += blockDim.x) G[k] = 0;
-      __syncthreads();
-      for (int i = t; i < n; i += blockDim.x) {
-        K2[i] = a.key2[b + i];
-        atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1);
+// Pass 3: after the exclusive scan E[k + 1] is the start of group k; each object takes the next
+// position of its group. Afterwards E[k] is the start of group k for every k (E[0] stays 0).
+__global__ void __launch_bounds__(32 * kGrpWarps) k_grp_place(Ws w, GroupArgs a, int32_t* E, int chunk) {
+  const int lane = threadIdx.x & 31;
+  const int nk = *a.n_keys_dev;
+  const int n_tasks = (w.eff[w.V] + chunk - 1) / chunk;   // (of the weights)
+  for (int t = blockIdx.x * kGrpWarps + (threadIdx.x >> 5); t < n_tasks; t += gridDim.x * kGrpWarps)
+    visit_task(w, a, t, lane, [&](bool v, int s) {
+      const int k1 = v ? clamp_key(a.key1[s], nk) : 0;
+      const int p = warp_agg_slot_keyed(v, k1 + 1, E);
+      if (v && p >= 0 && p < a.dense_cap) {
+        w.grp_pos[p] = s;
+        w.grp_key12[p] = make_int2(k1, a.key2[s]);
       }
-      __syncthreads();
-      // exclusive scan of G[0..R]: each thread a contiguous run, then a scan of the run totals
-      const int per = (R + 1 + blockDim.x - 1) / blockDim.x;
-      const int r0 = t * per, r1 = min(r0 + per, R + 1);
-      int sum = 0;
-      for (int k = r0; k < r1; ++k) sum += G[k];
-      part[t] = sum;
-      __syncthreads();
-      if (t < 32) {
-        int run = 0;
-        for (int c0 = 0; c0 < kBigThreads; c0 += 32) {
-          const int v = part[c0 + t];
-          int incl = v;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (t >= o) incl += y;
-          }
-          part[c0 + t] = run + incl - v;
-          run += __shfl_sync(0xffffffffu, incl, 31);
+    });
+}
+
+// Pass 0: zero the counts of the actual keys
+__global__ void k_grp_zero(int32_t* E, GroupArgs a) {
+  const int nk = *a.n_keys_dev;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nk; k += gridDim.x * blockDim.x) E[k] = 0;
+}
+
+// Pass 4: the rank of each placed object inside its group by (second member, slot), which gives its
+// dense position; the permutation (or, for LS, the dense objects themselves) is written there, with
+// the per-module dense offsets and the dense-overflow word. A block ranks a
+// tile of kRankTile positions with the (slot, second member) of the tile and kRankHalo positions on
+// each side in shared memory; groups reaching further (none at the sizes seen) read memory.
+constexpr int kRankTile = 256, kRankHalo = 64;
+enum { kOutPerm = 0, kOutLs = 1 };   // what the rank pass writes: the permutation, or the dense LS
+
+template <int OUT>
+__global__ void __launch_bounds__(kRankTile) k_grp_rank(Ws w, GroupArgs a, const int32_t* E) {
+  __shared__ int sh_s[kRankTile + 2 * kRankHalo];
+  __shared__ int sh_k[kRankTile + 2 * kRankHalo];
+  const int nk = *a.n_keys_dev;
+  const int total = E[nk];
+  const int n = (int)lst_min64(total, a.dense_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && total > a.dense_cap) atomicMax(&w.status[a.dense_word], total);
+  for (int t0 = blockIdx.x * kRankTile; t0 < n; t0 += gridDim.x * kRankTile) {
+    for (int i = threadIdx.x; i < kRankTile + 2 * kRankHalo; i += kRankTile) {
+      const int q = t0 - kRankHalo + i;
+      if (q >= 0 && q < n) {
+        sh_s[i] = w.grp_pos[q];
+        sh_k[i] = w.grp_key12[q].y;
+      }
+    }
+    __syncthreads();
+    const int p = t0 + threadIdx.x;
+    const bool valid = p < n;
+    int s = 0, k1 = 0, k2 = 0, d = 0;
+    if (valid) {
+      s = sh_s[kRankHalo + threadIdx.x];
+      k2 = sh_k[kRankHalo + threadIdx.x];
+      k1 = w.grp_key12[p].x;
+      const int g_beg = E[k1], g_end = (int)lst_min64(E[k1 + 1], n);
+      int r = 0;
+      if (g_beg >= t0 - kRankHalo && g_end <= t0 + kRankTile + kRankHalo) {
+        for (int i = g_beg - (t0 - kRankHalo); i < g_end - (t0 - kRankHalo); ++i) {
+          const int kq = sh_k[i], sq = sh_s[i];
+          r += kq < k2 || (kq == k2 && sq < s);
         }
-      }
-      __syncthreads();
-      int acc = part[t];
-      for (int k = r0; k < r1; ++k) {
-        const int v = G[k];
-        G[k] = acc;
-        acc += v;
-      }
-      __syncthreads();
-      if (a.grp_off)
-        for (int k = t; k < R; k += blockDim.x) a.grp_off[k0 + k] = (int)lst_min64(dest + G[k], cap);
-      __syncthreads();
-      for (int i = t; i < n; i += blockDim.x) POS[atomicAdd(&G[min(max(a.key1[b + i] - k0, 0), gmax)], 1)] = i;
-      __syncthreads();
-      for (int p = t; p < n; p += blockDim.x) {   // G[g] is now the end of group g
-        const int i = POS[p];
-        const int g = min(max(a.key1[b + i] - k0, 0), gmax);
-        const int g_end = G[g], g_beg = g > 0 ? G[g - 1] : 0;
-        const int k2 = K2[i];
-        int r = g_beg;
+      } else {
         for (int q = g_beg; q < g_end; ++q) {
-          const int j = POS[q];
-          const int kj = K2[j];
-          r += kj < k2 || (kj == k2 && j < i);
+          const int sq = w.grp_pos[q];
+          const int kq = w.grp_key12[q].y;
+          r += kq < k2 || (kq == k2 && sq < s);
         }
-        if (dest + r < cap) w.perm[dest + r] = b + i;
       }
-      __syncthreads();
-    } else {
-      for (int i = t; i < n; i += blockDim.x) {
-        const unsigned long long ki = pair_key(a.key1[b + i], a.key2[b + i]);
-        int rank = 0;
-        for (int j = 0; j < n; ++j) {
-          const unsigned long long kj = pair_key(a.key1[b + j], a.key2[b + j]);
-          rank += kj < ki || (kj == ki && j < i);
-        }
-        if (dest + rank < cap) w.perm[dest + rank] = b + i;
-      }
-      for (int k = k0 + t; a.grp_off && k < k1; k += blockDim.x) {
-        int below = 0;
-        for (int j = 0; j < n; ++j) below += a.key1[b + j] < k;
-        a.grp_off[k] = (int)lst_min64(dest + below, cap);
-      }
+      d = g_beg + r;
     }
+    if (OUT == kOutLs) ls_dense_write(w, valid, d, s, k1, k2, E, n);
+    else if (valid) w.perm[d] = s;
+    __syncthreads();
   }
+  for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm <= w.V; vm += gridDim.x * blockDim.x)
+    a.mod_off[vm] = (int)lst_min64(E[a.mod_first[(int64_t)vm * a.mod_first_stride]], a.dense_cap);
 }
 
-// group offsets of the keys past the last module's range: the (clamped) total
-__global__ void k_grp_tail(Ws w, SortArgs a) {
-  const int k_end = a.mod_first[(int64_t)w.V * a.stride];
-  const int total = (int)lst_min64(w.eff[w.V], a.dense_cap);
-  for (int64_t k = k_end + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= a.n_keys;
-       k += (int64_t)gridDim.x * blockDim.x)
-    a.grp_off[k] = total;
+// after a dense overflow the group offsets handed to the next stage are clamped to the capacity
+__global__ void k_grp_clamp(Ws w, int32_t* E, GroupArgs a) {
+  if (w.status[a.dense_word] == 0) return;
+  const int nk = *a.n_keys_dev;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nk; k += gridDim.x * blockDim.x)
+    if (E[k] > a.dense_cap) E[k] = (int)a.dense_cap;
 }
 
-// out[i] = min(grp_off[first[i * stride]], cap), i in [0, n] (the clamp keeps later stages inside
-// the dense arrays when they overflowed; the run is then retried with larger ones)
-__global__ void k_off_compose(int32_t* out, int n, const int32_t* first, int stride, const int32_t* grp_off,
-                              int64_t cap) {
+// out[i] = min(grp_off[first[min(i, *n_dev) * stride]], cap), i in [0, n] (the clamp keeps later
+// stages inside the dense arrays when they overflowed; the run is then retried with larger ones)
+__global__ void k_off_compose(int32_t* out, int n, const int32_t* first, int stride, const int32_t* n_dev,
+                              const int32_t* grp_off, int64_t cap) {
+  const int nf = *n_dev;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
-    out[i] = (int)lst_min64(grp_off[first[(int64_t)i * stride]], cap);
+    out[i] = (int)lst_min64(grp_off[first[(int64_t)min(i, nf) * stride]], cap);
 }
 
 }  // namespace
 
-void group_configure() {
-  cudaFuncSetAttribute(k_mod_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kBigCap * (int)sizeof(int));
-}
-
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
-  k_mod_eff<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, a.cnt, a.cap, a.base, a.slots, a.ovf_word, a.arena_word);
+  int32_t* E = a.grp_off ? a.grp_off : w.grp_key;
+  // objects per warp task: about two tasks per resident warp at the stage's dense capacity
+  const int64_t resident_warps = (int64_t)L.n_sm * 64;
+  int chunk = 64;
+  while (chunk < 1024 && (int64_t)chunk * 2 * resident_warps * 2 <= a.dense_cap + w.V) chunk *= 2;
+  const int blocks = L.n_sm * (64 / kGrpWarps);
+  const int key_blocks = grid_for(a.n_keys + 1, 256, L.n_sm * 8);
+  k_grp_eff<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, a);
   LST_LAUNCH(L);
   scan_exclusive(w.eff, w.eff, w.V, w.scan_tmp, L);
-  SortArgs s{a.base, a.key1, a.key2, a.mod_first, a.mod_first_stride, a.grp_off, a.n_keys, a.dense_cap,
-             a.mod_off, a.dense_word, a.big_word};
-  k_mod_sort_small<<<grid_for((int64_t)w.V * 32, 32 * kSmallWarps, 152 * 32), 32 * kSmallWarps, 0, L.stream>>>(w, s);
+  k_grp_tasks<<<grid_for((a.slots + w.V) / chunk + 2, 256), 256, 0, L.stream>>>(w, chunk);
   LST_LAUNCH(L);
-  k_mod_sort_big<<<L.n_sm * 2, kBigThreads, 3 * kBigCap * sizeof(int), L.stream>>>(w, s);
+  k_grp_zero<<<key_blocks, 256, 0, L.stream>>>(E, a);
+  LST_LAUNCH(L);
+  k_grp_count<<<blocks, 32 * kGrpWarps, 0, L.stream>>>(w, a, E, chunk);
+  LST_LAUNCH(L);
+  scan_exclusive_dev(E, E, a.n_keys + 1, a.n_keys_dev, 1, w.scan_tmp, L);
+  k_grp_place<<<blocks, 32 * kGrpWarps, 0, L.stream>>>(w, a, E, chunk);
+  LST_LAUNCH(L);
+  if (a.dense_ls) k_grp_rank<kOutLs><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
+  else k_grp_rank<kOutPerm><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
   LST_LAUNCH(L);
   if (a.grp_off) {
-    k_grp_tail<<<grid_for(a.n_keys + 1, 256), 256, 0, L.stream>>>(w, s);
+    k_grp_clamp<<<key_blocks, 256, 0, L.stream>>>(w, E, a);
     LST_LAUNCH(L);
   }
 }
 
-void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* grp_off, int64_t cap,
-                     const Launch& L) {
-  k_off_compose<<<grid_for(n + 1, 256), 256, 0, L.stream>>>(out, n, first, stride, grp_off, cap);
+void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* n_dev,
+                     const int32_t* grp_off, int64_t cap, const Launch& L) {
+  k_off_compose<<<grid_for(n + 1, 256), 256, 0, L.stream>>>(out, n, first, stride, n_dev, grp_off, cap);
   LST_LAUNCH(L);
 }
 

@@ -639,37 +639,6 @@ __global__ void k_ls_recheck(Ws w, Cst<double> c) {
   }
 }
 
-// dense LS ordered by (inner MD, outer MD); z0 is recomputed in float64 (its float32 form
-// amplifies radius rounding up to ~20x for endcap pairs)
-// dense LS ordered by (inner MD, outer MD), with z0, dphi, the outer anchor cache, and each LS's
-// count of outer partners (the T3 candidates it starts) summed per module for the T3 capacities
-__global__ void k_ls_dense(Ws w) {
-  const int n = (int)lst_min64(w.ls_off[w.V], w.cap.ls_dense);
-  for (int d0 = blockIdx.x * blockDim.x; d0 < n; d0 += gridDim.x * blockDim.x) {
-    const int d = d0 + threadIdx.x;
-    int vm = 0;
-    unsigned outs = 0;
-    if (d < n) {
-      const int s = w.perm[d];
-      const int a = w.lss_in[s], b = w.lss_out[s];
-      w.ls_in[d] = a;
-      w.ls_out[d] = b;
-      // z0 = (z1 r2 - z2 r1) / (r2 - r1) with the radii in float-float: the float32 rounding of the
-      // radii would be amplified up to ~20x for endcap pairs
-      const float z1 = w.md_z[a], z2 = w.md_z[b];
-      const float r1 = w.md_r[a], r1l = w.md_rlo[a], r2 = w.md_r[b], r2l = w.md_rlo[b];
-      const float num = diff_prod(z1, r2, z2, r1) + (z1 * r2l - z2 * r1l);
-      const float den = (r2 - r1) + (r2l - r1l);
-      w.ls_z0[d] = num / den;
-      w.ls_dphi[d] = w.lss_dphi[s];
-      w.ls_xy_out[d] = make_float2(w.md_x[b], w.md_y[b]);
-      vm = w.md_vm[a];
-      outs = (unsigned)(min(w.lsin_off[b + 1], n) - min(w.lsin_off[b], n));
-    }
-    warp_add_keyed(w.t3_bound, vm, outs);
-  }
-}
-
 // single-event binning on plain arrays (the standalone lst_bin_hits entry point)
 __global__ void k_braw_count(const int32_t* sensor, int n, int n_sens, int32_t* cnt, int32_t* err) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -741,8 +710,8 @@ void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   KT_BEGIN(L, K_MD_COMPACT);
   GroupArgs ga{w.md_cnt, w.md_cap, w.md_base, w.cap.md_slots, ST_OVF_MD, ST_ARENA_MD, w.ms_lo, w.ms_up,
-               nullptr, w.cap.H, w.cap.md_dense, ST_DENSE_MD,
-               w.md_off, w.sens_off, 2, 0};
+               nullptr, w.cap.H, &w.ev_hit_off[w.E], w.cap.md_dense, ST_DENSE_MD,
+               w.md_off, w.sens_off, 2};
   group_slots(w, ga, L);
   k_md_dense<<<grid_for(w.cap.md_dense, 256), 256, 0, L.stream>>>(w, g, c.f);
   KT_END(L, K_MD_COMPACT);
@@ -777,12 +746,10 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   // LS ordered by inner MD: the per-MD group offsets are the "LS by inner MD" adjacency
   KT_BEGIN(L, K_LS_COMPACT);
   GroupArgs ga{w.ls_cnt, w.ls_cap, w.ls_base, w.cap.ls_slots, ST_OVF_LS, ST_ARENA_LS, w.lss_in, w.lss_out,
-               w.lsin_off, w.cap.md_dense, w.cap.ls_dense, ST_DENSE_LS,
-               w.ls_off, w.md_off, 1, 1};
+               w.lsin_off, w.cap.md_dense, &w.md_off[w.V], w.cap.ls_dense, ST_DENSE_LS,
+               w.ls_off, w.md_off, 1, true};
   group_slots(w, ga, L);
-  k_ls_dense<<<grid_for(w.cap.ls_dense, 256), 256, 0, L.stream>>>(w);
   KT_END(L, K_LS_COMPACT);
-  LST_LAUNCH(L);
 }
 
 }  // namespace lst

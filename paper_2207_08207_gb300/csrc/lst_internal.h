@@ -163,9 +163,11 @@ struct Ws {
   int2 *q_t3 = nullptr, *q_t5 = nullptr, *q_p3 = nullptr, *q_p5 = nullptr;
   // scan scratch and status
   int32_t* scan_tmp = nullptr;
-  int32_t* eff = nullptr;    // [V + 1] valid slots per module of the stage being compacted, then their scan
-  int32_t* grp_big = nullptr;       // [V] modules with more than 32 objects (compaction)
-  int32_t* grp_big_cnt = nullptr;   // [4] their counts, one per stage
+  int32_t* eff = nullptr;    // [V + 1] weights (valid slots + 1) per module of the stage being compacted, then their scan
+  int32_t* grp_key = nullptr;       // [max(H, t3_dense) + 2] per-key counts / group starts (compaction)
+  int32_t* grp_pos = nullptr;       // [max dense] objects placed by group (compaction)
+  int2* grp_key12 = nullptr;        // [max dense] their (first, second) members
+  int32_t* grp_task = nullptr;      // [(max slots + V) / 64 + 2] first module of each compaction task
   unsigned long long* t3_bound = nullptr;   // [V] T3 candidates per module (summed over its dense LS)
   unsigned long long* t5_bound = nullptr;   // [V] T5 candidates per module (summed over its dense T3)
   int32_t* perm = nullptr;   // [max dense] slot of each dense object of the stage being compacted
@@ -208,6 +210,10 @@ int ls_resident_blocks(int block);
 
 // scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);
+// the same with the entry count min(n, *n_dev + n_add) read on the device (n sizes the launch);
+// out[count] receives the total
+void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_t* n_dev, int n_add, int32_t* tmp,
+                        const Launch& L);
 int64_t scan_tmp_elems(int64_t n);
 
 // compaction of one stage's slots into ordered dense arrays (lst_group.cu)
@@ -217,18 +223,21 @@ struct GroupArgs {
   int ovf_word, arena_word;
   const int32_t *key1, *key2;        // first / second member of each slot
   int32_t* grp_off;                  // out: [n_keys + 1] objects whose first member is below each key
-                                     // (nullptr: not needed by a later stage, not computed)
-  int64_t n_keys;                    // key1 range
+                                     // (nullptr: not needed by a later stage; scratch is used)
+  int64_t n_keys;                    // key1 range (capacity)
+  const int32_t* n_keys_dev;         // device: the actual number of keys (<= n_keys); grp_off is
+                                     // defined on [0, *n_keys_dev]
   int64_t dense_cap;
   int dense_word;
   int32_t* mod_off;                  // [V + 1] out: per-module dense offsets
   const int32_t* mod_first;          // first key of each module, at [vm * stride]
   int mod_first_stride;
-  int big_word;                      // which of the four large-module list counters the stage uses
+  bool dense_ls = false;             // write the dense LS arrays directly (ls_dense_write)
 };
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L);
-void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* grp_off, int64_t cap,
-                     const Launch& L);
+// out[i] = min(grp_off[first[min(i, *n_dev) * stride]], cap) for i in [0, n]
+void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* n_dev,
+                     const int32_t* grp_off, int64_t cap, const Launch& L);
 
 // message returned by lst_last_error(NULL) (calls that have no context)
 void set_global_error(const char* msg);
@@ -248,7 +257,6 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L);
 void run_finalize(const Ws& w, const Geo& g, const Launch& L);
 int tc_cells_per_event();
 void tc_configure();
-void group_configure();
 // after an overflowing run: raise the per-module capacity overrides to the observed counts
 void run_raise_overrides(const Ws& w, const Launch& L);
 
@@ -270,6 +278,32 @@ __device__ __forceinline__ void warp_add_keyed(unsigned long long* counters, int
   const unsigned grp = __match_any_sync(0xffffffffu, key);
   const unsigned sum = __reduce_add_sync(grp, v);
   if ((threadIdx.x & 31) == __ffs(grp) - 1 && sum) atomicAdd(&counters[key], (unsigned long long)sum);
+}
+
+// The dense LS at position d (ordered by (inner MD a, outer MD b)) from slot s: members, z0, dphi,
+// the outer anchor cache, and each LS's count of outer partners (the T3 candidates it starts, from
+// the LS-by-inner-MD offsets lsin_off) summed per module for the T3 capacities. All lanes of the
+// warp call it; n is the number of dense LS.
+__device__ __forceinline__ void ls_dense_write(const Ws& w, bool valid, int d, int s, int a, int b,
+                                               const int32_t* lsin_off, int n) {
+  int vm = 0;
+  unsigned outs = 0;
+  if (valid) {
+    w.ls_in[d] = a;
+    w.ls_out[d] = b;
+    // z0 = (z1 r2 - z2 r1) / (r2 - r1) with the radii in float-float: the float32 rounding of the
+    // radii would be amplified up to ~20x for endcap pairs
+    const float4 pa = w.md_xyzr[a], pb = w.md_xyzr[b];
+    const float r1l = w.md_rlo[a], r2l = w.md_rlo[b];
+    const float num = diff_prod(pa.z, pb.w, pb.z, pa.w) + (pa.z * r2l - pb.z * r1l);
+    const float den = (pb.w - pa.w) + (r2l - r1l);
+    w.ls_z0[d] = num / den;
+    w.ls_dphi[d] = w.lss_dphi[s];
+    w.ls_xy_out[d] = make_float2(pb.x, pb.y);
+    vm = w.md_vm[a];
+    outs = (unsigned)(min(lsin_off[b + 1], n) - min(lsin_off[b], n));
+  }
+  warp_add_keyed(w.t3_bound, vm, outs);
 }
 
 inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {

@@ -409,7 +409,6 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.tc_cnt, c.E);
   z.add(w.sens_cnt, S); z.add(w.sens_cur, S);
   z.add(w.md_cnt, V); z.add(w.ls_cnt, V); z.add(w.t3_cnt, V); z.add(w.t5_cnt, V);
-  z.add(w.grp_big_cnt, 4);
   z.add(w.t3_bound, V); z.add(w.t5_bound, V);
   z.add(w.p3_cnt, c.P); z.add(w.p3_cur, c.P); z.add(w.p5_cnt, c.P); z.add(w.p5_cur, c.P);
   z.add(w.h5_cnt, c.H + 1); z.add(w.h5_cur, c.H + 1);
@@ -419,7 +418,11 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
   pl.add(w.bx, c.H); pl.add(w.by, c.H); pl.add(w.bz, c.H); pl.add(w.borig, c.H);
   // compaction scratch, LS work list
-  pl.add(w.eff, V + 1); pl.add(w.grp_big, V);
+  pl.add(w.eff, V + 1);
+  pl.add(w.grp_key, std::max(c.H, c.t3_dense) + 2);
+  pl.add(w.grp_pos, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
+  pl.add(w.grp_key12, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
+  pl.add(w.grp_task, (std::max({c.md_slots, c.ls_slots, c.t3_slots, c.t5_slots}) + V) / 64 + 2);
   pl.add(w.work, V); pl.add(w.work_bucket, V); pl.add(w.work_off, 33);
   pl.add(w.perm, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
   // MD
@@ -683,7 +686,6 @@ int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
   ctx->pageable_access = pageable != 0;
   ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls);
   tc_configure();
-  group_configure();
   *out = ctx;
   return LST_OK;
 }

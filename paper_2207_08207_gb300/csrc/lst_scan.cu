@@ -37,8 +37,18 @@ __device__ __forceinline__ int block_excl_scan(int v, int& total) {
   return warp_prefix + x - v;
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(const int32_t* in, int32_t* out, int64_t n,
-                                                           int32_t* tile_sums) {
+// n_dev (nullable): the entry count is then min(n, *n_dev + n_add), read on the device
+__device__ __forceinline__ int64_t scan_count(int64_t n, const int32_t* n_dev, int n_add) {
+  return n_dev ? lst_min64(n, (int64_t)*n_dev + n_add) : n;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(const int32_t* in, int32_t* out, int64_t n_max,
+                                                           int32_t* tile_sums, const int32_t* n_dev, int n_add) {
+  const int64_t n = scan_count(n_max, n_dev, n_add);
+  if ((int64_t)blockIdx.x * kTile >= n) {   // a tile past the entries: nothing to scan
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = 0;
+    return;
+  }
   const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
   int v[kScanItems];
   int local = 0;
@@ -58,7 +68,9 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_tiles(const int32_t* in, in
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_sums(int32_t* tile_sums, int64_t n_tiles, int32_t* out,
-                                                          int64_t n) {
+                                                          int64_t n_max, const int32_t* n_dev, int n_add) {
+  const int64_t n = scan_count(n_max, n_dev, n_add);
+  n_tiles = lst_min64(n_tiles, (n + kTile - 1) / kTile);
   int carry = 0;
   for (int64_t b0 = 0; b0 < n_tiles; b0 += kScanBlock) {
     const int64_t i = b0 + threadIdx.x;
@@ -72,9 +84,11 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(int32_t* tile_sums, in
   if (threadIdx.x == 0) out[n] = carry;
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_scan_add(int32_t* out, int64_t n, const int32_t* tile_sums) {
+__global__ void __launch_bounds__(kScanBlock) k_scan_add(int32_t* out, int64_t n_max, const int32_t* tile_sums,
+                                                         const int32_t* n_dev, int n_add) {
   const int add = tile_sums[blockIdx.x];
   if (add == 0) return;
+  const int64_t n = scan_count(n_max, n_dev, n_add);
   const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k)
@@ -85,17 +99,22 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_add(int32_t* out, int64_t n
 
 int64_t scan_tmp_elems(int64_t n) { return (n + kTile - 1) / kTile + 1; }
 
-void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L) {
+void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_t* n_dev, int n_add, int32_t* tmp,
+                        const Launch& L) {
   const int64_t tiles = (n + kTile - 1) / kTile;
   if (tiles == 0) {
-    k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, 0, out, 0);
+    k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, 0, out, 0, nullptr, 0);
     LST_LAUNCH(L);
     return;
   }
-  k_scan_tiles<<<(unsigned)tiles, kScanBlock, 0, L.stream>>>(in, out, n, tmp);
-  k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, tiles, out, n);
-  k_scan_add<<<(unsigned)tiles, kScanBlock, 0, L.stream>>>(out, n, tmp);
+  k_scan_tiles<<<(unsigned)tiles, kScanBlock, 0, L.stream>>>(in, out, n, tmp, n_dev, n_add);
+  k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, tiles, out, n, n_dev, n_add);
+  k_scan_add<<<(unsigned)tiles, kScanBlock, 0, L.stream>>>(out, n, tmp, n_dev, n_add);
   *L.launches += 3;
+}
+
+void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L) {
+  scan_exclusive_dev(in, out, n, nullptr, 0, tmp, L);
 }
 
 }  // namespace lst

@@ -517,11 +517,11 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T3_COMPACT);
   GroupArgs ga{w.t3_cnt, w.t3_cap, w.t3_base, w.cap.t3_slots, ST_OVF_T3, ST_ARENA_T3, w.t3s_a, w.t3s_b,
-               w.t3in_off, w.cap.ls_dense, w.cap.t3_dense, ST_DENSE_T3,
-               w.t3_off, w.ls_off, 1, 2};
+               w.t3in_off, w.cap.ls_dense, &w.ls_off[w.V], w.cap.t3_dense, ST_DENSE_T3,
+               w.t3_off, w.ls_off, 1};
   group_slots(w, ga, L);
   // T3 by first MD: T3 are ordered by inner LS, and LS by inner MD
-  compose_offsets(w.t3md_off, (int)w.cap.md_dense, w.lsin_off, 1, w.t3in_off, w.cap.t3_dense, L);
+  compose_offsets(w.t3md_off, (int)w.cap.md_dense, w.lsin_off, 1, &w.md_off[w.V], w.t3in_off, w.cap.t3_dense, L);
   k_t3_dense<<<grid_for(w.cap.t3_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   KT_END(L, K_T3_COMPACT);
@@ -541,8 +541,8 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_END(L, K_T5_DECIDE);
   LST_LAUNCH(L);
   GroupArgs ga{w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, ST_OVF_T5, ST_ARENA_T5, w.t5s_a, w.t5s_b,
-               nullptr, w.cap.t3_dense, w.cap.t5_dense, ST_DENSE_T5,
-               w.t5_off, w.t3_off, 1, 3};
+               nullptr, w.cap.t3_dense, &w.t3_off[w.V], w.cap.t5_dense, ST_DENSE_T5,
+               w.t5_off, w.t3_off, 1};
   group_slots(w, ga, L);
   k_t5_dense<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
