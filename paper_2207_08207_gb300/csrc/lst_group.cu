@@ -5,6 +5,8 @@
 // objects lie in that module's own range of first-member indices (the previous stage's dense
 // objects, or the module's binned hits for MDs), and those ranges increase with the module, so this
 // order is also the module order, and the objects sharing a first member form one contiguous group.
+// Groups may also be coarser, by a monotone map of the first member (T3 by the inner MD of their
+// inner LS): the order inside a group is then by (first, second) member.
 // The compaction therefore works per object, with no per-module sort:
 //   1. count the objects of every first member (atomics on a key-indexed array);
 //   2. exclusive scan: the start of every group, which are also the per-key group offsets that the
@@ -50,8 +52,12 @@ __device__ __forceinline__ void visit_slots(int lane, int eff, int b, F&& f) {
   }
 }
 
-// a first member inside [0, nk) (they all are, unless an earlier stage overflowed)
-__device__ __forceinline__ int clamp_key(int k, int nk) { return max(min(k, nk - 1), 0); }
+// the group of an object with first member k1: k1 itself, or key_map[k1]; inside [0, nk) (they all
+// are, unless an earlier stage overflowed)
+__device__ __forceinline__ int group_of(const GroupArgs& a, int k1, int nk) {
+  const int g = a.key_map ? a.key_map[k1] : k1;
+  return max(min(g, nk - 1), 0);
+}
 
 // per-module valid slots = min(count, capacity, arena room), the excess recorded
 __global__ void k_grp_eff(Ws w, GroupArgs a) {
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(32 * kGrpWarps) k_grp_count(Ws w, GroupArgs a,
   const int n_tasks = (w.eff[w.V] + chunk - 1) / chunk;   // (of the weights)
   for (int t = blockIdx.x * kGrpWarps + (threadIdx.x >> 5); t < n_tasks; t += gridDim.x * kGrpWarps)
     visit_task(w, a, t, lane, [&](bool v, int s) {
-      const int key = v ? clamp_key(a.key1[s], nk) + 1 : 0;
+      const int key = v ? group_of(a, a.key1[s], nk) + 1 : 0;
       const unsigned grp = __match_any_sync(kFull, key);
       const int cnt = __popc(grp & __ballot_sync(kFull, v));
       if (v && lane == __ffs(grp) - 1) atomicAdd(&E[key], cnt);
@@ -122,8 +128,8 @@ __global__ void __launch_bounds__(32 * kGrpWarps) k_grp_place(Ws w, GroupArgs a,
   const int n_tasks = (w.eff[w.V] + chunk - 1) / chunk;   // (of the weights)
   for (int t = blockIdx.x * kGrpWarps + (threadIdx.x >> 5); t < n_tasks; t += gridDim.x * kGrpWarps)
     visit_task(w, a, t, lane, [&](bool v, int s) {
-      const int k1 = v ? clamp_key(a.key1[s], nk) : 0;
-      const int p = warp_agg_slot_keyed(v, k1 + 1, E);
+      const int k1 = v ? a.key1[s] : 0;
+      const int p = warp_agg_slot_keyed(v, v ? group_of(a, k1, nk) + 1 : 0, E);
       if (v && p >= 0 && p < a.dense_cap) {
         w.grp_pos[p] = s;
         w.grp_key12[p] = make_int2(k1, a.key2[s]);
@@ -148,7 +154,9 @@ enum { kOutPerm = 0, kOutLs = 1 };   // what the rank pass writes: the permutati
 template <int OUT>
 __global__ void __launch_bounds__(kRankTile) k_grp_rank(Ws w, GroupArgs a, const int32_t* E) {
   __shared__ int sh_s[kRankTile + 2 * kRankHalo];
-  __shared__ int sh_k[kRankTile + 2 * kRankHalo];
+  __shared__ int sh_k1[kRankTile + 2 * kRankHalo];   // (only with a key map: else equal in a group)
+  __shared__ int sh_k2[kRankTile + 2 * kRankHalo];
+  const bool mapped = a.key_map != nullptr;
   const int nk = *a.n_keys_dev;
   const int total = E[nk];
   const int n = (int)lst_min64(total, a.dense_cap);
@@ -158,7 +166,9 @@ __global__ void __launch_bounds__(kRankTile) k_grp_rank(Ws w, GroupArgs a, const
       const int q = t0 - kRankHalo + i;
       if (q >= 0 && q < n) {
         sh_s[i] = w.grp_pos[q];
-        sh_k[i] = w.grp_key12[q].y;
+        const int2 kq = w.grp_key12[q];
+        sh_k1[i] = kq.x;
+        sh_k2[i] = kq.y;
       }
     }
     __syncthreads();
@@ -167,20 +177,29 @@ __global__ void __launch_bounds__(kRankTile) k_grp_rank(Ws w, GroupArgs a, const
     int s = 0, k1 = 0, k2 = 0, d = 0;
     if (valid) {
       s = sh_s[kRankHalo + threadIdx.x];
-      k2 = sh_k[kRankHalo + threadIdx.x];
-      k1 = w.grp_key12[p].x;
-      const int g_beg = E[k1], g_end = (int)lst_min64(E[k1 + 1], n);
-      int r = 0;
+      k1 = sh_k1[kRankHalo + threadIdx.x];
+      k2 = sh_k2[kRankHalo + threadIdx.x];
+      const int g = group_of(a, k1, nk);
+      const int g_beg = E[g], g_end = (int)lst_min64(E[g + 1], n);
+      int r = 0;   // members before this one: by (first, second) member, then slot
       if (g_beg >= t0 - kRankHalo && g_end <= t0 + kRankTile + kRankHalo) {
-        for (int i = g_beg - (t0 - kRankHalo); i < g_end - (t0 - kRankHalo); ++i) {
-          const int kq = sh_k[i], sq = sh_s[i];
-          r += kq < k2 || (kq == k2 && sq < s);
+        const int i0 = g_beg - (t0 - kRankHalo), i1 = g_end - (t0 - kRankHalo);
+        if (mapped) {
+          for (int i = i0; i < i1; ++i) {
+            const int q1 = sh_k1[i], q2 = sh_k2[i], sq = sh_s[i];
+            r += q1 < k1 || (q1 == k1 && (q2 < k2 || (q2 == k2 && sq < s)));
+          }
+        } else {
+          for (int i = i0; i < i1; ++i) {
+            const int q2 = sh_k2[i], sq = sh_s[i];
+            r += q2 < k2 || (q2 == k2 && sq < s);
+          }
         }
       } else {
         for (int q = g_beg; q < g_end; ++q) {
           const int sq = w.grp_pos[q];
-          const int kq = w.grp_key12[q].y;
-          r += kq < k2 || (kq == k2 && sq < s);
+          const int2 kq = w.grp_key12[q];
+          r += kq.x < k1 || (kq.x == k1 && (kq.y < k2 || (kq.y == k2 && sq < s)));
         }
       }
       d = g_beg + r;
@@ -199,15 +218,6 @@ __global__ void k_grp_clamp(Ws w, int32_t* E, GroupArgs a) {
   const int nk = *a.n_keys_dev;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nk; k += gridDim.x * blockDim.x)
     if (E[k] > a.dense_cap) E[k] = (int)a.dense_cap;
-}
-
-// out[i] = min(grp_off[first[min(i, *n_dev) * stride]], cap), i in [0, n] (the clamp keeps later
-// stages inside the dense arrays when they overflowed; the run is then retried with larger ones)
-__global__ void k_off_compose(int32_t* out, int n, const int32_t* first, int stride, const int32_t* n_dev,
-                              const int32_t* grp_off, int64_t cap) {
-  const int nf = *n_dev;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
-    out[i] = (int)lst_min64(grp_off[first[(int64_t)min(i, nf) * stride]], cap);
 }
 
 }  // namespace
@@ -239,12 +249,6 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
     k_grp_clamp<<<key_blocks, 256, 0, L.stream>>>(w, E, a);
     LST_LAUNCH(L);
   }
-}
-
-void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* n_dev,
-                     const int32_t* grp_off, int64_t cap, const Launch& L) {
-  k_off_compose<<<grid_for(n + 1, 256), 256, 0, L.stream>>>(out, n, first, stride, n_dev, grp_off, cap);
-  LST_LAUNCH(L);
 }
 
 }  // namespace lst

@@ -101,8 +101,7 @@ struct Ws {
   int32_t* t3_off = nullptr;
   int32_t *t3_a = nullptr, *t3_b = nullptr, *t3_md0 = nullptr, *t3_md1 = nullptr, *t3_md2 = nullptr;
   float *t3_R = nullptr, *t3_xc = nullptr, *t3_yc = nullptr, *t3_chi2 = nullptr, *t3_pte = nullptr;
-  int32_t* t3md_off = nullptr;   // T3 by first MD
-  int32_t* t3in_off = nullptr;   // T3 grouped by inner LS
+  int32_t* t3md_off = nullptr;   // [md_dense + 2] T3 by first MD (their group offsets)
   float4* t3_anc = nullptr;      // [3][t3_dense] anchor (x, y, z, r) of each member MD
   uint8_t* t3_ecm = nullptr;     // endcap bit per anchor
   // T5
@@ -222,9 +221,10 @@ struct GroupArgs {
   int64_t slots;
   int ovf_word, arena_word;
   const int32_t *key1, *key2;        // first / second member of each slot
-  int32_t* grp_off;                  // out: [n_keys + 1] objects whose first member is below each key
+  const int32_t* key_map;            // group key of a first member k1: key_map[k1] (monotone), or k1 if nullptr
+  int32_t* grp_off;                  // out: [n_keys + 1] objects whose group key is below each key
                                      // (nullptr: not needed by a later stage; scratch is used)
-  int64_t n_keys;                    // key1 range (capacity)
+  int64_t n_keys;                    // group key range (capacity)
   const int32_t* n_keys_dev;         // device: the actual number of keys (<= n_keys); grp_off is
                                      // defined on [0, *n_keys_dev]
   int64_t dense_cap;
@@ -235,9 +235,7 @@ struct GroupArgs {
   bool dense_ls = false;             // write the dense LS arrays directly (ls_dense_write)
 };
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L);
-// out[i] = min(grp_off[first[min(i, *n_dev) * stride]], cap) for i in [0, n]
-void compose_offsets(int32_t* out, int n, const int32_t* first, int stride, const int32_t* n_dev,
-                     const int32_t* grp_off, int64_t cap, const Launch& L);
+
 
 // message returned by lst_last_error(NULL) (calls that have no context)
 void set_global_error(const char* msg);
@@ -280,8 +278,8 @@ __device__ __forceinline__ void warp_add_keyed(unsigned long long* counters, int
   if ((threadIdx.x & 31) == __ffs(grp) - 1 && sum) atomicAdd(&counters[key], (unsigned long long)sum);
 }
 
-// The dense LS at position d (ordered by (inner MD a, outer MD b)) from slot s: members, z0, dphi,
-// the outer anchor cache, and each LS's count of outer partners (the T3 candidates it starts, from
+// The dense LS at position d (ordered by (inner MD a, outer MD b)) from slot s: members (global and
+// event-local), z0, dphi, the outer anchor cache, and each LS's count of outer partners (the T3 candidates it starts, from
 // the LS-by-inner-MD offsets lsin_off) summed per module for the T3 capacities. All lanes of the
 // warp call it; n is the number of dense LS.
 __device__ __forceinline__ void ls_dense_write(const Ws& w, bool valid, int d, int s, int a, int b,
@@ -302,6 +300,11 @@ __device__ __forceinline__ void ls_dense_write(const Ws& w, bool valid, int d, i
     w.ls_xy_out[d] = make_float2(pb.x, pb.y);
     vm = w.md_vm[a];
     outs = (unsigned)(min(lsin_off[b + 1], n) - min(lsin_off[b], n));
+    // event-local member indices (the MDs of the event start at the first MD of its first module)
+    const int n_mods = w.V / w.E;
+    const int first_md = w.md_off[vm - vm % n_mods];
+    w.o_ls_in[d] = a - first_md;
+    w.o_ls_out[d] = b - first_md;
   }
   warp_add_keyed(w.t3_bound, vm, outs);
 }

@@ -70,9 +70,10 @@ __global__ void k_gather(const EvPtr* tab, Ws w, int H, int P) {
 
 // event-local copies of member indices, and the per-event summary
 __global__ void k_finalize(Ws w, int n_mods) {
-  const int nmd = w.md_off[w.V], nls = w.ls_off[w.V], nt3 = w.t3_off[w.V], nt5 = w.t5_off[w.V];
+  // (the LS and T3 copies are written with the dense objects)
+  const int nmd = w.md_off[w.V], nt5 = w.t5_off[w.V];
   const int np3 = w.pt3_off[w.P], np5 = w.pt5_off[w.P];
-  const int n = max(max(max(nmd, nls), max(nt3, nt5)), max(np3, np5));
+  const int n = max(max(nmd, nt5), max(np3, np5));
   const int64_t S5 = w.cap.t5_slots;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < nmd) {
@@ -80,18 +81,6 @@ __global__ void k_finalize(Ws w, int n_mods) {
       w.o_md_lo[i] = w.borig[w.md_lo[i]];
       w.o_md_up[i] = w.borig[w.md_up[i]];
       w.o_md_mod[i] = vm % n_mods;
-    }
-    if (i < nls) {
-      const int e = w.md_vm[w.ls_in[i]] / n_mods;
-      const int b = w.md_off[e * n_mods];
-      w.o_ls_in[i] = w.ls_in[i] - b;
-      w.o_ls_out[i] = w.ls_out[i] - b;
-    }
-    if (i < nt3) {
-      const int e = w.md_vm[w.t3_md0[i]] / n_mods;
-      const int b = w.ls_off[e * n_mods];
-      w.o_t3_a[i] = w.t3_a[i] - b;
-      w.o_t3_b[i] = w.t3_b[i] - b;
     }
     if (i < nt5) {
       const int e = w.md_vm[w.t5_md[i]] / n_mods;
@@ -439,7 +428,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.ls_in, c.ls_dense); pl.add(w.ls_out, c.ls_dense); pl.add(w.ls_z0, c.ls_dense); pl.add(w.ls_dphi, c.ls_dense);
   pl.add(w.ls_xy_out, c.ls_dense);
   // T3
-  pl.add(w.t3_cap, V); pl.add(w.t3_base, V + 1); pl.add(w.t3_off, V + 1); pl.add(w.t3in_off, c.ls_dense + 2);
+  pl.add(w.t3_cap, V); pl.add(w.t3_base, V + 1); pl.add(w.t3_off, V + 1);
   pl.add(w.t3s_a, c.t3_slots); pl.add(w.t3s_b, c.t3_slots); pl.add(w.t3s_R, c.t3_slots); pl.add(w.t3s_xc, c.t3_slots);
   pl.add(w.t3s_yc, c.t3_slots); pl.add(w.t3s_chi2, c.t3_slots); pl.add(w.t3s_pte, c.t3_slots);
   pl.add(w.t3_a, c.t3_dense); pl.add(w.t3_b, c.t3_dense); pl.add(w.t3_md0, c.t3_dense); pl.add(w.t3_md1, c.t3_dense);

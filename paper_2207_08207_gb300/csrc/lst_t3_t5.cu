@@ -247,6 +247,7 @@ __global__ void k_t3_caps(Ws w) {
 // each T3's count of outer partners (the T5 candidates it starts) summed per module
 __global__ void k_t3_dense(Ws w) {
   const int n = (int)lst_min64(w.t3_off[w.V], w.cap.t3_dense);
+  const int n_mods = w.V / w.E;
   const int64_t T = w.cap.t3_dense;
   for (int d0 = blockIdx.x * blockDim.x; d0 < n; d0 += gridDim.x * blockDim.x) {
     const int d = d0 + threadIdx.x;
@@ -275,6 +276,10 @@ __global__ void k_t3_dense(Ws w) {
       w.t3_ecm[d] = ecm;
       vm = w.md_vm[md[0]];
       outs = (unsigned)(min(w.t3md_off[md[2] + 1], n) - min(w.t3md_off[md[2]], n));
+      // event-local member indices (the LS of the event start at the first LS of its first module)
+      const int first_ls = w.ls_off[vm - vm % n_mods];
+      w.o_t3_a[d] = a - first_ls;
+      w.o_t3_b[d] = b - first_ls;
     }
     warp_add_keyed(w.t5_bound, vm, outs);
   }
@@ -517,11 +522,12 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T3_COMPACT);
   GroupArgs ga{w.t3_cnt, w.t3_cap, w.t3_base, w.cap.t3_slots, ST_OVF_T3, ST_ARENA_T3, w.t3s_a, w.t3s_b,
-               w.t3in_off, w.cap.ls_dense, &w.ls_off[w.V], w.cap.t3_dense, ST_DENSE_T3,
-               w.t3_off, w.ls_off, 1};
+               w.ls_in, w.t3md_off, w.cap.md_dense, &w.md_off[w.V], w.cap.t3_dense, ST_DENSE_T3,
+               w.t3_off, w.md_off, 1};
+  // T3 grouped by their first MD (the inner MD of their inner LS; LS are ordered by inner MD, so the
+  // (inner LS, outer LS) order is kept inside each group): the group offsets are the T3-by-first-MD
+  // adjacency that the T5 stage reads
   group_slots(w, ga, L);
-  // T3 by first MD: T3 are ordered by inner LS, and LS by inner MD
-  compose_offsets(w.t3md_off, (int)w.cap.md_dense, w.lsin_off, 1, &w.md_off[w.V], w.t3in_off, w.cap.t3_dense, L);
   k_t3_dense<<<grid_for(w.cap.t3_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   KT_END(L, K_T3_COMPACT);
@@ -541,7 +547,7 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_END(L, K_T5_DECIDE);
   LST_LAUNCH(L);
   GroupArgs ga{w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, ST_OVF_T5, ST_ARENA_T5, w.t5s_a, w.t5s_b,
-               nullptr, w.cap.t3_dense, &w.t3_off[w.V], w.cap.t5_dense, ST_DENSE_T5,
+               nullptr, nullptr, w.cap.t3_dense, &w.t3_off[w.V], w.cap.t5_dense, ST_DENSE_T5,
                w.t5_off, w.t3_off, 1};
   group_slots(w, ga, L);
   k_t5_dense<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w);
