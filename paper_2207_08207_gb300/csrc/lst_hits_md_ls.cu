@@ -21,6 +21,7 @@ __device__ __forceinline__ int find_seg(const int32_t* off, int n, int i) {
 // hit binning: counting sort by virtual sensor (2 * vm + side), stable in the input order
 // ---------------------------------------------------------------------------------------------
 __global__ void k_bin_count(Ws w, int n_sens) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) ++*w.scan_run;   // a new chain run: new scan epochs
   const int H = w.n_hits();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H; i += gridDim.x * blockDim.x) {
     const int e = find_seg(w.ev_hit_off, w.E, i);

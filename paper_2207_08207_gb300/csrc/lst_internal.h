@@ -166,6 +166,10 @@ struct Ws {
   int32_t* grp_key = nullptr;       // [max(H, t3_dense) + 2] per-key counts / group starts (compaction)
   int32_t* grp_pos = nullptr;       // [max dense] objects placed by group (compaction)
   int2* grp_key12 = nullptr;        // [max dense] their (first, second) members
+  unsigned long long* scan_state = nullptr;   // single-pass scan tile states (zeroed at allocation)
+  int32_t* scan_ctr = nullptr;      // [kScanMax] their tile tickets (zeroed every run)
+  int32_t* scan_run = nullptr;      // chain runs so far (zeroed at allocation; advanced by k_bin_count)
+  int64_t scan_state_n = 0;         // entries of scan_state
   int32_t* grp_task = nullptr;      // [(max slots + V) / 64 + 2] first module of each compaction task
   unsigned long long* t3_bound = nullptr;   // [V] T3 candidates per module (summed over its dense LS)
   unsigned long long* t5_bound = nullptr;   // [V] T5 candidates per module (summed over its dense T3)
@@ -190,7 +194,16 @@ struct Launch {
   int ls_blocks_per_sm = 0;        // resident blocks of the Line-Segment kernel (0: not queried)
   long long* launches = nullptr;   // host counter
   cudaEvent_t* kev = nullptr;      // when set: [2 * kernel id] start / end events of timed kernels
+  // single-pass scans of the chain (nullptr: three-pass scans). Tile states are tagged with an
+  // epoch = run * kScanMax + scan index, where the run counter is advanced on the device once per
+  // chain run, so that no state needs clearing between scans or runs.
+  unsigned long long* scan_state = nullptr;   // [tiles of the largest scan], zeroed once
+  int32_t* scan_ctr = nullptr;                // [kScanMax] tile tickets, zeroed every run
+  const int32_t* scan_run = nullptr;          // device run counter
+  int32_t* scan_err = nullptr;                // incremented when a look-back gives up
+  int* scan_idx = nullptr;                    // host: next scan index of the chain being enqueued
 };
+constexpr int kScanMax = 64;   // single-pass scans per chain run at most
 
 // kernels timed individually when timing is enabled (index order of lst_get_kernel_ms)
 enum KernelId : int {

@@ -369,6 +369,9 @@ int plan_work(lst_ctx* ctx, const Caps& want) {
   CK(cudaMallocFromPoolAsync(&ctx->work_mem, total, ctx->pool, ctx->stream));
   layout_work(ctx->ws, c, ctx->geo.n_mods, ctx->work_mem, &zb);
   Ws& w = ctx->ws;
+  // single-pass scan states start empty (epoch 0 never matches a run's epochs)
+  CK(cudaMemsetAsync(w.scan_state, 0, w.scan_state_n * sizeof(unsigned long long), ctx->stream));
+  CK(cudaMemsetAsync(w.scan_run, 0, sizeof(int32_t), ctx->stream));
   ctx->zero_begin = ctx->work_mem;
   ctx->zero_bytes = zb;
   ctx->work_bytes = total;
@@ -403,6 +406,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.h5_cnt, c.H + 1); z.add(w.h5_cur, c.H + 1);
   z.add(w.cell_cnt, NC); z.add(w.cell_cur, NC);
   z.add(w.work_cnt, 32); z.add(w.work_cur, 32);
+  z.add(w.scan_ctr, kScanMax);
   // binning
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
   pl.add(w.bx, c.H); pl.add(w.by, c.H); pl.add(w.bz, c.H); pl.add(w.borig, c.H);
@@ -477,6 +481,9 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.q_p3, c.q_p3); pl.add(w.q_p5, c.q_p5);
   const int64_t scan_n = std::max({S + 1, V + 1, c.H + 2, c.md_dense + 2, c.ls_dense + 2, c.t3_dense + 2, NC + 1, c.P + 1});
   pl.add(w.scan_tmp, scan_tmp_elems(scan_n) + 8);
+  w.scan_state_n = scan_tmp_elems(scan_n) + 8;
+  pl.add(w.scan_state, w.scan_state_n);
+  pl.add(w.scan_run, 1);
   const size_t zb = z.layout();
   const size_t pb = pl.layout();
   if (base) {
@@ -511,7 +518,13 @@ int enqueue_chain(lst_ctx* ctx) {
   w.S = 2 * w.V;
   w.cap_scale = ctx->cfg.cap_scale;
   w.cycle_budget = ctx->cfg.cycle_budget;
-  const Launch L = make_launch(ctx);
+  Launch L = make_launch(ctx);
+  int scan_idx = 0;
+  L.scan_state = w.scan_state;
+  L.scan_ctr = w.scan_ctr;
+  L.scan_run = w.scan_run;
+  L.scan_err = &w.status[ST_TIMEOUT];
+  L.scan_idx = &scan_idx;
   const Geo& g = ctx->geo;
   const Consts& c = ctx->consts;
   CK(cudaMemsetAsync(ctx->zero_begin, 0, ctx->zero_bytes, ctx->stream));

@@ -1,6 +1,7 @@
-// Exclusive prefix sum over int32 counts (three passes: per-tile scan, scan of tile totals,
-// add-back). Used for every count -> offset step of the chain (sensor offsets, per-module object
-// offsets, per-MD adjacency offsets).
+// Exclusive prefix sums over int32 counts, used for every count -> offset step of the chain
+// (sensor offsets, per-module object offsets, per-key group offsets). Inside a chain run: one
+// single-pass kernel per scan (decoupled look-back); elsewhere (the standalone binning entry
+// points): three passes (per-tile scan, scan of tile totals, add-back).
 #include "lst_internal.h"
 
 namespace lst {
@@ -95,6 +96,81 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_add(int32_t* out, int64_t n
     if (base + k < n) out[base + k] += add;
 }
 
+// Single-pass exclusive scan with decoupled look-back (D. Merrill and M. Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", NVIDIA tech. report NVR-2016-002). Each block takes
+// the next tile ticket, scans its tile, publishes the tile total, then adds the totals of the
+// preceding tiles, walking back until a tile whose inclusive prefix is published, and publishes its
+// own inclusive prefix. A block only waits on tiles whose tickets were taken before its own, by
+// blocks already running, so the waits end; each is bounded all the same (kSpinMax polls), and a
+// wait that gives up counts itself in *err (the run then reports a timeout).
+// State word: epoch (30 bits) | flag (2 bits: 1 tile total, 2 inclusive prefix) | value (32 bits).
+constexpr int kSpinMax = 1 << 22;
+
+__device__ __forceinline__ unsigned long long scan_word(unsigned epoch, unsigned flag, int v) {
+  return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | (unsigned)v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_1pass(const int32_t* in, int32_t* out, int64_t n_max,
+                                                           const int32_t* n_dev, int n_add,
+                                                           unsigned long long* state, int32_t* ticket,
+                                                           const int32_t* run, int scan_idx, int32_t* err) {
+  __shared__ int s_tile, s_excl;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1);
+  __syncthreads();
+  const int tile = s_tile;
+  const int64_t n = scan_count(n_max, n_dev, n_add);
+  const int64_t last = (n + kTile - 1) / kTile - 1;
+  if (tile > last) {
+    if (n == 0 && tile == 0 && threadIdx.x == 0) out[0] = 0;
+    return;
+  }
+  const int64_t base = (int64_t)tile * kTile + (int64_t)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int local = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    local += v[k];
+  }
+  int total;
+  int pre = block_excl_scan(local, total);
+  if (threadIdx.x == 0) {
+    const unsigned epoch = ((unsigned)*run * kScanMax + (unsigned)scan_idx) & 0x3fffffffu;
+    int excl = 0;
+    if (tile == 0) {
+      atomicExch(&state[0], scan_word(epoch, 2, total));
+    } else {
+      atomicExch(&state[tile], scan_word(epoch, 1, total));
+      int p = tile - 1, spins = 0;
+      while (p >= 0) {
+        const unsigned long long sw = *reinterpret_cast<volatile unsigned long long*>(&state[p]);
+        const unsigned flag = (unsigned)(sw >> 32) & 3u;
+        if ((unsigned)(sw >> 34) != epoch || flag == 0) {
+          if (++spins > kSpinMax) {
+            atomicAdd(err, 1);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += (int)(unsigned)sw;
+        if (flag == 2) break;
+        --p;
+      }
+      atomicExch(&state[tile], scan_word(epoch, 2, excl + total));
+    }
+    s_excl = excl;
+  }
+  __syncthreads();
+  pre += s_excl;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = pre;
+    pre += v[k];
+  }
+  if (tile == last && threadIdx.x == 0) out[n] = s_excl + total;
+}
+
 }  // namespace
 
 int64_t scan_tmp_elems(int64_t n) { return (n + kTile - 1) / kTile + 1; }
@@ -102,6 +178,13 @@ int64_t scan_tmp_elems(int64_t n) { return (n + kTile - 1) / kTile + 1; }
 void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_t* n_dev, int n_add, int32_t* tmp,
                         const Launch& L) {
   const int64_t tiles = (n + kTile - 1) / kTile;
+  if (L.scan_state && *L.scan_idx < kScanMax) {
+    const int idx = (*L.scan_idx)++;
+    k_scan_1pass<<<(unsigned)std::max<int64_t>(tiles, 1), kScanBlock, 0, L.stream>>>(
+        in, out, n, n_dev, n_add, L.scan_state, L.scan_ctr + idx, L.scan_run, idx, L.scan_err);
+    LST_LAUNCH(L);
+    return;
+  }
   if (tiles == 0) {
     k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, 0, out, 0, nullptr, 0);
     LST_LAUNCH(L);
