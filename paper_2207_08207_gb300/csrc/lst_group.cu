@@ -8,7 +8,8 @@
 // Groups may also be coarser, by a monotone map of the first member (T3 by the inner MD of their
 // inner LS): the order inside a group is then by (first, second) member.
 // The compaction therefore works per object, with no per-module sort:
-//   1. count the objects of every first member (atomics on a key-indexed array);
+//   1. count the objects of every first member (atomics on a key-indexed array, done by the kernels
+//      that store the objects);
 //   2. exclusive scan: the start of every group, which are also the per-key group offsets that the
 //      next stage uses as its adjacency ("objects whose first member is below k");
 //   3. place each object at its group's cursor (order inside a group arbitrary);
@@ -106,20 +107,6 @@ __device__ __forceinline__ void visit_task(const Ws& w, const GroupArgs& a, int 
   }
 }
 
-// Pass 1: one count per object at E[first member + 1] (lanes of one key summed first)
-__global__ void __launch_bounds__(32 * kGrpWarps) k_grp_count(Ws w, GroupArgs a, int32_t* E, int chunk) {
-  const int lane = threadIdx.x & 31;
-  const int nk = *a.n_keys_dev;
-  const int n_tasks = (w.eff[w.V] + chunk - 1) / chunk;   // (of the weights)
-  for (int t = blockIdx.x * kGrpWarps + (threadIdx.x >> 5); t < n_tasks; t += gridDim.x * kGrpWarps)
-    visit_task(w, a, t, lane, [&](bool v, int s) {
-      const int key = v ? group_of(a, a.key1[s], nk) + 1 : 0;
-      const unsigned grp = __match_any_sync(kFull, key);
-      const int cnt = __popc(grp & __ballot_sync(kFull, v));
-      if (v && lane == __ffs(grp) - 1) atomicAdd(&E[key], cnt);
-    });
-}
-
 // Pass 3: after the exclusive scan E[k + 1] is the start of group k; each object takes the next
 // position of its group. Afterwards E[k] is the start of group k for every k (E[0] stays 0).
 __global__ void __launch_bounds__(32 * kGrpWarps) k_grp_place(Ws w, GroupArgs a, int32_t* E, int chunk) {
@@ -135,12 +122,6 @@ __global__ void __launch_bounds__(32 * kGrpWarps) k_grp_place(Ws w, GroupArgs a,
         w.grp_key12[p] = make_int2(k1, a.key2[s]);
       }
     });
-}
-
-// Pass 0: zero the counts of the actual keys
-__global__ void k_grp_zero(int32_t* E, GroupArgs a) {
-  const int nk = *a.n_keys_dev;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nk; k += gridDim.x * blockDim.x) E[k] = 0;
 }
 
 // Pass 4: the rank of each placed object inside its group by (second member, slot), which gives its
@@ -234,10 +215,6 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.eff, w.eff, w.V, w.scan_tmp, L);
   k_grp_tasks<<<grid_for((a.slots + w.V) / chunk + 2, 256), 256, 0, L.stream>>>(w, chunk);
-  LST_LAUNCH(L);
-  k_grp_zero<<<key_blocks, 256, 0, L.stream>>>(E, a);
-  LST_LAUNCH(L);
-  k_grp_count<<<blocks, 32 * kGrpWarps, 0, L.stream>>>(w, a, E, chunk);
   LST_LAUNCH(L);
   scan_exclusive_dev(E, E, a.n_keys + 1, a.n_keys_dev, 1, w.scan_tmp, L);
   k_grp_place<<<blocks, 32 * kGrpWarps, 0, L.stream>>>(w, a, E, chunk);

@@ -169,6 +169,7 @@ __device__ __forceinline__ int clamp_cap(double pred, long long bound, int ovr) 
 }
 
 __global__ void k_md_caps(Ws w) {
+  zero_group_counts(w.grp_key, w.n_hits());   // MDs are grouped by lower hit
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long nlo = w.sens_off[2 * vm + 1] - w.sens_off[2 * vm];
     const long long nup = w.sens_off[2 * vm + 2] - w.sens_off[2 * vm + 1];
@@ -225,6 +226,7 @@ __device__ __forceinline__ void md_flush(const Ws& w, const Geo& g, const Cst<fl
       w.ms_up[base + slot] = u;
       w.ms_dpc[base + slot] = dpc;
       w.ms_pte[base + slot] = pte;
+      atomicAdd(&w.grp_key[l + 1], 1);
     }
   }
   const int q = warp_agg_slot(v == kUnsure, &w.status[ST_Q_MD]);
@@ -301,6 +303,7 @@ __global__ void k_md_recheck(Ws w, Geo g, Cst<double> c) {
       w.ms_up[base + slot] = u;
       w.ms_dpc[base + slot] = (float)dpc;
       w.ms_pte[base + slot] = (float)pte;
+      atomicAdd(&w.grp_key[l + 1], 1);
     }
   }
 }
@@ -353,6 +356,7 @@ __device__ __forceinline__ int md_count(const Ws& w, int vm) { return w.md_off[v
 // LS capacity of each module (exact bound: its MDs x the MDs of its connected modules) and its
 // cost bucket floor(log2(bound)) for the persistent kernel's work list
 __global__ void k_ls_caps(Ws w, Geo g) {
+  zero_group_counts(w.lsin_off, w.md_off[w.V]);   // LS are grouped by inner MD
   __shared__ int hist[32];
   if (threadIdx.x < 32) hist[threadIdx.x] = 0;
   __syncthreads();
@@ -472,14 +476,17 @@ __device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const
                        w.md_sa[b].x, w.md_ec[b] != 0, kGuardWindow, z0, dphi);
   }
   const int slot = warp_agg_slot_keyed(v == kAccept, vm, w.ls_cnt);
+  bool stored = false;
   if (slot >= 0) {
     const int cap = w.ls_cap[vm], base = w.ls_base[vm];
     if (slot < cap && (int64_t)base + slot < w.cap.ls_slots) {
       w.lss_in[base + slot] = a;
       w.lss_out[base + slot] = b;
       w.lss_dphi[base + slot] = dphi;
+      stored = true;
     }
   }
+  warp_count_keyed(stored, a + 1, w.lsin_off);   // the group sizes of the compaction
   const int q = warp_agg_slot(v == kUnsure, &w.status[ST_Q_LS]);
   if (q >= 0 && q < w.cap.q_ls) w.q_ls[q] = make_int4(vm, a, b, 0);
 }
@@ -636,6 +643,7 @@ __global__ void k_ls_recheck(Ws w, Cst<double> c) {
       w.lss_in[base + slot] = a;
       w.lss_out[base + slot] = b;
       w.lss_dphi[base + slot] = (float)dphi;
+      atomicAdd(&w.lsin_off[a + 1], 1);
     }
   }
 }

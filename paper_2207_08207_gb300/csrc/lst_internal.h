@@ -239,7 +239,8 @@ struct GroupArgs {
                                      // (nullptr: not needed by a later stage; scratch is used)
   int64_t n_keys;                    // group key range (capacity)
   const int32_t* n_keys_dev;         // device: the actual number of keys (<= n_keys); grp_off is
-                                     // defined on [0, *n_keys_dev]
+                                     // defined on [0, *n_keys_dev]. The group sizes are counted by the
+                                     // producing kernels into grp_off (or grp_key) at [group + 1].
   int64_t dense_cap;
   int dense_word;
   int32_t* mod_off;                  // [V + 1] out: per-module dense offsets
@@ -289,6 +290,22 @@ __device__ __forceinline__ void warp_add_keyed(unsigned long long* counters, int
   const unsigned grp = __match_any_sync(0xffffffffu, key);
   const unsigned sum = __reduce_add_sync(grp, v);
   if ((threadIdx.x & 31) == __ffs(grp) - 1 && sum) atomicAdd(&counters[key], (unsigned long long)sum);
+}
+
+// Group counts of a compaction: the producing kernels count each stored object at E[group + 1] of an
+// array zeroed on [0, n] before them (by the stage's capacity kernel; all threads of its grid call
+// this).
+__device__ __forceinline__ void zero_group_counts(int32_t* E, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) E[k] = 0;
+}
+
+// E[key] += 1 for every lane with pred, one atomic per distinct key of the warp (all lanes call it)
+__device__ __forceinline__ void warp_count_keyed(bool pred, int key, int32_t* E) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (pred) {
+    const unsigned grp = __match_any_sync(m, key);
+    if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&E[key], __popc(grp));
+  }
 }
 
 // The dense LS at position d (ordered by (inner MD a, outer MD b)) from slot s: members (global and

@@ -215,6 +215,7 @@ __global__ void k_t3_decide(Ws w, Cst<ff> c) {
       const int s = base + slot;
       w.t3s_a[s] = q.x;
       w.t3s_b[s] = q.y;
+      atomicAdd(&w.t3md_off[md0 + 1], 1);
       w.t3s_R[s] = (float)circ.R;
       w.t3s_xc[s] = (float)circ.xc;
       w.t3s_yc[s] = (float)circ.yc;
@@ -235,6 +236,7 @@ __device__ __forceinline__ int clamp_cap2(double pred, long long bound, int ovr)
 // T3 capacity of module vm from its bound (the number of (inner LS, outer LS) pairs whose inner LS
 // starts in vm, summed while the LS were compacted)
 __global__ void k_t3_caps(Ws w) {
+  zero_group_counts(w.t3md_off, w.md_off[w.V]);   // T3 are grouped by first MD
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long bound = (long long)w.t3_bound[vm];
     const int cc = clamp_cap2(w.cap_scale * w.stage_scale[2] * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
@@ -369,6 +371,7 @@ __device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T 
 // T5 capacity of module vm from its bound (the number of (inner T3, outer T3) pairs whose inner T3
 // starts in vm, summed while the T3 were compacted)
 __global__ void k_t5_caps(Ws w) {
+  zero_group_counts(w.grp_key, w.t3_off[w.V]);   // T5 are grouped by inner T3
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long bound = (long long)w.t5_bound[vm];
     const int cc = clamp_cap2(w.cap_scale * w.stage_scale[3] * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
@@ -470,6 +473,7 @@ __global__ void k_t5_decide(Ws w, Cst<ff> c) {
       const int64_t S = w.cap.t5_slots;
       w.t5s_a[s] = i;
       w.t5s_b[s] = j;
+      atomicAdd(&w.grp_key[i + 1], 1);
       w.t5s_f[0 * S + s] = (float)kin;
       w.t5s_f[1 * S + s] = (float)kout;
       w.t5s_f[2 * S + s] = (float)rho;
