@@ -456,78 +456,83 @@ __device__ bool key_less(const Ws& w, int type, int a, int b) {
   return na < nb;
 }
 
-// best pT5 and pT3 of each seed by (score, hit tuple): a warp per seed, each lane the best of its
-// share of the candidates, then a shuffle reduction
-template <int Type>
-__device__ __forceinline__ int best_of(const Ws& w, const int32_t* off, const float* sc, int p) {
-  const int lane = threadIdx.x & 31;
+// best pT5 and pT3 of each seed by (score, hit tuple): a group of G lanes per seed (gmask: the
+// group's lanes), each lane the best of its share of the candidates, then a shuffle reduction
+template <int Type, int G>
+__device__ __forceinline__ int best_of(const Ws& w, const int32_t* off, const float* sc, int p, int sub,
+                                       unsigned gmask) {
   int b = -1;
-  for (int i = off[p] + lane; i < off[p + 1]; i += 32)
+  for (int i = off[p] + sub; i < off[p + 1]; i += G)
     if (b < 0 || sc[i] < sc[b] || (sc[i] == sc[b] && key_less(w, Type, i, b))) b = i;
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const int c = __shfl_xor_sync(0xffffffffu, b, o);
+  for (int o = G / 2; o >= 1; o >>= 1) {
+    const int c = __shfl_xor_sync(gmask, b, o, G);
     if (c >= 0 && (b < 0 || sc[c] < sc[b] || (sc[c] == sc[b] && key_less(w, Type, c, b)))) b = c;
   }
   return b;
 }
 
-// order each seed's objects by object index (unique within a seed): a warp per seed; each element's
-// output position is its rank, the number of the seed's keys below its own (keys staged in shared
-// memory for groups up to kPtOrderSmem). The same warp then picks the seed's best candidate by
-// (score, hit tuple) for the track-candidate stage; the pT5 pass (the second) also records whether
-// the seed is in any pT3 / pT5.
+// order each seed's objects by object index (unique within a seed): a group of kPtLanes lanes per
+// seed (seeds hold a few objects: a median of 2-3; 16 lanes for pT3, whose seeds reach dozens more
+// often, 8 for pT5); each element's output position is its rank, the number of the seed's keys below
+// its own (by shuffles up to kPtLanes objects, else with the keys staged in shared memory for up to
+// kPtStage). The same group then picks the seed's best candidate
+// by (score, hit tuple) for the track-candidate stage; the pT5 pass (the second) also records
+// whether the seed is in any pT3 / pT5.
 constexpr int kPtOrderWarps = 4;
-constexpr int kPtOrderSmem = 256;
+constexpr int kPtStage = 64;
+template <int Type> __host__ __device__ constexpr int pt_lanes() { return Type == TC_PT3 ? 16 : 8; }
 
 template <int Type>
 __global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
     Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls, const int32_t* a_obj, const float* a_xy,
     const float* a_rz, const float* a_sc, int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc,
     int32_t* best) {
-  __shared__ int keys[kPtOrderWarps][kPtOrderSmem];
-  int* K = keys[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
+  constexpr int kPtLanes = pt_lanes<Type>();
+  __shared__ int keys[32 * kPtOrderWarps / kPtLanes][kPtStage];
+  int* K = keys[threadIdx.x / kPtLanes];
+  const int sub = threadIdx.x & (kPtLanes - 1);
+  const unsigned gmask = ((1u << kPtLanes) - 1u) << ((threadIdx.x & 31) & ~(kPtLanes - 1));
   const int P = w.n_pls();
-  const int nwarps = gridDim.x * kPtOrderWarps;
-  for (int p = blockIdx.x * kPtOrderWarps + (threadIdx.x >> 5); p < P; p += nwarps) {
+  const int ngroups = gridDim.x * (blockDim.x / kPtLanes);
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) / kPtLanes; p < P; p += ngroups) {
     const int a = off[p], n = off[p + 1] - a;
     if (n == 0) {
-      if (lane == 0) {
+      if (sub == 0) {
         best[p] = -1;
         if (Type == TC_PT5) w.pls_member[p] = w.best3[p] >= 0 ? 1 : 0;
       }
       continue;
     }
-    if (n <= 32) {
+    if (n <= kPtLanes) {
       int v = 0, key = 0x7fffffff;
-      if (lane < n) {
-        v = tmp_idx[a + lane];
+      if (sub < n) {
+        v = tmp_idx[a + sub];
         key = a_obj[v];
       }
       int rank = 0;
-      for (int j = 0; j < n; ++j) rank += __shfl_sync(0xffffffffu, key, j) < key;
-      if (lane < n) {
+      for (int j = 0; j < n; ++j) rank += __shfl_sync(gmask, key, j, kPtLanes) < key;
+      if (sub < n) {
         const int o = a + rank;
         d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
       }
     } else {
-    const bool staged = n <= kPtOrderSmem;
-    if (staged)
-      for (int j = lane; j < n; j += 32) K[j] = a_obj[tmp_idx[a + j]];
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      const int v = tmp_idx[a + i];
-      const int key = a_obj[v];
-      int rank = 0;
-      for (int j = 0; j < n; ++j) rank += (staged ? K[j] : a_obj[tmp_idx[a + j]]) < key;
-      const int o = a + rank;
-      d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+      const bool staged = n <= kPtStage;
+      if (staged)
+        for (int j = sub; j < n; j += kPtLanes) K[j] = a_obj[tmp_idx[a + j]];
+      __syncwarp(gmask);
+      for (int i = sub; i < n; i += kPtLanes) {
+        const int v = tmp_idx[a + i];
+        const int key = a_obj[v];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) rank += (staged ? K[j] : a_obj[tmp_idx[a + j]]) < key;
+        const int o = a + rank;
+        d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+      }
     }
-    }
-    __syncwarp();   // the ordered rows are read back by the other lanes below
-    const int b = best_of<Type>(w, off, d_sc, p);
-    if (lane == 0) {
+    __syncwarp(gmask);   // the ordered rows are read back by the other lanes below
+    const int b = best_of<Type, kPtLanes>(w, off, d_sc, p, sub, gmask);
+    if (sub == 0) {
       best[p] = b;
       if (Type == TC_PT5) w.pls_member[p] = (b >= 0 || w.best3[p] >= 0) ? 1 : 0;
     }
@@ -559,15 +564,18 @@ __global__ void k_h5_count(Ws w, int fill) {
 // T5 duplicate removal: T5 a is dropped when another passing T5 shares at least `overlap` of its
 // ten hits and ranks lower (chi2_c as float32, then hit tuple). A T5 sharing `overlap` hits with a
 // contains at least one of a's first 11 - overlap hits (a misses at most 10 - overlap of them), so
-// only those hits' T5 lists are searched. A warp per T5: the candidates of the searched lists are
-// spread over the lanes, and any lane's hit drops it.
+// only those hits' T5 lists are searched (about a dozen T5 in all, typically). kCleanLanes lanes per
+// T5: the candidates of the searched lists are spread over them, and any lane's hit drops it.
+constexpr int kCleanLanes = 8;
+
 __global__ void k_t5_clean(Ws w, int overlap) {
   const int n = w.t5_off[w.V];
   const int64_t S = w.cap.t5_dense;
   const int n_probe = min(10, max(1, 11 - overlap));
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); a < n; a += nwarps) {
+  const int sub = threadIdx.x & (kCleanLanes - 1);
+  const unsigned gmask = ((1u << kCleanLanes) - 1u) << ((threadIdx.x & 31) & ~(kCleanLanes - 1));
+  const int ngroups = gridDim.x * (blockDim.x / kCleanLanes);
+  for (int a = (blockIdx.x * blockDim.x + threadIdx.x) / kCleanLanes; a < n; a += ngroups) {
     int ha[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) ha[k] = w.t5_hit[(int64_t)a * 10 + k];
@@ -583,7 +591,7 @@ __global__ void k_t5_clean(Ws w, int overlap) {
       end_[t] = total;
     }
     bool drop = false;
-    for (int k = lane; k < total && !drop; k += 32) {
+    for (int k = sub; k < total && !drop; k += kCleanLanes) {
       int t = 0;
 #pragma unroll
       for (int u = 0; u < 9; ++u) t += k >= end_[u];
@@ -607,8 +615,8 @@ __global__ void k_t5_clean(Ws w, int overlap) {
       const float cb = w.t5_f[3 * S + b];
       if (cb < ca || (cb == ca && key_less(w, TC_T5, b, a))) drop = true;
     }
-    drop = __any_sync(0xffffffffu, drop);
-    if (lane == 0) w.t5_kept[a] = drop ? 0 : 1;
+    drop = __any_sync(gmask, drop);
+    if (sub == 0) w.t5_kept[a] = drop ? 0 : 1;
   }
 }
 
@@ -1009,12 +1017,12 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   scan_exclusive(w.p5_cnt, w.pt5_off, w.P, w.scan_tmp, L);
   k_pt_group<<<grid_for(w.cap.p3_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT3, w.cap.p3_slots, w.p3a_pls,
                                                                    w.p3a_obj, w.pt3_off, w.p3_cur, w.grp_tmp);
-  k_pt_order<TC_PT3><<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
+  k_pt_order<TC_PT3><<<grid_for((int64_t)w.P * pt_lanes<TC_PT3>(), 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt3_off, w.grp_tmp, w.p3a_pls, w.p3a_obj, w.p3a_xy, w.p3a_rz, w.p3a_sc, w.pt3_pls, w.pt3_obj,
       w.pt3_xy, w.pt3_rz, w.pt3_sc, w.best3);
   k_pt_group<<<grid_for(w.cap.p5_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT5, w.cap.p5_slots, w.p5a_pls,
                                                                    w.p5a_obj, w.pt5_off, w.p5_cur, w.grp_tmp);
-  k_pt_order<TC_PT5><<<grid_for((int64_t)w.P * 32, 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
+  k_pt_order<TC_PT5><<<grid_for((int64_t)w.P * pt_lanes<TC_PT5>(), 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt5_off, w.grp_tmp, w.p5a_pls, w.p5a_obj, w.p5a_xy, w.p5a_rz, w.p5a_sc, w.pt5_pls, w.pt5_obj,
       w.pt5_xy, w.pt5_rz, w.pt5_sc, w.best5);
   *L.launches += 4;
@@ -1027,7 +1035,8 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   scan_exclusive(w.h5_cnt, w.h5_off, w.cap.H, w.scan_tmp, L);
   k_h5_count<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, 1);
   KT_BEGIN(L, K_TC_CLEAN);
-  k_t5_clean<<<grid_for((int64_t)w.cap.t5_dense * 32, 256, 152 * 32), 256, 0, L.stream>>>(w, c.d.t5_overlap_hits);
+  k_t5_clean<<<grid_for((int64_t)w.cap.t5_dense * kCleanLanes, 256, 152 * 32), 256, 0, L.stream>>>(
+      w, c.d.t5_overlap_hits);
   KT_END(L, K_TC_CLEAN);
   k_grid_items<<<grid_for(w.P + w.cap.t5_dense, 256), 256, 0, L.stream>>>(w, g, 0);
   *L.launches += 3;
