@@ -313,11 +313,14 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
   const int n = (int)lst_min64(w.md_off[w.V], w.cap.md_dense);
   for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
     const int s = w.perm[d];
-    const int lo = w.ms_lo[s];
+    const int lo = w.ms_lo[s], up = w.ms_up[s];
     const int vm = w.hit_vs[w.bidx[lo]] >> 1;
     w.md_lo[d] = lo;
-    w.md_up[d] = w.ms_up[s];
+    w.md_up[d] = up;
     w.md_vm[d] = vm;
+    w.o_md_lo[d] = w.borig[lo];   // event-local outputs: input hit indices, module
+    w.o_md_up[d] = w.borig[up];
+    w.o_md_mod[d] = vm % g.n_mods;
     w.md_dpc[d] = w.ms_dpc[s];
     w.md_pte[d] = w.ms_pte[s];
     const float x = w.bx[lo], y = w.by[lo];

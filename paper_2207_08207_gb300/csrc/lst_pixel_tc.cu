@@ -116,32 +116,36 @@ struct ObjAnc {
   int64_t stride;
 };
 
-// bounding box of the first anchors of each module's objects (a warp per module)
+// bounding box of the first anchors of each module's objects (kBoxLanes lanes per module: modules
+// hold a few T3 / T5 each, most none)
+constexpr int kBoxLanes = 4;
+
 __global__ void k_obj_box(Ws w, const int32_t* obj_off, const float4* anc0, float4* box) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+  const int sub = threadIdx.x & (kBoxLanes - 1);
+  const unsigned gmask = ((1u << kBoxLanes) - 1u) << ((threadIdx.x & 31) & ~(kBoxLanes - 1));
+  const int ngroups = gridDim.x * (blockDim.x / kBoxLanes);
+  for (int vm = (blockIdx.x * blockDim.x + threadIdx.x) / kBoxLanes; vm < w.V; vm += ngroups) {
     const int a = obj_off[vm], b = obj_off[vm + 1];
     if (a == b) continue;
     float4 lo = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
     float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
-    for (int i = a + lane; i < b; i += 32) {
+    for (int i = a + sub; i < b; i += kBoxLanes) {
       const float4 h = anc0[i];
       lo.x = fminf(lo.x, h.x); lo.y = fminf(lo.y, h.y); lo.z = fminf(lo.z, h.z); lo.w = fminf(lo.w, h.w);
       hi.x = fmaxf(hi.x, h.x); hi.y = fmaxf(hi.y, h.y); hi.z = fmaxf(hi.z, h.z); hi.w = fmaxf(hi.w, h.w);
     }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
-      lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
-      lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
-      lo.w = fminf(lo.w, __shfl_xor_sync(0xffffffffu, lo.w, o));
-      hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
-      hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
-      hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
-      hi.w = fmaxf(hi.w, __shfl_xor_sync(0xffffffffu, hi.w, o));
+    for (int o = kBoxLanes / 2; o >= 1; o >>= 1) {
+      lo.x = fminf(lo.x, __shfl_xor_sync(gmask, lo.x, o, kBoxLanes));
+      lo.y = fminf(lo.y, __shfl_xor_sync(gmask, lo.y, o, kBoxLanes));
+      lo.z = fminf(lo.z, __shfl_xor_sync(gmask, lo.z, o, kBoxLanes));
+      lo.w = fminf(lo.w, __shfl_xor_sync(gmask, lo.w, o, kBoxLanes));
+      hi.x = fmaxf(hi.x, __shfl_xor_sync(gmask, hi.x, o, kBoxLanes));
+      hi.y = fmaxf(hi.y, __shfl_xor_sync(gmask, hi.y, o, kBoxLanes));
+      hi.z = fmaxf(hi.z, __shfl_xor_sync(gmask, hi.z, o, kBoxLanes));
+      hi.w = fmaxf(hi.w, __shfl_xor_sync(gmask, hi.w, o, kBoxLanes));
     }
-    if (lane == 0) {
+    if (sub == 0) {
       box[vm] = lo;
       box[w.V + vm] = hi;
     }
@@ -481,14 +485,24 @@ __device__ __forceinline__ int best_of(const Ws& w, const int32_t* off, const fl
 // whether the seed is in any pT3 / pT5.
 constexpr int kPtOrderWarps = 4;
 constexpr int kPtStage = 64;
+
+// event-local outputs of a pT object of seed p and object obj at position o: the seed's index in its
+// event, the object's index among the event's T3 / T5 (obj_off: per-module T3 / T5 offsets)
+__device__ __forceinline__ void pt_local(const Ws& w, int p, int obj, int o, int n_mods, int32_t* o_pls,
+                                         int32_t* o_obj, const int32_t* obj_off) {
+  const int e = w.pls_ev[p];
+  o_pls[o] = p - w.ev_pls_off[e];
+  o_obj[o] = obj - obj_off[e * n_mods];
+}
 template <int Type> __host__ __device__ constexpr int pt_lanes() { return Type == TC_PT3 ? 16 : 8; }
 
 template <int Type>
 __global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
     Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls, const int32_t* a_obj, const float* a_xy,
     const float* a_rz, const float* a_sc, int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc,
-    int32_t* best) {
+    int32_t* best, int32_t* o_pls, int32_t* o_obj, const int32_t* obj_off) {
   constexpr int kPtLanes = pt_lanes<Type>();
+  const int n_mods = w.V / w.E;
   __shared__ int keys[32 * kPtOrderWarps / kPtLanes][kPtStage];
   int* K = keys[threadIdx.x / kPtLanes];
   const int sub = threadIdx.x & (kPtLanes - 1);
@@ -515,6 +529,7 @@ __global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
       if (sub < n) {
         const int o = a + rank;
         d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+        pt_local(w, p, key, o, n_mods, o_pls, o_obj, obj_off);
       }
     } else {
       const bool staged = n <= kPtStage;
@@ -528,6 +543,7 @@ __global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
         for (int j = 0; j < n; ++j) rank += (staged ? K[j] : a_obj[tmp_idx[a + j]]) < key;
         const int o = a + rank;
         d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+        pt_local(w, p, key, o, n_mods, o_pls, o_obj, obj_off);
       }
     }
     __syncwarp(gmask);   // the ordered rows are read back by the other lanes below
@@ -987,8 +1003,8 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   ObjAnc om5{w.t5_anc, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
     k_seed_cache<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, c.f);
-    k_obj_box<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, w.t3_off, w.t3_anc, w.box3);
-    k_obj_box<<<grid_for((int64_t)w.V * 32, 256), 256, 0, L.stream>>>(w, w.t5_off, w.t5_anc, w.box5);
+    k_obj_box<<<grid_for((int64_t)w.V * kBoxLanes, 256), 256, 0, L.stream>>>(w, w.t3_off, w.t3_anc, w.box3);
+    k_obj_box<<<grid_for((int64_t)w.V * kBoxLanes, 256), 256, 0, L.stream>>>(w, w.t5_off, w.t5_anc, w.box5);
     *L.launches += 3;
     KT_BEGIN(L, K_PT3_PRE);
   k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, w.box3, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
@@ -1019,12 +1035,12 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
                                                                    w.p3a_obj, w.pt3_off, w.p3_cur, w.grp_tmp);
   k_pt_order<TC_PT3><<<grid_for((int64_t)w.P * pt_lanes<TC_PT3>(), 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt3_off, w.grp_tmp, w.p3a_pls, w.p3a_obj, w.p3a_xy, w.p3a_rz, w.p3a_sc, w.pt3_pls, w.pt3_obj,
-      w.pt3_xy, w.pt3_rz, w.pt3_sc, w.best3);
+      w.pt3_xy, w.pt3_rz, w.pt3_sc, w.best3, w.o_pt3_pls, w.o_pt3_obj, w.t3_off);
   k_pt_group<<<grid_for(w.cap.p5_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT5, w.cap.p5_slots, w.p5a_pls,
                                                                    w.p5a_obj, w.pt5_off, w.p5_cur, w.grp_tmp);
   k_pt_order<TC_PT5><<<grid_for((int64_t)w.P * pt_lanes<TC_PT5>(), 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt5_off, w.grp_tmp, w.p5a_pls, w.p5a_obj, w.p5a_xy, w.p5a_rz, w.p5a_sc, w.pt5_pls, w.pt5_obj,
-      w.pt5_xy, w.pt5_rz, w.pt5_sc, w.best5);
+      w.pt5_xy, w.pt5_rz, w.pt5_sc, w.best5, w.o_pt5_pls, w.o_pt5_obj, w.t5_off);
   *L.launches += 4;
 }
 

@@ -68,42 +68,7 @@ __global__ void k_gather(const EvPtr* tab, Ws w, int H, int P) {
   }
 }
 
-// event-local copies of member indices, and the per-event summary
-__global__ void k_finalize(Ws w, int n_mods) {
-  // (the LS and T3 copies are written with the dense objects)
-  const int nmd = w.md_off[w.V], nt5 = w.t5_off[w.V];
-  const int np3 = w.pt3_off[w.P], np5 = w.pt5_off[w.P];
-  const int n = max(max(nmd, nt5), max(np3, np5));
-  const int64_t S5 = w.cap.t5_slots;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (i < nmd) {
-      const int vm = w.md_vm[i];
-      w.o_md_lo[i] = w.borig[w.md_lo[i]];
-      w.o_md_up[i] = w.borig[w.md_up[i]];
-      w.o_md_mod[i] = vm % n_mods;
-    }
-    if (i < nt5) {
-      const int e = w.md_vm[w.t5_md[i]] / n_mods;
-      const int b = w.t3_off[e * n_mods];
-      w.o_t5_a[i] = w.t5_a[i] - b;
-      w.o_t5_b[i] = w.t5_b[i] - b;
-    }
-    if (i < np3) {
-      const int p = w.pt3_pls[i];
-      const int e = find_seg_rt(w.ev_pls_off, w.E, p);
-      w.o_pt3_pls[i] = p - w.ev_pls_off[e];
-      w.o_pt3_obj[i] = w.pt3_obj[i] - w.t3_off[e * n_mods];
-    }
-    if (i < np5) {
-      const int p = w.pt5_pls[i];
-      const int e = find_seg_rt(w.ev_pls_off, w.E, p);
-      w.o_pt5_pls[i] = p - w.ev_pls_off[e];
-      w.o_pt5_obj[i] = w.pt5_obj[i] - w.t5_off[e * n_mods];
-    }
-  }
-  (void)S5;
-}
-
+// the per-event summary
 __global__ void k_ev_stat(Ws w, int n_mods) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w.E; e += gridDim.x * blockDim.x) {
     int* st = w.ev_stat + e * kEvWords;
@@ -546,10 +511,9 @@ int enqueue_chain(lst_ctx* ctx) {
   mark();
   run_tc(w, g, c, L);
   mark();
-  k_finalize<<<grid_for(std::max({ctx->caps.ls_dense, ctx->caps.p3_slots, ctx->caps.md_dense}), 256), 256, 0,
-               ctx->stream>>>(w, g.n_mods);
+  // (the event-local copies of member indices are written with the dense objects)
   k_ev_stat<<<grid_for(w.E, 64), 64, 0, ctx->stream>>>(w, g.n_mods);
-  ctx->launches += 2;
+  ctx->launches += 1;
   mark();
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ctx->h_status, w.status, (ST_N_WORDS + (size_t)w.E * kEvWords) * sizeof(int32_t),

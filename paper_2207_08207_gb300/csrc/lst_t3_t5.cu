@@ -489,6 +489,7 @@ __global__ void k_t5_decide(Ws w, Cst<ff> c) {
 // dense T5 ordered by (inner T3, outer T3), with member MDs, fit results and an anchor cache
 __global__ void k_t5_dense(Ws w) {
   const int n = (int)lst_min64(w.t5_off[w.V], w.cap.t5_dense);
+  const int n_mods = w.V / w.E;
   const int64_t S = w.cap.t5_slots, D = w.cap.t5_dense;
   for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < n; d += gridDim.x * blockDim.x) {
     const int s = w.perm[d];
@@ -500,10 +501,15 @@ __global__ void k_t5_dense(Ws w) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
       w.t5_md[k * D + d] = md[k];
-      w.t5_anc[k * D + d] = make_float4(w.md_x[md[k]], w.md_y[md[k]], w.md_z[md[k]], w.md_r[md[k]]);
+      w.t5_anc[k * D + d] = w.md_xyzr[md[k]];
       ecm |= (uint8_t)(w.md_ec[md[k]] << k);
     }
     w.t5_ecm[d] = ecm;
+    // event-local member indices (the T3 of the event start at the first T3 of its first module)
+    const int vm = w.md_vm[md[0]];
+    const int first_t3 = w.t3_off[vm - vm % n_mods];
+    w.o_t5_a[d] = a - first_t3;
+    w.o_t5_b[d] = b - first_t3;
 #pragma unroll
     for (int f = 0; f < 8; ++f) w.t5_f[f * D + d] = w.t5s_f[f * S + s];
   }
