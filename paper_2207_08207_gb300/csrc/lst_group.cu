@@ -26,11 +26,12 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGrpWarps = 8;   // warps per block of the slot-visiting kernels
 
-// Visit every valid slot of up to 32 modules with all lanes of the warp. eff and b are the
-// lane's module's valid-slot count and slot base (0 on lanes without a module); f(valid, s) is
-// called by all lanes together, once per valid slot s with valid = true.
+// Visit every valid slot of up to 32 modules with all lanes of the warp, two slots per lane at a
+// time so that the work of both (their loads and atomics) is in flight together. eff and b are the
+// lane's module's valid-slot count and slot base (0 on lanes without a module); f(valid_a, s_a,
+// valid_b, s_b) is called by all lanes together, and every valid slot comes once with valid = true.
 template <class F>
-__device__ __forceinline__ void visit_slots(int lane, int eff, int b, F&& f) {
+__device__ __forceinline__ void visit_slots2(int lane, int eff, int b, F&& f) {
   int incl = eff;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -38,18 +39,19 @@ __device__ __forceinline__ void visit_slots(int lane, int eff, int b, F&& f) {
     if (lane >= o) incl += y;
   }
   const int total = __shfl_sync(kFull, incl, 31);
-  for (int i0 = 0; i0 < total; i0 += 32) {
-    const int i = i0 + lane;
-    // the lane whose slot range holds i: the number of lanes whose inclusive end is <= i
-    int j = 0;
+  for (int i0 = 0; i0 < total; i0 += 64) {
+    const int ia = i0 + lane, ib = i0 + 32 + lane;
+    int ja = 0, jb = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
-      const int v = __shfl_sync(kFull, incl, j + step - 1);
-      if (v <= i) j += step;
+      const int va = __shfl_sync(kFull, incl, ja + step - 1);
+      const int vb = __shfl_sync(kFull, incl, jb + step - 1);
+      if (va <= ia) ja += step;
+      if (vb <= ib) jb += step;
     }
-    const int start = __shfl_sync(kFull, incl, j) - __shfl_sync(kFull, eff, j);
-    const int s = __shfl_sync(kFull, b, j) + (i - start);
-    f(i < total, s);
+    const int sa = __shfl_sync(kFull, b, ja) + ia - (__shfl_sync(kFull, incl, ja) - __shfl_sync(kFull, eff, ja));
+    const int sb = __shfl_sync(kFull, b, jb) + ib - (__shfl_sync(kFull, incl, jb) - __shfl_sync(kFull, eff, jb));
+    f(ia < total, sa, ib < total, sb);
   }
 }
 
@@ -103,8 +105,28 @@ __device__ __forceinline__ void visit_task(const Ws& w, const GroupArgs& a, int 
       eff = w.eff[vm + 1] - w.eff[vm] - 1;
       b = a.base[vm];
     }
-    visit_slots(lane, eff, b, f);
+    visit_slots2(lane, eff, b, f);
   }
+}
+
+// warp_agg_slot_keyed for two (pred, key) sets at once, both atomics issued before either result is
+// used
+__device__ __forceinline__ void warp_agg_slot_keyed2(bool pa, int ka, bool pb, int kb, int* counters, int& sa,
+                                                     int& sb) {
+  const int lane = threadIdx.x & 31;
+  const unsigned ma = __ballot_sync(kFull, pa), mb = __ballot_sync(kFull, pb);
+  unsigned ga = 0, gb = 0;
+  if (pa) ga = __match_any_sync(ma, ka);
+  if (pb) gb = __match_any_sync(mb, kb);
+  const int la = pa ? __ffs(ga) - 1 : 0, lb = pb ? __ffs(gb) - 1 : 0;
+  int base_a = 0, base_b = 0;
+  if (pa && lane == la) base_a = atomicAdd(&counters[ka], __popc(ga));
+  if (pb && lane == lb) base_b = atomicAdd(&counters[kb], __popc(gb));
+  base_a = __shfl_sync(kFull, base_a, la);
+  base_b = __shfl_sync(kFull, base_b, lb);
+  const unsigned below = (1u << lane) - 1u;
+  sa = pa ? base_a + __popc(ga & below) : -1;
+  sb = pb ? base_b + __popc(gb & below) : -1;
 }
 
 // Pass 3: after the exclusive scan E[k + 1] is the start of group k; each object takes the next
@@ -114,12 +136,19 @@ __global__ void __launch_bounds__(32 * kGrpWarps) k_grp_place(Ws w, GroupArgs a,
   const int nk = *a.n_keys_dev;
   const int n_tasks = (w.eff[w.V] + chunk - 1) / chunk;   // (of the weights)
   for (int t = blockIdx.x * kGrpWarps + (threadIdx.x >> 5); t < n_tasks; t += gridDim.x * kGrpWarps)
-    visit_task(w, a, t, lane, [&](bool v, int s) {
-      const int k1 = v ? a.key1[s] : 0;
-      const int p = warp_agg_slot_keyed(v, v ? group_of(a, k1, nk) + 1 : 0, E);
-      if (v && p >= 0 && p < a.dense_cap) {
-        w.grp_pos[p] = s;
-        w.grp_key12[p] = make_int2(k1, a.key2[s]);
+    visit_task(w, a, t, lane, [&](bool va, int sa, bool vb, int sb) {
+      const int k1a = va ? a.key1[sa] : 0, k1b = vb ? a.key1[sb] : 0;
+      const int k2a = va ? a.key2[sa] : 0, k2b = vb ? a.key2[sb] : 0;
+      int pa, pb;
+      warp_agg_slot_keyed2(va, va ? group_of(a, k1a, nk) + 1 : 0, vb, vb ? group_of(a, k1b, nk) + 1 : 0, E, pa,
+                           pb);
+      if (va && pa >= 0 && pa < a.dense_cap) {
+        w.grp_pos[pa] = sa;
+        w.grp_key12[pa] = make_int2(k1a, k2a);
+      }
+      if (vb && pb >= 0 && pb < a.dense_cap) {
+        w.grp_pos[pb] = sb;
+        w.grp_key12[pb] = make_int2(k1b, k2b);
       }
     });
 }
