@@ -18,6 +18,8 @@
 // The key-indexed arrays are zeroed and scanned up to the actual key count, read on the device, so
 // that the launches stay shaped by capacities (one CUDA graph serves every batch).
 // The per-module dense offsets are the group offsets of each module's first key.
+#include <cassert>
+
 #include "lst_internal.h"
 
 namespace lst {
@@ -154,12 +156,11 @@ __global__ void __launch_bounds__(32 * kGrpWarps) k_grp_place(Ws w, GroupArgs a,
 }
 
 // Pass 4: the rank of each placed object inside its group by (second member, slot), which gives its
-// dense position; the permutation (or, for LS, the dense objects themselves) is written there, with
+// dense position; the permutation (or, for LS and T3, the dense objects themselves) is written there, with
 // the per-module dense offsets and the dense-overflow word. A block ranks a
 // tile of kRankTile positions with the (slot, second member) of the tile and kRankHalo positions on
 // each side in shared memory; groups reaching further (none at the sizes seen) read memory.
 constexpr int kRankTile = 256, kRankHalo = 64;
-enum { kOutPerm = 0, kOutLs = 1 };   // what the rank pass writes: the permutation, or the dense LS
 
 template <int OUT>
 __global__ void __launch_bounds__(kRankTile) k_grp_rank(Ws w, GroupArgs a, const int32_t* E) {
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(kRankTile) k_grp_rank(Ws w, GroupArgs a, const
       }
       d = g_beg + r;
     }
-    if (OUT == kOutLs) ls_dense_write(w, valid, d, s, k1, k2, E, n);
+    if (OUT == kDenseLs) ls_dense_write(w, valid, d, s, k1, k2, E, n);
+    else if (OUT == kDenseT3) t3_dense_write(w, valid, d, s, k1, k2, E, n);
     else if (valid) w.perm[d] = s;
     __syncthreads();
   }
@@ -233,6 +235,7 @@ __global__ void k_grp_clamp(Ws w, int32_t* E, GroupArgs a) {
 }  // namespace
 
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
+  assert(a.dense_out == kDensePerm || a.dense_out == kDenseLs || a.dense_out == kDenseT3);
   int32_t* E = a.grp_off ? a.grp_off : w.grp_key;
   // objects per warp task: about two tasks per resident warp at the stage's dense capacity
   const int64_t resident_warps = (int64_t)L.n_sm * 64;
@@ -248,8 +251,9 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
   scan_exclusive_dev(E, E, a.n_keys + 1, a.n_keys_dev, 1, w.scan_tmp, L);
   k_grp_place<<<blocks, 32 * kGrpWarps, 0, L.stream>>>(w, a, E, chunk);
   LST_LAUNCH(L);
-  if (a.dense_ls) k_grp_rank<kOutLs><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
-  else k_grp_rank<kOutPerm><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
+  if (a.dense_out == kDenseLs) k_grp_rank<kDenseLs><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
+  else if (a.dense_out == kDenseT3) k_grp_rank<kDenseT3><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
+  else k_grp_rank<kDensePerm><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
   LST_LAUNCH(L);
   if (a.grp_off) {
     k_grp_clamp<<<key_blocks, 256, 0, L.stream>>>(w, E, a);

@@ -723,7 +723,7 @@ void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_BEGIN(L, K_MD_COMPACT);
   GroupArgs ga{w.md_cnt, w.md_cap, w.md_base, w.cap.md_slots, ST_OVF_MD, ST_ARENA_MD, w.ms_lo, w.ms_up,
                nullptr, nullptr, w.cap.H, &w.ev_hit_off[w.E], w.cap.md_dense, ST_DENSE_MD,
-               w.md_off, w.sens_off, 2};
+               w.md_off, w.sens_off, 2, kDensePerm};
   group_slots(w, ga, L);
   k_md_dense<<<grid_for(w.cap.md_dense, 256), 256, 0, L.stream>>>(w, g, c.f);
   KT_END(L, K_MD_COMPACT);
@@ -759,7 +759,7 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_BEGIN(L, K_LS_COMPACT);
   GroupArgs ga{w.ls_cnt, w.ls_cap, w.ls_base, w.cap.ls_slots, ST_OVF_LS, ST_ARENA_LS, w.lss_in, w.lss_out,
                nullptr, w.lsin_off, w.cap.md_dense, &w.md_off[w.V], w.cap.ls_dense, ST_DENSE_LS,
-               w.ls_off, w.md_off, 1, true};
+               w.ls_off, w.md_off, 1, kDenseLs};
   group_slots(w, ga, L);
   KT_END(L, K_LS_COMPACT);
 }

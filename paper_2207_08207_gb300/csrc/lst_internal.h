@@ -246,8 +246,12 @@ struct GroupArgs {
   int32_t* mod_off;                  // [V + 1] out: per-module dense offsets
   const int32_t* mod_first;          // first key of each module, at [vm * stride]
   int mod_first_stride;
-  bool dense_ls = false;             // write the dense LS arrays directly (ls_dense_write)
+  int dense_out = -1;                // what the rank pass writes (kDensePerm / kDenseLs / kDenseT3)
 };
+// kDensePerm: the permutation (perm[dense position] = slot; the stage's own kernel gathers the
+// dense arrays); kDenseLs / kDenseT3: the dense LS / T3 arrays themselves (ls_dense_write,
+// t3_dense_write)
+enum { kDensePerm = 0, kDenseLs = 1, kDenseT3 = 2 };
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L);
 
 
@@ -337,6 +341,46 @@ __device__ __forceinline__ void ls_dense_write(const Ws& w, bool valid, int d, i
     w.o_ls_out[d] = b - first_md;
   }
   warp_add_keyed(w.t3_bound, vm, outs);
+}
+
+// The dense T3 at position d (ordered by first MD, then (inner LS a, outer LS b)) from slot s:
+// members (global and event-local), member MDs, fit values, an anchor cache for the pT3 stage, and
+// each T3's count of outer partners (the T5 candidates it starts, from the T3-by-first-MD offsets
+// t3md_off) summed per module for the T5 capacities. All lanes of the warp call it; n is the number
+// of dense T3.
+__device__ __forceinline__ void t3_dense_write(const Ws& w, bool valid, int d, int s, int a, int b,
+                                               const int32_t* t3md_off, int n) {
+  int vm = 0;
+  unsigned outs = 0;
+  if (valid) {
+    const int64_t T = w.cap.t3_dense;
+    w.t3_a[d] = a;
+    w.t3_b[d] = b;
+    const int md[3] = {w.ls_in[a], w.ls_out[a], w.ls_out[b]};
+    w.t3_md0[d] = md[0];
+    w.t3_md1[d] = md[1];
+    w.t3_md2[d] = md[2];
+    w.t3_R[d] = w.t3s_R[s];
+    w.t3_xc[d] = w.t3s_xc[s];
+    w.t3_yc[d] = w.t3s_yc[s];
+    w.t3_chi2[d] = w.t3s_chi2[s];
+    w.t3_pte[d] = w.t3s_pte[s];
+    uint8_t ecm = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      w.t3_anc[k * T + d] = w.md_xyzr[md[k]];
+      ecm |= (uint8_t)(w.md_ec[md[k]] << k);
+    }
+    w.t3_ecm[d] = ecm;
+    vm = w.md_vm[md[0]];
+    outs = (unsigned)(min(t3md_off[md[2] + 1], n) - min(t3md_off[md[2]], n));
+    // event-local member indices (the LS of the event start at the first LS of its first module)
+    const int n_mods = w.V / w.E;
+    const int first_ls = w.ls_off[vm - vm % n_mods];
+    w.o_t3_a[d] = a - first_ls;
+    w.o_t3_b[d] = b - first_ls;
+  }
+  warp_add_keyed(w.t5_bound, vm, outs);
 }
 
 inline int grid_for(int64_t n, int block, int max_blocks = 152 * 32) {

@@ -245,48 +245,6 @@ __global__ void k_t3_caps(Ws w) {
   }
 }
 
-// dense T3 ordered by (inner LS, outer LS), with member MDs, an anchor cache for the pT3 stage, and
-// each T3's count of outer partners (the T5 candidates it starts) summed per module
-__global__ void k_t3_dense(Ws w) {
-  const int n = (int)lst_min64(w.t3_off[w.V], w.cap.t3_dense);
-  const int n_mods = w.V / w.E;
-  const int64_t T = w.cap.t3_dense;
-  for (int d0 = blockIdx.x * blockDim.x; d0 < n; d0 += gridDim.x * blockDim.x) {
-    const int d = d0 + threadIdx.x;
-    int vm = 0;
-    unsigned outs = 0;
-    if (d < n) {
-      const int s = w.perm[d];
-      const int a = w.t3s_a[s], b = w.t3s_b[s];
-      w.t3_a[d] = a;
-      w.t3_b[d] = b;
-      const int md[3] = {w.ls_in[a], w.ls_out[a], w.ls_out[b]};
-      w.t3_md0[d] = md[0];
-      w.t3_md1[d] = md[1];
-      w.t3_md2[d] = md[2];
-      w.t3_R[d] = w.t3s_R[s];
-      w.t3_xc[d] = w.t3s_xc[s];
-      w.t3_yc[d] = w.t3s_yc[s];
-      w.t3_chi2[d] = w.t3s_chi2[s];
-      w.t3_pte[d] = w.t3s_pte[s];
-      uint8_t ecm = 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        w.t3_anc[k * T + d] = w.md_xyzr[md[k]];
-        ecm |= (uint8_t)(w.md_ec[md[k]] << k);
-      }
-      w.t3_ecm[d] = ecm;
-      vm = w.md_vm[md[0]];
-      outs = (unsigned)(min(w.t3md_off[md[2] + 1], n) - min(w.t3md_off[md[2]], n));
-      // event-local member indices (the LS of the event start at the first LS of its first module)
-      const int first_ls = w.ls_off[vm - vm % n_mods];
-      w.o_t3_a[d] = a - first_ls;
-      w.o_t3_b[d] = b - first_ls;
-    }
-    warp_add_keyed(w.t5_bound, vm, outs);
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
 // Karimaki's circle fit (V. Karimaki, NIM A305 (1991) 187) with equal weights.
 // Circle: 1/2 rho (x^2 + y^2) - (1 + rho d)(x sin phi - y cos phi) + 1/2 rho d^2 + d = 0;
@@ -533,13 +491,11 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   KT_BEGIN(L, K_T3_COMPACT);
   GroupArgs ga{w.t3_cnt, w.t3_cap, w.t3_base, w.cap.t3_slots, ST_OVF_T3, ST_ARENA_T3, w.t3s_a, w.t3s_b,
                w.ls_in, w.t3md_off, w.cap.md_dense, &w.md_off[w.V], w.cap.t3_dense, ST_DENSE_T3,
-               w.t3_off, w.md_off, 1};
+               w.t3_off, w.md_off, 1, kDenseT3};
   // T3 grouped by their first MD (the inner MD of their inner LS; LS are ordered by inner MD, so the
   // (inner LS, outer LS) order is kept inside each group): the group offsets are the T3-by-first-MD
   // adjacency that the T5 stage reads
-  group_slots(w, ga, L);
-  k_t3_dense<<<grid_for(w.cap.t3_dense, 256), 256, 0, L.stream>>>(w);
-  LST_LAUNCH(L);
+  group_slots(w, ga, L);   // (writes the dense T3: t3_dense_write)
   KT_END(L, K_T3_COMPACT);
 }
 
@@ -558,7 +514,7 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   GroupArgs ga{w.t5_cnt, w.t5_cap, w.t5_base, w.cap.t5_slots, ST_OVF_T5, ST_ARENA_T5, w.t5s_a, w.t5s_b,
                nullptr, nullptr, w.cap.t3_dense, &w.t3_off[w.V], w.cap.t5_dense, ST_DENSE_T5,
-               w.t5_off, w.t3_off, 1};
+               w.t5_off, w.t3_off, 1, kDensePerm};
   group_slots(w, ga, L);
   k_t5_dense<<<grid_for(w.cap.t5_dense, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
