@@ -67,6 +67,35 @@ __device__ __forceinline__ void bin_gather(Ws& w, int pos, int src, int h0) {
   w.borig[pos] = src - h0;
 }
 
+// the grouped path for sensors of at most kBinG * T hits: lane `sub` of the sensor's group holds
+// hits sub, sub + kBinG, ... and ranks them by the group's input indices
+template <int T>
+__device__ __forceinline__ void bin_rank_gather(Ws& w, int a, int n, int sub, int vs, bool valid, int n_sens) {
+  const int h0 = valid ? w.ev_hit_off[vs / n_sens] : 0;
+  int v[T], rk[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int idx = sub + kBinG * t;
+    v[t] = idx < n ? w.bidx[a + idx] : 0x7fffffff;
+    rk[t] = 0;
+  }
+#pragma unroll
+  for (int t2 = 0; t2 < T; ++t2) {
+#pragma unroll
+    for (int s2 = 0; s2 < kBinG; ++s2) {
+      const int vj = __shfl_sync(0xffffffffu, v[t2], s2, kBinG);
+#pragma unroll
+      for (int t = 0; t < T; ++t) rk[t] += vj < v[t];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int idx = sub + kBinG * t;
+    if (idx < n) bin_gather(w, a + rk[t], v[t], h0);
+  }
+}
+
 __global__ void k_bin_sort_gather(Ws w, int n_sens) {
   const int lane = threadIdx.x & 31;
   const int tile = lane / kBinG, sub = lane % kBinG;
@@ -81,32 +110,17 @@ __global__ void k_bin_sort_gather(Ws w, int n_sens) {
     for (int o = 16; o >= 1; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
     if (nmax == 0) continue;
     if (nmax <= kBinG * kBinPer) {
-      const int h0 = valid ? w.ev_hit_off[vs / n_sens] : 0;
-      const int T = (nmax + kBinG - 1) / kBinG;
-      int v[kBinPer], rk[kBinPer];
-#pragma unroll
-      for (int t = 0; t < kBinPer; ++t) {
-        const int idx = sub + kBinG * t;
-        v[t] = idx < n ? w.bidx[a + idx] : 0x7fffffff;
-        rk[t] = 0;
-      }
-#pragma unroll
-      for (int t2 = 0; t2 < kBinPer; ++t2) {
-        if (t2 < T) {
-#pragma unroll
-          for (int s2 = 0; s2 < kBinG; ++s2) {
-            const int vj = __shfl_sync(0xffffffffu, v[t2], s2, kBinG);
-#pragma unroll
-            for (int t = 0; t < kBinPer; ++t)
-              if (t < T) rk[t] += vj < v[t];
-          }
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < kBinPer; ++t) {
-        const int idx = sub + kBinG * t;
-        if (idx < n) bin_gather(w, a + rk[t], v[t], h0);
+      // T = hits per lane, uniform over the warp: the rank loops are unrolled for each T, so that a
+      // warp of small sensors (most hold a few hits) runs only the comparisons it needs
+      switch ((nmax + kBinG - 1) / kBinG) {
+        case 1: bin_rank_gather<1>(w, a, n, sub, vs, valid, n_sens); break;
+        case 2: bin_rank_gather<2>(w, a, n, sub, vs, valid, n_sens); break;
+        case 3: bin_rank_gather<3>(w, a, n, sub, vs, valid, n_sens); break;
+        case 4: bin_rank_gather<4>(w, a, n, sub, vs, valid, n_sens); break;
+        case 5: bin_rank_gather<5>(w, a, n, sub, vs, valid, n_sens); break;
+        case 6: bin_rank_gather<6>(w, a, n, sub, vs, valid, n_sens); break;
+        case 7: bin_rank_gather<7>(w, a, n, sub, vs, valid, n_sens); break;
+        default: bin_rank_gather<8>(w, a, n, sub, vs, valid, n_sens); break;
       }
       continue;
     }
