@@ -247,42 +247,75 @@ __device__ __forceinline__ void md_flush(const Ws& w, const Geo& g, const Cst<fl
   if (q >= 0 && q < w.cap.q_md) w.q_md[q] = make_int4(vm, l, u, 0);
 }
 
-// MD candidates: every (lower hit, upper hit) pair of each module, a warp per module (modules taken
-// in a grid-stride loop, which spreads the busy inner-layer modules over the warps); pairs that
-// pass the quick window test go to a per-warp queue that carries over from module to module and is
-// evaluated fully 32 pairs at a time.
+// MD candidates: every (lower hit, upper hit) pair of each module. A warp takes G modules at a time
+// (G = 1..32, chosen at launch so that the resident warps stay busy), one per lane, spread over the
+// whole range (module vm = sweep * G W + lane * W + warp for W warps, which spreads the busy
+// inner-layer modules over the warps); a warp scan of their pair counts turns their pairs into one
+// index range, and each lane finds its pair's module by a shuffle search, so a warp's lanes stay
+// busy however few hits a module holds. Pairs that pass the quick window test
+// go to a per-warp queue that carries over and is evaluated fully 32 pairs at a time.
 constexpr int kMdWarps = 8;
 constexpr int kMdQ = 64;
 
-__global__ void __launch_bounds__(32 * kMdWarps) k_md(Ws w, Geo g, Cst<float> c) {
+__global__ void __launch_bounds__(32 * kMdWarps) k_md(Ws w, Geo g, Cst<float> c, int G) {
   __shared__ int4 qbuf[kMdWarps][kMdQ];
   int4* qe = qbuf[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const float gmax = (1.0f + 1e-5f) / sqrtf((1.0f - c.sin_max) * (1.0f + c.sin_max));
   int qn = 0;
   const long long t0 = clock64();
-  for (int vm = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vm < w.V; vm += nwarps) {
+  for (int64_t sweep = 0; sweep * G * nwarps < w.V; ++sweep) {
     if (warp_over_budget(w, t0)) break;
-    const int lo0 = w.sens_off[2 * vm], up0 = w.sens_off[2 * vm + 1];
-    const int nup = w.sens_off[2 * vm + 2] - up0;
-    const int np = (up0 - lo0) * nup;
-    if (np == 0) continue;
-    const int m = vm % g.n_mods;
-    const bool ec = g.endcap[m] != 0;
-    const float delta = g.spacing[m];
-    for (int p0 = 0; p0 < np; p0 += 32) {
+    const int64_t vm64 = sweep * G * nwarps + (int64_t)lane * nwarps + gw;
+    const int vm = (int)vm64;
+    int lo0 = 0, up0 = 0, nup = 0, np = 0;
+    bool ec = false;
+    float delta = 0.f;
+    if (lane < G && vm64 < w.V) {
+      lo0 = w.sens_off[2 * vm];
+      up0 = w.sens_off[2 * vm + 1];
+      nup = w.sens_off[2 * vm + 2] - up0;
+      np = (up0 - lo0) * nup;
+      if (np > 0) {
+        const int m = vm % g.n_mods;
+        ec = g.endcap[m] != 0;
+        delta = g.spacing[m];
+      }
+    }
+    int incl = np;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - np;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int p0 = 0; p0 < total; p0 += 32) {
       const int p = p0 + lane;
+      int j = 0;   // the lane whose module holds pair p: the last lane with excl <= p
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = j + step;
+        if (__shfl_sync(0xffffffffu, excl, cand) <= p) j = cand;
+      }
+      const int pj = p - __shfl_sync(0xffffffffu, excl, j);
+      const int nupj = __shfl_sync(0xffffffffu, nup, j);
+      const int lo0j = __shfl_sync(0xffffffffu, lo0, j), up0j = __shfl_sync(0xffffffffu, up0, j);
+      const bool ecj = __shfl_sync(0xffffffffu, (int)ec, j) != 0;
+      const float deltaj = __shfl_sync(0xffffffffu, delta, j);
+      const int vmj = __shfl_sync(0xffffffffu, vm, j);
       bool keep = false;
       int l = 0, u = 0;
-      if (p < np) {
-        const int il = p / nup;
-        l = lo0 + il;
-        u = up0 + (p - il * nup);
-        keep = !md_quick_reject(c, ec, delta, gmax, w.bx[l], w.by[l], w.bz[l], w.bx[u], w.by[u], w.bz[u]);
+      if (p < total) {
+        const int il = pj / nupj;
+        l = lo0j + il;
+        u = up0j + (pj - il * nupj);
+        keep = !md_quick_reject(c, ecj, deltaj, gmax, w.bx[l], w.by[l], w.bz[l], w.bx[u], w.by[u], w.bz[u]);
       }
       const unsigned km = __ballot_sync(0xffffffffu, keep);
-      if (keep) qe[qn + __popc(km & ((1u << lane) - 1u))] = make_int4(vm, l, u, 0);
+      if (keep) qe[qn + __popc(km & ((1u << lane) - 1u))] = make_int4(vmj, l, u, 0);
       qn += __popc(km);
       if (qn >= 32) {
         __syncwarp();
@@ -729,7 +762,13 @@ void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.md_base, w.md_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_MD);
-  k_md<<<grid_for((int64_t)w.V * 32, 32 * kMdWarps, 152 * 16), 32 * kMdWarps, 0, L.stream>>>(w, g, c.f);
+  {
+    const int64_t resident_warps = (int64_t)L.n_sm * 8 * kMdWarps;
+    int G = 1;   // modules per warp and sweep: about two sweeps over the resident warps
+    while (G < 32 && (int64_t)G * 2 * resident_warps * 2 <= w.V) G *= 2;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((w.V / G + kMdWarps - 1) / kMdWarps, L.n_sm * 8));
+    k_md<<<blocks, 32 * kMdWarps, 0, L.stream>>>(w, g, c.f, G);
+  }
   KT_END(L, K_MD);
   LST_LAUNCH(L);
   k_md_recheck<<<grid_for(w.cap.q_md, 128, 152 * 4), 128, 0, L.stream>>>(w, g, c.d);
