@@ -370,22 +370,22 @@ def exported_symbols():
 
 # Per-event instruction and DRAM counts of the timed kernels on PU200 events: ncu (smsp__inst_executed;
 # DRAM bytes = dram__bytes_read + dram__bytes_write, or the section's DRAM rate x duration) of one
-# launch on a batch of 16 events, divided by 16 (the captures summarised in
-# profiles/kernel_metrics_pu200_batch16.md and profiles/hot_kernels_pu200_batch16.md); used for the
-# issue-slot roofline of the dominant kernel. An entry is removed when its kernel changes.
+# launch on a batch of 16 events, divided by 16 (the capture summarised in
+# profiles/kernel_metrics_pu200_batch16.md); used for the issue-slot roofline of the dominant
+# kernel. An entry is removed when its kernel changes.
 _PROF_MET = "profiles/kernel_metrics_pu200_batch16.md"
-_PROF_HOT = "profiles/hot_kernels_pu200_batch16.md"
 KERNEL_PROFILE = {
-    "ls": {"warp_inst_per_event": 274011210 / 16, "dram_bytes_per_event": 68359680 / 16, "source": _PROF_HOT},
-    "t3_pre": {"warp_inst_per_event": 144089538 / 16, "dram_bytes_per_event": 81534976 / 16, "source": _PROF_HOT},
-    "pt3_pre": {"warp_inst_per_event": 149792024 / 16, "dram_bytes_per_event": 44718848 / 16, "source": _PROF_HOT},
-    "pt5_pre": {"warp_inst_per_event": 81948186 / 16, "dram_bytes_per_event": 19770624 / 16, "source": _PROF_HOT},
-    "md": {"warp_inst_per_event": 68216449 / 16, "dram_bytes_per_event": (24448512 + 7280896) / 16,
+    "ls": {"warp_inst_per_event": 277429392 / 16, "dram_bytes_per_event": (28499968 + 17012224) / 16,
            "source": _PROF_MET},
-    "t5_clean": {"warp_inst_per_event": 57343849 / 16, "dram_bytes_per_event": (17619968 + 1899264) / 16,
+    "t3_pre": {"warp_inst_per_event": 144089538 / 16, "dram_bytes_per_event": (76945152 + 1118976) / 16,
+               "source": _PROF_MET},
+    "pt3_pre": {"warp_inst_per_event": 140172934 / 16, "dram_bytes_per_event": (44587520 + 38912) / 16,
+                "source": _PROF_MET},
+    "pt5_pre": {"warp_inst_per_event": 73522178 / 16, "dram_bytes_per_event": 20154368 / 16, "source": _PROF_MET},
+    "md": {"warp_inst_per_event": 56914619 / 16, "dram_bytes_per_event": (29822720 + 8168448) / 16,
+           "source": _PROF_MET},
+    "t5_clean": {"warp_inst_per_event": 32108575 / 16, "dram_bytes_per_event": (17908992 + 2072320) / 16,
                  "source": _PROF_MET},
-    "tc_assemble": {"warp_inst_per_event": 23378912 / 16, "dram_bytes_per_event": (25655808 + 11264) / 16,
-                    "source": _PROF_MET},
 }
 
 
