@@ -403,8 +403,9 @@ constexpr int kMaxTargets = 256;   // module-map degree limit (checked when load
 
 __device__ __forceinline__ int md_count(const Ws& w, int vm) { return w.md_off[vm + 1] - w.md_off[vm]; }
 
-// LS capacity of each module (exact bound: its MDs x the MDs of its connected modules) and its
-// cost bucket floor(log2(bound)) for the persistent kernel's work list
+// LS capacity of each module (exact bound: its MDs x the MDs of its connected modules), its number
+// of work items (chunks of its outer MDs: ceil(outer MDs / ls_chunk), at most kLsMaxChunks) and
+// their cost bucket floor(log2(pairs per chunk)) for the persistent kernel's work list
 __global__ void k_ls_caps(Ws w, Geo g) {
   zero_group_counts(w.lsin_off, w.md_off[w.V]);   // LS are grouped by inner MD
   __shared__ int hist[32];
@@ -421,13 +422,16 @@ __global__ void k_ls_caps(Ws w, Geo g) {
     const int cc = clamp_cap(pred, bound, w.ls_ovr[vm]);
     w.ls_cap[vm] = cc;
     w.ls_base[vm] = cc;
-    int b = -1;
+    int b = -1, nch = 0;
     if (bound > 0) {
-      b = 63 - __clzll((unsigned long long)bound);
+      nch = (int)lst_min64((nb + w.ls_chunk - 1) / w.ls_chunk, kLsMaxChunks);
+      const long long per = na * ((nb + nch - 1) / nch);
+      b = 63 - __clzll((unsigned long long)per);
       if (b > 31) b = 31;
-      atomicAdd(&hist[b], 1);
+      atomicAdd(&hist[b], nch);
     }
     w.work_bucket[vm] = b;
+    w.work_nch[vm] = nch;
   }
   __syncthreads();
   if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&w.work_cnt[threadIdx.x], hist[threadIdx.x]);
@@ -448,18 +452,34 @@ __global__ void k_ls_work_scan(Ws w) {
 __global__ void k_ls_work_fill(Ws w) {
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm - (int)(threadIdx.x & 31) < w.V;
        vm += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
     const int b = vm < w.V ? w.work_bucket[vm] : -1;
-    // one atomic per bucket and warp: lanes with the same bucket share it
+    const int nch = b >= 0 ? w.work_nch[vm] : 0;
+    // one atomic per bucket and warp: lanes with the same bucket share it; a lane's items follow
+    // those of the lower lanes of its bucket
     const unsigned grp = __match_any_sync(0xffffffffu, b);
     const int leader = __ffs(grp) - 1;
+    int pre = 0;
+    for (int j = 0; j < 32; ++j) {
+      const int v = __shfl_sync(0xffffffffu, nch, j);
+      if (j < lane && ((grp >> j) & 1u)) pre += v;
+    }
+    const int sum = __reduce_add_sync(grp, nch);
     int base = 0;
-    if (b >= 0 && (int)(threadIdx.x & 31) == leader) base = atomicAdd(&w.work_cur[b], __popc(grp));
+    if (b >= 0 && lane == leader) base = atomicAdd(&w.work_cur[b], sum);
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (b >= 0) w.work[w.work_off[b] + base + __popc(grp & ((1u << (threadIdx.x & 31)) - 1u))] = vm;
+    if (b >= 0)
+      for (int k = 0; k < nch; ++k) {
+        const int at = w.work_off[b] + base + pre + k;
+        w.work[at] = vm;
+        w.work_c[at] = k;
+      }
   }
 }
 
-// One warp per module at a time. Each lane holds one MD of the connected modules (B) in registers
+// One warp per work item at a time: a module, or, in small batches, one of up to kLsMaxChunks equal
+// chunks of a heavy module's outer MDs (so that one module does not hold the whole launch). Each
+// lane holds one MD of the connected modules (B) in registers
 // and sweeps the module's own MDs (A, staged in shared memory): a conservative division-free test
 // (below) rejects most pairs, and the survivors go to a per-warp queue that carries over from module
 // to module; whenever it holds 32 pairs, every lane takes one of them through the full evaluation, so
@@ -555,6 +575,8 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
     const int item = sweep * n_warps + ((sweep & 1) ? n_warps - 1 - gw : gw);
     if (item >= n_items) continue;
     const int vm = persistent ? w.work[item] : item;
+    const int chunk = persistent ? w.work_c[item] : 0;
+    const int nch = persistent ? w.work_nch[vm] : 1;
     const int na = md_count(w, vm);
     if (na == 0) continue;
     const int m = vm % g.n_mods, e0 = vm - m;
@@ -582,7 +604,10 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
     }
     if (lane == 0) S.tpre[0] = 0;
     const int totB = run;
-    if (totB == 0) {
+    // this item's outer MDs: chunk `chunk` of the module's nch equal chunks
+    const int csz = (totB + nch - 1) / max(nch, 1);
+    const int jbeg = chunk * csz, jend = min(totB, jbeg + csz);
+    if (jend <= jbeg) {
       __syncwarp();
       continue;
     }
@@ -599,9 +624,9 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
         S.a_id[lane] = d;
       }
       __syncwarp();
-      for (int j0 = 0; j0 < totB; j0 += 32) {
+      for (int j0 = jbeg; j0 < jend; j0 += 32) {
         const int j = j0 + lane;
-        const bool has_b = j < totB;
+        const bool has_b = j < jend;
         float x2 = 0.f, y2 = 0.f, z2 = 0.f, r2 = 1.f, s2 = 1.f, al2 = 0.f, sz2 = 0.f, sr2 = 0.f;
         int bid = 0;
         if (has_b) {

@@ -177,9 +177,12 @@ struct Ws {
   int32_t* status = nullptr;   // [ST_N_WORDS]
   int32_t* ev_stat = nullptr;  // [E][kEvWords]
   // persistent LS kernel: modules ordered by descending predicted cost (log2 buckets)
-  int32_t* work = nullptr;        // [V] module list
-  int32_t* work_bucket = nullptr; // [V] cost bucket of each module (-1: no candidates)
-  int32_t* work_cnt = nullptr;    // [32] modules per bucket
+  int32_t* work = nullptr;        // [kLsMaxChunks V] work items: module
+  int32_t* work_c = nullptr;      // [kLsMaxChunks V] work items: chunk of the module's outer MDs
+  int32_t* work_bucket = nullptr; // [V] cost bucket of each module's chunks (-1: no candidates)
+  int32_t* work_nch = nullptr;    // [V] chunks of each module
+  int ls_chunk = 1 << 30;         // outer MDs per chunk of a module's LS work (small batches split)
+  int32_t* work_cnt = nullptr;    // [32] items per bucket
   int32_t* work_cur = nullptr;    // [32]
   int32_t* work_off = nullptr;    // [33]
 };
@@ -204,6 +207,7 @@ struct Launch {
   int* scan_idx = nullptr;                    // host: next scan index of the chain being enqueued
 };
 constexpr int kScanMax = 64;   // single-pass scans per chain run at most
+constexpr int kLsMaxChunks = 8;   // LS work items per module at most
 
 // kernels timed individually when timing is enabled (index order of lst_get_kernel_ms)
 enum KernelId : int {

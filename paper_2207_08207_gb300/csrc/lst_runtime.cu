@@ -381,7 +381,8 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.grp_pos, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
   pl.add(w.grp_key12, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
   pl.add(w.grp_task, (std::max({c.md_slots, c.ls_slots, c.t3_slots, c.t5_slots}) + V) / 64 + 2);
-  pl.add(w.work, V); pl.add(w.work_bucket, V); pl.add(w.work_off, 33);
+  pl.add(w.work, kLsMaxChunks * V); pl.add(w.work_c, kLsMaxChunks * V); pl.add(w.work_bucket, V);
+  pl.add(w.work_nch, V); pl.add(w.work_off, 33);
   pl.add(w.perm, std::max({c.md_dense, c.ls_dense, c.t3_dense, c.t5_dense}));
   // MD
   pl.add(w.md_cap, V); pl.add(w.md_base, V + 1); pl.add(w.md_off, V + 1);
@@ -482,6 +483,9 @@ int enqueue_chain(lst_ctx* ctx) {
   w.V = w.E * ctx->geo.n_mods;
   w.S = 2 * w.V;
   w.cap_scale = ctx->cfg.cap_scale;
+  // a small batch has too few modules to balance the LS kernel's warps: its heavy modules are split
+  // into chunks of outer MDs (for 64 events the whole-module items already balance)
+  w.ls_chunk = w.E < 8 ? 64 : (1 << 30);
   w.cycle_budget = ctx->cfg.cycle_budget;
   Launch L = make_launch(ctx);
   int scan_idx = 0;
@@ -595,7 +599,7 @@ void lst_config_default(lst_config* c) {
   c->pls_pt_err = 0.01f;
   c->sigma_floor = 1.0e-4f;
   c->t5_overlap_hits = 7;
-  c->persistent = 0;
+  c->persistent = 1;
   c->use_graph = 0;
   c->block_ls = 128;
   c->warps_px = 4;
