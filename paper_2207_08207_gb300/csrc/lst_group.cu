@@ -245,9 +245,11 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
   const int key_blocks = grid_for(a.n_keys + 1, 256, L.n_sm * 8);
   k_grp_eff<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, a);
   LST_LAUNCH(L);
-  scan_exclusive(w.eff, w.eff, w.V, w.scan_tmp, L);
-  k_grp_tasks<<<grid_for((a.slots + w.V) / chunk + 2, 256), 256, 0, L.stream>>>(w, chunk);
-  LST_LAUNCH(L);
+  if (!scan_tasks(w.eff, w.V, w.grp_task, chunk, L)) {
+    scan_exclusive(w.eff, w.eff, w.V, w.scan_tmp, L);
+    k_grp_tasks<<<grid_for((a.slots + w.V) / chunk + 2, 256), 256, 0, L.stream>>>(w, chunk);
+    LST_LAUNCH(L);
+  }
   scan_exclusive_dev(E, E, a.n_keys + 1, a.n_keys_dev, 1, w.scan_tmp, L);
   k_grp_place<<<blocks, 32 * kGrpWarps, 0, L.stream>>>(w, a, E, chunk);
   LST_LAUNCH(L);

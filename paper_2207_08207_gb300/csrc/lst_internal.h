@@ -226,6 +226,11 @@ int ls_resident_blocks(int block);
 
 // scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);
+// In-place single-pass scan of n positive weights that also writes the compaction task starts:
+// first[t] = the first k whose prefix is >= t * chunk, for t up to ceil(total / chunk) (that one = n).
+// Only inside a chain run (single-pass scans); returns false when it cannot run (the caller then
+// scans and searches separately).
+bool scan_tasks(int32_t* data, int64_t n, int32_t* first, int chunk, const Launch& L);
 // the same with the entry count min(n, *n_dev + n_add) read on the device (n sizes the launch);
 // out[count] receives the total
 void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_t* n_dev, int n_add, int32_t* tmp,

@@ -110,10 +110,32 @@ __device__ __forceinline__ unsigned long long scan_word(unsigned epoch, unsigned
   return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | (unsigned)v;
 }
 
+// What a scan does with each element's exclusive prefix besides storing it.
+struct NoEpilogue {
+  __device__ void element(int64_t, int, int) const {}
+  __device__ void finish(int64_t, int) const {}
+};
+
+// Compaction tasks from the scan of per-module weights: task t starts at the first module whose
+// prefix is >= t * chunk; an element k with prefix [excl, excl + v) starts the tasks whose t * chunk
+// lies in (excl, excl + v] at module k + 1 (task 0 starts at module 0). finish() closes the last
+// task at module n.
+struct TaskEpilogue {
+  int32_t* first;
+  int chunk;
+  __device__ void element(int64_t k, int excl, int v) const {
+    for (int64_t t = (int64_t)excl / chunk + 1; t * chunk <= (int64_t)excl + v; ++t) first[t] = (int)(k + 1);
+    if (k == 0) first[0] = 0;
+  }
+  __device__ void finish(int64_t n, int total) const { first[(total + chunk - 1) / chunk] = (int)n; }
+};
+
+template <class Epi>
 __global__ void __launch_bounds__(kScanBlock) k_scan_1pass(const int32_t* in, int32_t* out, int64_t n_max,
                                                            const int32_t* n_dev, int n_add,
                                                            unsigned long long* state, int32_t* ticket,
-                                                           const int32_t* run, int scan_idx, int32_t* err) {
+                                                           const int32_t* run, int scan_idx, int32_t* err,
+                                                           Epi epi) {
   __shared__ int s_tile, s_excl;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1);
   __syncthreads();
@@ -165,10 +187,16 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_1pass(const int32_t* in, in
   pre += s_excl;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < n) out[base + k] = pre;
+    if (base + k < n) {
+      out[base + k] = pre;
+      epi.element(base + k, pre, v[k]);
+    }
     pre += v[k];
   }
-  if (tile == last && threadIdx.x == 0) out[n] = s_excl + total;
+  if (tile == last && threadIdx.x == 0) {
+    out[n] = s_excl + total;
+    epi.finish(n, s_excl + total);
+  }
 }
 
 }  // namespace
@@ -181,7 +209,7 @@ void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_
   if (L.scan_state && *L.scan_idx < kScanMax) {
     const int idx = (*L.scan_idx)++;
     k_scan_1pass<<<(unsigned)std::max<int64_t>(tiles, 1), kScanBlock, 0, L.stream>>>(
-        in, out, n, n_dev, n_add, L.scan_state, L.scan_ctr + idx, L.scan_run, idx, L.scan_err);
+        in, out, n, n_dev, n_add, L.scan_state, L.scan_ctr + idx, L.scan_run, idx, L.scan_err, NoEpilogue{});
     LST_LAUNCH(L);
     return;
   }
@@ -194,6 +222,17 @@ void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_
   k_scan_sums<<<1, kScanBlock, 0, L.stream>>>(tmp, tiles, out, n, n_dev, n_add);
   k_scan_add<<<(unsigned)tiles, kScanBlock, 0, L.stream>>>(out, n, tmp, n_dev, n_add);
   *L.launches += 3;
+}
+
+bool scan_tasks(int32_t* data, int64_t n, int32_t* first, int chunk, const Launch& L) {
+  if (!L.scan_state || *L.scan_idx >= kScanMax) return false;
+  const int64_t tiles = (n + kTile - 1) / kTile;
+  const int idx = (*L.scan_idx)++;
+  k_scan_1pass<<<(unsigned)std::max<int64_t>(tiles, 1), kScanBlock, 0, L.stream>>>(
+      data, data, n, nullptr, 0, L.scan_state, L.scan_ctr + idx, L.scan_run, idx, L.scan_err,
+      TaskEpilogue{first, chunk});
+  LST_LAUNCH(L);
+  return true;
 }
 
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L) {
