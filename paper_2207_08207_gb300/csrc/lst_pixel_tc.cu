@@ -894,6 +894,9 @@ __global__ void __launch_bounds__(1024) k_tc_sort(Ws w, Geo g) {
     sidx[k] = k < n ? k : 0x7fffffff;
   }
   __syncthreads();
+  // a stage of stride <= 32 exchanges elements inside one warp's 64-element blocks (pair t touches
+  // [64 (t / 32), 64 (t / 32) + 64)), so between two such stages a warp barrier suffices; a wider
+  // stage, before or after, needs the block
   for (int size = 2; size <= m; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int t = threadIdx.x; t < m / 2; t += blockDim.x) {
@@ -907,9 +910,12 @@ __global__ void __launch_bounds__(1024) k_tc_sort(Ws w, Geo g) {
           const int ti = sidx[lo]; sidx[lo] = sidx[hi]; sidx[hi] = ti;
         }
       }
-      __syncthreads();
+      const int next = stride > 1 ? stride >> 1 : size;   // the next stage's stride
+      if (stride <= 32 && next <= 32) __syncwarp();
+      else __syncthreads();
     }
   }
+  __syncthreads();
   // exact order inside runs of equal prefix keys (rare, short: insertion sort on full tuples by the
   // thread at the start of each run)
   for (int r0 = threadIdx.x; r0 < n; r0 += blockDim.x) {
