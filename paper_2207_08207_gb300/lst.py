@@ -375,7 +375,7 @@ def exported_symbols():
 # kernel. An entry is removed when its kernel changes.
 _PROF_MET = "profiles/kernel_metrics_pu200_batch16.md"
 KERNEL_PROFILE = {
-    "ls": {"warp_inst_per_event": 277429392 / 16, "dram_bytes_per_event": (28499968 + 17012224) / 16,
+    "ls": {"warp_inst_per_event": 280648507 / 16, "dram_bytes_per_event": (29301504 + 17486592) / 16,
            "source": _PROF_MET},
     "t3_pre": {"warp_inst_per_event": 144089538 / 16, "dram_bytes_per_event": (76945152 + 1118976) / 16,
                "source": _PROF_MET},
