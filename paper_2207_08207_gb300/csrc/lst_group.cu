@@ -133,7 +133,7 @@ __device__ __forceinline__ void warp_agg_slot_keyed2(bool pa, int ka, bool pb, i
 
 // Pass 3: after the exclusive scan E[k + 1] is the start of group k; each object takes the next
 // position of its group. Afterwards E[k] is the start of group k for every k (E[0] stays 0).
-__global__ void __launch_bounds__(32 * kGrpWarps) k_grp_place(Ws w, GroupArgs a, int32_t* E, int chunk) {
+__global__ void __launch_bounds__(32 * kGrpWarps, 8) k_grp_place(Ws w, GroupArgs a, int32_t* E, int chunk) {
   const int lane = threadIdx.x & 31;
   const int nk = *a.n_keys_dev;
   const int n_tasks = (w.eff[w.V] + chunk - 1) / chunk;   // (of the weights)
