@@ -313,6 +313,14 @@ int64_t lst_predict_bytes(const lst_ctx* ctx, int32_t n_events, int64_t n_hits, 
  * kernel node). */
 int64_t lst_launch_count(const lst_ctx* ctx);
 
+/* Self-test of the one place where blocks wait on other blocks: the chain's single-pass scans
+ * (each block adds the published totals of the tiles before it). Runs such a scan over three tiles
+ * on `device` with the first tile withheld, so that the next tile's wait can never be satisfied and
+ * must give up at its bound (2000 polls here; about a second in the chain, where a wait that gives
+ * up ends the run with LST_ETIMEOUT). *gave_up receives the number of waits that gave up: >= 1 when
+ * the bound works. No fault is involved; the device stays usable. Returns LST_OK or LST_ECUDA. */
+int lst_selftest_bounded_wait(int device, int32_t* gave_up);
+
 /* One-line description of the last error on this context (or of the last failed lst_create when
  * ctx is NULL). Never NULL. */
 const char* lst_last_error(const lst_ctx* ctx);

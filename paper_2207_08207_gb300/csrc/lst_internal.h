@@ -231,6 +231,8 @@ void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, co
 // Only inside a chain run (single-pass scans); returns false when it cannot run (the caller then
 // scans and searches separately).
 bool scan_tasks(int32_t* data, int64_t n, int32_t* first, int chunk, const Launch& L);
+// The single-pass scan with its first tile withheld (see lst_selftest_bounded_wait); 0 or -1.
+int scan_wait_selftest(int device, int32_t* gave_up);
 // the same with the entry count min(n, *n_dev + n_add) read on the device (n sizes the launch);
 // out[count] receives the total
 void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_t* n_dev, int n_add, int32_t* tmp,

@@ -1204,6 +1204,12 @@ int64_t lst_predict_bytes(const lst_ctx* ctx, int32_t n_events, int64_t n_hits, 
 
 int64_t lst_launch_count(const lst_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int lst_selftest_bounded_wait(int device, int32_t* gave_up) {
+  if (!gave_up) return LST_EINVAL;
+  *gave_up = 0;
+  return scan_wait_selftest(device, gave_up) == 0 ? LST_OK : LST_ECUDA;
+}
+
 const char* lst_last_error(const lst_ctx* ctx) {
   if (!ctx) return g_create_error.c_str();
   return ctx->err.c_str();

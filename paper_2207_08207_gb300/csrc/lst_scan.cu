@@ -2,6 +2,8 @@
 // (sensor offsets, per-module object offsets, per-key group offsets). Inside a chain run: one
 // single-pass kernel per scan (decoupled look-back); elsewhere (the standalone binning entry
 // points): three passes (per-tile scan, scan of tile totals, add-back).
+#include <vector>
+
 #include "lst_internal.h"
 
 namespace lst {
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_add(int32_t* out, int64_t n
 // blocks already running, so the waits end; each is bounded all the same (kSpinMax polls), and a
 // wait that gives up counts itself in *err (the run then reports a timeout).
 // State word: epoch (30 bits) | flag (2 bits: 1 tile total, 2 inclusive prefix) | value (32 bits).
-constexpr int kSpinMax = 1 << 22;
+constexpr int kSpinMax = 1 << 22;   // polls of one wait in the chain (about a second at most)
 
 __device__ __forceinline__ unsigned long long scan_word(unsigned epoch, unsigned flag, int v) {
   return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | (unsigned)v;
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_1pass(const int32_t* in, in
                                                            const int32_t* n_dev, int n_add,
                                                            unsigned long long* state, int32_t* ticket,
                                                            const int32_t* run, int scan_idx, int32_t* err,
-                                                           Epi epi) {
+                                                           Epi epi, int spin_max) {
   __shared__ int s_tile, s_excl;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1);
   __syncthreads();
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_1pass(const int32_t* in, in
         const unsigned long long sw = *reinterpret_cast<volatile unsigned long long*>(&state[p]);
         const unsigned flag = (unsigned)(sw >> 32) & 3u;
         if ((unsigned)(sw >> 34) != epoch || flag == 0) {
-          if (++spins > kSpinMax) {
+          if (++spins > spin_max) {
             atomicAdd(err, 1);
             break;
           }
@@ -209,7 +211,8 @@ void scan_exclusive_dev(const int32_t* in, int32_t* out, int64_t n, const int32_
   if (L.scan_state && *L.scan_idx < kScanMax) {
     const int idx = (*L.scan_idx)++;
     k_scan_1pass<<<(unsigned)std::max<int64_t>(tiles, 1), kScanBlock, 0, L.stream>>>(
-        in, out, n, n_dev, n_add, L.scan_state, L.scan_ctr + idx, L.scan_run, idx, L.scan_err, NoEpilogue{});
+        in, out, n, n_dev, n_add, L.scan_state, L.scan_ctr + idx, L.scan_run, idx, L.scan_err, NoEpilogue{},
+        kSpinMax);
     LST_LAUNCH(L);
     return;
   }
@@ -230,9 +233,42 @@ bool scan_tasks(int32_t* data, int64_t n, int32_t* first, int chunk, const Launc
   const int idx = (*L.scan_idx)++;
   k_scan_1pass<<<(unsigned)std::max<int64_t>(tiles, 1), kScanBlock, 0, L.stream>>>(
       data, data, n, nullptr, 0, L.scan_state, L.scan_ctr + idx, L.scan_run, idx, L.scan_err,
-      TaskEpilogue{first, chunk});
+      TaskEpilogue{first, chunk}, kSpinMax);
   LST_LAUNCH(L);
   return true;
+}
+
+int scan_wait_selftest(int device, int32_t* gave_up) {
+  // three tiles of ones; the ticket counter starts at 1, so no block takes tile 0 and the block of
+  // tile 1 waits for a state that is never published, until its bound (spin_max polls)
+  constexpr int kTiles = 3;
+  constexpr int64_t n = (int64_t)kTiles * kTile;
+  if (cudaSetDevice(device) != cudaSuccess) return -1;
+  int32_t *in = nullptr, *out = nullptr, *words = nullptr;
+  unsigned long long* state = nullptr;
+  int rc = -1;
+  const int32_t init[3] = {1, 1, 0};   // ticket, run counter, gave-up count
+  std::vector<int32_t> ones(n, 1);
+  if (cudaMalloc(&in, n * sizeof(int32_t)) == cudaSuccess && cudaMalloc(&out, (n + 1) * sizeof(int32_t)) == cudaSuccess &&
+      cudaMalloc(&words, 3 * sizeof(int32_t)) == cudaSuccess &&
+      cudaMalloc(&state, kTiles * sizeof(unsigned long long)) == cudaSuccess &&
+      cudaMemcpy(in, ones.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
+      cudaMemcpy(words, init, sizeof(init), cudaMemcpyHostToDevice) == cudaSuccess &&
+      cudaMemset(state, 0, kTiles * sizeof(unsigned long long)) == cudaSuccess) {
+    k_scan_1pass<<<kTiles - 1, kScanBlock>>>(in, out, n, nullptr, 0, state, words, words + 1, 0, words + 2,
+                                             NoEpilogue{}, 2000);
+    int32_t back[3] = {0, 0, 0};
+    if (cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+        cudaMemcpy(back, words, sizeof(back), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      *gave_up = back[2];
+      rc = 0;
+    }
+  }
+  cudaFree(in);
+  cudaFree(out);
+  cudaFree(words);
+  cudaFree(state);
+  return rc;
 }
 
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L) {

@@ -128,6 +128,7 @@ def lib():
         L.lst_launch_count.restype = ctypes.c_int64
         L.lst_last_error.argtypes = [ctypes.c_void_p]
         L.lst_last_error.restype = ctypes.c_char_p
+        L.lst_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
         _lib = L
         return L
 
@@ -357,6 +358,16 @@ def bin_hits_noalloc(sensor_dev, n_sensors, order_dev, offsets_dev, stream=None)
                                 _ptr(offsets_dev), st)
     if rc != LST_OK:
         raise LSTError(rc, L.lst_last_error(None).decode())
+
+
+def selftest_bounded_wait(device: int = 0) -> int:
+    """Number of block waits that gave up in the library's bounded-wait self-test (>= 1 when the
+    bound works); raises on a CUDA error."""
+    n = ctypes.c_int32(0)
+    rc = lib().lst_selftest_bounded_wait(device, ctypes.byref(n))
+    if rc != LST_OK:
+        raise LSTError(rc, "lst_selftest_bounded_wait failed")
+    return int(n.value)
 
 
 def exported_symbols():

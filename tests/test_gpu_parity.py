@@ -182,6 +182,14 @@ def test_cycle_budget_ends_run_with_timeout(det_full):
 
 
 @pytest.mark.slow
+def test_scan_wait_gives_up_at_its_bound():
+    """The single-pass scan's wait on an earlier tile is bounded: with the first tile withheld the
+    next tile's wait gives up (counted) instead of hanging, and the device stays usable."""
+    assert lst.selftest_bounded_wait(0) >= 1
+    torch.cuda.synchronize()
+    assert torch.ones(4, device="cuda").sum().item() == 4.0
+
+
 def test_pu300_low_threshold_config4():
     det, ev = gen.config_event(4, 0)
     ctx = lst.Context(det)
