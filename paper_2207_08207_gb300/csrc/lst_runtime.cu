@@ -37,15 +37,18 @@ struct EvPtr {
   const lst_pls* pls;
 };
 
-// A device-readable address of host memory: pinned (page-locked) memory through its mapped device
-// pointer, pageable memory directly where the GPU reads it coherently; nullptr when neither.
+// A device-readable address of host memory: any host address where the GPU reads pageable memory
+// coherently (then no query is needed: pinned memory has the same address under unified
+// addressing), else pinned (page-locked) memory through its mapped device pointer; nullptr when
+// neither.
 const void* device_view(const void* host, bool pageable_access) {
   if (!host) return nullptr;
+  if (pageable_access) return host;
   cudaPointerAttributes attr{};
   if (cudaPointerGetAttributes(&attr, host) == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer)
     return attr.devicePointer;
   cudaGetLastError();
-  return pageable_access ? host : nullptr;
+  return nullptr;
 }
 
 // concatenate device-resident events into the input arena

@@ -152,7 +152,7 @@ def _ptr(a):
         return None
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr())
-    return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.ctypes.data)
 
 
 class _CudaArray:
