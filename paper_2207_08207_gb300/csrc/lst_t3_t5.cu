@@ -342,51 +342,111 @@ __device__ __forceinline__ float kappa_of(float R) { return isinf(R) ? 0.0f : 1.
 
 // T5 candidates: the curvature-compatibility window in float32 with the window guard, then
 // Karimaki's fit and the r-z fit in float32 as a pre-filter (rejects only chi2 > 1.25 cut + 1: the
-// float32 fit parameters enter chi2 at second order and the residual rounding at ~0.3 %)
-__global__ void k_t5_pre(Ws w, Cst<float> c) {
-  const int n_t3 = w.t3_off[w.V];
+// float32 fit parameters enter chi2 at second order and the residual rounding at ~0.3 %).
+// Flattened across each warp like the T3 candidates: the warp takes 32 inner T3, a warp scan of
+// their outer-T3 list lengths turns the (inner, outer) pairs into one index range, each lane takes
+// one pair through the window test, and the pairs that pass go to a per-warp queue whose fits run
+// 32 at a time with every lane busy.
+constexpr int kT5Warps = 8;
+constexpr int kT5Q = 64;
+
+// the float32 fits of the first n (<= 32) queued (inner, outer) T3 pairs, one per lane; the pairs
+// that pass go to the decision queue. Called by the whole warp.
+__device__ __forceinline__ void t5_flush(const Ws& w, const Cst<float>& c, const int2* qe, int n) {
+  const int lane = threadIdx.x & 31;
   const int64_t T = w.cap.t3_dense;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_t3; i += gridDim.x * blockDim.x) {
-    const int m3 = w.t3_md2[i];
-    const int j0 = w.t3md_off[m3], j1 = w.t3md_off[m3 + 1];
-    if (j0 == j1) continue;
-    const float kin = kappa_of(w.t3_R[i]);
+  bool keep = false;
+  int2 e = make_int2(0, 0);
+  if (lane < n) {
+    e = qe[lane];
     float x[5], y[5], z[5], r[5];
     bool ec[5];
-    const uint8_t ecm_i = w.t3_ecm[i];
+    const uint8_t ecm_i = w.t3_ecm[e.x], ecm_j = w.t3_ecm[e.y];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float4 a4 = w.t3_anc[k * T + i];
+      const float4 a4 = w.t3_anc[k * T + e.x];
       x[k] = a4.x; y[k] = a4.y; z[k] = a4.z; r[k] = a4.w;
       ec[k] = (ecm_i >> k) & 1;
     }
-    for (int j = j0; j < j1; ++j) {
-      const float kout = kappa_of(w.t3_R[j]);
-      Acc32 acc(kGuardWindow);
-      acc.cut(c.c_rel * fmaxf(kin, kout) + c.c_abs, fabsf(kin - kout));
-      bool keep = !acc.fail;
-      if (keep) {
-        const uint8_t ecm_j = w.t3_ecm[j];
 #pragma unroll
-        for (int k = 1; k < 3; ++k) {
-          const float4 a4 = w.t3_anc[k * T + j];
-          x[k + 2] = a4.x; y[k + 2] = a4.y; z[k + 2] = a4.z; r[k + 2] = a4.w;
-          ec[k + 2] = (ecm_j >> k) & 1;
-        }
-        float rho, phi, d, sp, cp;
-        karimaki<float, 5>(x, y, rho, phi, d, sp, cp);
-        const float chi2c = circle_chi2<float, 5>(x, y, rho, sp, cp, d, c.sigma_rphi);
-        if (chi2c > 1.25f * c.chi2_t5_c + 1.0f) keep = false;
-        if (keep) {
-          float chi2rz, slope;
-          if (rz_fit<float, 5>(c, fabsf(rho), r, z, ec, chi2rz, slope) && chi2rz > 1.25f * c.chi2_t5_rz + 1.0f)
-            keep = false;
-        }
-      }
-      const int q = warp_agg_slot(keep, &w.status[ST_Q_T5]);
-      if (q >= 0 && q < w.cap.q_t5) w.q_t5[q] = make_int2(i, j);
+    for (int k = 1; k < 3; ++k) {
+      const float4 a4 = w.t3_anc[k * T + e.y];
+      x[k + 2] = a4.x; y[k + 2] = a4.y; z[k + 2] = a4.z; r[k + 2] = a4.w;
+      ec[k + 2] = (ecm_j >> k) & 1;
+    }
+    float rho, phi, d, sp, cp;
+    karimaki<float, 5>(x, y, rho, phi, d, sp, cp);
+    const float chi2c = circle_chi2<float, 5>(x, y, rho, sp, cp, d, c.sigma_rphi);
+    keep = !(chi2c > 1.25f * c.chi2_t5_c + 1.0f);
+    if (keep) {
+      float chi2rz, slope;
+      if (rz_fit<float, 5>(c, fabsf(rho), r, z, ec, chi2rz, slope) && chi2rz > 1.25f * c.chi2_t5_rz + 1.0f)
+        keep = false;
     }
   }
+  const int q = warp_agg_slot(keep, &w.status[ST_Q_T5]);
+  if (q >= 0 && q < w.cap.q_t5) w.q_t5[q] = e;
+}
+
+__global__ void __launch_bounds__(32 * kT5Warps) k_t5_pre(Ws w, Cst<float> c) {
+  __shared__ int2 queue[kT5Warps][kT5Q];
+  int2* qe = queue[threadIdx.x >> 5];
+  const int n_t3 = w.t3_off[w.V];
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  int qn = 0;
+  const long long t0 = clock64();
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n_t3; base += nwarps * 32) {
+    if (warp_over_budget(w, t0)) break;
+    const int i = base + lane;
+    int j0 = 0, size = 0;
+    float kin = 0.f;
+    if (i < n_t3) {
+      const int m3 = w.t3_md2[i];
+      j0 = w.t3md_off[m3];
+      size = w.t3md_off[m3 + 1] - j0;
+      kin = kappa_of(w.t3_R[i]);
+    }
+    int incl = size;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - size;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int b = 0; b < total; b += 32) {
+      const int cidx = b + lane;
+      int lo = 0;   // the lane whose inner T3 holds pair cidx
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = lo + step;
+        if (__shfl_sync(0xffffffffu, excl, cand) <= cidx) lo = cand;
+      }
+      const int jj = __shfl_sync(0xffffffffu, j0, lo) + (cidx - __shfl_sync(0xffffffffu, excl, lo));
+      const float kin_i = __shfl_sync(0xffffffffu, kin, lo);
+      bool keep = false;
+      if (cidx < total) {
+        const float kout = kappa_of(w.t3_R[jj]);
+        Acc32 acc(kGuardWindow);
+        acc.cut(c.c_rel * fmaxf(kin_i, kout) + c.c_abs, fabsf(kin_i - kout));
+        keep = !acc.fail;
+      }
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      if (keep) qe[qn + __popc(km & ((1u << lane) - 1u))] = make_int2(base + lo, jj);
+      qn += __popc(km);
+      if (qn >= 32) {
+        __syncwarp();
+        t5_flush(w, c, qe, 32);
+        __syncwarp();
+        qn -= 32;
+        if (lane < qn) qe[lane] = qe[32 + lane];
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  if (qn > 0) t5_flush(w, c, qe, qn);
 }
 
 // float64-exact decision of the pre-filter's survivors, evaluated in double-float
@@ -505,7 +565,7 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.t5_base, w.t5_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T5_PRE);
-  k_t5_pre<<<152 * 8, 256, 0, L.stream>>>(w, c.f);
+  k_t5_pre<<<L.n_sm * 8, 32 * kT5Warps, 0, L.stream>>>(w, c.f);
   KT_END(L, K_T5_PRE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T5_DECIDE);
