@@ -224,14 +224,6 @@ __global__ void __launch_bounds__(kRankTile) k_grp_rank(Ws w, GroupArgs a, const
     a.mod_off[vm] = (int)lst_min64(E[a.mod_first[(int64_t)vm * a.mod_first_stride]], a.dense_cap);
 }
 
-// after a dense overflow the group offsets handed to the next stage are clamped to the capacity
-__global__ void k_grp_clamp(Ws w, int32_t* E, GroupArgs a) {
-  if (w.status[a.dense_word] == 0) return;
-  const int nk = *a.n_keys_dev;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nk; k += gridDim.x * blockDim.x)
-    if (E[k] > a.dense_cap) E[k] = (int)a.dense_cap;
-}
-
 }  // namespace
 
 void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
@@ -242,7 +234,6 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
   int chunk = 64;
   while (chunk < 1024 && (int64_t)chunk * 2 * resident_warps * 2 <= a.dense_cap + w.V) chunk *= 2;
   const int blocks = L.n_sm * (64 / kGrpWarps);
-  const int key_blocks = grid_for(a.n_keys + 1, 256, L.n_sm * 8);
   k_grp_eff<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, a);
   LST_LAUNCH(L);
   if (!scan_tasks(w.eff, w.V, w.grp_task, chunk, L)) {
@@ -257,10 +248,7 @@ void group_slots(const Ws& w, const GroupArgs& a, const Launch& L) {
   else if (a.dense_out == kDenseT3) k_grp_rank<kDenseT3><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
   else k_grp_rank<kDensePerm><<<L.n_sm * 8, kRankTile, 0, L.stream>>>(w, a, E);
   LST_LAUNCH(L);
-  if (a.grp_off) {
-    k_grp_clamp<<<key_blocks, 256, 0, L.stream>>>(w, E, a);
-    LST_LAUNCH(L);
-  }
+  // (after a dense overflow, the next stage's capacity kernel clamps the group offsets it reads)
 }
 
 }  // namespace lst

@@ -437,19 +437,20 @@ __global__ void k_ls_caps(Ws w, Geo g) {
   if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&w.work_cnt[threadIdx.x], hist[threadIdx.x]);
 }
 
-// offsets of the cost buckets, most expensive first
-__global__ void k_ls_work_scan(Ws w) {
+// the work list: items by cost bucket, most expensive first. Every block derives the bucket offsets
+// from the 32 bucket counts itself; block 0 also stores them (the LS kernel reads the total).
+__global__ void k_ls_work_fill(Ws w) {
+  __shared__ int off[33];
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int b = 31; b >= 0; --b) {
-      w.work_off[b] = acc;
+      off[b] = acc;
       acc += w.work_cnt[b];
     }
-    w.work_off[32] = acc;
+    off[32] = acc;
   }
-}
-
-__global__ void k_ls_work_fill(Ws w) {
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x <= 32) w.work_off[threadIdx.x] = off[threadIdx.x];
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm - (int)(threadIdx.x & 31) < w.V;
        vm += gridDim.x * blockDim.x) {
     const int lane = threadIdx.x & 31;
@@ -470,7 +471,7 @@ __global__ void k_ls_work_fill(Ws w) {
     base = __shfl_sync(0xffffffffu, base, leader);
     if (b >= 0)
       for (int k = 0; k < nch; ++k) {
-        const int at = w.work_off[b] + base + pre + k;
+        const int at = off[b] + base + pre + k;
         w.work[at] = vm;
         w.work_c[at] = k;
       }
@@ -813,9 +814,8 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.ls_base, w.ls_base, w.V, w.scan_tmp, L);
   if (L.persistent) {
-    k_ls_work_scan<<<1, 32, 0, L.stream>>>(w);
     k_ls_work_fill<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w);
-    *L.launches += 2;
+    *L.launches += 1;
   }
   KT_BEGIN(L, K_LS);
   {

@@ -314,6 +314,15 @@ __device__ __forceinline__ void zero_group_counts(int32_t* E, int n) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) E[k] = 0;
 }
 
+// After a dense overflow of the previous stage its group offsets E[0..n] are clamped to the dense
+// capacity before the next stage reads them (done by the next stage's capacity kernel; all threads
+// of its grid call this)
+__device__ __forceinline__ void clamp_group_offsets(int32_t* E, int n, int64_t cap, bool overflowed) {
+  if (!overflowed) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x)
+    if (E[k] > cap) E[k] = (int)cap;
+}
+
 // E[key] += 1 for every lane with pred, one atomic per distinct key of the warp (all lanes call it)
 __device__ __forceinline__ void warp_count_keyed(bool pred, int key, int32_t* E) {
   const unsigned m = __ballot_sync(0xffffffffu, pred);

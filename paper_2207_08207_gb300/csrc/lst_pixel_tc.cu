@@ -26,38 +26,6 @@ __device__ __forceinline__ int find_seg(const int32_t* off, int n, int i) {
   return lo;
 }
 
-// ---------------------------------------------------------------------------------------------
-// pixel seeds: validation and pixel-map bin. The bin index is computed in float64 with explicitly
-// rounded operations (floor(20 eta + 50), floor(phi_[0,2pi) * 64 / pi)), the same sequence of IEEE
-// operations any implementation of the definition performs.
-// ---------------------------------------------------------------------------------------------
-__global__ void k_pls_prep(Ws w, Geo g) {
-  const int P = w.n_pls();
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    const lst_pls s = w.pls[p];
-    const bool ok = isfinite(s.pt) && isfinite(s.eta) && isfinite(s.phi) && isfinite(s.x0) &&
-                    isfinite(s.y0) && isfinite(s.z0) && s.pt > 0.f && (s.charge == 1 || s.charge == -1);
-    int bin = -1;
-    const int e = find_seg(w.ev_pls_off, w.E, p);
-    w.pls_ev[p] = e;
-    if (!ok) {
-      atomicOr(&w.status[ST_ERROR], ERR_BAD_PLS);
-      atomicOr(&w.ev_stat[e * kEvWords + kEvErr], ERR_BAD_PLS);
-    } else if (g.n_pix_bins > 0) {
-      const double ie = floor(__dadd_rn(__dmul_rn((double)s.eta, 20.0), 50.0));
-      if (ie >= 0.0 && ie < (double)kPixNEta) {
-        double ph = (double)s.phi;
-        if (ph < 0.0) ph = __dadd_rn(ph, kTwoPiD);
-        double ip = floor(__dmul_rn(ph, 64.0 / kPiD));
-        ip = fmin(fmax(ip, 0.0), (double)(kPixNPhi - 1));
-        bin = ((int)ie * kPixNPhi + (int)ip) * 2 + (s.charge > 0 ? 1 : 0);
-        if (bin >= g.n_pix_bins) bin = -1;
-      }
-    }
-    w.pls_bin[p] = bin;
-  }
-}
-
 // seed helix in precision T: circle centre c = (x0, y0) + (1/rho) n, n = (sin phi, -cos phi),
 // rho = q / R, R = pT / k
 template <class T>
@@ -83,6 +51,43 @@ __device__ __forceinline__ Seed<T> make_seed(const lst_pls& s, const Cst<T>& c) 
     o.cot = sinh((double)s.eta);
   }
   return o;
+}
+
+// ---------------------------------------------------------------------------------------------
+// pixel seeds: validation and pixel-map bin. The bin index is computed in float64 with explicitly
+// rounded operations (floor(20 eta + 50), floor(phi_[0,2pi) * 64 / pi)), the same sequence of IEEE
+// operations any implementation of the definition performs.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_pls_prep(Ws w, Geo g, Cst<float> c) {
+  const int P = w.n_pls();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const lst_pls s = w.pls[p];
+    const bool ok = isfinite(s.pt) && isfinite(s.eta) && isfinite(s.phi) && isfinite(s.x0) &&
+                    isfinite(s.y0) && isfinite(s.z0) && s.pt > 0.f && (s.charge == 1 || s.charge == -1);
+    int bin = -1;
+    const int e = find_seg(w.ev_pls_off, w.E, p);
+    w.pls_ev[p] = e;
+    if (!ok) {
+      atomicOr(&w.status[ST_ERROR], ERR_BAD_PLS);
+      atomicOr(&w.ev_stat[e * kEvWords + kEvErr], ERR_BAD_PLS);
+    } else if (g.n_pix_bins > 0) {
+      const double ie = floor(__dadd_rn(__dmul_rn((double)s.eta, 20.0), 50.0));
+      if (ie >= 0.0 && ie < (double)kPixNEta) {
+        double ph = (double)s.phi;
+        if (ph < 0.0) ph = __dadd_rn(ph, kTwoPiD);
+        double ip = floor(__dmul_rn(ph, 64.0 / kPiD));
+        ip = fmin(fmax(ip, 0.0), (double)(kPixNPhi - 1));
+        bin = ((int)ie * kPixNPhi + (int)ip) * 2 + (s.charge > 0 ? 1 : 0);
+        if (bin >= g.n_pix_bins) bin = -1;
+      }
+    }
+    w.pls_bin[p] = bin;
+    if (bin >= 0) {   // the float32 seed helix, once per seed, for the candidate pre-filters
+      const Seed<float> sd = make_seed<float>(s, c);
+      w.pls_seed[p] = make_float4(sd.x0, sd.y0, sd.z0, sd.rho);
+      w.pls_seed[w.P + p] = make_float4(sd.akap, sd.sp, sd.cp, sd.cot);
+    }
+  }
 }
 
 // distance of (x, y) from the seed circle, |p - c| - R up to sign, as 2A / (1 + sqrt(1 + 2 rho A))
@@ -116,15 +121,20 @@ struct ObjAnc {
   int64_t stride;
 };
 
-// bounding box of the first anchors of each module's objects (kBoxLanes lanes per module: modules
-// hold a few T3 / T5 each, most none)
+// bounding boxes of the first anchors of each module's T3 and of its T5 (kBoxLanes lanes per module
+// and type: modules hold a few T3 / T5 each, most none)
 constexpr int kBoxLanes = 4;
 
-__global__ void k_obj_box(Ws w, const int32_t* obj_off, const float4* anc0, float4* box) {
+__global__ void k_obj_box(Ws w) {
   const int sub = threadIdx.x & (kBoxLanes - 1);
   const unsigned gmask = ((1u << kBoxLanes) - 1u) << ((threadIdx.x & 31) & ~(kBoxLanes - 1));
   const int ngroups = gridDim.x * (blockDim.x / kBoxLanes);
-  for (int vm = (blockIdx.x * blockDim.x + threadIdx.x) / kBoxLanes; vm < w.V; vm += ngroups) {
+  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) / kBoxLanes; item < 2 * w.V; item += ngroups) {
+    const bool t5 = item >= w.V;   // items [0, V): T3 boxes; [V, 2V): T5 boxes
+    const int vm = t5 ? item - w.V : item;
+    const int32_t* obj_off = t5 ? w.t5_off : w.t3_off;
+    const float4* anc0 = t5 ? w.t5_anc : w.t3_anc;
+    float4* box = t5 ? w.box5 : w.box3;
     const int a = obj_off[vm], b = obj_off[vm + 1];
     if (a == b) continue;
     float4 lo = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
@@ -192,17 +202,6 @@ __device__ __forceinline__ bool seed_box_reject(const Seed<float>& s, const Cst<
     if (gap * gap > lim_rz * (sz * sz + th * th) * 1.0625f) return true;
   }
   return false;
-}
-
-// float32 seed helices, once per seed, for the candidate pre-filters
-__global__ void k_seed_cache(Ws w, Cst<float> c) {
-  const int P = w.n_pls();
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    if (w.pls_bin[p] < 0) continue;
-    const Seed<float> s = make_seed<float>(w.pls[p], c);
-    w.pls_seed[p] = make_float4(s.x0, s.y0, s.z0, s.rho);
-    w.pls_seed[w.P + p] = make_float4(s.akap, s.sp, s.cp, s.cot);
-  }
 }
 
 __device__ __forceinline__ Seed<float> cached_seed(const Ws& w, int p) {
@@ -1001,17 +1000,15 @@ __global__ void k_tc_dense(Ws w, Geo g) {
 }  // namespace
 
 void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
-  k_pls_prep<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, g);
+  k_pls_prep<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, g, c.f);
   LST_LAUNCH(L);
   const int threads = 32 * L.warps_px;
   const int blocks = grid_for((int64_t)w.P * 32, threads, 152 * 16);
   ObjAnc om3{w.t3_anc, w.t3_ecm, w.cap.t3_dense};
   ObjAnc om5{w.t5_anc, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
-    k_seed_cache<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, c.f);
-    k_obj_box<<<grid_for((int64_t)w.V * kBoxLanes, 256), 256, 0, L.stream>>>(w, w.t3_off, w.t3_anc, w.box3);
-    k_obj_box<<<grid_for((int64_t)w.V * kBoxLanes, 256), 256, 0, L.stream>>>(w, w.t5_off, w.t5_anc, w.box5);
-    *L.launches += 3;
+    k_obj_box<<<grid_for((int64_t)w.V * 2 * kBoxLanes, 256), 256, 0, L.stream>>>(w);
+    *L.launches += 1;
     KT_BEGIN(L, K_PT3_PRE);
   k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, w.box3, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
                                                    c.f.chi2_pt3_xy, c.f.chi2_pt3_rz);

@@ -237,6 +237,7 @@ __device__ __forceinline__ int clamp_cap2(double pred, long long bound, int ovr)
 // starts in vm, summed while the LS were compacted)
 __global__ void k_t3_caps(Ws w) {
   zero_group_counts(w.t3md_off, w.md_off[w.V]);   // T3 are grouped by first MD
+  clamp_group_offsets(w.lsin_off, w.md_off[w.V], w.cap.ls_dense, w.status[ST_DENSE_LS] != 0);
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long bound = (long long)w.t3_bound[vm];
     const int cc = clamp_cap2(w.cap_scale * w.stage_scale[2] * (32.0 + 0.5 * (double)bound), bound, w.t3_ovr[vm]);
@@ -330,6 +331,7 @@ __device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T 
 // starts in vm, summed while the T3 were compacted)
 __global__ void k_t5_caps(Ws w) {
   zero_group_counts(w.grp_key, w.t3_off[w.V]);   // T5 are grouped by inner T3
+  clamp_group_offsets(w.t3md_off, w.md_off[w.V], w.cap.t3_dense, w.status[ST_DENSE_T3] != 0);
   for (int vm = blockIdx.x * blockDim.x + threadIdx.x; vm < w.V; vm += gridDim.x * blockDim.x) {
     const long long bound = (long long)w.t5_bound[vm];
     const int cc = clamp_cap2(w.cap_scale * w.stage_scale[3] * (16.0 + 0.5 * (double)bound), bound, w.t5_ovr[vm]);
