@@ -81,6 +81,27 @@ def test_batch_equals_single_runs(det_full, ctx_full):
     _check(oracle.run(det_full, evs[1]), batched[1], evs[1])
 
 
+def test_bench_batch_matches_single_runs_and_oracle(det_full, ctx_full):
+    """The batched launch configuration the benchmark times (64 PU200 events per run, persistent LS
+    work list, CUDA graph): every event of the batch equals its one-event run (a different launch
+    shape: small-batch LS chunks, per-module tasks), and sampled events match the oracle."""
+    evs = [gen.config_event(2, e, pu=200.0)[1] for e in range(64)]
+    ctx = lst.Context(det_full, persistent=1, use_graph=1)
+    try:
+        ctx.run(evs)
+        batched = [ctx.results(e) for e in range(64)]
+    finally:
+        ctx.close()
+    for e, ev in enumerate(evs):
+        ctx_full.run([ev])
+        single = ctx_full.results(0)
+        for k in single:
+            if k != "counts":
+                assert np.array_equal(single[k], batched[e][k]), (e, k)
+    for e in (0, 37):
+        _check(oracle.run(det_full, evs[e]), batched[e], evs[e])
+
+
 def test_device_inputs_equal_host_inputs(det_full, ctx_full):
     _, ev = gen.small_event(800, seed=9)
     ctx_full.run([ev])
