@@ -31,6 +31,7 @@ __device__ __forceinline__ Anchor<T> anchor(const Ws& w, int d) {
   a.y = (T)p.y;
   a.z = (T)p.z;
   if constexpr (sizeof(T) == 4) a.r = p.w;
+  else if constexpr (std::is_same<T, ff>::value) a.r = ff_fast_two_sum(p.w, w.md_rlo[d]);   // r to ~2^-47
   else a.r = m_sqrt(a.x * a.x + a.y * a.y);
   a.ec = w.md_ec[d] != 0;
   return a;
@@ -468,10 +469,11 @@ __global__ void k_t5_decide(Ws w, Cst<ff> c) {
     bool ec[5];
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
-      x[a] = ff(w.md_x[md[a]]);
-      y[a] = ff(w.md_y[md[a]]);
-      z[a] = ff(w.md_z[md[a]]);
-      r[a] = m_sqrt(x[a] * x[a] + y[a] * y[a]);
+      const float4 p = w.md_xyzr[md[a]];
+      x[a] = ff(p.x);
+      y[a] = ff(p.y);
+      z[a] = ff(p.z);
+      r[a] = ff_fast_two_sum(p.w, w.md_rlo[md[a]]);   // the MD's radius as a float pair (~2^-47)
       ec[a] = w.md_ec[md[a]] != 0;
     }
     ff rho, phi, d, sp, cp;
