@@ -103,6 +103,7 @@ struct Ws {
   float *t3_R = nullptr, *t3_xc = nullptr, *t3_yc = nullptr, *t3_chi2 = nullptr, *t3_pte = nullptr;
   int32_t* t3md_off = nullptr;   // [md_dense + 2] T3 by first MD (their group offsets)
   float4* t3_anc = nullptr;      // [3][t3_dense] anchor (x, y, z, r) of each member MD
+  float* t3_anc_rlo = nullptr;   // [3][t3_dense] low part of each anchor's radius (r + rlo to ~2^-47)
   uint8_t* t3_ecm = nullptr;     // endcap bit per anchor
   // T5
   int32_t *t5_cap = nullptr, *t5_base = nullptr, *t5_cnt = nullptr, *t5_ovr = nullptr;
@@ -113,6 +114,7 @@ struct Ws {
   int32_t* t5_md = nullptr;  // [5][t5_dense]
   float* t5_f = nullptr;     // [8][t5_dense]
   float4* t5_anc = nullptr;      // [5][t5_dense]
+  float* t5_anc_rlo = nullptr;   // [5][t5_dense]
   uint8_t* t5_ecm = nullptr;
   // per module: lo[vm], hi[V + vm] = bounding box (x, y, z, r) of the first anchors of its T3 / T5
   float4* box3 = nullptr;
@@ -121,6 +123,7 @@ struct Ws {
   int32_t* pls_bin = nullptr;
   int32_t* pls_ev = nullptr;     // [P] event of each seed
   float4* pls_seed = nullptr;    // [2][P] float32 seed helix: (x0, y0, z0, rho), (|kappa|, sin phi, cos phi, cot theta)
+  float2* pls_seed_ff = nullptr; // [P][9] the same in double-float (x0, y0, z0, rho, |kappa|, sin, cos, cot, R)
   int32_t *p3a_pls = nullptr, *p3a_obj = nullptr;
   float *p3a_xy = nullptr, *p3a_rz = nullptr, *p3a_sc = nullptr;
   int32_t *p3_cnt = nullptr, *p3_cur = nullptr, *pt3_off = nullptr;   // [P], [P], [P + 1]
@@ -389,6 +392,7 @@ __device__ __forceinline__ void t3_dense_write(const Ws& w, bool valid, int d, i
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       w.t3_anc[k * T + d] = w.md_xyzr[md[k]];
+      w.t3_anc_rlo[k * T + d] = w.md_rlo[md[k]];
       ecm |= (uint8_t)(w.md_ec[md[k]] << k);
     }
     w.t3_ecm[d] = ecm;

@@ -58,7 +58,7 @@ __device__ __forceinline__ Seed<T> make_seed(const lst_pls& s, const Cst<T>& c) 
 // rounded operations (floor(20 eta + 50), floor(phi_[0,2pi) * 64 / pi)), the same sequence of IEEE
 // operations any implementation of the definition performs.
 // ---------------------------------------------------------------------------------------------
-__global__ void k_pls_prep(Ws w, Geo g, Cst<float> c) {
+__global__ void k_pls_prep(Ws w, Geo g, Cst<float> c, Cst<ff> cx) {
   const int P = w.n_pls();
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const lst_pls s = w.pls[p];
@@ -82,10 +82,16 @@ __global__ void k_pls_prep(Ws w, Geo g, Cst<float> c) {
       }
     }
     w.pls_bin[p] = bin;
-    if (bin >= 0) {   // the float32 seed helix, once per seed, for the candidate pre-filters
+    if (bin >= 0) {   // the seed helix, once per seed: float32 for the pre-filters, double-float
+                      // for the decisions
       const Seed<float> sd = make_seed<float>(s, c);
       w.pls_seed[p] = make_float4(sd.x0, sd.y0, sd.z0, sd.rho);
       w.pls_seed[w.P + p] = make_float4(sd.akap, sd.sp, sd.cp, sd.cot);
+      const Seed<ff> sx = make_seed<ff>(s, cx);
+      const ff v[9] = {sx.x0, sx.y0, sx.z0, sx.rho, sx.akap, sx.sp, sx.cp, sx.cot, sx.R};
+      float2* o = w.pls_seed_ff + (int64_t)p * 9;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) o[k] = make_float2(v[k].hi, v[k].lo);
     }
   }
 }
@@ -117,6 +123,7 @@ __device__ __forceinline__ void seed_terms(const Seed<T>& s, const Cst<T>& c, T 
 // ecm[i] bit k = anchor k is on an endcap module
 struct ObjAnc {
   const float4* anc;
+  const float* rlo;   // low part of each anchor's radius
   const uint8_t* ecm;
   int64_t stride;
 };
@@ -358,13 +365,19 @@ __global__ void k_pt_decide(Ws w, Cst<ff> c, ObjAnc oa, const int2* queue, int q
   const int n = min((int64_t)w.status[q_word], q_cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int2 q = queue[k];
-    const Seed<ff> s = make_seed<ff>(w.pls[q.x], c);
+    Seed<ff> s;   // the seed's double-float helix, cached per seed
+    {
+      const float2* v = w.pls_seed_ff + (int64_t)q.x * 9;
+      s.x0 = ff(v[0].x, v[0].y); s.y0 = ff(v[1].x, v[1].y); s.z0 = ff(v[2].x, v[2].y);
+      s.rho = ff(v[3].x, v[3].y); s.akap = ff(v[4].x, v[4].y); s.sp = ff(v[5].x, v[5].y);
+      s.cp = ff(v[6].x, v[6].y); s.cot = ff(v[7].x, v[7].y); s.R = ff(v[8].x, v[8].y);
+    }
     ff xy = ff(0.0f), rz = ff(0.0f);
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       const float4 h = oa.anc[a * oa.stride + q.y];
       const ff x(h.x), y(h.y), z(h.z);
-      const ff r = m_sqrt(x * x + y * y);
+      const ff r = ff_fast_two_sum(h.w, oa.rlo[a * oa.stride + q.y]);   // the anchor's radius (~2^-47)
       ff t1, t2;
       seed_terms<ff>(s, c, x, y, z, r, ((oa.ecm[q.y] >> a) & 1) != 0, t1, t2);
       xy += t1;
@@ -1000,12 +1013,12 @@ __global__ void k_tc_dense(Ws w, Geo g) {
 }  // namespace
 
 void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
-  k_pls_prep<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, g, c.f);
+  k_pls_prep<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, g, c.f, c.x);
   LST_LAUNCH(L);
   const int threads = 32 * L.warps_px;
   const int blocks = grid_for((int64_t)w.P * 32, threads, 152 * 16);
-  ObjAnc om3{w.t3_anc, w.t3_ecm, w.cap.t3_dense};
-  ObjAnc om5{w.t5_anc, w.t5_ecm, w.cap.t5_dense};
+  ObjAnc om3{w.t3_anc, w.t3_anc_rlo, w.t3_ecm, w.cap.t3_dense};
+  ObjAnc om5{w.t5_anc, w.t5_anc_rlo, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
     k_obj_box<<<grid_for((int64_t)w.V * 2 * kBoxLanes, 256), 256, 0, L.stream>>>(w);
     *L.launches += 1;

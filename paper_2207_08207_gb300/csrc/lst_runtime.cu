@@ -407,17 +407,17 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.t3_a, c.t3_dense); pl.add(w.t3_b, c.t3_dense); pl.add(w.t3_md0, c.t3_dense); pl.add(w.t3_md1, c.t3_dense);
   pl.add(w.t3_md2, c.t3_dense); pl.add(w.t3_R, c.t3_dense); pl.add(w.t3_xc, c.t3_dense); pl.add(w.t3_yc, c.t3_dense);
   pl.add(w.t3_chi2, c.t3_dense); pl.add(w.t3_pte, c.t3_dense);
-  pl.add(w.t3_anc, 3 * c.t3_dense); pl.add(w.t3_ecm, c.t3_dense);
+  pl.add(w.t3_anc, 3 * c.t3_dense); pl.add(w.t3_anc_rlo, 3 * c.t3_dense); pl.add(w.t3_ecm, c.t3_dense);
   pl.add(w.t3md_off, c.md_dense + 2);
   // T5
   pl.add(w.t5_cap, V); pl.add(w.t5_base, V + 1); pl.add(w.t5_off, V + 1);
   pl.add(w.t5s_a, c.t5_slots); pl.add(w.t5s_b, c.t5_slots); pl.add(w.t5s_f, 8 * c.t5_slots);
   pl.add(w.t5_a, c.t5_dense); pl.add(w.t5_b, c.t5_dense); pl.add(w.t5_md, 5 * c.t5_dense); pl.add(w.t5_f, 8 * c.t5_dense);
-  pl.add(w.t5_anc, 5 * c.t5_dense); pl.add(w.t5_ecm, c.t5_dense);
+  pl.add(w.t5_anc, 5 * c.t5_dense); pl.add(w.t5_anc_rlo, 5 * c.t5_dense); pl.add(w.t5_ecm, c.t5_dense);
   pl.add(w.t5_kept, c.t5_dense); pl.add(w.acc5t, c.t5_dense);
   pl.add(w.box3, 2 * V); pl.add(w.box5, 2 * V);
   // pixel
-  pl.add(w.pls_bin, c.P); pl.add(w.pls_ev, c.P); pl.add(w.pls_seed, 2 * c.P);
+  pl.add(w.pls_bin, c.P); pl.add(w.pls_ev, c.P); pl.add(w.pls_seed, 2 * c.P); pl.add(w.pls_seed_ff, 9 * c.P);
   pl.add(w.p3a_pls, c.p3_slots); pl.add(w.p3a_obj, c.p3_slots); pl.add(w.p3a_xy, c.p3_slots);
   pl.add(w.p3a_rz, c.p3_slots); pl.add(w.p3a_sc, c.p3_slots); pl.add(w.pt3_off, c.P + 1);
   pl.add(w.pt3_pls, c.p3_slots); pl.add(w.pt3_obj, c.p3_slots); pl.add(w.pt3_xy, c.p3_slots);

@@ -524,6 +524,7 @@ __global__ void k_t5_dense(Ws w) {
     for (int k = 0; k < 5; ++k) {
       w.t5_md[k * D + d] = md[k];
       w.t5_anc[k * D + d] = w.md_xyzr[md[k]];
+      w.t5_anc_rlo[k * D + d] = w.md_rlo[md[k]];
       ecm |= (uint8_t)(w.md_ec[md[k]] << k);
     }
     w.t5_ecm[d] = ecm;
