@@ -381,15 +381,9 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
     const float qe = qs + exx + eyy;
     const float r = sqrtf(q);
     const float rlo = (fmaf(-r, r, q) + qe) / (2.0f * r);
-    w.md_x[d] = x;
-    w.md_y[d] = y;
-    w.md_z[d] = w.bz[lo];
-    w.md_r[d] = r;
     w.md_rlo[d] = r > 0.f ? rlo : 0.f;
     const float sthr = c.two_rthr * asinf(fminf(r / c.two_rthr, 1.0f));
     const float alpha = asinf(fminf(r * c.k2p, c.sin_max));
-    w.md_sthr[d] = sthr;
-    w.md_alpha[d] = alpha;
     w.md_xyzr[d] = make_float4(x, y, w.bz[lo], r);
     w.md_sa[d] = make_float2(sthr, alpha);
     w.md_ec[d] = g.endcap[vm % g.n_mods];
@@ -696,7 +690,8 @@ namespace {
 
 __device__ __forceinline__ void md_anchor64(const Ws& w, const Cst<double>& c, int d, double& x,
                                             double& y, double& z, double& r, double& s) {
-  x = w.md_x[d]; y = w.md_y[d]; z = w.md_z[d];
+  const float4 p = w.md_xyzr[d];
+  x = p.x; y = p.y; z = p.z;
   r = sqrt(x * x + y * y);
   s = c.two_rthr * asin(fmin(r / c.two_rthr, 1.0));
 }

@@ -78,11 +78,9 @@ struct Ws {
   float *ms_dpc = nullptr, *ms_pte = nullptr;
   int32_t* md_off = nullptr;
   int32_t *md_lo = nullptr, *md_up = nullptr, *md_vm = nullptr;
-  float *md_x = nullptr, *md_y = nullptr, *md_z = nullptr, *md_r = nullptr, *md_sthr = nullptr;
-  float *md_rlo = nullptr;     // r = md_r + md_rlo to ~1e-14 relative (float-float)
-  float *md_alpha = nullptr;   // alpha_thr(r) = asin(min(r k / (2 pT_thr), sin_max)), float32
-  float4* md_xyzr = nullptr;     // [md_dense] (x, y, z, r) of each MD anchor, one load (LS kernel)
-  float2* md_sa = nullptr;       // [md_dense] (arc length at R_thr, alpha_thr)
+  float4* md_xyzr = nullptr;     // [md_dense] (x, y, z, r) of each MD anchor (the lower hit)
+  float *md_rlo = nullptr;       // [md_dense] r + md_rlo = the anchor radius to ~2^-47 (float pair)
+  float2* md_sa = nullptr;       // [md_dense] (arc length at R_thr, alpha_thr(r) = asin(min(r k / (2 pT_thr), sin_max)))
   float *md_dpc = nullptr, *md_pte = nullptr;
   uint8_t* md_ec = nullptr;
   // LS

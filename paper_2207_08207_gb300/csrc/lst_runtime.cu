@@ -391,8 +391,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.md_cap, V); pl.add(w.md_base, V + 1); pl.add(w.md_off, V + 1);
   pl.add(w.ms_lo, c.md_slots); pl.add(w.ms_up, c.md_slots); pl.add(w.ms_dpc, c.md_slots); pl.add(w.ms_pte, c.md_slots);
   pl.add(w.md_lo, c.md_dense); pl.add(w.md_up, c.md_dense); pl.add(w.md_vm, c.md_dense);
-  pl.add(w.md_x, c.md_dense); pl.add(w.md_y, c.md_dense); pl.add(w.md_z, c.md_dense); pl.add(w.md_r, c.md_dense);
-  pl.add(w.md_sthr, c.md_dense); pl.add(w.md_rlo, c.md_dense); pl.add(w.md_alpha, c.md_dense);
+  pl.add(w.md_rlo, c.md_dense);
   pl.add(w.md_dpc, c.md_dense); pl.add(w.md_pte, c.md_dense); pl.add(w.md_ec, c.md_dense);
   pl.add(w.md_xyzr, c.md_dense); pl.add(w.md_sa, c.md_dense);
   // LS

@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(32 * kT3Warps) k_t3_pre(Ws w, Cst<float> c) {
       const int d1 = w.ls_in[i], d2 = w.ls_out[i];
       j0 = min(w.lsin_off[d2], n_ls);
       size = min(w.lsin_off[d2 + 1], n_ls) - j0;
-      x1 = w.md_x[d1]; y1 = w.md_y[d1];
+      const float4 p1 = w.md_xyzr[d1];
+      x1 = p1.x; y1 = p1.y;
       const float2 p2 = w.ls_xy_out[i];
       x2 = p2.x; y2 = p2.y;
     }
