@@ -77,6 +77,7 @@ def lib():
         L.orc_line_fit.restype = ctypes.c_double
         L.orc_pixel_bin.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int32]
         L.orc_pixel_bin.restype = ctypes.c_int32
+        L.orc_seed_terms.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 6
         _lib = L
     return _lib
 
@@ -178,3 +179,18 @@ def line_fit(s, z, sig):
 
 def pixel_bin(eta, phi, charge):
     return int(lib().orc_pixel_bin(float(eta), float(phi), int(charge)))
+
+
+def seed_terms(seed, x, y, z, endcap):
+    """Per-anchor pT3 / pT5 terms of one seed (a PLS_DTYPE record) against anchors (x, y, z, endcap):
+    returns (terms [n, 4] = distance from the seed circle, its variance, z offset from the seed's
+    r-z line, its variance; (chi2_xy, chi2_rz))."""
+    rec = np.ascontiguousarray(np.asarray(seed).reshape(1))
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    ec = np.ascontiguousarray(endcap, dtype=np.int32)
+    terms = np.zeros((x.size, 4))
+    chi2 = np.zeros(2)
+    lib().orc_seed_terms(_p(rec), int(x.size), _p(x), _p(y), _p(z), _p(ec), _p(terms), _p(chi2))
+    return terms, (float(chi2[0]), float(chi2[1]))

@@ -459,28 +459,39 @@ int32_t pixel_bin(const PlsRec& s) {
   return ((int32_t)ie * kPixNPhi + (int32_t)ip) * 2 + (s.charge > 0 ? 1 : 0);
 }
 
-Verdict pobj_cuts(const Params& P, const PlsRec& s, int n, const Hit* const* h, double cut_xy,
-                  double cut_rz, PObj& o) {
-  Verdict v;
+// The terms one outer anchor contributes: its distance from the seed's circle and the variance of
+// that distance (hit resolution plus the seed's direction and curvature uncertainties carried out to
+// the anchor's radius), and its z offset from the seed's r-z line with that offset's variance.
+struct SeedTerms { double dist, var_xy, dz, var_rz; };
+
+SeedTerms seed_terms(const Params& P, const PlsRec& s, const Hit& a) {
   double R = (double)s.pt / P.k;
   double q = s.charge > 0 ? 1.0 : -1.0;
   double phi = s.phi;
   double cx = (double)s.x0 + q * R * std::sin(phi);
   double cy = (double)s.y0 - q * R * std::cos(phi);
   double cot = std::sinh((double)s.eta);
+  SeedTerms t;
+  t.dist = std::sqrt((a.x - cx) * (a.x - cx) + (a.y - cy) * (a.y - cy)) - R;
+  t.var_xy = P.sigma_rphi * P.sigma_rphi + (a.r * P.pls_dir_err) * (a.r * P.pls_dir_err) +
+             (P.pls_pt_err * a.r * a.r / (2.0 * R)) * (P.pls_pt_err * a.r * a.r / (2.0 * R));
+  double sa = arc_s(R, a.r);
+  double zpred = (double)s.z0 + sa * cot;
+  double sz = a.endcap ? P.sigma_r * std::fabs(cot) : P.sigma_z;
+  double th = sa * (1.0 + cot * cot) * P.pls_dir_err;
+  t.dz = a.z - zpred;
+  t.var_rz = sz * sz + th * th;
+  return t;
+}
+
+Verdict pobj_cuts(const Params& P, const PlsRec& s, int n, const Hit* const* h, double cut_xy,
+                  double cut_rz, PObj& o) {
+  Verdict v;
   double chi2xy = 0, chi2rz = 0;
   for (int i = 0; i < n; ++i) {
-    const Hit& a = *h[i];
-    double dist = std::sqrt((a.x - cx) * (a.x - cx) + (a.y - cy) * (a.y - cy)) - R;
-    double sxy2 = P.sigma_rphi * P.sigma_rphi + (a.r * P.pls_dir_err) * (a.r * P.pls_dir_err) +
-                  (P.pls_pt_err * a.r * a.r / (2.0 * R)) * (P.pls_pt_err * a.r * a.r / (2.0 * R));
-    chi2xy += dist * dist / sxy2;
-    double sa = arc_s(R, a.r);
-    double zpred = (double)s.z0 + sa * cot;
-    double sz = a.endcap ? P.sigma_r * std::fabs(cot) : P.sigma_z;
-    double th = sa * (1.0 + cot * cot) * P.pls_dir_err;
-    double srz2 = sz * sz + th * th;
-    chi2rz += (a.z - zpred) * (a.z - zpred) / srz2;
+    SeedTerms t = seed_terms(P, s, *h[i]);
+    chi2xy += t.dist * t.dist / t.var_xy;
+    chi2rz += t.dz * t.dz / t.var_rz;
   }
   v.cut(cut_xy, chi2xy);
   v.cut(cut_rz, chi2rz);
@@ -1073,6 +1084,31 @@ void orc_karimaki(int n, const double* x, const double* y, double* out) {
 double orc_line_fit(int n, const double* s, const double* z, const double* sig, double* slope) {
   return line_fit_chi2(n, s, z, sig, *slope);
 }
+// The pT3 / pT5 terms of one seed against n anchors (x, y, z; endcap flag): per anchor
+// (distance from the seed circle, its variance, z offset from the seed line, its variance) in
+// terms[4 n]; chi2[0] = chi2_xy and chi2[1] = chi2_rz summed as the pT3 / pT5 selection sums them.
+void orc_seed_terms(const void* seed, int32_t n, const double* x, const double* y, const double* z,
+                    const int32_t* endcap, double* terms, double* chi2) {
+  Params P = default_params();
+  const PlsRec& s = *static_cast<const PlsRec*>(seed);
+  chi2[0] = chi2[1] = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    Hit a;
+    a.x = x[i]; a.y = y[i]; a.z = z[i];
+    a.r = std::sqrt(a.x * a.x + a.y * a.y);
+    a.phi = std::atan2(a.y, a.x);
+    a.orig = i; a.sensor = 0; a.module = 0;
+    a.endcap = endcap[i] != 0;
+    SeedTerms t = seed_terms(P, s, a);
+    terms[4 * i + 0] = t.dist;
+    terms[4 * i + 1] = t.var_xy;
+    terms[4 * i + 2] = t.dz;
+    terms[4 * i + 3] = t.var_rz;
+    chi2[0] += t.dist * t.dist / t.var_xy;
+    chi2[1] += t.dz * t.dz / t.var_rz;
+  }
+}
+
 int32_t orc_pixel_bin(float eta, float phi, int32_t charge) {
   PlsRec s;
   std::memset(&s, 0, sizeof(s));
