@@ -156,7 +156,8 @@ typedef struct {
 /*
  * Device pointers to one event's objects, inside the context's arenas. Valid until the next
  * lst_run_events on the same context. Objects of each type are dense and ordered: MD by
- * (module, lower hit, upper hit), LS by (inner MD, outer MD), T3 by (inner LS, outer LS), T5 by
+ * (module, lower hit, upper hit) where a module's hits are taken in order of azimuth about the module
+ * centre (ties by input index), LS by (inner MD, outer MD), T3 by (inner LS, outer LS), T5 by
  * (inner T3, outer T3), pT3 / pT5 by (seed, object), TC by (type, sorted hit tuple).
  * Member indices (ls_md_in, t3_ls_in, ...) are event-local indices into the same event's arrays.
  * Hit indices are the event's input hit indices.
@@ -208,6 +209,17 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
                       int32_t n_pix_bins);
 
 /*
+ * The checks lst_load_geometry applies to its tables, on the host alone (no context, no GPU):
+ * module ids equal their index, subdet is 0 or 1, spacing > 0; conn_off starts at 0 and never
+ * decreases, no module has more than 256 connections, every conn_tgt is a module; the pixel map,
+ * when n_pix_bins > 0, has exactly 100 x 128 x 2 bins, pix_off starts at 0 and never decreases, and
+ * every pix_tgt is a module. Returns LST_OK (and the largest module-map degree in *max_degree, which
+ * may be NULL) or LST_EINVAL with the reason in lst_last_error(NULL).
+ */
+int lst_check_geometry(const lst_module* mods, int32_t n_mods, const int32_t* conn_off, const int32_t* conn_tgt,
+                       const int32_t* pix_off, const int32_t* pix_tgt, int32_t n_pix_bins, int32_t* max_degree);
+
+/*
  * Reserve arenas for batches of up to n_events events of up to max_hits hits and max_pls seeds
  * each (optional: lst_run_events grows the arenas on demand).
  */
@@ -253,12 +265,13 @@ int lst_bin_hits(lst_ctx* ctx, const int32_t* d_sensor, int32_t n_hits, int32_t*
  * The paper has no counterpart of this call; it exists for such embedding constraints only.
  *  d_sensor[n_hits] (device, in), d_order[n_hits] and d_offsets[n_sensors + 1] (device, out): as in
  *    lst_bin_hits, with the sensor count given explicitly.
- * The first call on a device looks up the scratch array's device address (a one-time set-up per
- * device, done with that device current); make that first call before any stream capture. Every
- * call on a device shares the one scratch array, so calls whose work overlaps on the GPU (several
- * streams, or several host threads) race and must be serialized by the caller. The call waits for
- * cuda_stream (NULL: the legacy default stream) before returning. Errors: LST_EINVAL for bad sizes
- * or an out-of-range sensor id, LST_ECUDA for a CUDA failure; lst_last_error(NULL) says which.
+ * Each call looks up the scratch array's address on the current device (the lookup allocates
+ * nothing and is not cached, so it stays right after the device's context is reset). Every call on
+ * a device shares the one scratch array, so calls whose work overlaps on the GPU (several streams,
+ * or several host threads) race and must be serialized by the caller. The call waits for
+ * cuda_stream (NULL: the legacy default stream) before returning, because it reads the error word
+ * back to the host. Errors: LST_EINVAL for bad sizes or an out-of-range sensor id, LST_ECUDA for a
+ * CUDA failure; lst_last_error(NULL) says which.
  */
 int lst_bin_hits_noalloc(const int32_t* d_sensor, int32_t n_hits, int32_t n_sensors, int32_t* d_order,
                          int32_t* d_offsets, void* cuda_stream);

@@ -371,6 +371,21 @@ __device__ __forceinline__ bool rz_fit(const Cst<T>& c, T akappa, const T* r, co
 
 __host__ __device__ __forceinline__ int64_t lst_min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
+// Azimuth of (x, y) relative to a module's centre azimuth phic (in [0, 2 pi)), wrapped to
+// (-pi, pi]. Hits are binned, and MDs ordered, by this value; the Line-Segment search windows are
+// taken in it. Every use evaluates this one function, so its float32 rounding is the same everywhere.
+__device__ __forceinline__ float rel_phi(float x, float y, float phic) {
+  float d = atan2f(y, x) - phic;
+  if (d <= -3.14159265f) d += 6.28318531f;
+  if (d > 3.14159265f) d -= 6.28318531f;
+  return d;
+}
+// Unsigned key with the order of the float (for sorting floats as integers)
+__device__ __forceinline__ unsigned float_key(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
 // ---------------------------------------------------------------------------------------------
 // warp helpers
 // ---------------------------------------------------------------------------------------------

@@ -52,10 +52,12 @@ __global__ void k_bin_scatter(Ws w) {
   }
 }
 
-// order each sensor's hits by input index (makes the binning identical to a stable sort), then
-// gather the binned coordinates. Groups of 8 lanes take one sensor each (4 per warp); a hit's
-// position is its rank among the sensor's input indices (unique). Sensors with more than 64 hits
-// are taken by the whole warp (ranks up to 256 hits, else one lane's insertion sort).
+// order each sensor's hits by (azimuth relative to the module centre, input index), then gather the
+// binned coordinates. The MDs of a module, ordered by lower hit, are then in azimuth order of their
+// anchors, which the Line-Segment search uses to take windows of them. The order is a pure function
+// of the input (the keys are unique). Groups of 8 lanes take one sensor each (4 per warp); a hit's
+// position is its rank among the sensor's keys. Sensors with more than 64 hits are taken by the
+// whole warp (ranks up to 256 hits, else one lane's insertion sort).
 constexpr int kBinG = 8;      // lanes per sensor
 constexpr int kBinPer = 8;    // hits per lane in the grouped path
 
@@ -67,23 +69,31 @@ __device__ __forceinline__ void bin_gather(Ws& w, int pos, int src, int h0) {
   w.borig[pos] = src - h0;
 }
 
+// sort key of input hit src on a module of centre azimuth pc: (relative azimuth, input index)
+__device__ __forceinline__ unsigned long long bin_key(const Ws& w, int src, float pc) {
+  return ((unsigned long long)float_key(rel_phi(w.x[src], w.y[src], pc)) << 32) | (unsigned)src;
+}
+
 // the grouped path for sensors of at most kBinG * T hits: lane `sub` of the sensor's group holds
-// hits sub, sub + kBinG, ... and ranks them by the group's input indices
+// hits sub, sub + kBinG, ... and ranks them by the group's keys
 template <int T>
-__device__ __forceinline__ void bin_rank_gather(Ws& w, int a, int n, int sub, int vs, bool valid, int n_sens) {
+__device__ __forceinline__ void bin_rank_gather(Ws& w, const Geo& g, int a, int n, int sub, int vs, bool valid,
+                                                int n_sens) {
   const int h0 = valid ? w.ev_hit_off[vs / n_sens] : 0;
-  int v[T], rk[T];
+  const float pc = valid ? g.phic[(vs % n_sens) >> 1] : 0.f;
+  unsigned long long v[T];
+  int rk[T];
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     const int idx = sub + kBinG * t;
-    v[t] = idx < n ? w.bidx[a + idx] : 0x7fffffff;
+    v[t] = idx < n ? bin_key(w, w.bidx[a + idx], pc) : ~0ull;
     rk[t] = 0;
   }
 #pragma unroll
   for (int t2 = 0; t2 < T; ++t2) {
 #pragma unroll
     for (int s2 = 0; s2 < kBinG; ++s2) {
-      const int vj = __shfl_sync(0xffffffffu, v[t2], s2, kBinG);
+      const unsigned long long vj = __shfl_sync(0xffffffffu, v[t2], s2, kBinG);
 #pragma unroll
       for (int t = 0; t < T; ++t) rk[t] += vj < v[t];
     }
@@ -92,11 +102,11 @@ __device__ __forceinline__ void bin_rank_gather(Ws& w, int a, int n, int sub, in
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     const int idx = sub + kBinG * t;
-    if (idx < n) bin_gather(w, a + rk[t], v[t], h0);
+    if (idx < n) bin_gather(w, a + rk[t], (int)(unsigned)(v[t] & 0xffffffffu), h0);
   }
 }
 
-__global__ void k_bin_sort_gather(Ws w, int n_sens) {
+__global__ void k_bin_sort_gather(Ws w, Geo g, int n_sens) {
   const int lane = threadIdx.x & 31;
   const int tile = lane / kBinG, sub = lane % kBinG;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -113,14 +123,14 @@ __global__ void k_bin_sort_gather(Ws w, int n_sens) {
       // T = hits per lane, uniform over the warp: the rank loops are unrolled for each T, so that a
       // warp of small sensors (most hold a few hits) runs only the comparisons it needs
       switch ((nmax + kBinG - 1) / kBinG) {
-        case 1: bin_rank_gather<1>(w, a, n, sub, vs, valid, n_sens); break;
-        case 2: bin_rank_gather<2>(w, a, n, sub, vs, valid, n_sens); break;
-        case 3: bin_rank_gather<3>(w, a, n, sub, vs, valid, n_sens); break;
-        case 4: bin_rank_gather<4>(w, a, n, sub, vs, valid, n_sens); break;
-        case 5: bin_rank_gather<5>(w, a, n, sub, vs, valid, n_sens); break;
-        case 6: bin_rank_gather<6>(w, a, n, sub, vs, valid, n_sens); break;
-        case 7: bin_rank_gather<7>(w, a, n, sub, vs, valid, n_sens); break;
-        default: bin_rank_gather<8>(w, a, n, sub, vs, valid, n_sens); break;
+        case 1: bin_rank_gather<1>(w, g, a, n, sub, vs, valid, n_sens); break;
+        case 2: bin_rank_gather<2>(w, g, a, n, sub, vs, valid, n_sens); break;
+        case 3: bin_rank_gather<3>(w, g, a, n, sub, vs, valid, n_sens); break;
+        case 4: bin_rank_gather<4>(w, g, a, n, sub, vs, valid, n_sens); break;
+        case 5: bin_rank_gather<5>(w, g, a, n, sub, vs, valid, n_sens); break;
+        case 6: bin_rank_gather<6>(w, g, a, n, sub, vs, valid, n_sens); break;
+        case 7: bin_rank_gather<7>(w, g, a, n, sub, vs, valid, n_sens); break;
+        default: bin_rank_gather<8>(w, g, a, n, sub, vs, valid, n_sens); break;
       }
       continue;
     }
@@ -131,18 +141,20 @@ __global__ void k_bin_sort_gather(Ws w, int n_sens) {
       const int aq = w.sens_off[vq], nq = w.sens_off[vq + 1] - aq;
       if (nq == 0) continue;
       const int h0 = w.ev_hit_off[vq / n_sens];
+      const float pc = g.phic[(vq % n_sens) >> 1];
       if (nq <= 256) {
-        int vv[8], rr[8];
+        unsigned long long vv[8];
+        int rr[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-          vv[t] = lane + 32 * t < nq ? w.bidx[aq + lane + 32 * t] : 0x7fffffff;
+          vv[t] = lane + 32 * t < nq ? bin_key(w, w.bidx[aq + lane + 32 * t], pc) : ~0ull;
           rr[t] = 0;
         }
         for (int j0 = 0; j0 < nq; j0 += 32) {
-          const int own = j0 + lane < nq ? w.bidx[aq + j0 + lane] : 0x7fffffff;
+          const unsigned long long own = j0 + lane < nq ? bin_key(w, w.bidx[aq + j0 + lane], pc) : ~0ull;
           const int m = min(32, nq - j0);
           for (int j = 0; j < m; ++j) {
-            const int vj = __shfl_sync(0xffffffffu, own, j);
+            const unsigned long long vj = __shfl_sync(0xffffffffu, own, j);
 #pragma unroll
             for (int t = 0; t < 8; ++t) rr[t] += vj < vv[t];
           }
@@ -150,13 +162,14 @@ __global__ void k_bin_sort_gather(Ws w, int n_sens) {
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-          if (lane + 32 * t < nq) bin_gather(w, aq + rr[t], vv[t], h0);
+          if (lane + 32 * t < nq) bin_gather(w, aq + rr[t], (int)(unsigned)(vv[t] & 0xffffffffu), h0);
       } else {
         if (lane == 0) {
           for (int i = aq + 1; i < aq + nq; ++i) {
             const int val = w.bidx[i];
+            const unsigned long long kv = bin_key(w, val, pc);
             int j = i - 1;
-            while (j >= aq && w.bidx[j] > val) {
+            while (j >= aq && bin_key(w, w.bidx[j], pc) > kv) {
               w.bidx[j + 1] = w.bidx[j];
               --j;
             }
@@ -191,6 +204,8 @@ __global__ void k_md_caps(Ws w) {
     const int c = clamp_cap(pred, nlo * nup, w.md_ovr[vm]);
     w.md_cap[vm] = c;
     w.md_base[vm] = c;
+    w.md_rmin[vm] = 0x7f800000;   // +inf: the dense pass takes the minimum anchor radius
+    w.md_rmax[vm] = 0;
   }
 }
 
@@ -387,6 +402,15 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
     w.md_xyzr[d] = make_float4(x, y, w.bz[lo], r);
     w.md_sa[d] = make_float2(sthr, alpha);
     w.md_ec[d] = g.endcap[vm % g.n_mods];
+    w.md_rphi[d] = rel_phi(x, y, g.phic[vm % g.n_mods]);
+    // radius range of the module's anchors (r >= 0: float bits order like the values), one atomic
+    // per module and warp (a module's MDs are contiguous)
+    const unsigned grp = __match_any_sync(__activemask(), vm);
+    const int rmin = __reduce_min_sync(grp, __float_as_int(r)), rmax = __reduce_max_sync(grp, __float_as_int(r));
+    if ((threadIdx.x & 31) == __ffs(grp) - 1) {
+      atomicMin(&w.md_rmin[vm], rmin);
+      atomicMax(&w.md_rmax[vm], rmax);
+    }
   }
 }
 
@@ -773,7 +797,7 @@ void run_binning(const Ws& w, const Geo& g, const Launch& L) {
   k_bin_scatter<<<grid_for(w.H, 256), 256, 0, L.stream>>>(w);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_BIN);
-  k_bin_sort_gather<<<grid_for((int64_t)w.S * 8, 256, 152 * 32), 256, 0, L.stream>>>(w, n_sens);
+  k_bin_sort_gather<<<grid_for((int64_t)w.S * 8, 256, 152 * 32), 256, 0, L.stream>>>(w, g, n_sens);
   KT_END(L, K_BIN);
   LST_LAUNCH(L);
 }

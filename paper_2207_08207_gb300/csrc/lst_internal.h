@@ -15,6 +15,7 @@ struct Geo {
   int32_t n_pix_bins = 0;
   const uint8_t* endcap = nullptr;   // [n_mods] 1 for endcap modules
   const float* spacing = nullptr;    // [n_mods]
+  const float* phic = nullptr;       // [n_mods] centre azimuth of each module, (phi_lo + phi_hi) / 2
   const int32_t* conn_off = nullptr; // [n_mods + 1]
   const int32_t* conn_tgt = nullptr;
   const int32_t* pix_off = nullptr;  // [n_pix_bins + 1]
@@ -83,6 +84,10 @@ struct Ws {
   float2* md_sa = nullptr;       // [md_dense] (arc length at R_thr, alpha_thr(r) = asin(min(r k / (2 pT_thr), sin_max)))
   float *md_dpc = nullptr, *md_pte = nullptr;
   uint8_t* md_ec = nullptr;
+  float* md_rphi = nullptr;      // [md_dense] anchor azimuth relative to its module's centre, (-pi, pi]:
+                                 // the MDs of a module are ordered by it (hits are binned in azimuth order)
+  int32_t *md_rmin = nullptr, *md_rmax = nullptr;   // [V] smallest / largest anchor radius of each
+                                                    // module's MDs (float bits; set by k_md_dense)
   // LS
   int32_t *ls_cap = nullptr, *ls_base = nullptr, *ls_cnt = nullptr, *ls_ovr = nullptr;
   int32_t *lss_in = nullptr, *lss_out = nullptr;

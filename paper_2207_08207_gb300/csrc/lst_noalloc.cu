@@ -8,7 +8,6 @@
 // synchronize the device in the middle of its event loop). lst_bin_hits_noalloc() serves them: its
 // scratch is one file-scope __device__ array of fixed size, which exists on every GPU that loads this
 // library for as long as the process runs, so the call itself allocates nothing.
-#include <mutex>
 #include <string>
 
 #include "lst_internal.h"
@@ -23,25 +22,15 @@ constexpr int kNoAllocWords = 2 * kNoAllocMaxSensors + 1 + 64;
 
 static __device__ __align__(256) int32_t g_bin_scratch[kNoAllocWords];
 
-// Host code cannot use g_bin_scratch's name as a device address: it resolves it once per device,
-// with that device current, and keeps the result.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-int32_t* g_scratch_dev[kMaxDevices] = {};
-
+// Host code cannot use g_bin_scratch's name as a device address: every call resolves it for the
+// current device, with that device current. The lookup allocates nothing; it is not cached, because
+// the address belongs to the device's context and changes when that context is destroyed and
+// created again (cudaDeviceReset), and a cached address would then point at freed memory.
 cudaError_t scratch_for_current_device(int32_t** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_dev[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_bin_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_dev[dev] = static_cast<int32_t*>(p);
-  }
-  *out = g_scratch_dev[dev];
+  *out = static_cast<int32_t*>(p);
   return cudaSuccess;
 }
 

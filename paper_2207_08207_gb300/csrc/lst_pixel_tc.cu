@@ -891,10 +891,13 @@ __global__ void __launch_bounds__(1024) k_tc_sort(Ws w, Geo g) {
   const unsigned long long* key = w.tc_key + region;
   const int* hk = w.tc_hit_key + (int64_t)region * 14;
   int* perm = w.tc_perm + region;
-  if (n > kTcSortMax) {   // ranks counted directly
+  if (n > kTcSortMax) {   // ranks counted directly, equal tuples ordered by collected index as below
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       int rank = 0;
-      for (int j = 0; j < n; ++j) rank += hit_key_cmp(hk + (int64_t)j * 14, hk + (int64_t)k * 14) < 0;
+      for (int j = 0; j < n; ++j) {
+        const int cmp = hit_key_cmp(hk + (int64_t)j * 14, hk + (int64_t)k * 14);
+        rank += cmp < 0 || (cmp == 0 && j < k);
+      }
       perm[rank] = k;
     }
     return;

@@ -393,7 +393,8 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.md_lo, c.md_dense); pl.add(w.md_up, c.md_dense); pl.add(w.md_vm, c.md_dense);
   pl.add(w.md_rlo, c.md_dense);
   pl.add(w.md_dpc, c.md_dense); pl.add(w.md_pte, c.md_dense); pl.add(w.md_ec, c.md_dense);
-  pl.add(w.md_xyzr, c.md_dense); pl.add(w.md_sa, c.md_dense);
+  pl.add(w.md_xyzr, c.md_dense); pl.add(w.md_sa, c.md_dense); pl.add(w.md_rphi, c.md_dense);
+  pl.add(w.md_rmin, V); pl.add(w.md_rmax, V);
   // LS
   pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1); pl.add(w.lsin_off, c.md_dense + 2);
   pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
@@ -686,51 +687,71 @@ void lst_destroy(lst_ctx* ctx) {
   delete ctx;
 }
 
+int lst_check_geometry(const lst_module* mods, int32_t n_mods, const int32_t* conn_off, const int32_t* conn_tgt,
+                       const int32_t* pix_off, const int32_t* pix_tgt, int32_t n_pix_bins, int32_t* max_degree) {
+  lst_ctx* none = nullptr;   // messages go to lst_last_error(NULL)
+  if (!mods || n_mods <= 0 || !conn_off) return fail(none, LST_EINVAL, "lst_load_geometry: empty module table");
+  if (n_pix_bins < 0 || (n_pix_bins > 0 && !pix_off)) return fail(none, LST_EINVAL, "lst_load_geometry: bad pixel map");
+  if (n_pix_bins > 0 && n_pix_bins != kPixNEta * kPixNPhi * 2)
+    return fail(none, LST_EINVAL, "lst_load_geometry: the pixel map must have 100 x 128 x 2 bins");
+  if (conn_off[0] != 0) return fail(none, LST_EINVAL, "lst_load_geometry: conn_off[0] != 0");
+  int32_t maxdeg = 0;
+  for (int32_t m = 0; m < n_mods; ++m) {
+    if (mods[m].id != m) return fail(none, LST_EINVAL, "lst_load_geometry: module ids must equal their index");
+    if (mods[m].subdet != 0 && mods[m].subdet != 1) return fail(none, LST_EINVAL, "lst_load_geometry: bad subdet");
+    if (!(mods[m].spacing > 0.f)) return fail(none, LST_EINVAL, "lst_load_geometry: spacing must be positive");
+    const int32_t d = conn_off[m + 1] - conn_off[m];
+    if (d < 0) return fail(none, LST_EINVAL, "lst_load_geometry: conn_off not monotone");
+    maxdeg = std::max(maxdeg, d);
+  }
+  if (maxdeg > 256) return fail(none, LST_EINVAL, "lst_load_geometry: a module has more than 256 connections");
+  const int32_t n_conn = conn_off[n_mods];
+  if (n_conn > 0 && !conn_tgt) return fail(none, LST_EINVAL, "lst_load_geometry: conn_tgt is NULL");
+  for (int32_t k = 0; k < n_conn; ++k)
+    if (conn_tgt[k] < 0 || conn_tgt[k] >= n_mods)
+      return fail(none, LST_EINVAL, "lst_load_geometry: conn_tgt out of range");
+  if (n_pix_bins > 0) {
+    if (pix_off[0] != 0) return fail(none, LST_EINVAL, "lst_load_geometry: pix_off[0] != 0");
+    for (int32_t b = 0; b < n_pix_bins; ++b)
+      if (pix_off[b + 1] < pix_off[b]) return fail(none, LST_EINVAL, "lst_load_geometry: pix_off not monotone");
+    const int32_t n_pix = pix_off[n_pix_bins];
+    if (n_pix > 0 && !pix_tgt) return fail(none, LST_EINVAL, "lst_load_geometry: pix_tgt is NULL");
+    for (int32_t k = 0; k < n_pix; ++k)
+      if (pix_tgt[k] < 0 || pix_tgt[k] >= n_mods)
+        return fail(none, LST_EINVAL, "lst_load_geometry: pix_tgt out of range");
+  }
+  if (max_degree) *max_degree = maxdeg;
+  return LST_OK;
+}
+
 int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, const int32_t* conn_off,
                       const int32_t* conn_tgt, const int32_t* pix_off, const int32_t* pix_tgt,
                       int32_t n_pix_bins) {
   if (!ctx) return LST_EINVAL;
   if (ctx->pending) return fail(ctx, LST_ESTATE, "lst_load_geometry: a run is in flight");
-  if (!mods || n_mods <= 0 || !conn_off) return fail(ctx, LST_EINVAL, "lst_load_geometry: empty module table");
-  if (n_pix_bins < 0 || (n_pix_bins > 0 && !pix_off)) return fail(ctx, LST_EINVAL, "lst_load_geometry: bad pixel map");
-  if (n_pix_bins > 0 && n_pix_bins != kPixNEta * kPixNPhi * 2)
-    return fail(ctx, LST_EINVAL, "lst_load_geometry: the pixel map must have 100 x 128 x 2 bins");
-  if (conn_off[0] != 0) return fail(ctx, LST_EINVAL, "lst_load_geometry: conn_off[0] != 0");
   int32_t maxdeg = 0;
-  for (int32_t m = 0; m < n_mods; ++m) {
-    if (mods[m].id != m) return fail(ctx, LST_EINVAL, "lst_load_geometry: module ids must equal their index");
-    if (mods[m].subdet != 0 && mods[m].subdet != 1) return fail(ctx, LST_EINVAL, "lst_load_geometry: bad subdet");
-    if (!(mods[m].spacing > 0.f)) return fail(ctx, LST_EINVAL, "lst_load_geometry: spacing must be positive");
-    const int32_t d = conn_off[m + 1] - conn_off[m];
-    if (d < 0) return fail(ctx, LST_EINVAL, "lst_load_geometry: conn_off not monotone");
-    maxdeg = std::max(maxdeg, d);
-  }
-  if (maxdeg > 256) return fail(ctx, LST_EINVAL, "lst_load_geometry: a module has more than 256 connections");
+  const int vrc = lst_check_geometry(mods, n_mods, conn_off, conn_tgt, pix_off, pix_tgt, n_pix_bins, &maxdeg);
+  if (vrc != LST_OK) return fail(ctx, vrc, g_create_error);
   const int32_t n_conn = conn_off[n_mods];
-  if (n_conn > 0 && !conn_tgt) return fail(ctx, LST_EINVAL, "lst_load_geometry: conn_tgt is NULL");
-  for (int32_t k = 0; k < n_conn; ++k)
-    if (conn_tgt[k] < 0 || conn_tgt[k] >= n_mods) return fail(ctx, LST_EINVAL, "lst_load_geometry: conn_tgt out of range");
-  int32_t n_pix = 0;
-  if (n_pix_bins > 0) {
-    if (pix_off[0] != 0) return fail(ctx, LST_EINVAL, "lst_load_geometry: pix_off[0] != 0");
-    for (int32_t b = 0; b < n_pix_bins; ++b)
-      if (pix_off[b + 1] < pix_off[b]) return fail(ctx, LST_EINVAL, "lst_load_geometry: pix_off not monotone");
-    n_pix = pix_off[n_pix_bins];
-    if (n_pix > 0 && !pix_tgt) return fail(ctx, LST_EINVAL, "lst_load_geometry: pix_tgt is NULL");
-    for (int32_t k = 0; k < n_pix; ++k)
-      if (pix_tgt[k] < 0 || pix_tgt[k] >= n_mods) return fail(ctx, LST_EINVAL, "lst_load_geometry: pix_tgt out of range");
-  }
+  const int32_t n_pix = n_pix_bins > 0 ? pix_off[n_pix_bins] : 0;
   CK(cudaSetDevice(ctx->device));
   CK(cudaStreamSynchronize(ctx->stream));
   std::vector<uint8_t> ec(n_mods);
-  std::vector<float> sp(n_mods);
+  std::vector<float> sp(n_mods), pc(n_mods);
   for (int32_t m = 0; m < n_mods; ++m) {
     ec[m] = (uint8_t)mods[m].subdet;
     sp[m] = mods[m].spacing;
+    // centre azimuth in [0, 2 pi) (used only to order hits and to centre search windows; any value
+    // is valid, a module's true centre keeps its hits away from the wrap at +-pi)
+    double c = 0.5 * ((double)mods[m].phi_lo + (double)mods[m].phi_hi);
+    c = std::fmod(c, 6.283185307179586);
+    if (!(c >= 0.0)) c = std::isfinite(c) ? c + 6.283185307179586 : 0.0;
+    pc[m] = (float)c;
   }
   Planner pl;
-  uint8_t* d_ec = nullptr; float* d_sp = nullptr; int32_t *d_co = nullptr, *d_ct = nullptr, *d_po = nullptr, *d_pt = nullptr;
-  pl.add(d_ec, n_mods); pl.add(d_sp, n_mods); pl.add(d_co, n_mods + 1); pl.add(d_ct, n_conn);
+  uint8_t* d_ec = nullptr; float *d_sp = nullptr, *d_pc = nullptr;
+  int32_t *d_co = nullptr, *d_ct = nullptr, *d_po = nullptr, *d_pt = nullptr;
+  pl.add(d_ec, n_mods); pl.add(d_sp, n_mods); pl.add(d_pc, n_mods); pl.add(d_co, n_mods + 1); pl.add(d_ct, n_conn);
   pl.add(d_po, n_pix_bins + 1); pl.add(d_pt, n_pix);
   const size_t bytes = pl.layout();
   if (ctx->geo_mem) CK(cudaFree(ctx->geo_mem));
@@ -740,6 +761,7 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   pl.assign(ctx->geo_mem);
   CK(cudaMemcpy(d_ec, ec.data(), n_mods, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_sp, sp.data(), n_mods * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_pc, pc.data(), n_mods * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_co, conn_off, (n_mods + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
   if (n_conn) CK(cudaMemcpy(d_ct, conn_tgt, n_conn * sizeof(int32_t), cudaMemcpyHostToDevice));
   if (n_pix_bins > 0) {
@@ -750,6 +772,7 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   ctx->geo.n_pix_bins = n_pix_bins;
   ctx->geo.endcap = d_ec;
   ctx->geo.spacing = d_sp;
+  ctx->geo.phic = d_pc;
   ctx->geo.conn_off = d_co;
   ctx->geo.conn_tgt = d_ct;
   ctx->geo.pix_off = d_po;

@@ -129,6 +129,8 @@ def lib():
         L.lst_last_error.argtypes = [ctypes.c_void_p]
         L.lst_last_error.restype = ctypes.c_char_p
         L.lst_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
+        L.lst_check_geometry.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 4 + \
+            [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         _lib = L
         return L
 
@@ -322,6 +324,9 @@ class Context:
 
     def bin_hits(self, sensor_dev, order_dev, offsets_dev, stream=None):
         """Standalone hit binning of one event (torch CUDA int32 tensors)."""
+        _check_dev_i32("sensor", sensor_dev, 0)
+        _check_dev_i32("order", order_dev, int(sensor_dev.numel()))
+        _check_dev_i32("offsets", offsets_dev, 2 * self.det.n_mods + 1)
         st = None
         if stream is not None:
             st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -347,9 +352,23 @@ class Context:
         return algorithmic_bytes(kernel, counts, n_hits, n_pls)
 
 
+def _check_dev_i32(name, t, n_min):
+    """The C call writes and reads through raw pointers: each tensor must be a contiguous CUDA int32
+    tensor holding at least n_min elements."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+        raise LSTError(LST_EINVAL, f"{name}: expected a contiguous CUDA int32 tensor")
+    if t.numel() < n_min:
+        raise LSTError(LST_EINVAL, f"{name}: {t.numel()} elements, at least {n_min} needed")
+
+
 def bin_hits_noalloc(sensor_dev, n_sensors, order_dev, offsets_dev, stream=None):
     """Hit binning without any device allocation (lst_bin_hits_noalloc): for callers whose device
     memory is fixed up front. torch CUDA int32 tensors; at most 65536 sensors."""
+    n_hits = int(sensor_dev.numel()) if hasattr(sensor_dev, "numel") else -1
+    _check_dev_i32("sensor", sensor_dev, 0)
+    _check_dev_i32("order", order_dev, n_hits)
+    _check_dev_i32("offsets", offsets_dev, int(n_sensors) + 1)
     L = lib()
     st = None
     if stream is not None:
@@ -358,6 +377,28 @@ def bin_hits_noalloc(sensor_dev, n_sensors, order_dev, offsets_dev, stream=None)
                                 _ptr(offsets_dev), st)
     if rc != LST_OK:
         raise LSTError(rc, L.lst_last_error(None).decode())
+
+
+def check_geometry(mods, conn_off, conn_tgt, pix_off=None, pix_tgt=None):
+    """lst_check_geometry on host tables (needs no GPU): returns the largest module-map degree or
+    raises LSTError(LST_EINVAL) with the library's reason."""
+    L = lib()
+    mods = np.ascontiguousarray(mods)
+    co = np.ascontiguousarray(conn_off, dtype=np.int32)
+    ct = np.ascontiguousarray(conn_tgt, dtype=np.int32)
+    n_pix = 0
+    po = pt = None
+    if pix_off is not None:
+        po = np.ascontiguousarray(pix_off, dtype=np.int32)
+        pt = np.ascontiguousarray(pix_tgt, dtype=np.int32)
+        n_pix = int(po.size - 1)
+    deg = ctypes.c_int32(-1)
+    rc = L.lst_check_geometry(_ptr(mods) if mods.size else None, int(mods.size), _ptr(co) if co.size else None,
+                              _ptr(ct) if ct.size else None, _ptr(po) if po is not None else None,
+                              _ptr(pt) if pt is not None and pt.size else None, n_pix, ctypes.byref(deg))
+    if rc != LST_OK:
+        raise LSTError(rc, L.lst_last_error(None).decode())
+    return int(deg.value)
 
 
 def selftest_bounded_wait(device: int = 0) -> int:

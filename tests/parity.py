@@ -133,9 +133,15 @@ def compare_event(ref, got, ev=None, check_floats=True) -> dict:
                 tainted_etaphi.append((float(ev.pls["eta"][p]), float(ev.pls["phi"][p])))
                 tainted_hits.update(int(h) for h in ev.pls["pix_hit"][p])
     rep["n_borderline"] = n_border
+    rep["n_objects"] = n_all + n_border
     rep["borderline_fraction"] = n_border / max(1, n_all + n_border)
-    if rep["borderline_fraction"] >= 1e-4 and n_all + n_border > 1e4:
-        rep["errors"].append(f"borderline fraction {rep['borderline_fraction']:.2e} >= 1e-4")
+    # borderline objects must stay below 1e-4 of all objects at every size: below 1e4 objects that
+    # allows at most one (the limit rounded up)
+    if n_all + n_border > 1e4:
+        if rep["borderline_fraction"] >= 1e-4:
+            rep["errors"].append(f"borderline fraction {rep['borderline_fraction']:.2e} >= 1e-4")
+    elif n_border > 1:
+        rep["errors"].append(f"{n_border} borderline objects among {n_all + n_border} (at most 1 below 1e4)")
 
     # referential integrity of the GPU arrays
     nmd, nls, nt3, nt5 = (len(gk[s]) for s in ("md", "ls", "t3", "t5"))

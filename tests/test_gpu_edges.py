@@ -1,0 +1,57 @@
+"""Edge cases of the CUDA chain beyond the parity events: more than 8192 track candidates of one
+type in one event (the track-candidate sort's rank-count path, used above its shared-memory sort's
+size), with duplicated seeds whose hit tuples are equal (the order must still be a permutation)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_08207_gb300 import gen, lst
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _seeds_only_event(n, seed):
+    """An event without outer-tracker hits and n pixel seeds: every seed becomes a pLS track
+    candidate (no pT3 / pT5 can form, and pLS are not cleaned against each other). Seeds 2k and
+    2k + 1 carry the same pixel hit ids, so their sorted hit tuples are equal."""
+    rng = np.random.default_rng(seed)
+    pls = np.zeros(n, dtype=gen.PLS_DTYPE)
+    pls["pt"] = rng.uniform(1.0, 5.0, n)
+    pls["eta"] = rng.uniform(-2.4, 2.4, n)
+    pls["phi"] = rng.uniform(-np.pi, np.pi, n)
+    pls["z0"] = rng.normal(0, 5, n)
+    pls["charge"] = rng.choice([-1, 1], n)
+    ids = rng.permutation(4 * n).reshape(n, 4).astype(np.int32)
+    ids[1::2] = ids[0::2][: n // 2]
+    pls["pix_hit"] = ids
+    e = np.zeros(0, np.float32)
+    return gen.Event(x=e, y=e, z=e, sensor=np.zeros(0, np.int32), pls=pls,
+                     hit_particle=np.zeros(0, np.int32), pls_particle=np.arange(n, dtype=np.int32),
+                     particles={})
+
+
+@pytest.mark.parametrize("n", [9000, 8192])
+def test_many_pls_candidates_sorted_as_permutation(n):
+    det = gen.make_detector(barrel_only=False, pt_thr=0.8)
+    ev = _seeds_only_event(n, seed=n)
+    ctx = lst.Context(det)
+    try:
+        ctx.run([ev])
+        got = ctx.results(0)
+    finally:
+        ctx.close()
+    assert got["counts"]["n_tc"] == n
+    assert np.all(got["tc_type"] == lst.TC_TYPES.index("pLS"))
+    obj = got["tc_obj"]
+    assert np.array_equal(np.sort(obj), np.arange(n))          # every seed exactly once
+    assert np.array_equal(got["tc_hits"][:, :4], ev.pls["pix_hit"][obj])   # each row holds its seed's hits
+    assert np.all(got["tc_hits"][:, 4:] == -1)
+    rows = np.sort(got["tc_hits"][:, :4], axis=1)
+    keys = [tuple(r) for r in rows]
+    assert keys == sorted(keys)                                 # rows ordered by sorted hit tuple
+    ref = oracle.run(det, ev)
+    rt = ref["tc"]
+    ref_rows = sorted(tuple(sorted(int(rt[f"hit{k}"][i]) for k in range(4))) for i in range(len(rt["type"])))
+    assert ref_rows == keys
