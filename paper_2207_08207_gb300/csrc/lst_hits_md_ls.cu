@@ -417,7 +417,6 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
 // ---------------------------------------------------------------------------------------------
 // Line Segments
 // ---------------------------------------------------------------------------------------------
-constexpr int kMaxTargets = 256;   // module-map degree limit (checked when loading the geometry)
 
 __device__ __forceinline__ int md_count(const Ws& w, int vm) { return w.md_off[vm + 1] - w.md_off[vm]; }
 
@@ -497,27 +496,78 @@ __global__ void k_ls_work_fill(Ws w) {
 }
 
 // One warp per work item at a time: a module, or, in small batches, one of up to kLsMaxChunks equal
-// chunks of a heavy module's outer MDs (so that one module does not hold the whole launch). Each
-// lane holds one MD of the connected modules (B) in registers
-// and sweeps the module's own MDs (A, staged in shared memory): a conservative division-free test
-// (below) rejects most pairs, and the survivors go to a per-warp queue that carries over from module
-// to module; whenever it holds 32 pairs, every lane takes one of them through the full evaluation, so
-// the expensive path runs with a full warp. Persistent mode: the grid holds every resident warp and
-// the warps take the cost-ordered work list in a boustrophedon order (heaviest modules first, one
-// pass forward and the next backward, which evens out the sums); otherwise warps stride over all
-// modules in index order.
+// chunks of a heavy module's candidate outer MDs (so that one module does not hold the whole launch).
+// The module's own MDs (A) are staged 32 at a time in shared memory; each lane holds one MD of the
+// connected modules (B) in registers and sweeps the staged A. The MDs of every module are ordered by
+// anchor azimuth about the module centre (the binning orders hits so), so for each staged chunk of A
+// only a contiguous window of each connected module's MDs can pass the azimuth cut: the window
+// [min phi_A - W, max phi_A + W] (in B's own azimuth frame), W an upper bound of the cut's
+// bound over the chunk's and the target's radius ranges (alpha_thr(r2max) - alpha_thr(r1min) +
+// (n_sigma sigma_rphi + d0_max)(1 / r1min + 1 / r2min), plus a margin far above the float32 error of
+// the azimuths), is found by two binary searches per target and only those B are swept. A pair
+// outside the window fails the exact azimuth cut, so the skipped pairs are ones every evaluation
+// rejects. Inside it a conservative division-free test (below) rejects most pairs, and the survivors
+// go to a per-warp queue that carries over from item to item; whenever it holds 32 pairs, every lane
+// takes one of them through the full evaluation, so the expensive path runs with a full warp.
+// Persistent mode: the grid holds every resident warp and the warps take the cost-ordered work list
+// in a boustrophedon order (heaviest modules first, one pass forward and the next backward, which
+// evens out the sums); otherwise warps stride over all modules in index order.
 constexpr int kLsAW = 32;   // inner MDs staged per chunk
 constexpr int kLsQ = 64;    // survivor queue per warp (at most 31 carried + 32 new)
 
-struct LsWarpSmem {
-  int tpre[kMaxTargets + 1];   // prefix of the MD counts of the connected modules
-  int tbase[kMaxTargets];      // their first dense MD
-  uint8_t tec[kMaxTargets];    // their endcap flag
-  float4 a_xyzr[kLsAW];
-  float2 a_sal[kLsAW];         // (arc length at threshold, alpha)
-  int a_id[kLsAW];
-  int q_vm[kLsQ], q_a[kLsQ], q_b[kLsQ];
+// Per-warp shared memory of k_ls: T target slots (the loaded map's largest degree rounded up to 32).
+struct LsSmem {
+  float4* a_xyzr;   // [kLsAW] staged inner anchors (x, y, z, r)
+  float4* tinfo;    // [T] per connected module: (its centre azimuth relative to A's, alpha_thr of its
+                    //     largest anchor radius, 1 / its smallest anchor radius, endcap flag)
+  float2* a_sal;    // [kLsAW] (arc length at threshold, alpha)
+  int2* tbc;        // [T] (first dense MD, MD count) of each connected module
+  int* wpre;        // [T + 1] prefix of the window sizes of the current inner chunk
+  int* wbeg;        // [T] first dense MD of each window
+  int* a_id;        // [kLsAW]
+  int *q_vm, *q_a, *q_b;   // [kLsQ] survivor queue
 };
+
+__host__ __device__ inline size_t ls_smem_per_warp(int T) {
+  const size_t b = (size_t)kLsAW * 16 + (size_t)T * 16 + (size_t)kLsAW * 8 + (size_t)T * 8 + (size_t)(T + 1) * 4 +
+                   (size_t)T * 4 + (size_t)kLsAW * 4 + 3 * (size_t)kLsQ * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ LsSmem ls_smem(unsigned char* base, int T) {
+  LsSmem S;
+  unsigned char* p = base;
+  S.a_xyzr = reinterpret_cast<float4*>(p); p += kLsAW * 16;
+  S.tinfo = reinterpret_cast<float4*>(p); p += T * 16;
+  S.a_sal = reinterpret_cast<float2*>(p); p += kLsAW * 8;
+  S.tbc = reinterpret_cast<int2*>(p); p += T * 8;
+  S.wpre = reinterpret_cast<int*>(p); p += (T + 1) * 4;
+  S.wbeg = reinterpret_cast<int*>(p); p += T * 4;
+  S.a_id = reinterpret_cast<int*>(p); p += kLsAW * 4;
+  S.q_vm = reinterpret_cast<int*>(p); p += kLsQ * 4;
+  S.q_a = reinterpret_cast<int*>(p); p += kLsQ * 4;
+  S.q_b = reinterpret_cast<int*>(p);
+  return S;
+}
+
+// first index k in [0, n) with v[k] >= x (n if none); v sorted ascending
+__device__ __forceinline__ int lower_bound_f(const float* v, int n, float x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+// first index k in [0, n) with v[k] > x (n if none)
+__device__ __forceinline__ int upper_bound_f(const float* v, int n, float x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
 
 // Quick rejection of an (a, b) pair, exact-safe: it returns true only when the float64 evaluation
 // is certain to reject, with margins far above the float32 rounding of the anchors and of this
@@ -552,7 +602,7 @@ __device__ __forceinline__ bool ls_quick_reject(const Cst<float>& c, float4 a, f
 
 
 // full float32 evaluation of the first n (<= 32) queued pairs, one per lane; called by the whole warp
-__device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const LsWarpSmem& S, int n) {
+__device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const LsSmem& S, int n) {
   const int lane = lane_id();
   int v = kReject, vm = 0, a = 0, b = 0;
   float z0 = 0.f, dphi = 0.f;
@@ -581,12 +631,15 @@ __device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const
 }
 
 __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persistent) {
-  extern __shared__ __align__(16) unsigned char ls_smem[];
-  LsWarpSmem& S = reinterpret_cast<LsWarpSmem*>(ls_smem)[threadIdx.x >> 5];
+  extern __shared__ __align__(16) unsigned char ls_smem_raw[];
+  const int T = g.ls_tcap;
+  const LsSmem S = ls_smem(ls_smem_raw + (threadIdx.x >> 5) * ls_smem_per_warp(T), T);
   const int lane = lane_id();
   const int n_warps = gridDim.x * (blockDim.x >> 5);
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int n_items = persistent ? w.work_off[32] : w.V;
+  const float kwin = c.n_sigma * c.sigma_rphi + c.d0_max;
+  const float kPiF = 3.14159265f;
   int qn = 0;   // pairs waiting in this warp's queue
   const long long t0 = clock64();
   for (int sweep = 0; (int64_t)sweep * n_warps < n_items; ++sweep) {
@@ -599,36 +652,24 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
     const int na = md_count(w, vm);
     if (na == 0) continue;
     const int m = vm % g.n_mods, e0 = vm - m;
-    const int t0 = g.conn_off[m];
-    const int nt = min(g.conn_off[m + 1] - t0, kMaxTargets);
-    // target prefix by a warp scan, 32 targets at a time
-    int run = 0;
-    for (int t = lane; t - lane < nt; t += 32) {
-      int cnt = 0;
-      if (t < nt) {
-        const int tm = g.conn_tgt[t0 + t];
-        const int vb = e0 + tm;
-        cnt = md_count(w, vb);
-        S.tbase[t] = w.md_off[vb];
-        S.tec[t] = g.endcap[tm];
+    const int t0c = g.conn_off[m];
+    const int nt = min(g.conn_off[m + 1] - t0c, T);
+    const float pcA = g.phic[m];
+    // the connected modules: their MD ranges and the window parameters that depend on them alone
+    for (int t = lane; t < nt; t += 32) {
+      const int tm = g.conn_tgt[t0c + t];
+      const int vb = e0 + tm;
+      const int cnt = md_count(w, vb);
+      float dpc = 0.f, al2 = 0.f, ir2 = 0.f;
+      if (cnt > 0) {
+        dpc = pcA - g.phic[tm];
+        if (dpc > kPiF) dpc -= 6.28318531f;
+        if (dpc <= -kPiF) dpc += 6.28318531f;
+        al2 = asinf(fminf(__int_as_float(w.md_rmax[vb]) * c.k2p, c.sin_max));
+        ir2 = 1.0f / __int_as_float(w.md_rmin[vb]);
       }
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (t < nt) S.tpre[t + 1] = run + incl;
-      run += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) S.tpre[0] = 0;
-    const int totB = run;
-    // this item's outer MDs: chunk `chunk` of the module's nch equal chunks
-    const int csz = (totB + nch - 1) / max(nch, 1);
-    const int jbeg = chunk * csz, jend = min(totB, jbeg + csz);
-    if (jend <= jbeg) {
-      __syncwarp();
-      continue;
+      S.tbc[t] = make_int2(w.md_off[vb], cnt);
+      S.tinfo[t] = make_float4(dpc, al2, ir2, g.endcap[tm] ? 1.f : 0.f);
     }
     const bool aec = g.endcap[m] != 0;
     const float sz1 = aec ? 0.f : c.sigma_z, sr1 = aec ? c.sigma_r : 0.f;
@@ -636,30 +677,79 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
     for (int a0 = 0; a0 < na; a0 += kLsAW) {
       const int nA = min(kLsAW, na - a0);
       __syncwarp();
+      float r1 = 3.0e38f, al1 = 3.0e38f;
       if (lane < nA) {
         const int d = a_begin + a0 + lane;
-        S.a_xyzr[lane] = w.md_xyzr[d];
-        S.a_sal[lane] = w.md_sa[d];
+        const float4 pa = w.md_xyzr[d];
+        const float2 sa = w.md_sa[d];
+        S.a_xyzr[lane] = pa;
+        S.a_sal[lane] = sa;
         S.a_id[lane] = d;
+        r1 = pa.w;
+        al1 = sa.y;
       }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        r1 = fminf(r1, __shfl_xor_sync(0xffffffffu, r1, o));
+        al1 = fminf(al1, __shfl_xor_sync(0xffffffffu, al1, o));
+      }
+      // the chunk's azimuth range (the module's MDs are in azimuth order)
+      const float ph_lo = w.md_rphi[a_begin + a0], ph_hi = w.md_rphi[a_begin + a0 + nA - 1];
+      const float ir1 = 1.0f / r1;
+      // each target's window, and their prefix by a warp scan, 32 targets at a time
+      int run = 0;
+      for (int t = lane; t - lane < nt; t += 32) {
+        int cw = 0;
+        if (t < nt) {
+          const int2 bc = S.tbc[t];
+          int jl = 0, jh = 0;
+          if (bc.y > 0) {
+            const float4 ti = S.tinfo[t];
+            const float W = (ti.y - al1) + kwin * (ir1 + ti.z) + 2e-4f;
+            const float lo = ti.x + ph_lo - W, hi = ti.x + ph_hi + W;
+            if (lo < -kPiF || hi > kPiF) {   // the window wraps: take the whole module
+              jh = bc.y;
+            } else if (lo <= hi) {
+              const float* rp = w.md_rphi + bc.x;
+              jl = lower_bound_f(rp, bc.y, lo);
+              jh = upper_bound_f(rp, bc.y, hi);
+            }
+          }
+          S.wbeg[t] = bc.x + jl;
+          cw = jh - jl;
+        }
+        int incl = cw;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (t < nt) S.wpre[t + 1] = run + incl;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) S.wpre[0] = 0;
       __syncwarp();
+      const int totB = run;
+      // this item's share of the windowed outer MDs: chunk `chunk` of nch equal chunks
+      const int csz = (totB + nch - 1) / max(nch, 1);
+      const int jbeg = chunk * csz, jend = min(totB, jbeg + csz);
       for (int j0 = jbeg; j0 < jend; j0 += 32) {
         const int j = j0 + lane;
         const bool has_b = j < jend;
         float x2 = 0.f, y2 = 0.f, z2 = 0.f, r2 = 1.f, s2 = 1.f, al2 = 0.f, sz2 = 0.f, sr2 = 0.f;
         int bid = 0;
         if (has_b) {
-          int lo = 0, hi = nt;   // target k with tpre[k] <= j < tpre[k + 1]
+          int lo = 0, hi = nt;   // target k with wpre[k] <= j < wpre[k + 1]
           while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (S.tpre[mid] <= j) lo = mid; else hi = mid;
+            if (S.wpre[mid] <= j) lo = mid; else hi = mid;
           }
-          bid = S.tbase[lo] + (j - S.tpre[lo]);
+          bid = S.wbeg[lo] + (j - S.wpre[lo]);
           const float4 pb = w.md_xyzr[bid];
           const float2 sb = w.md_sa[bid];
           x2 = pb.x; y2 = pb.y; z2 = pb.z; r2 = pb.w;
           s2 = sb.x; al2 = sb.y;
-          const bool bec = S.tec[lo] != 0;
+          const bool bec = S.tinfo[lo].w != 0.f;
           sz2 = bec ? 0.f : c.sigma_z;
           sr2 = bec ? c.sigma_r : 0.f;
         }
@@ -691,19 +781,22 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
         }
       }
     }
+    __syncwarp();
   }
   __syncwarp();
   if (qn > 0) ls_flush(w, c, S, qn);
 }
 
-// dynamic shared memory of k_ls for a block of `block` threads
-inline size_t ls_smem_bytes(int block) { return sizeof(LsWarpSmem) * (size_t)(block / 32); }
+// dynamic shared memory of k_ls for a block of `block` threads and T target slots per warp
+inline size_t ls_smem_bytes(int block, int T) { return ls_smem_per_warp(T) * (size_t)(block / 32); }
 
 }  // namespace
 
-int ls_resident_blocks(int block) {
+int ls_resident_blocks(int block, int T) {
+  const size_t bytes = ls_smem_bytes(block, T);
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ls, block, ls_smem_bytes(block)) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_ls, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ls, block, bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -838,7 +931,7 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   }
   KT_BEGIN(L, K_LS);
   {
-    const size_t smem = ls_smem_bytes(L.block_ls);
+    const size_t smem = ls_smem_bytes(L.block_ls, g.ls_tcap);
     const int warps = L.block_ls / 32;
     if (L.persistent) {
       // every resident warp, no more: the boustrophedon assignment is static

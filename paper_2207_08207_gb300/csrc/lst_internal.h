@@ -16,6 +16,8 @@ struct Geo {
   const uint8_t* endcap = nullptr;   // [n_mods] 1 for endcap modules
   const float* spacing = nullptr;    // [n_mods]
   const float* phic = nullptr;       // [n_mods] centre azimuth of each module, (phi_lo + phi_hi) / 2
+  int32_t ls_tcap = 32;              // connected-module slots per warp of the LS kernel: the largest
+                                     // module-map degree rounded up to 32
   const int32_t* conn_off = nullptr; // [n_mods + 1]
   const int32_t* conn_tgt = nullptr;
   const int32_t* pix_off = nullptr;  // [n_pix_bins + 1]
@@ -228,7 +230,7 @@ enum KernelId : int {
   if ((L).kev) cudaEventRecordWithFlags((L).kev[2 * (id) + 1], (L).stream, cudaEventRecordExternal)
 
 // resident blocks per SM of the Line-Segment kernel at `block` threads (0 when the query fails)
-int ls_resident_blocks(int block);
+int ls_resident_blocks(int block, int targets);
 
 // scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);

@@ -657,7 +657,6 @@ int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
   int pageable = 0;
   cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
   ctx->pageable_access = pageable != 0;
-  ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls);
   tc_configure();
   *out = ctx;
   return LST_OK;
@@ -778,6 +777,8 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   ctx->geo.pix_off = d_po;
   ctx->geo.pix_tgt = d_pt;
   ctx->max_degree = maxdeg;
+  ctx->geo.ls_tcap = std::max(32, (maxdeg + 31) / 32 * 32);
+  ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls, ctx->geo.ls_tcap);
   ctx->geo_loaded = true;
   // arenas depend on the module count
   if (ctx->in_mem) CK(cudaFreeAsync(ctx->in_mem, ctx->stream));
