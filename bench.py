@@ -47,6 +47,43 @@ def _pinned_copy(a):
     return t.view(a.dtype)
 
 
+def kernel_profile(kernel):
+    """The ncu counters of a timed kernel (profiles/kernel_metrics.json), or None when there is no
+    entry or the kernel's source file has changed since the capture (its SHA-1 differs)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "kernel_metrics.json")) as f:
+            ent = json.load(f)["kernels"].get(kernel)
+        if ent is None:
+            return None
+        with open(os.path.join(ROOT, ent["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != ent["source_sha1"]:
+                return None
+        return ent
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def _sm_max_mhz():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -212,7 +249,8 @@ def run_reference(args):
         "config": {"workload": f"PU200 events (full outer tracker), {len(evs)} events per step on {threads} threads",
                    "events_per_step": len(evs)},
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{len(evs)} PU200 events per step, one thread per event"},
+                         "sample": f"{len(evs)} PU200 events per step, one thread per event",
+                         "cpu_model": cpu_model(), "host_cores": os.cpu_count()},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -232,7 +270,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-rates", default="1000",
+    ap.add_argument("--no-streams", action="store_true")
+    ap.add_argument("--serving-rates", default="500,1000,2000,3000",
                     help="comma-separated Poisson rates (events/s) of the serving measurement")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -320,14 +359,17 @@ def main():
     hbm_achieved = alg_bytes / dur_s / 1e9
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     issue_peak = n_sm * 4 * _sm_max_mhz() * 1e6 / 1e9          # G warp instructions / s
-    prof = lst.KERNEL_PROFILE.get(dom) if args.config == 2 else None
+    prof = kernel_profile(dom) if args.config == 2 else None
     if prof is not None:
-        inst = prof["warp_inst_per_event"] * B
+        per_ev = B / prof["events_per_launch"]
+        inst = prof["warp_inst"] * per_ev
         achieved = inst / dur_s / 1e9
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": issue_peak,
                     "unit": "G warp-instructions/s", "frac": achieved / issue_peak,
-                    "traffic": prof["dram_bytes_per_event"] * B, "peak_kind": "derived: SMs x 4 schedulers x max SM clock",
-                    "warp_inst_per_launch": inst, "profile": prof["source"]}
+                    "traffic": (prof["dram_read_bytes"] + prof["dram_write_bytes"]) * per_ev,
+                    "peak_kind": "derived: SMs x 4 schedulers x max SM clock",
+                    "warp_inst_per_launch": inst,
+                    "profile": f"profiles/kernel_metrics.json ({prof['events_per_launch']}-event capture scaled to {B})"}
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
@@ -357,6 +399,20 @@ def main():
         lat_s = sorted(lat)
         plain = {"events_per_s": 1e3 / statistics.mean(lat), "p50_ms": float(np.percentile(lat_s, 50)),
                  "p99_ms": float(np.percentile(lat_s, 99)), "events": len(lat)}
+
+    # the paper's multi-stream plain path (Sec. 4.2.2, Table 1): N one-event contexts on their own
+    # streams, fed round-robin, inputs resident; events/s over the whole batch of events
+    streams = None
+    if not args.no_streams:
+        from paper_2207_08207_gb300.streams import MultiStream
+        streams = {"events": B, "events_per_s": {}}
+        for n_st in (1, 2, 4, 8):
+            with MultiStream(det, n_st, max(e.n_hits for e in evs), max(e.n_pls for e in evs),
+                             device=local) as ms:
+                ms.run(dev[: max(n_st, 4)])   # first runs: graph capture, arena first touch
+                torch.cuda.synchronize()
+                wall = ms.run(dev)
+            streams["events_per_s"][str(n_st)] = B / wall
 
     # end to end through the public API: host buffers in, track candidates out
     e2e_ms = [float("nan")]
@@ -406,10 +462,17 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle in both of its modes: all host cores across events (the reported value) and
+        # one thread, each on a bounded sample of the same events
         threads = min(os.cpu_count() or 1, 16)
-        r, dt = oracle_events_per_s(det, evs[:threads], threads)
+        runs = [oracle_events_per_s(det, evs[:threads], threads) for _ in range(2)]
+        r = len(runs) * threads / sum(dt for _, dt in runs)
+        r1, dt1 = oracle_events_per_s(det, evs[:3], 1)
         cpu = {"value": r, "unit": "events/s", "cores": threads, "kind": "oracle",
-               "sample": f"{threads} of the PU200 events, one thread per event ({dt:.1f} s wall)"}
+               "sample": f"{threads} of the PU200 events, one thread per event, twice "
+                         f"({sum(dt for _, dt in runs):.1f} s wall); single thread: 3 events ({dt1:.1f} s)",
+               "single_thread": {"value": r1, "unit": "events/s", "cores": 1},
+               "cpu_model": cpu_model(), "host_cores": os.cpu_count()}
 
     if rank == 0:
         line = {
@@ -423,6 +486,7 @@ def main():
             "latency_ms": {"batched_p50": float(np.percentile(step_ms, 50)),
                            "batched_p99": float(np.percentile(step_ms, 99))},
             "plain": plain,
+            "streams": streams,
             "serving": serving,
             "tuned": tuned,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

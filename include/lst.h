@@ -302,7 +302,9 @@ int lst_copy_tc_all(lst_ctx* ctx, int32_t* offsets, int32_t* type, int32_t* obj,
                     float* eta, float* phi);
 
 /* Device time of each stage of the last run, in ms (CUDA events on the run's stream), indexed by
- * LST_STAGE_*; stage_ms[LST_N_STAGES] receives the whole chain. Needs lst_set_timing(ctx, 1). */
+ * LST_STAGE_*; stage_ms[LST_N_STAGES] receives the whole chain. Needs lst_set_timing(ctx, 1). The
+ * pT3 and pT5 kernels run interleaved in one pixel stage: LST_STAGE_PT5 holds the time of pT5's two
+ * candidate kernels (pre-filter and decision), LST_STAGE_PT3 the rest of that stage. */
 int lst_set_timing(lst_ctx* ctx, int enable);
 int lst_get_stage_ms(const lst_ctx* ctx, float* stage_ms);
 

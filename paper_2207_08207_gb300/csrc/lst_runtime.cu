@@ -1055,6 +1055,13 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
       ctx->kern_ms[k] = 0.f;
       if (cudaEventElapsedTime(&ms, ctx->ev_kern[2 * k], ctx->ev_kern[2 * k + 1]) == cudaSuccess) ctx->kern_ms[k] = ms;
     }
+    // the pT3 and pT5 kernels interleave in one pixel stage: pT5's share is its two candidate
+    // kernels, the rest (seed preparation, module boxes, pT3 kernels, grouping) stays with pT3
+    const float pt5 = ctx->kern_ms[K_PT5_PRE] + ctx->kern_ms[K_PT5_DECIDE];
+    if (pt5 > 0.f && pt5 <= ctx->stage_ms[LST_STAGE_PT3]) {
+      ctx->stage_ms[LST_STAGE_PT5] = pt5;
+      ctx->stage_ms[LST_STAGE_PT3] -= pt5;
+    }
   }
   const Ws& w = ctx->ws;
   for (int32_t ev = 0; ev < ctx->E; ++ev) {

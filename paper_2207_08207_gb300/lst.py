@@ -347,9 +347,8 @@ class Context:
         self._L.lst_get_kernel_ms(self._h, _ptr(a), len(KERNELS))
         return dict(zip(KERNELS, a.tolist()))
 
-    @staticmethod
-    def kernel_algorithmic_bytes(kernel, counts, n_hits, n_pls) -> int:
-        return algorithmic_bytes(kernel, counts, n_hits, n_pls)
+    def kernel_algorithmic_bytes(self, kernel, counts, n_hits, n_pls) -> int:
+        return algorithmic_bytes(kernel, counts, n_hits, n_pls, self.det.n_mods)
 
 
 def _check_dev_i32(name, t, n_min):
@@ -420,35 +419,14 @@ def exported_symbols():
     return sorted(set(re.findall(r"^\s*(?:int|void|int64_t|const char\*)\s+(lst_[a-z_]+)\s*\(", txt, re.M)))
 
 
-# Per-event instruction and DRAM counts of the timed kernels on PU200 events: ncu (smsp__inst_executed;
-# DRAM bytes = dram__bytes_read + dram__bytes_write, or the section's DRAM rate x duration) of one
-# launch on a batch of 16 events, divided by 16 (the capture summarised in
-# profiles/kernel_metrics_pu200_batch16.md); used for the issue-slot roofline of the dominant
-# kernel. An entry is removed when its kernel changes.
-_PROF_MET = "profiles/kernel_metrics_pu200_batch16.md"
-KERNEL_PROFILE = {
-    "ls": {"warp_inst_per_event": 280648507 / 16, "dram_bytes_per_event": (29301504 + 17486592) / 16,
-           "source": _PROF_MET},
-    "t3_pre": {"warp_inst_per_event": 144089538 / 16, "dram_bytes_per_event": (76945152 + 1118976) / 16,
-               "source": _PROF_MET},
-    "pt3_pre": {"warp_inst_per_event": 140172934 / 16, "dram_bytes_per_event": (44587520 + 38912) / 16,
-                "source": _PROF_MET},
-    "pt5_pre": {"warp_inst_per_event": 73522178 / 16, "dram_bytes_per_event": 20154368 / 16, "source": _PROF_MET},
-    "md": {"warp_inst_per_event": 56914619 / 16, "dram_bytes_per_event": (29822720 + 8168448) / 16,
-           "source": _PROF_MET},
-    "t5_clean": {"warp_inst_per_event": 32108575 / 16, "dram_bytes_per_event": (17908992 + 2072320) / 16,
-                 "source": _PROF_MET},
-}
-
-
-def algorithmic_bytes(kernel, counts, n_hits, n_pls) -> int:
+def algorithmic_bytes(kernel, counts, n_hits, n_pls, n_mods) -> int:
     """Compulsory HBM bytes of one launch of a timed kernel: every input element it needs read once,
-    every output it produces written once (sizes of the SoA fields). `counts` is the
-    list of per-event count dicts of the launch's batch."""
+    every output it produces written once (sizes of the SoA fields). `counts` is the list of
+    per-event count dicts of the launch's batch; n_mods the detector's module count."""
     s = lambda k: sum(c[k] for c in counts)
     n_md, n_ls, n_t3, n_t5 = s("n_md"), s("n_ls"), s("n_t3"), s("n_t5")
     n_pt3, n_pt5, n_tc = s("n_pt3"), s("n_pt5"), s("n_tc")
-    n_mod = 9138 * len(counts)
+    n_mod = n_mods * len(counts)
     table = {
         # binned x, y, z (12 B) + input index (4 B) written, sensor offsets read
         "bin_sort_gather": n_hits * (16 + 12 + 4) + 2 * n_mod * 4,
