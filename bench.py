@@ -447,6 +447,23 @@ def main():
         e2e_ms = e2e_ms[1:]   # first pass: host staging buffers
     e2e_value = B / (statistics.mean(e2e_ms) / 1e3)
 
+    # physics performance of the copied-out track candidates on the generator's truth (Sec. 3):
+    # efficiency at 75 % hit matching, fake and duplicate rates (host-side, after the timed region)
+    phys = None
+    if not args.no_e2e:
+        from paper_2207_08207_gb300 import physics
+        pc = physics.Counts()
+        off = tc["offsets"]
+        for e, ev in enumerate(evs):
+            pc.add(ev, tc["type"][off[e]:off[e + 1]], tc["hits"][off[e]:off[e + 1]])
+        ps = pc.summary()
+        phys = {"events": B, "eff_above_1gev": ps["eff_above_1gev"], "fake_rate": ps["fake_rate"],
+                "duplicate_rate": ps["duplicate_rate"],
+                "eff_pt": {f"{lo:g}-{hi:g}": round(v, 4) for lo, hi, v in
+                           zip(ps["pt_bins"][:-1], ps["pt_bins"][1:], ps["eff_pt"]) if v == v},
+                "eff_eta_pt_gt_0.9": [round(v, 4) for v in ps["eff_eta"]],
+                "by_type": ps["by_type"]}
+
     # serving: Poisson arrivals of PU ~ U[50, 300] events, continuous batching vs one at a time
     serving = None
     if not args.no_serving and rank == 0 and args.config == 2:
@@ -487,6 +504,7 @@ def main():
                            "batched_p99": float(np.percentile(step_ms, 99))},
             "plain": plain,
             "streams": streams,
+            "physics": phys,
             "serving": serving,
             "tuned": tuned,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
