@@ -151,6 +151,7 @@ typedef struct {
   int32_t recheck[LST_N_STAGES];
   int32_t retries;
   int32_t status;
+  int32_t n_tc_ext;   /* track candidates that were extended (Sec. 2.5.1) */
 } lst_counts;
 
 /*
@@ -179,6 +180,19 @@ typedef struct {
   const float *pt5_chi2_xy, *pt5_chi2_rz;
   const int32_t *tc_type, *tc_obj, *tc_hits;   /* tc_hits: [n_tc][14], -1 padded */
   const float *tc_pt, *tc_eta, *tc_phi;
+  /* Track extensions (Sec. 2.5.1), one per TC row: the T3 that continues the candidate outward
+   * (event-local T3 index, -1 when the candidate is not extended), the MDs it adds (1 or 2; 0 when
+   * none), their hits ([n_tc][4], lower and upper hit of each added MD inner to outer, -1 padded),
+   * and the chi2 of the extended track's circle and r-z line fits. A pT5, pT3 or T5 candidate with
+   * MDs m_1..m_K is extended by a T3 that starts at m_K (adding two MDs) or at m_(K-1) with its
+   * second MD m_K (adding one), whose curvature agrees with the candidate's (|k_T3 - k_TC| <=
+   * c_rel max + c_abs; k_TC from the seed's pT or the T5 fit), and for which the n-anchor extended
+   * track passes the r-z line fit with chi2 <= chi2_t5_rz (n - 2) / 3 (the T5 cut per degree of
+   * freedom); of several, the lowest (circle chi2 + r-z chi2, sorted hit tuple of the T3), the circle
+   * chi2 being that of Karimaki's fit of the n anchors (reported, not cut on). pLS candidates are
+   * not extended. */
+  const int32_t *tc_ext_t3, *tc_ext_n_md, *tc_ext_hits;
+  const float *tc_ext_chi2_c, *tc_ext_chi2_rz;
 } lst_event_out;
 
 typedef struct lst_ctx lst_ctx;
@@ -291,6 +305,13 @@ int lst_copy_tc(lst_ctx* ctx, int32_t ev, int32_t* type, int32_t* obj, int32_t* 
                 float* eta, float* phi);
 
 /*
+ * Copy event `ev`'s track extensions to host memory, one per TC row (see lst_event_out): t3[n],
+ * n_md[n], hits[n * 4], chi2_c[n], chi2_rz[n] with n = counts.n_tc (any pointer may be NULL).
+ */
+int lst_copy_tc_ext(lst_ctx* ctx, int32_t ev, int32_t* t3, int32_t* n_md, int32_t* hits, float* chi2_c,
+                    float* chi2_rz);
+
+/*
  * Copy the track candidates of every event of the last completed run to host memory with one
  * transfer per array (the "copy track candidates to the CPU" step of Sec. 4.2). Event e's rows are
  * [offsets[e], offsets[e + 1]) (offsets has n_ev + 1 entries); type / obj / pt / eta / phi hold
@@ -312,8 +333,9 @@ int lst_get_stage_ms(const lst_ctx* ctx, float* stage_ms);
  * Device time, in ms, of individual kernels of the last run (CUDA events on the run's stream;
  * needs lst_set_timing(ctx, 1)). Index order: hit binning sort/gather, MD, MD compaction, LS,
  * LS compaction, T3 pre-filter, T3 float64 decision, T3 compaction, T5 pre-filter, T5 decision,
- * pT3 pre-filter, pT5 pre-filter, pT3 decision, pT5 decision, T5 duplicate removal, TC assembly.
- * Writes min(n, count) values and returns the count (16), or a negative lst_status on error.
+ * pT3 pre-filter, pT5 pre-filter, pT3 decision, pT5 decision, T5 duplicate removal, TC assembly,
+ * track extensions. Writes min(n, count) values and returns the count (17), or a negative
+ * lst_status on error.
  */
 int lst_get_kernel_ms(const lst_ctx* ctx, float* ms, int32_t n);
 

@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 # table ids and column layouts of the C interface
-T_ORDER, T_OFFSETS, T_MD, T_LS, T_T3, T_T5, T_PLSBIN, T_PT3, T_PT5, T_TC, T_T5KEPT = range(11)
+T_ORDER, T_OFFSETS, T_MD, T_LS, T_T3, T_T5, T_PLSBIN, T_PT3, T_PT5, T_TC, T_T5KEPT, T_TCEXT = range(12)
 I_COLS = {
     T_MD: ["hit_lo", "hit_up", "module", "pass", "definite"],
     T_LS: ["md_in", "md_out", "pass", "definite"],
@@ -30,6 +30,7 @@ I_COLS = {
     T_PT3: ["pls", "obj", "pass", "definite"],
     T_PT5: ["pls", "obj", "pass", "definite"],
     T_TC: ["type", "obj"] + [f"hit{k}" for k in range(14)],
+    T_TCEXT: ["t3", "n_add", "definite"] + [f"hit{k}" for k in range(4)],
 }
 F_COLS = {
     T_MD: ["dphichange", "pt_est", "x", "y", "z", "r"],
@@ -39,8 +40,10 @@ F_COLS = {
     T_PT3: ["chi2_xy", "chi2_rz", "score"],
     T_PT5: ["chi2_xy", "chi2_rz", "score"],
     T_TC: ["pt", "eta", "phi"],
+    T_TCEXT: ["chi2_c", "chi2_rz"],
 }
-TABLE_NAMES = {T_MD: "md", T_LS: "ls", T_T3: "t3", T_T5: "t5", T_PT3: "pt3", T_PT5: "pt5", T_TC: "tc"}
+TABLE_NAMES = {T_MD: "md", T_LS: "ls", T_T3: "t3", T_T5: "t5", T_PT3: "pt3", T_PT5: "pt5", T_TC: "tc",
+               T_TCEXT: "tc_ext"}
 
 
 def build(force: bool = False) -> str:

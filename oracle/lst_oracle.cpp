@@ -8,7 +8,7 @@
 // Stages (paper Sec. 2 and Fig. "GPU implementation flowchart", Sec. 4.2):
 //   hit binning by module (Sec. 4.2) -> Mini-Doublets (Sec. 2.2) -> Line Segments (Sec. 2.2)
 //   -> Triplets (Sec. 2.3) -> Quintuplets (Sec. 2.3) -> pixel seeds, pT3, pT5 (Sec. 2.4)
-//   -> cross-cleaning and Track Candidates (Sec. 2.5).
+//   -> cross-cleaning and Track Candidates (Sec. 2.5) -> track extensions (Sec. 2.5.1).
 //
 // The paper prints no cut formula or constant; each selection below is the reading fixed for this
 // project (anchor hit = lower-sensor hit, cut windows from the pT threshold, luminous region and
@@ -171,6 +171,15 @@ struct TC {
   double pt, eta, phi;
 };
 
+// Track extension of a track candidate (Sec. 2.5.1): the T3 that continues it outward, or t3 = -1.
+struct TCExt {
+  int32_t t3 = -1;       // extending T3 (index in the T3 table)
+  int32_t n_add = 0;     // MDs added: 2 (the T3 shares the TC's last MD) or 1 (its last two MDs)
+  bool definite = true;  // no candidate of this TC had a borderline cut, and its objects are definite
+  double chi2_c = 0, chi2_rz = 0;
+  int32_t hits[4] = {-1, -1, -1, -1};   // the added MDs' hits (lower, upper), inner -> outer
+};
+
 struct Geometry {
   int32_t n_mods;
   std::vector<ModuleRec> mods;
@@ -189,6 +198,7 @@ struct Result {
   std::vector<PObj> pt3, pt5;
   std::vector<TC> tc;
   std::vector<uint8_t> t5_kept;   // T5 survives duplicate removal
+  std::vector<TCExt> tc_ext;      // per TC row
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -341,7 +351,7 @@ double line_fit_chi2(int n, const double* s, const double* z, const double* sig,
 // barrel anchors carry sigma_z, endcap anchors sigma_r * |b0| with b0 the first-to-last slope.
 // Returns false when the arc length does not grow from the first to the last anchor.
 bool rz_chi2(const Params& P, int n, const Hit* const* h, double R, double& chi2, double& slope) {
-  double s[5], z[5], sig[5];
+  double s[8], z[8], sig[8];
   for (int i = 0; i < n; ++i) { s[i] = arc_s(R, h[i]->r); z[i] = h[i]->z; }
   if (!(s[n - 1] > s[0])) return false;
   double b0 = (z[n - 1] - z[0]) / (s[n - 1] - s[0]);
@@ -496,6 +506,36 @@ Verdict pobj_cuts(const Params& P, const PlsRec& s, int n, const Hit* const* h, 
   v.cut(cut_xy, chi2xy);
   v.cut(cut_rz, chi2rz);
   o.chi2_xy = chi2xy; o.chi2_rz = chi2rz; o.score = chi2xy + chi2rz;
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Track extension (Sec. 2.5.1): a track candidate's MDs plus the MDs a T3 adds beyond its outer
+// end must be one track. Reading: the T3's circle agrees in curvature with the candidate's (as the
+// two T3 of a T5 must), and the extended track's n anchors lie on one r-z line in arc length (the
+// Quintuplet's r-z fit) with chi2_rz <= chi2_T5,rz (n - 2) / 3, the T5 cut per degree of freedom
+// (equal to it at n = 5). Karimaki's circle fit of the n anchors is evaluated for the ranking of
+// candidates and as an output, not cut on: with the r-phi resolution alone as its error it
+// rejects about half of the true continuations into the endcap (whose radial hit error it does not
+// carry), at unchanged purity.
+// ---------------------------------------------------------------------------------------------
+Verdict ext_cuts(const Params& P, int n, const Hit* const* h, double kappa_t3, double kappa_tc,
+                 double& chi2c, double& chi2rz) {
+  Verdict v;
+  v.cut(P.c_rel * std::max(kappa_t3, kappa_tc) + P.c_abs, std::fabs(kappa_t3 - kappa_tc));
+  double x[8], y[8];
+  for (int i = 0; i < n; ++i) { x[i] = h[i]->x; y[i] = h[i]->y; }
+  double rho, phi, d;
+  karimaki(n, x, y, rho, phi, d);
+  chi2c = 0;
+  for (int i = 0; i < n; ++i) {
+    double res = circle_residual(rho, phi, d, x[i], y[i]) / P.sigma_rphi;
+    chi2c += res * res;
+  }
+  double R = (rho == 0.0) ? INFINITY : 1.0 / std::fabs(rho);
+  double slope = 0;
+  if (!rz_chi2(P, n, h, R, chi2rz, slope)) { v.fail(); chi2rz = INFINITY; }
+  else v.cut(P.chi2_t5_rz * (n - 2) / 3.0, chi2rz);
   return v;
 }
 
@@ -850,6 +890,90 @@ struct Runner {
     }
   }
 
+  // Track extensions (Sec. 2.5.1): for each pT5, pT3 and T5 track candidate, the T3 that continues
+  // it outward best: candidates share the candidate's last MD (adding two MDs) or its last two MDs
+  // (adding one); the passing one with the lowest (chi2_c + chi2_rz as float32, sorted hit tuple of
+  // the T3) is chosen.
+  void run_ext() {
+    const int32_t nt3 = (int32_t)R.t3.size();
+    std::vector<std::vector<int32_t>> by_first;
+    if (!brute) {
+      by_first.resize(R.md.size());
+      for (int32_t j = 0; j < nt3; ++j) by_first[R.t3[j].md[0]].push_back(j);
+    }
+    R.tc_ext.assign(R.tc.size(), TCExt{});
+    for (size_t i = 0; i < R.tc.size(); ++i) {
+      const TC& t = R.tc[i];
+      std::vector<int32_t> m;
+      double kappa_tc = 0;
+      bool tc_definite = true;
+      if (t.type == 0) {
+        const PObj& o = R.pt5[t.obj];
+        m.assign(R.t5[o.obj].md, R.t5[o.obj].md + 5);
+        kappa_tc = P.k / (double)pls[o.pls].pt;
+        tc_definite = o.definite;
+      } else if (t.type == 1) {
+        const PObj& o = R.pt3[t.obj];
+        m.assign(R.t3[o.obj].md, R.t3[o.obj].md + 3);
+        kappa_tc = P.k / (double)pls[o.pls].pt;
+        tc_definite = o.definite;
+      } else if (t.type == 2) {
+        m.assign(R.t5[t.obj].md, R.t5[t.obj].md + 5);
+        kappa_tc = std::fabs(R.t5[t.obj].kappa_fit);
+        tc_definite = R.t5[t.obj].definite;
+      } else {
+        continue;   // a pixel line segment has no outer-tracker MD to extend from
+      }
+      const int K = (int)m.size();
+      TCExt best;
+      bool have = false, any_border = false;
+      float best_score = 0.f;
+      std::vector<int32_t> best_key;
+      for (int overlap = 1; overlap <= 2; ++overlap) {
+        const int32_t first = m[K - overlap];
+        std::vector<int32_t> cands;
+        if (brute) {
+          for (int32_t j = 0; j < nt3; ++j) if (R.t3[j].md[0] == first) cands.push_back(j);
+        } else {
+          cands = by_first[first];
+        }
+        for (int32_t j : cands) {
+          const T3& c3 = R.t3[j];
+          if (overlap == 2 && c3.md[1] != m[K - 1]) continue;
+          std::vector<int32_t> all = m;
+          for (int k = overlap; k < 3; ++k) all.push_back(c3.md[k]);
+          const int n = (int)all.size();
+          const Hit* h[8];
+          for (int k = 0; k < n; ++k) h[k] = &anchor(all[k]);
+          double chi2c, chi2rz;
+          Verdict v = ext_cuts(P, n, h, std::isinf(c3.R) ? 0.0 : 1.0 / c3.R, kappa_tc, chi2c, chi2rz);
+          if (!v.keep()) continue;
+          if (!v.definite() || !c3.definite) any_border = true;
+          if (!(v.all_pass && c3.pass)) continue;
+          float sc = (float)(chi2c + chi2rz);
+          std::vector<int32_t> key;
+          md_hits(c3.md, 3, key);
+          key = sorted_key(key);
+          if (!have || sc < best_score || (sc == best_score && key_less(key, best_key))) {
+            have = true;
+            best_score = sc;
+            best_key = key;
+            best = TCExt{};
+            best.t3 = j;
+            best.n_add = 3 - overlap;
+            best.chi2_c = chi2c;
+            best.chi2_rz = chi2rz;
+            std::vector<int32_t> added;
+            md_hits(&c3.md[overlap], 3 - overlap, added);
+            for (size_t k = 0; k < added.size(); ++k) best.hits[k] = added[k];
+          }
+        }
+      }
+      best.definite = !any_border && tc_definite;
+      R.tc_ext[i] = best;
+    }
+  }
+
   void run(const float* x, const float* y, const float* z, const int32_t* sensor, int32_t n_hits,
            const PlsRec* pl, int32_t np, bool brute_force) {
     pls = pl; n_pls = np; brute = brute_force;
@@ -863,6 +987,7 @@ struct Runner {
     run_pobj(R.t3, 3, P.chi2_pt3_xy, P.chi2_pt3_rz, R.pt3);
     run_pobj(R.t5, 5, P.chi2_pt5_xy, P.chi2_pt5_rz, R.pt5);
     run_tc();
+    run_ext();
   }
 };
 
@@ -918,7 +1043,7 @@ void* orc_run(double pt_thr, const void* mods, int32_t n_mods, const int32_t* co
 void orc_free(void* h) { delete static_cast<Handle*>(h); }
 
 // tables: 0 binned order, 1 sensor offsets, 2 MD, 3 LS, 4 T3, 5 T5, 6 pLS bins, 7 pT3, 8 pT5,
-// 9 TC, 10 T5 kept flags
+// 9 TC, 10 T5 kept flags, 11 TC extensions (one per TC row)
 int64_t orc_count(void* hp, int32_t table) {
   Result& R = static_cast<Handle*>(hp)->res;
   switch (table) {
@@ -933,6 +1058,7 @@ int64_t orc_count(void* hp, int32_t table) {
     case 8: return (int64_t)R.pt5.size();
     case 9: return (int64_t)R.tc.size();
     case 10: return (int64_t)R.t5_kept.size();
+    case 11: return (int64_t)R.tc_ext.size();
   }
   return -1;
 }
@@ -944,6 +1070,7 @@ int64_t orc_count(void* hp, int32_t table) {
 //  T5: 0 t3_in 1 t3_out 2 pass 3 definite 4..8 md[0..4]
 //  pT3/pT5: 0 pls 1 obj 2 pass 3 definite
 //  TC: 0 type 1 obj 2..15 hits
+//  TC extension: 0 t3 (-1: none) 1 MDs added 2 definite 3..6 added hits (-1 padded)
 int orc_get_i32(void* hp, int32_t table, int32_t col, int32_t* dst) {
   Handle* h = static_cast<Handle*>(hp);
   Result& R = h->res;
@@ -1001,6 +1128,16 @@ int orc_get_i32(void* hp, int32_t table, int32_t col, int32_t* dst) {
       }
       return 0;
     case 10: for (size_t i = 0; i < R.t5_kept.size(); ++i) dst[i] = R.t5_kept[i]; return 0;
+    case 11:
+      for (size_t i = 0; i < R.tc_ext.size(); ++i) {
+        const TCExt& o = R.tc_ext[i];
+        if (col == 0) dst[i] = o.t3;
+        else if (col == 1) dst[i] = o.n_add;
+        else if (col == 2) dst[i] = o.definite;
+        else if (col >= 3 && col < 7) dst[i] = o.hits[col - 3];
+        else return -1;
+      }
+      return 0;
   }
   return -1;
 }
@@ -1012,6 +1149,7 @@ int orc_get_i32(void* hp, int32_t table, int32_t col, int32_t* dst) {
 //  T5: 0 kappa_in 1 kappa_out 2 kappa_fit 3 chi2_c 4 chi2_rz 5 eta 6 phi 7 pt
 //  pT3/pT5: 0 chi2_xy 1 chi2_rz 2 score
 //  TC: 0 pt 1 eta 2 phi
+//  TC extension: 0 chi2_c 1 chi2_rz
 int orc_get_f64(void* hp, int32_t table, int32_t col, double* dst) {
   Handle* h = static_cast<Handle*>(hp);
   Result& R = h->res;
@@ -1062,6 +1200,13 @@ int orc_get_f64(void* hp, int32_t table, int32_t col, double* dst) {
         double v[] = {R.tc[i].pt, R.tc[i].eta, R.tc[i].phi};
         if (col < 0 || col > 2) return -1;
         dst[i] = v[col];
+      }
+      return 0;
+    case 11:
+      for (size_t i = 0; i < R.tc_ext.size(); ++i) {
+        if (col == 0) dst[i] = R.tc_ext[i].chi2_c;
+        else if (col == 1) dst[i] = R.tc_ext[i].chi2_rz;
+        else return -1;
       }
       return 0;
   }

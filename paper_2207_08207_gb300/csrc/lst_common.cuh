@@ -14,6 +14,7 @@
 // evaluation of the cut definitions except within ~1e-12 relative of a threshold.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "lst.h"
@@ -367,6 +368,87 @@ __device__ __forceinline__ bool rz_fit(const Cst<T>& c, T akappa, const T* r, co
   for (int i = 0; i < N; ++i) sig[i] = m_max(ec[i] ? c.sigma_r * m_abs(b0) : c.sigma_z, c.sigma_floor);
   chi2 = line_chi2<T, N>(s, z, sig, slope);
   return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Karimaki's circle fit (V. Karimaki, NIM A305 (1991) 187) with equal weights.
+// Circle: 1/2 rho (x^2 + y^2) - (1 + rho d)(x sin phi - y cos phi) + 1/2 rho d^2 + d = 0;
+// phi is the direction at the point of closest approach to the origin, oriented first -> last.
+// ---------------------------------------------------------------------------------------------
+template <class T, int N>
+__device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi, T& d, T& sp, T& cp) {
+  T mx = 0, my = 0, mxx = 0, mxy = 0, myy = 0, mr2 = 0, mxr = 0, myr = 0, mrr = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const T r2 = x[i] * x[i] + y[i] * y[i];
+    mx += x[i]; my += y[i];
+    mxx += x[i] * x[i]; mxy += x[i] * y[i]; myy += y[i] * y[i];
+    mr2 += r2; mxr += x[i] * r2; myr += y[i] * r2; mrr += r2 * r2;
+  }
+  const T inv = T(1) / T(N);
+  mx *= inv; my *= inv; mxx *= inv; mxy *= inv; myy *= inv; mr2 *= inv; mxr *= inv; myr *= inv; mrr *= inv;
+  const T Cxx = mxx - mx * mx, Cxy = mxy - mx * my, Cyy = myy - my * my;
+  const T Cxr = mxr - mx * mr2, Cyr = myr - my * mr2, Crr = mrr - mr2 * mr2;
+  const T q1 = Crr * Cxy - Cxr * Cyr;
+  const T q2 = Crr * (Cxx - Cyy) - Cxr * Cxr + Cyr * Cyr;
+  if constexpr (std::is_same<T, ff>::value) {
+    // phi = atan2(2 q1, q2) / 2 in (-pi/2, pi/2], so cos phi >= 0: its sine and cosine from the
+    // double angle's, (cos 2phi, sin 2phi) = (q2, 2 q1) / h, by the half-angle formulas, each in
+    // the form free of cancellation; the angle itself (an output only) in float32
+    const ff s2 = ff(2.0f) * q1;
+    const ff h = m_sqrt(s2 * s2 + q2 * q2);
+    if (h.hi == 0.0f) {
+      sp = ff(0.0f);
+      cp = ff(1.0f);
+    } else {
+      const ff c2 = q2 / h, sn2 = s2 / h;
+      if (c2.hi >= 0.0f) {
+        cp = m_sqrt((ff(1.0f) + c2) * ff(0.5f));
+        sp = sn2 / (ff(2.0f) * cp);
+      } else {
+        sp = m_sqrt((ff(1.0f) - c2) * ff(0.5f));
+        if (signbit(sn2.hi)) sp = -sp;
+        cp = sn2 / (ff(2.0f) * sp);
+      }
+    }
+    if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
+      sp = -sp;
+      cp = -cp;
+    }
+    phi = ff(atan2f(sp.hi, cp.hi));
+  } else {
+    phi = T(0.5) * m_atan2(T(2) * q1, q2);
+    if constexpr (sizeof(T) == 4) sincosf(phi, &sp, &cp);
+    else sincos(phi, &sp, &cp);
+    if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
+      phi += T(kPiD);
+      sp = -sp;
+      cp = -cp;
+    }
+    if (phi > T(kPiD)) phi -= T(kTwoPiD);
+    if (phi <= -T(kPiD)) phi += T(kTwoPiD);
+  }
+  const T kap = (sp * Cxr - cp * Cyr) / Crr;
+  const T del = -kap * mr2 + sp * mx - cp * my;
+  const T root = m_sqrt(T(1) - T(4) * del * kap);
+  rho = T(2) * kap / root;
+  d = T(2) * del / (T(1) + root);
+}
+
+// sum over the anchors of ((|p - c| - R) / sigma)^2 at the circle (rho, phi, d) given by rho,
+// (sin phi, cos phi) and d, each residual in
+// the exact cancellation-free form 2 eps / (1 + sqrt(1 + 2 rho eps))
+template <class T, int N>
+__device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T cp, T d, T sigma) {
+  T chi2 = 0;
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const T eps = T(0.5) * rho * (x[a] * x[a] + y[a] * y[a]) - (T(1) + rho * d) * (x[a] * sp - y[a] * cp) +
+                  T(0.5) * rho * d * d + d;
+    const T res = T(2) * eps / (T(1) + m_sqrt(T(1) + T(2) * rho * eps)) / sigma;
+    chi2 += res * res;
+  }
+  return chi2;
 }
 
 __host__ __device__ __forceinline__ int64_t lst_min64(int64_t a, int64_t b) { return a < b ? a : b; }

@@ -28,17 +28,43 @@ struct ff {
   __host__ __device__ explicit operator float() const { return hi + lo; }
 };
 
+// Rounded float operations that the compiler may not fuse with their neighbours: the error-free
+// transformations below assume that each product and sum is rounded on its own, and a product
+// contracted into a following addition (an FMA) would count its rounding error twice. On the device
+// the _rn intrinsics are never contracted; host builds of this header must disable contraction.
+__host__ __device__ __forceinline__ float f_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float f_add(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float f_sub(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+
 __host__ __device__ __forceinline__ ff ff_two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return ff(s, (a - (s - bb)) + (b - bb));
+  const float s = f_add(a, b);
+  const float bb = f_sub(s, a);
+  return ff(s, f_add(f_sub(a, f_sub(s, bb)), f_sub(b, bb)));
 }
 __host__ __device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
-  const float s = a + b;
-  return ff(s, b - (s - a));
+  const float s = f_add(a, b);
+  return ff(s, f_sub(b, f_sub(s, a)));
 }
 __host__ __device__ __forceinline__ ff ff_two_prod(float a, float b) {
-  const float p = a * b;
+  const float p = f_mul(a, b);
   return ff(p, fmaf(a, b, -p));
 }
 
@@ -72,11 +98,11 @@ __host__ __device__ __forceinline__ ff operator/(ff a, ff b) {
 #else
   const float inv = 1.0f / b.hi;
 #endif
-  const float q1 = a.hi * inv;
+  const float q1 = f_mul(a.hi, inv);
   if (!isfinite(q1) || b.hi == 0.0f) return ff(a.hi / b.hi, 0.0f);
   const ff p = ff_two_prod(b.hi, q1);
   const float r = (((a.hi - p.hi) - p.lo) + a.lo) - b.lo * q1;
-  return ff_fast_two_sum(q1, r * inv);
+  return ff_fast_two_sum(q1, f_mul(r, inv));
 }
 
 // comparisons (exact for normalised pairs)
@@ -97,7 +123,7 @@ __host__ __device__ __forceinline__ ff m_sqrt(ff a) {
   const float s = sqrtf(a.hi);
   const ff p = ff_two_prod(s, s);
   const float e = ((a.hi - p.hi) - p.lo) + a.lo;
-  return ff_fast_two_sum(s, e / (2.0f * s));
+  return ff_fast_two_sum(s, e / f_mul(2.0f, s));
 }
 
 // a*d - b*c

@@ -40,9 +40,11 @@ enum ErrorBit : int { ERR_BAD_SENSOR = 1, ERR_BAD_COORD = 2, ERR_BAD_PLS = 4 };
 
 // Per-event summary written by the final kernel: object counts [0..6] (MD, LS, T3, T5, pT3, pT5, TC),
 // TC counts per type [7..10], first dense index of the event in each object array [11..17]
-// (same order; TC: first row), error bits [kEvErr].
+// (same order; TC: first row), extended TCs [kEvExt], error bits [kEvErr].
 constexpr int kEvWords = 24;
 constexpr int kEvErr = 23;
+constexpr int kEvExt = 18;
+constexpr int kExtRefs = 8;   // candidate references stored per track candidate
 
 // Capacities of one workspace (element counts).
 struct Caps {
@@ -159,6 +161,19 @@ struct Ws {
   int32_t* tcd_off = nullptr;   // [E + 1] first dense row of each event
   int32_t *tcd_type = nullptr, *tcd_obj = nullptr, *tcd_hits = nullptr;   // dense over the batch
   float *tcd_pt = nullptr, *tcd_eta = nullptr, *tcd_phi = nullptr;
+  // track extensions of the dense rows: extending T3 (event-local, -1: none), MDs added, the added
+  // hits ([4] per row, -1 padded), chi2 of the extended track's circle and r-z fits
+  int32_t *tcd_ext_t3 = nullptr, *tcd_ext_n = nullptr, *tcd_ext_hits = nullptr;
+  float *tcd_ext_c = nullptr, *tcd_ext_rz = nullptr;
+  // their candidates: per row the count and up to kExtRefs references into the candidate queues
+  // (one region of ext_qcap entries per anchor count 4..7: (row, T3 | overlap << 30) and the
+  // result (score, chi2_c, chi2_rz, passed))
+  int32_t* ext_cnt = nullptr;     // [tc_cap]
+  int32_t* ext_ref = nullptr;     // [tc_cap][kExtRefs]: region << 28 | position
+  int2* ext_q = nullptr;          // [4][ext_qcap]
+  float4* ext_res = nullptr;      // [4][ext_qcap]
+  int32_t* ext_qn = nullptr;      // [4] entries pushed per region (zeroed every run)
+  int64_t ext_qcap = 0;
   int64_t tc_capacity = 0;
   // event-local output copies
   int32_t *o_md_lo = nullptr, *o_md_up = nullptr, *o_md_mod = nullptr;
@@ -204,6 +219,7 @@ struct Launch {
   int n_sm = 152;
   int ls_blocks_per_sm = 0;        // resident blocks of the Line-Segment kernel (0: not queried)
   long long* launches = nullptr;   // host counter
+  bool capturing = false;          // the chain is being captured into a CUDA graph
   cudaEvent_t* kev = nullptr;      // when set: [2 * kernel id] start / end events of timed kernels
   // single-pass scans of the chain (nullptr: three-pass scans). Tile states are tagged with an
   // epoch = run * kScanMax + scan index, where the run counter is advanced on the device once per
@@ -220,14 +236,17 @@ constexpr int kLsMaxChunks = 8;   // LS work items per module at most
 // kernels timed individually when timing is enabled (index order of lst_get_kernel_ms)
 enum KernelId : int {
   K_BIN = 0, K_MD, K_MD_COMPACT, K_LS, K_LS_COMPACT, K_T3_PRE, K_T3_DECIDE, K_T3_COMPACT, K_T5_PRE,
-  K_T5_DECIDE, K_PT3_PRE, K_PT5_PRE, K_PT3_DECIDE, K_PT5_DECIDE, K_TC_CLEAN, K_TC_ASSEMBLE, K_N_TIMED
+  K_T5_DECIDE, K_PT3_PRE, K_PT5_PRE, K_PT3_DECIDE, K_PT5_DECIDE, K_TC_CLEAN, K_TC_ASSEMBLE, K_TC_EXT, K_N_TIMED
 };
-// (recorded as external events so that, inside a captured CUDA graph, they become real event-record
-// nodes that can be timed)
+// (recorded as external events while the chain is captured, so that inside the CUDA graph they
+// become event-record nodes that can be timed; plain records otherwise, where the external flag is
+// not allowed)
+#define KT_REC(L, ev) \
+  cudaEventRecordWithFlags((ev), (L).stream, (L).capturing ? cudaEventRecordExternal : cudaEventRecordDefault)
 #define KT_BEGIN(L, id) \
-  if ((L).kev) cudaEventRecordWithFlags((L).kev[2 * (id)], (L).stream, cudaEventRecordExternal)
+  if ((L).kev) KT_REC(L, (L).kev[2 * (id)])
 #define KT_END(L, id) \
-  if ((L).kev) cudaEventRecordWithFlags((L).kev[2 * (id) + 1], (L).stream, cudaEventRecordExternal)
+  if ((L).kev) KT_REC(L, (L).kev[2 * (id) + 1])
 
 // resident blocks per SM of the Line-Segment kernel at `block` threads (0 when the query fails)
 int ls_resident_blocks(int block, int targets);

@@ -1013,6 +1013,243 @@ __global__ void k_tc_dense(Ws w, Geo g) {
     w.tcd_hits[(int64_t)dst0 * 14 + k] = w.tc_hits[(int64_t)src0 * 14 + k];
 }
 
+// ---------------------------------------------------------------------------------------------
+// Track extensions (Sec. 2.5.1). A pT5, pT3 or T5 track candidate (MDs m_1..m_K inner to outer) is
+// extended by the T3 that continues it outward: a T3 starting at m_K adds its two other MDs, one
+// starting at m_(K-1) whose second MD is m_K adds its third. A candidate T3 must agree in curvature
+// with the track candidate (the T5 compatibility: |k_T3 - k_TC| <= c_rel max(k) + c_abs, k_TC the
+// seed's k / pT or the T5 fit's |kappa|) and the extended track's n anchors must lie on the T5's
+// r-z line in arc length with the T5 cut per degree of freedom, chi2_rz <= chi2_t5_rz (n - 2) / 3.
+// Karimaki's circle through the n anchors gives the arc lengths and a circle chi2 that ranks the
+// candidates (it is not cut on). Decided in double-float, like the T5 selection; of several passing
+// T3 the one with the lowest (chi2_c + chi2_rz as float32, sorted hit tuple) is taken. One thread
+// per dense track-candidate row (a row has a few candidate T3).
+// ---------------------------------------------------------------------------------------------
+struct ExtCuts {
+  ff rz[8];   // r-z chi2 bounds for n anchors (n = 4..7)
+};
+
+template <int N>
+__device__ __forceinline__ bool ext_fit(const Ws& w, const Cst<ff>& c, const int* md, ff cut_rz, ff& chi2c,
+                                        ff& chi2rz) {
+  ff x[N], y[N], z[N], r[N];
+  bool ec[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const float4 p = w.md_xyzr[md[a]];
+    x[a] = ff(p.x);
+    y[a] = ff(p.y);
+    z[a] = ff(p.z);
+    r[a] = ff_fast_two_sum(p.w, w.md_rlo[md[a]]);
+    ec[a] = w.md_ec[md[a]] != 0;
+  }
+  ff rho, phi, d, sp, cp;
+  karimaki<ff, N>(x, y, rho, phi, d, sp, cp);
+  chi2c = circle_chi2<ff, N>(x, y, rho, sp, cp, d, c.sigma_rphi);
+  ff slope;
+  if (!rz_fit<ff, N>(c, m_abs(rho), r, z, ec, chi2rz, slope)) return false;
+  AccFF acc;
+  acc.cut(cut_rz, chi2rz);
+  return !acc.fail;
+}
+
+__device__ __forceinline__ void t3_sorted_hits(const Ws& w, int t3, int* h) {
+  int n = 0;
+  const int md[3] = {w.t3_md0[t3], w.t3_md1[t3], w.t3_md2[t3]};
+  for (int k = 0; k < 3; ++k) n += md_hits(w, md[k], h + n);
+  sort_small(h, 6);
+}
+
+// the MDs of a dense track-candidate row (inner to outer) and its curvature; K = 0 for pLS rows
+__device__ __forceinline__ int ext_row(const Ws& w, const Geo& g, const Cst<ff>& c, int e, int row, int* md,
+                                       ff& ktc) {
+  const int type = w.tcd_type[row], obj = w.tcd_obj[row];
+  const int p0 = w.ev_pls_off[e];
+  const int64_t S5 = w.cap.t5_dense;
+  if (type == TC_PT5) {
+    const int gi = obj + w.pt5_off[p0];
+    const int t5 = w.pt5_obj[gi];
+    for (int a = 0; a < 5; ++a) md[a] = w.t5_md[a * S5 + t5];
+    ktc = c.k / ff(w.pls[w.pt5_pls[gi]].pt);
+    return 5;
+  }
+  if (type == TC_PT3) {
+    const int gi = obj + w.pt3_off[p0];
+    const int t3 = w.pt3_obj[gi];
+    md[0] = w.t3_md0[t3]; md[1] = w.t3_md1[t3]; md[2] = w.t3_md2[t3];
+    ktc = c.k / ff(w.pls[w.pt3_pls[gi]].pt);
+    return 3;
+  }
+  if (type == TC_T5) {
+    const int t5 = obj + w.t5_off[e * g.n_mods];
+    for (int a = 0; a < 5; ++a) md[a] = w.t5_md[a * S5 + t5];
+    ktc = m_abs(ff(w.t5_f[2 * S5 + t5]));
+    return 5;
+  }
+  return 0;
+}
+
+// the candidate T3 of a row, in a fixed order: those starting at m_K (overlap 1), then those
+// starting at m_(K-1) whose second MD is m_K (overlap 2), each in dense T3 order. Calls f(t3,
+// overlap) for each that agrees with the row's curvature.
+template <class F>
+__device__ __forceinline__ void ext_candidates(const Ws& w, const Cst<ff>& c, const int* md, int K, ff ktc, F f) {
+  const int n_t3 = w.t3_off[w.V];
+  for (int overlap = 1; overlap <= 2 && K > 0; ++overlap) {
+    const int first = md[K - overlap];
+    const int j0 = min(w.t3md_off[first], n_t3), j1 = min(w.t3md_off[first + 1], n_t3);
+    for (int d = j0; d < j1; ++d) {
+      if (overlap == 2 && w.t3_md1[d] != md[K - 1]) continue;
+      const float R3 = w.t3_R[d];
+      const ff kt3 = isinf(R3) ? ff(0.0f) : ff(1.0f) / ff(R3);
+      AccFF acc;
+      acc.cut(c.c_rel * m_max(kt3, ktc) + c.c_abs, m_abs(kt3 - ktc));
+      if (!acc.fail) f(d, overlap);
+    }
+  }
+}
+
+// the fit of one candidate with N = K + 3 - overlap anchors; result (score, chi2_c, chi2_rz, passed)
+template <int N>
+__device__ __forceinline__ float4 ext_eval(const Ws& w, const Cst<ff>& c, const int* md, int K, int t3,
+                                           int overlap, ff cut_rz) {
+  int all[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    if (a < K) all[a] = md[a];
+  }
+  const int add[2] = {w.t3_md1[t3], w.t3_md2[t3]};
+  if (overlap == 1) { all[K] = add[0]; all[K + 1] = add[1]; }
+  else all[K] = add[1];
+  ff chi2c, chi2rz;
+  const bool ok = ext_fit<N>(w, c, all, cut_rz, chi2c, chi2rz);
+  return make_float4((float)(chi2c + chi2rz), (float)chi2c, (float)chi2rz, ok ? 1.f : 0.f);
+}
+
+__device__ __forceinline__ float4 ext_eval_n(const Ws& w, const Cst<ff>& c, const ExtCuts& xc, const int* md, int K,
+                                             int t3, int overlap) {
+  switch (K + 3 - overlap) {
+    case 4: return ext_eval<4>(w, c, md, K, t3, overlap, xc.rz[4]);
+    case 5: return ext_eval<5>(w, c, md, K, t3, overlap, xc.rz[5]);
+    case 6: return ext_eval<6>(w, c, md, K, t3, overlap, xc.rz[6]);
+    default: return ext_eval<7>(w, c, md, K, t3, overlap, xc.rz[7]);
+  }
+}
+
+// a queued candidate: dense T3 index (< 2^30) and overlap (1 or 2) in one word
+__device__ __forceinline__ int ext_pack(int t3, int overlap) { return (int)((unsigned)t3 | ((unsigned)overlap << 30)); }
+__device__ __forceinline__ int ext_t3(int v) { return (int)((unsigned)v & ((1u << 30) - 1u)); }
+__device__ __forceinline__ int ext_overlap(int v) { return (int)((unsigned)v >> 30); }
+
+// (A) each row's candidates that agree in curvature go to the queue region of their anchor count;
+// the row keeps up to kExtRefs references and the total
+__global__ void k_ext_cand(Ws w, Geo g, Cst<ff> c) {
+  const int nrow = w.tcd_off[w.E];
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrow; row += gridDim.x * blockDim.x) {
+    const int e = find_seg(w.tcd_off, w.E, row);
+    int md[5];
+    ff ktc;
+    const int K = ext_row(w, g, c, e, row, md, ktc);
+    int n = 0;
+    ext_candidates(w, c, md, K, ktc, [&](int d, int overlap) {
+      if (n < kExtRefs) {   // candidates beyond the row's references are evaluated by the selection pass
+        const int reg = K + 3 - overlap - 4;
+        const int pos = atomicAdd(&w.ext_qn[reg], 1);
+        if (pos < w.ext_qcap) {
+          w.ext_q[reg * w.ext_qcap + pos] = make_int2(row, ext_pack(d, overlap));
+          w.ext_ref[(int64_t)row * kExtRefs + n] = (reg << 28) | pos;
+        } else {
+          w.ext_ref[(int64_t)row * kExtRefs + n] = -1;   // not queued: evaluated by the selection pass
+        }
+      }
+      ++n;
+    });
+    w.ext_cnt[row] = n;
+  }
+}
+
+// (B) the fits of one anchor count, one thread per queued candidate
+template <int N>
+__global__ void k_ext_fit(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
+  const int reg = N - 4;
+  const int n = (int)min((int64_t)w.ext_qn[reg], w.ext_qcap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int2 q = w.ext_q[reg * w.ext_qcap + k];
+    const int row = q.x, d = ext_t3(q.y), overlap = ext_overlap(q.y);
+    const int e = find_seg(w.tcd_off, w.E, row);
+    int md[5];
+    ff ktc;
+    const int K = ext_row(w, g, c, e, row, md, ktc);
+    w.ext_res[reg * w.ext_qcap + k] = ext_eval<N>(w, c, md, K, d, overlap, xc.rz[N]);
+  }
+}
+
+// (C) per row, the best passing candidate by (score as float32, sorted hit tuple of the T3); the
+// candidates that did not fit the queue or the row's references are listed and fitted again here
+__global__ void k_ext_select(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
+  const int nrow = w.tcd_off[w.E];
+  int n_ext_acc = 0, e_acc = -1;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrow; row += gridDim.x * blockDim.x) {
+    const int e = find_seg(w.tcd_off, w.E, row);
+    const int ncand = w.ext_cnt[row];
+    int md[5];
+    ff ktc;
+    int K = 0;
+    int best = -1, best_n = 0, best_key[6];
+    float best_sc = 0.f, best_c = 0.f, best_rz = 0.f;
+    auto consider = [&](int d, int overlap, float4 r) {
+      if (r.w == 0.f) return;
+      int key[6];
+      t3_sorted_hits(w, d, key);
+      bool better = best < 0 || r.x < best_sc;
+      if (!better && r.x == best_sc) {
+        for (int t = 0; t < 6; ++t)
+          if (key[t] != best_key[t]) { better = key[t] < best_key[t]; break; }
+      }
+      if (better) {
+        best = d; best_n = 3 - overlap; best_sc = r.x; best_c = r.y; best_rz = r.z;
+        for (int t = 0; t < 6; ++t) best_key[t] = key[t];
+      }
+    };
+    bool slow = ncand > kExtRefs;
+    for (int k = 0; k < min(ncand, kExtRefs); ++k) {
+      const int ref = w.ext_ref[(int64_t)row * kExtRefs + k];
+      if (ref < 0) { slow = true; continue; }
+      const int reg = ref >> 28, pos = ref & ((1 << 28) - 1);
+      const int2 q = w.ext_q[reg * w.ext_qcap + pos];
+      consider(ext_t3(q.y), ext_overlap(q.y), w.ext_res[reg * w.ext_qcap + pos]);
+    }
+    if (slow) {   // rare: candidates beyond the references or the queue, fitted here
+      K = ext_row(w, g, c, e, row, md, ktc);
+      int k = 0;
+      ext_candidates(w, c, md, K, ktc, [&](int d, int overlap) {
+        const int ref = k < kExtRefs ? w.ext_ref[(int64_t)row * kExtRefs + k] : -1;
+        ++k;
+        if (ref >= 0) return;   // already considered
+        consider(d, overlap, ext_eval_n(w, c, xc, md, K, d, overlap));
+      });
+    }
+    int h[4] = {-1, -1, -1, -1};
+    if (best >= 0) {
+      const int add[2] = {w.t3_md1[best], w.t3_md2[best]};
+      int m = 0;
+      for (int a = 2 - best_n; a < 2; ++a) m += md_hits(w, add[a], h + m);
+      if (e != e_acc) {
+        if (n_ext_acc) atomicAdd(&w.ev_stat[e_acc * kEvWords + kEvExt], n_ext_acc);
+        e_acc = e;
+        n_ext_acc = 0;
+      }
+      ++n_ext_acc;
+    }
+    w.tcd_ext_t3[row] = best >= 0 ? best - w.t3_off[e * g.n_mods] : -1;
+    w.tcd_ext_n[row] = best_n;
+    for (int t = 0; t < 4; ++t) w.tcd_ext_hits[(int64_t)row * 4 + t] = h[t];
+    w.tcd_ext_c[row] = best >= 0 ? best_c : 0.f;
+    w.tcd_ext_rz[row] = best >= 0 ? best_rz : 0.f;
+  }
+  if (n_ext_acc) atomicAdd(&w.ev_stat[e_acc * kEvWords + kEvExt], n_ext_acc);
+}
+
 }  // namespace
 
 void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
@@ -1094,6 +1331,20 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_tc_dense<<<dim3(16, w.E), 256, 0, L.stream>>>(w, g);
   LST_LAUNCH(L);
   *L.launches += 5;
+  // track extensions of the dense rows; the per-anchor-count cut bounds in float64, as pairs
+  ExtCuts xc;
+  for (int na = 0; na < 8; ++na) xc.rz[na] = ff(c.d.chi2_t5_rz * (na - 2) / 3.0);
+  KT_BEGIN(L, K_TC_EXT);
+  const int rows_grid = grid_for(w.tc_capacity, 128, 152 * 8);
+  const int fit_grid = grid_for(w.ext_qcap, 64, 152 * 8);
+  k_ext_cand<<<rows_grid, 128, 0, L.stream>>>(w, g, c.x);
+  k_ext_fit<4><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
+  k_ext_fit<5><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
+  k_ext_fit<6><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
+  k_ext_fit<7><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
+  k_ext_select<<<rows_grid, 128, 0, L.stream>>>(w, g, c.x, xc);
+  KT_END(L, K_TC_EXT);
+  *L.launches += 6;
 }
 
 // the grid's cells per event

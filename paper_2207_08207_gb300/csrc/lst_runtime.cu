@@ -375,6 +375,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.cell_cnt, NC); z.add(w.cell_cur, NC);
   z.add(w.work_cnt, 32); z.add(w.work_cur, 32);
   z.add(w.scan_ctr, kScanMax);
+  z.add(w.ext_qn, 4);
   // binning
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
   pl.add(w.bx, c.H); pl.add(w.by, c.H); pl.add(w.bz, c.H); pl.add(w.borig, c.H);
@@ -438,6 +439,11 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.tcd_off, c.E + 1);
   pl.add(w.tcd_type, tc_cap); pl.add(w.tcd_obj, tc_cap); pl.add(w.tcd_hits, 14 * tc_cap);
   pl.add(w.tcd_pt, tc_cap); pl.add(w.tcd_eta, tc_cap); pl.add(w.tcd_phi, tc_cap);
+  pl.add(w.tcd_ext_t3, tc_cap); pl.add(w.tcd_ext_n, tc_cap); pl.add(w.tcd_ext_hits, 4 * tc_cap);
+  pl.add(w.tcd_ext_c, tc_cap); pl.add(w.tcd_ext_rz, tc_cap);
+  w.ext_qcap = tc_cap / 2 + 1024;   // candidates per anchor count (about one per candidate row in all)
+  pl.add(w.ext_cnt, tc_cap); pl.add(w.ext_ref, kExtRefs * tc_cap);
+  pl.add(w.ext_q, 4 * w.ext_qcap); pl.add(w.ext_res, 4 * w.ext_qcap);
   // event-local outputs
   pl.add(w.o_md_lo, c.md_dense); pl.add(w.o_md_up, c.md_dense); pl.add(w.o_md_mod, c.md_dense);
   pl.add(w.o_ls_in, c.ls_dense); pl.add(w.o_ls_out, c.ls_dense);
@@ -478,7 +484,7 @@ int ensure_pinned(lst_ctx* ctx, size_t bytes) {
 // Enqueue the whole chain on ctx->stream. Every launch is shaped by the arena capacities, never by
 // the batch (kernels read the actual hit / seed counts from the padded event offsets), so the same
 // sequence serves every batch that fits and can be captured once as a CUDA graph.
-int enqueue_chain(lst_ctx* ctx) {
+int enqueue_chain(lst_ctx* ctx, bool capturing) {
   Ws& w = ctx->ws;
   w.E = (int32_t)ctx->caps.E;
   w.H = (int32_t)ctx->caps.H;
@@ -499,30 +505,37 @@ int enqueue_chain(lst_ctx* ctx) {
   L.scan_idx = &scan_idx;
   const Geo& g = ctx->geo;
   const Consts& c = ctx->consts;
+  L.capturing = capturing;
   CK(cudaMemsetAsync(ctx->zero_begin, 0, ctx->zero_bytes, ctx->stream));
   int ei = 0;
-  auto mark = [&]() {
-    if (ctx->timing) cudaEventRecordWithFlags(ctx->ev_stage[ei++], ctx->stream, cudaEventRecordExternal);
+  // the first stage after which an error is pending (named in the error message)
+  const char* failed_at = nullptr;
+  auto mark = [&](const char* stage) {
+    if (ctx->timing) KT_REC(L, ctx->ev_stage[ei++]);
+    if (!failed_at && cudaPeekAtLastError() != cudaSuccess) failed_at = stage;
   };
-  mark();
+  mark("start");
   run_binning(w, g, L);
   run_md(w, g, c, L);
-  mark();
+  mark("hit binning and MD");
   run_ls(w, g, c, L);
-  mark();
+  mark("LS");
   run_t3(w, g, c, L);
-  mark();
+  mark("T3");
   run_t5(w, g, c, L);
-  mark();
+  mark("T5");
   run_pixel(w, g, c, L);
-  mark();
+  mark("pT3 / pT5");
   run_tc(w, g, c, L);
-  mark();
+  mark("TC");
   // (the event-local copies of member indices are written with the dense objects)
   k_ev_stat<<<grid_for(w.E, 64), 64, 0, ctx->stream>>>(w, g.n_mods);
   ctx->launches += 1;
-  mark();
-  CK(cudaGetLastError());
+  mark("summary");
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess)
+    return fail(ctx, LST_ECUDA, std::string("chain launch (first error after: ") + (failed_at ? failed_at : "?") +
+                                    "): " + cudaGetErrorString(le));
   CK(cudaMemcpyAsync(ctx->h_status, w.status, (ST_N_WORDS + (size_t)w.E * kEvWords) * sizeof(int32_t),
                      cudaMemcpyDeviceToHost, ctx->stream));
   return LST_OK;
@@ -531,7 +544,7 @@ int enqueue_chain(lst_ctx* ctx) {
 int launch_chain(lst_ctx* ctx) {
   const bool graph = ctx->cfg.use_graph != 0;
   if (!graph) {
-    int rc = enqueue_chain(ctx);
+    int rc = enqueue_chain(ctx, false);
     if (rc) return rc;
   } else {
     // the timing events, when enabled, are captured as event-record nodes of the graph
@@ -540,7 +553,7 @@ int launch_chain(lst_ctx* ctx) {
       ctx->graph_exec = nullptr;
       CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
       const long long before = ctx->launches;
-      const int rc = enqueue_chain(ctx);
+      const int rc = enqueue_chain(ctx, true);
       cudaGraph_t gr = nullptr;
       const cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
       if (rc) {
@@ -1071,6 +1084,7 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     c.n_pls = ctx->ev_pls[ev];
     c.n_md = es[0]; c.n_ls = es[1]; c.n_t3 = es[2]; c.n_t5 = es[3]; c.n_pt3 = es[4]; c.n_pt5 = es[5]; c.n_tc = es[6];
     for (int k = 0; k < 4; ++k) c.n_tc_type[k] = es[7 + k];
+    c.n_tc_ext = es[kEvExt];
     for (int s = 0; s < LST_N_STAGES; ++s) c.overflow[s] = ctx->first_ovf[s];
     c.recheck[LST_STAGE_MD] = st[ST_REC_MD];
     c.recheck[LST_STAGE_LS] = st[ST_REC_LS];
@@ -1110,6 +1124,9 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     o.pt5_pls = w.o_pt5_pls + bp5; o.pt5_t5 = w.o_pt5_obj + bp5; o.pt5_chi2_xy = w.pt5_xy + bp5; o.pt5_chi2_rz = w.pt5_rz + bp5;
     o.tc_type = w.tcd_type + btc; o.tc_obj = w.tcd_obj + btc; o.tc_hits = w.tcd_hits + (int64_t)btc * 14;
     o.tc_pt = w.tcd_pt + btc; o.tc_eta = w.tcd_eta + btc; o.tc_phi = w.tcd_phi + btc;
+    o.tc_ext_t3 = w.tcd_ext_t3 + btc; o.tc_ext_n_md = w.tcd_ext_n + btc;
+    o.tc_ext_hits = w.tcd_ext_hits + (int64_t)btc * 4;
+    o.tc_ext_chi2_c = w.tcd_ext_c + btc; o.tc_ext_chi2_rz = w.tcd_ext_rz + btc;
     if (ctx->user_out) ctx->user_out[ev] = o;
   }
   return first_err;
@@ -1167,6 +1184,23 @@ int lst_copy_tc(lst_ctx* ctx, int32_t ev, int32_t* type, int32_t* obj, int32_t* 
   if (pt) CK(cudaMemcpyAsync(pt, o.tc_pt, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
   if (eta) CK(cudaMemcpyAsync(eta, o.tc_eta, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
   if (phi) CK(cudaMemcpyAsync(phi, o.tc_phi, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LST_OK;
+}
+
+int lst_copy_tc_ext(lst_ctx* ctx, int32_t ev, int32_t* t3, int32_t* n_md, int32_t* hits, float* chi2_c,
+                    float* chi2_rz) {
+  if (!ctx) return LST_EINVAL;
+  if (ev < 0 || ev >= (int32_t)ctx->outs.size()) return fail(ctx, LST_EINVAL, "lst_copy_tc_ext: no such event");
+  CK(cudaSetDevice(ctx->device));
+  const lst_event_out& o = ctx->outs[ev];
+  const size_t n = o.counts.n_tc;
+  if (n == 0) return LST_OK;
+  if (t3) CK(cudaMemcpyAsync(t3, o.tc_ext_t3, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (n_md) CK(cudaMemcpyAsync(n_md, o.tc_ext_n_md, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (hits) CK(cudaMemcpyAsync(hits, o.tc_ext_hits, n * 4 * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (chi2_c) CK(cudaMemcpyAsync(chi2_c, o.tc_ext_chi2_c, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (chi2_rz) CK(cudaMemcpyAsync(chi2_rz, o.tc_ext_chi2_rz, n * 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return LST_OK;
 }

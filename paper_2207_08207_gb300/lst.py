@@ -25,7 +25,8 @@ STAGES = ["md", "ls", "t3", "t5", "pt3", "pt5", "tc", "queue"]
 TC_TYPES = ["pT5", "pT3", "T5", "pLS"]
 
 KERNELS = ["bin_sort_gather", "md", "md_compact", "ls", "ls_compact", "t3_pre", "t3_decide", "t3_compact",
-           "t5_pre", "t5_decide", "pt3_pre", "pt5_pre", "pt3_decide", "pt5_decide", "t5_clean", "tc_assemble"]
+           "t5_pre", "t5_decide", "pt3_pre", "pt5_pre", "pt3_decide", "pt5_decide", "t5_clean", "tc_assemble",
+           "tc_ext"]
 
 _CONST_FIELDS = ["k", "pt_thr", "sin_max", "z_lum", "d0_max", "n_sigma", "sigma_rphi", "sigma_z", "sigma_r",
                  "chi2_t3", "chi2_t5_c", "chi2_t5_rz", "chi2_pt3_xy", "chi2_pt3_rz", "chi2_pt5_xy",
@@ -50,11 +51,11 @@ class Counts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("n_hits", "n_pls", "n_md", "n_ls", "n_t3", "n_t5", "n_pt3",
                                               "n_pt5", "n_tc")] + [
         ("n_tc_type", ctypes.c_int32 * 4), ("overflow", ctypes.c_int32 * 8), ("recheck", ctypes.c_int32 * 8),
-        ("retries", ctypes.c_int32), ("status", ctypes.c_int32)]
+        ("retries", ctypes.c_int32), ("status", ctypes.c_int32), ("n_tc_ext", ctypes.c_int32)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n in ("n_hits", "n_pls", "n_md", "n_ls", "n_t3", "n_t5", "n_pt3", "n_pt5",
-                                           "n_tc", "retries", "status")}
+                                           "n_tc", "retries", "status", "n_tc_ext")}
         d["n_tc_type"] = dict(zip(TC_TYPES, list(self.n_tc_type)))
         d["overflow"] = dict(zip(STAGES, list(self.overflow)))
         d["recheck"] = dict(zip(STAGES, list(self.recheck)))
@@ -77,6 +78,8 @@ OUT_FIELDS = [
     ("pt5_chi2_rz", "f4", "n_pt5"),
     ("tc_type", "i4", "n_tc"), ("tc_obj", "i4", "n_tc"), ("tc_hits", "i4", "n_tc14"),
     ("tc_pt", "f4", "n_tc"), ("tc_eta", "f4", "n_tc"), ("tc_phi", "f4", "n_tc"),
+    ("tc_ext_t3", "i4", "n_tc"), ("tc_ext_n_md", "i4", "n_tc"), ("tc_ext_hits", "i4", "n_tc4"),
+    ("tc_ext_chi2_c", "f4", "n_tc"), ("tc_ext_chi2_rz", "f4", "n_tc"),
 ]
 
 
@@ -116,6 +119,7 @@ def lib():
                                            ctypes.c_void_p, ctypes.c_void_p]
         L.lst_get_counts.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Counts)]
         L.lst_copy_tc.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 6
+        L.lst_copy_tc_ext.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 5
         L.lst_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.lst_get_stage_ms.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.lst_tc_total.argtypes = [ctypes.c_void_p]
@@ -276,6 +280,7 @@ class Context:
         c = o.counts
         lens = {k: getattr(c, k) for k in ("n_md", "n_ls", "n_t3", "n_t5", "n_pt3", "n_pt5", "n_tc")}
         lens["n_tc14"] = c.n_tc * 14
+        lens["n_tc4"] = c.n_tc * 4
         out = {}
         for f, t, nk in OUT_FIELDS:
             n = lens[nk]
@@ -285,6 +290,7 @@ class Context:
             else:
                 out[f] = torch.as_tensor(_CudaArray(ptr, n, t), device=f"cuda:{self.device}")
         out["tc_hits"] = out["tc_hits"].view(-1, 14)
+        out["tc_ext_hits"] = out["tc_ext_hits"].view(-1, 4)
         return out
 
     def results(self, ev: int = 0) -> dict:
@@ -299,6 +305,15 @@ class Context:
                "pt": np.zeros(n, np.float32), "eta": np.zeros(n, np.float32), "phi": np.zeros(n, np.float32)}
         self._check(self._L.lst_copy_tc(self._h, ev, _ptr(out["type"]), _ptr(out["obj"]), _ptr(out["hits"]),
                                         _ptr(out["pt"]), _ptr(out["eta"]), _ptr(out["phi"])))
+        return out
+
+    def copy_tc_ext(self, ev: int = 0) -> dict:
+        """Event `ev`'s track extensions (one per TC row) in host memory."""
+        n = self.counts(ev)["n_tc"]
+        out = {"t3": np.zeros(n, np.int32), "n_md": np.zeros(n, np.int32), "hits": np.zeros((n, 4), np.int32),
+               "chi2_c": np.zeros(n, np.float32), "chi2_rz": np.zeros(n, np.float32)}
+        self._check(self._L.lst_copy_tc_ext(self._h, ev, _ptr(out["t3"]), _ptr(out["n_md"]), _ptr(out["hits"]),
+                                            _ptr(out["chi2_c"]), _ptr(out["chi2_rz"])))
         return out
 
     def copy_tc_all(self, out=None) -> dict:

@@ -19,7 +19,7 @@ REL = 1e-4
 FLOOR = {"kappa": 1e-6, "chi2": 1e-3, "angle": 1e-4, "pt": 1e-3, "length": 1e-3, "eta": 1e-4}
 
 
-def _close(a, b, floor, angle=False):
+def _close(a, b, floor, angle=False, rel=None):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     if angle:
@@ -28,7 +28,7 @@ def _close(a, b, floor, angle=False):
         d = np.abs(a - b)
     both_inf = np.isinf(a) & np.isinf(b) & (np.sign(a) == np.sign(b))
     scale = np.maximum(np.maximum(np.abs(np.where(np.isinf(a), 0, a)), np.abs(np.where(np.isinf(b), 0, b))), floor)
-    return both_inf | (d <= REL * scale)
+    return both_inf | (d <= (REL if rel is None else rel) * scale)
 
 
 def _kappa(R):
@@ -78,7 +78,10 @@ FLOAT_CHECKS = {
 }
 
 
-def compare_event(ref, got, ev=None, check_floats=True) -> dict:
+def compare_event(ref, got, ev=None, check_floats=True, rel=None, floor_scale=1.0,
+                  rel_stages=("t3", "t5", "pt3", "pt5", "tc_ext")) -> dict:
+    """rel / floor_scale: a tighter float tolerance than the shipped 1e-4 (relative) and floors, for
+    the stages in rel_stages (those evaluated in double-float)."""
     rep = {"ok": True, "errors": []}
     rk, gk = oracle_keys(ref), gpu_keys(got)
     n_all = 0
@@ -117,7 +120,9 @@ def compare_event(ref, got, ev=None, check_floats=True) -> dict:
                     if kind == "kappa":
                         if ocol == "R":
                             a, b = _kappa(a), _kappa(b)
-                    ok = _close(a, b, FLOOR[kind], angle=(kind == "angle"))
+                    tight = stage in rel_stages
+                    ok = _close(a, b, FLOOR[kind] * (floor_scale if tight else 1.0), angle=(kind == "angle"),
+                                rel=rel if tight else None)
                     if not ok.all():
                         bad = np.nonzero(~ok)[0][:3]
                         rep["errors"].append(f"{stage}.{ocol}: {int((~ok).sum())} floats differ, e.g. "
@@ -184,6 +189,38 @@ def compare_event(ref, got, ev=None, check_floats=True) -> dict:
             ok = _close(rtc[ocol], got[gcol], FLOOR[kind], angle=(kind == "angle"))
             if not ok.all():
                 rep["errors"].append(f"tc.{ocol}: {int((~ok).sum())} floats differ")
+
+    # track extensions (Sec. 2.5.1), row by row on the rows that match: the MDs added, their hits
+    # and the extending T3 (by its hit key) exactly, the fit chi2 within the float tolerance; rows
+    # where one of the oracle's candidate T3 was borderline are skipped
+    ext = ref.get("tc_ext")
+    if ext is not None and "tc_ext_n_md" in got:
+        ridx = [i for i in range(len(r_rows)) if not tainted(r_rows[i], rtc["eta"][i], rtc["phi"][i])]
+        gidx = [i for i in range(len(g_rows)) if not tainted(g_rows[i], got["tc_eta"][i], got["tc_phi"][i])]
+        n_cmp = n_ext = n_bad = 0
+        if [r_rows[i] for i in ridx] == [g_rows[i] for i in gidx]:
+            for i, j in zip(ridx, gidx):
+                if not ext["definite"][i]:
+                    continue
+                n_cmp += 1
+                ro = (int(ext["n_add"][i]),) + tuple(int(ext[f"hit{k}"][i]) for k in range(4))
+                go = (int(got["tc_ext_n_md"][j]),) + tuple(int(h) for h in got["tc_ext_hits"][j])
+                same = ro == go
+                if same and ro[0] > 0:
+                    n_ext += 1
+                    gt = int(got["tc_ext_t3"][j])
+                    same = 0 <= gt < len(gk["t3"]) and gk["t3"][gt] == rk["t3"][int(ext["t3"][i])]
+                    if same and check_floats:
+                        tight = "tc_ext" in rel_stages
+                        fl = FLOOR["chi2"] * (floor_scale if tight else 1.0)
+                        r_ = rel if tight else None
+                        same = bool(_close(ext["chi2_c"][i], got["tc_ext_chi2_c"][j], fl, rel=r_)) and \
+                            bool(_close(ext["chi2_rz"][i], got["tc_ext_chi2_rz"][j], fl, rel=r_))
+                n_bad += not same
+        rep["n_tc_ext"] = n_ext
+        rep["n_tc_ext_compared"] = n_cmp
+        if n_bad:
+            rep["errors"].append(f"tc_ext: {n_bad} of {n_cmp} rows differ")
     rep["ok"] = not rep["errors"]
     return rep
 

@@ -28,7 +28,9 @@ def ffc():
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
         cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
         tmp = f"{LIB}.{os.getpid()}.tmp"
-        subprocess.run(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-I" + cuda_inc,
+        # -ffp-contract=off: the header's host path relies on each product and sum being rounded on
+        # its own, as its device path does through non-contractible intrinsics
+        subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-I" + cuda_inc,
                         "-I" + os.path.dirname(HDR), "-o", tmp, SRC], check=True)
         os.replace(tmp, LIB)
     L = ctypes.CDLL(LIB)

@@ -55,3 +55,29 @@ def test_many_pls_candidates_sorted_as_permutation(n):
     rt = ref["tc"]
     ref_rows = sorted(tuple(sorted(int(rt[f"hit{k}"][i]) for k in range(4))) for i in range(len(rt["type"])))
     assert ref_rows == keys
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_stage_timing_with_and_without_graph(graph):
+    """Per-stage and per-kernel timing works with plain launches and inside a captured graph, and
+    switching it off and on again (a new capture each time) keeps the context usable, with device
+    and in-place host inputs."""
+    det = gen.make_detector(barrel_only=False, pt_thr=0.8)
+    evs = [gen.small_event(600, seed=80 + k)[1] for k in range(3)]
+    ctx = lst.Context(det, use_graph=graph)
+    try:
+        ref = None
+        for timing in (True, False, True):
+            ctx.set_timing(timing)
+            ctx.run(evs)
+            got = [ctx.counts(e)["n_tc"] for e in range(3)]
+            ref = ref or got
+            assert got == ref
+            if timing:
+                st, km = ctx.stage_ms(), ctx.kernel_ms()
+                assert st["total"] > 0 and km["ls"] > 0 and km["tc_ext"] > 0
+            ctx.submit(evs, host_async=True)
+            ctx.sync()
+            assert [ctx.counts(e)["n_tc"] for e in range(3)] == ref
+    finally:
+        ctx.close()

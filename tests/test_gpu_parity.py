@@ -245,3 +245,16 @@ def test_executor_modes_identical(det_full, ctx_full, persistent, graph):
         ctx.run(evs)
         assert ctx.launch_count() - n0 > 50   # graph replays count their kernel nodes
     ctx.close()
+
+
+def test_double_float_outputs_agree_to_1e6(det_full, ctx_full):
+    """The T3 / T5 / pT3 / pT5 and extension floats are computed in double-float (~1e-14 per
+    operation) and stored as float32: they must agree with the float64 oracle to float32 storage
+    precision, far inside the shipped 1e-4 tolerance. (A product contracted into a following
+    addition by the compiler degrades the double-float operations to about float precision; this
+    catches it.)"""
+    _, ev = gen.config_event(2, 3)
+    ctx_full.run([ev])
+    rep = parity.compare_event(oracle.run(det_full, ev), ctx_full.results(0), ev, rel=1e-6, floor_scale=1e-3)
+    assert rep["ok"], rep["errors"]
+    assert rep["n_tc_ext"] > 1000

@@ -29,6 +29,9 @@ def key_sets(r):
     out["pt5"] = {(int(p), t5k[o], bool(s)) for p, o, s in zip(r["pt5"]["pls"], r["pt5"]["obj"], r["pt5"]["pass"])}
     tc = r["tc"]
     out["tc"] = [(int(tc["type"][i]),) + tuple(int(tc[f"hit{k}"][i]) for k in range(14)) for i in range(len(tc["type"]))]
+    ext = r["tc_ext"]
+    out["tc_ext"] = [(int(ext["n_add"][i]), t3k[ext["t3"][i]] if ext["t3"][i] >= 0 else None, bool(ext["definite"][i]))
+                     + tuple(int(ext[f"hit{k}"][i]) for k in range(4)) for i in range(len(ext["t3"]))]
     return out
 
 
