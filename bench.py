@@ -271,6 +271,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-streams", action="store_true")
+    ap.add_argument("--no-half", action="store_true")
     ap.add_argument("--serving-rates", default="500,1000,2000,3000",
                     help="comma-separated Poisson rates (events/s) of the serving measurement")
     args = ap.parse_args()
@@ -400,6 +401,35 @@ def main():
         plain = {"events_per_s": 1e3 / statistics.mean(lat), "p50_ms": float(np.percentile(lat_s, 50)),
                  "p99_ms": float(np.percentile(lat_s, 99)), "events": len(lat)}
 
+    # half-precision storage of the output-only per-object floats (Sec. 5): the same batched launch
+    # with binary16 columns; objects are identical (GPU test), the arenas smaller
+    half = None
+    if not args.no_half:
+        hctx = lst.Context(det, device=local, use_graph=1, half_floats=1, **tuned)
+        hctx.reserve(B, max(e.n_hits for e in evs), max(e.n_pls for e in evs))
+        for _ in range(3):
+            hctx.submit(dev, stream=stream)
+            hctx.sync()
+        hms = []
+        for _ in range(max(5, args.steps // 2)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hctx.submit(dev, stream=stream)
+            hctx.sync()
+            e1.record(stream)
+            e1.synchronize()
+            hms.append(e0.elapsed_time(e1))
+        nh, npl = sum(e.n_hits for e in evs), sum(e.n_pls for e in evs)
+        b32, b16 = ctx.predict_bytes(B, nh, npl), hctx.predict_bytes(B, nh, npl)
+        c = counts
+        n_vals = sum(2 * x["n_md"] + 2 * x["n_ls"] + 4 * x["n_t3"] + 3 * x["n_t5"] + 2 * x["n_pt3"] + 2 * x["n_pt5"]
+                     for x in c)
+        half = {"events_per_s": B / (statistics.mean(hms) / 1e3), "ms_per_step": statistics.mean(hms),
+                "arena_bytes_float32": b32, "arena_bytes_half": b16,
+                "output_bytes_saved_per_event": 2 * n_vals / B}
+        hctx.close()
+
     # the paper's multi-stream plain path (Sec. 4.2.2, Table 1): N one-event contexts on their own
     # streams, fed round-robin, inputs resident; events/s over the whole batch of events
     streams = None
@@ -504,6 +534,7 @@ def main():
                            "batched_p99": float(np.percentile(step_ms, 99))},
             "plain": plain,
             "streams": streams,
+            "half_floats": half,
             "physics": phys,
             "serving": serving,
             "tuned": tuned,

@@ -98,6 +98,16 @@ typedef struct {
   int64_t cycle_budget;     /* per-warp clock64 budget of the candidate kernels (MD, LS, T3, pT3/pT5 loops);
                                0 = none. A warp past it stops taking work and the run ends with
                                LST_ETIMEOUT (results incomplete; the context stays usable) */
+  int32_t half_floats;      /* 1: store the output-only per-object floats as IEEE binary16 (round to
+                               nearest) instead of float32, halving their device memory and copy-out
+                               bytes (the "half precision" storage of Sec. 5): MD dPhiChange and pT
+                               estimate, LS z0 and dphi, T3 centre, r-z chi2 and pT estimate, T5
+                               kappa_in, kappa_out and r-z chi2, pT3 / pT5 chi2_xy and chi2_rz. No
+                               selection reads these values, so every object and every other output
+                               is the same; their float32 pointers in lst_event_out are then NULL and
+                               the *_h pointers hold them. binary16 spans +-65504: larger magnitudes
+                               (the centre of a nearly straight T3's circle, a huge chi2) are stored as
+                               +-inf, as the round-to-nearest conversion gives. Default 0. */
 } lst_config;
 
 /* One detector module (a pair of closely spaced sensors, "bi-layer pT module", Sec. 1). */
@@ -193,6 +203,12 @@ typedef struct {
    * not extended. */
   const int32_t *tc_ext_t3, *tc_ext_n_md, *tc_ext_hits;
   const float *tc_ext_chi2_c, *tc_ext_chi2_rz;
+  /* With lst_config.half_floats = 1: the output-only columns as IEEE binary16 bit patterns (the
+   * float32 pointers of the same columns are then NULL); NULL otherwise. */
+  const uint16_t *md_dphichange_h, *md_pt_est_h, *ls_z0_h, *ls_dphi_h;
+  const uint16_t *t3_xc_h, *t3_yc_h, *t3_chi2_rz_h, *t3_pt_est_h;
+  const uint16_t *t5_kappa_in_h, *t5_kappa_out_h, *t5_chi2_rz_h;
+  const uint16_t *pt3_chi2_xy_h, *pt3_chi2_rz_h, *pt5_chi2_xy_h, *pt5_chi2_rz_h;
 } lst_event_out;
 
 typedef struct lst_ctx lst_ctx;

@@ -15,6 +15,7 @@
 #pragma once
 #include <cstdint>
 #include <type_traits>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lst.h"
@@ -462,6 +463,13 @@ __device__ __forceinline__ float rel_phi(float x, float y, float phic) {
   if (d > 3.14159265f) d -= 6.28318531f;
   return d;
 }
+// An output-only per-object float: stored as IEEE binary16 (round to nearest) when the half array
+// is set, else as float32.
+__device__ __forceinline__ void store_out(float* f32, uint16_t* f16, int64_t i, float v) {
+  if (f16) f16[i] = __half_as_ushort(__float2half_rn(v));
+  else f32[i] = v;
+}
+
 // Unsigned key with the order of the float (for sorting floats as integers)
 __device__ __forceinline__ unsigned float_key(float f) {
   const unsigned u = __float_as_uint(f);

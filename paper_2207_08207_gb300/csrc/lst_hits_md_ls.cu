@@ -3,6 +3,8 @@
 // Every per-module array is indexed by the virtual module vm = event * n_mods + module, so one
 // launch processes a whole batch of events; objects of different events never meet because a
 // module's connections stay inside its own event.
+#include <mutex>
+
 #include "lst_internal.h"
 
 namespace lst {
@@ -383,8 +385,8 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
     w.o_md_lo[d] = w.borig[lo];   // event-local outputs: input hit indices, module
     w.o_md_up[d] = w.borig[up];
     w.o_md_mod[d] = vm % g.n_mods;
-    w.md_dpc[d] = w.ms_dpc[s];
-    w.md_pte[d] = w.ms_pte[s];
+    store_out(w.md_dpc, w.md_dpc_h, d, w.ms_dpc[s]);
+    store_out(w.md_pte, w.md_pte_h, d, w.ms_pte[s]);
     const float x = w.bx[lo], y = w.by[lo];
     // x^2 + y^2 as an unevaluated float pair (products exact by FMA), its float32 square root, and
     // the low part of the radius: r = r_hi + (q - r_hi^2) / (2 r_hi) to float-float accuracy
@@ -792,11 +794,26 @@ inline size_t ls_smem_bytes(int block, int T) { return ls_smem_per_warp(T) * (si
 
 }  // namespace
 
+// The kernel's dynamic shared memory limit is a property of the function, shared by every context of
+// the process: it is only ever raised, to what the largest block (256 threads) of the largest map
+// loaded so far needs, so that no context lowers it below what another one launches with.
 int ls_resident_blocks(int block, int T) {
+  static std::mutex mu;
+  static size_t limit = 0;
   const size_t bytes = ls_smem_bytes(block, T);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const size_t want = ls_smem_bytes(256, T);
+    if (want > limit) {
+      if (cudaFuncSetAttribute(k_ls, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      limit = want;
+    }
+  }
   int n = 0;
-  if (cudaFuncSetAttribute(k_ls, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ls, block, bytes) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ls, block, bytes) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

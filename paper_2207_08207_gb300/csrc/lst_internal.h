@@ -53,6 +53,7 @@ struct Caps {
   int64_t md_dense = 0, ls_dense = 0, t3_dense = 0, t5_dense = 0;   // dense (compacted) objects
   int64_t q_md = 0, q_ls = 0, q_t3 = 0, q_t5 = 0, q_p3 = 0, q_p5 = 0;
   int64_t n_mods = 0;
+  int64_t half = 0;   // 1: the output-only per-object floats are stored as binary16
 };
 
 // Per-batch workspace: every device array the chain uses. Passed to kernels by value.
@@ -88,6 +89,13 @@ struct Ws {
   float2* md_sa = nullptr;       // [md_dense] (arc length at R_thr, alpha_thr(r) = asin(min(r k / (2 pT_thr), sin_max)))
   float *md_dpc = nullptr, *md_pte = nullptr;
   uint8_t* md_ec = nullptr;
+  // binary16 storage of the output-only per-object floats (lst_config.half_floats; nullptr
+  // otherwise, and then their float32 arrays are used): MD dPhiChange, pT estimate; LS z0, dphi;
+  // T3 centre, r-z chi2, pT estimate; T5 kappa_in, kappa_out, r-z chi2 ([3][t5_dense]); pT3 / pT5
+  // chi2_xy, chi2_rz
+  uint16_t *md_dpc_h = nullptr, *md_pte_h = nullptr, *ls_z0_h = nullptr, *ls_dphi_h = nullptr;
+  uint16_t *t3_xc_h = nullptr, *t3_yc_h = nullptr, *t3_chi2_h = nullptr, *t3_pte_h = nullptr, *t5_h = nullptr;
+  uint16_t *pt3_xy_h = nullptr, *pt3_rz_h = nullptr, *pt5_xy_h = nullptr, *pt5_rz_h = nullptr;
   float* md_rphi = nullptr;      // [md_dense] anchor azimuth relative to its module's centre, (-pi, pi]:
                                  // the MDs of a module are ordered by it (hits are binned in azimuth order)
   int32_t *md_rmin = nullptr, *md_rmax = nullptr;   // [V] smallest / largest anchor radius of each
@@ -376,8 +384,8 @@ __device__ __forceinline__ void ls_dense_write(const Ws& w, bool valid, int d, i
     const float r1l = w.md_rlo[a], r2l = w.md_rlo[b];
     const float num = diff_prod(pa.z, pb.w, pb.z, pa.w) + (pa.z * r2l - pb.z * r1l);
     const float den = (pb.w - pa.w) + (r2l - r1l);
-    w.ls_z0[d] = num / den;
-    w.ls_dphi[d] = w.lss_dphi[s];
+    store_out(w.ls_z0, w.ls_z0_h, d, num / den);
+    store_out(w.ls_dphi, w.ls_dphi_h, d, w.lss_dphi[s]);
     w.ls_xy_out[d] = make_float2(pb.x, pb.y);
     vm = w.md_vm[a];
     outs = (unsigned)(min(lsin_off[b + 1], n) - min(lsin_off[b], n));
@@ -408,10 +416,10 @@ __device__ __forceinline__ void t3_dense_write(const Ws& w, bool valid, int d, i
     w.t3_md1[d] = md[1];
     w.t3_md2[d] = md[2];
     w.t3_R[d] = w.t3s_R[s];
-    w.t3_xc[d] = w.t3s_xc[s];
-    w.t3_yc[d] = w.t3s_yc[s];
-    w.t3_chi2[d] = w.t3s_chi2[s];
-    w.t3_pte[d] = w.t3s_pte[s];
+    store_out(w.t3_xc, w.t3_xc_h, d, w.t3s_xc[s]);
+    store_out(w.t3_yc, w.t3_yc_h, d, w.t3s_yc[s]);
+    store_out(w.t3_chi2, w.t3_chi2_h, d, w.t3s_chi2[s]);
+    store_out(w.t3_pte, w.t3_pte_h, d, w.t3s_pte[s]);
     uint8_t ecm = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

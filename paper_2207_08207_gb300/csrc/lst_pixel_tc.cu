@@ -512,7 +512,7 @@ template <int Type>
 __global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
     Ws w, const int32_t* off, int32_t* tmp_idx, const int32_t* a_pls, const int32_t* a_obj, const float* a_xy,
     const float* a_rz, const float* a_sc, int32_t* d_pls, int32_t* d_obj, float* d_xy, float* d_rz, float* d_sc,
-    int32_t* best, int32_t* o_pls, int32_t* o_obj, const int32_t* obj_off) {
+    int32_t* best, int32_t* o_pls, int32_t* o_obj, const int32_t* obj_off, uint16_t* d_xy_h, uint16_t* d_rz_h) {
   constexpr int kPtLanes = pt_lanes<Type>();
   const int n_mods = w.V / w.E;
   __shared__ int keys[32 * kPtOrderWarps / kPtLanes][kPtStage];
@@ -540,7 +540,9 @@ __global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
       for (int j = 0; j < n; ++j) rank += __shfl_sync(gmask, key, j, kPtLanes) < key;
       if (sub < n) {
         const int o = a + rank;
-        d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+        d_pls[o] = a_pls[v]; d_obj[o] = key; d_sc[o] = a_sc[v];
+        store_out(d_xy, d_xy_h, o, a_xy[v]);
+        store_out(d_rz, d_rz_h, o, a_rz[v]);
         pt_local(w, p, key, o, n_mods, o_pls, o_obj, obj_off);
       }
     } else {
@@ -554,7 +556,9 @@ __global__ void __launch_bounds__(32 * kPtOrderWarps) k_pt_order(
         int rank = 0;
         for (int j = 0; j < n; ++j) rank += (staged ? K[j] : a_obj[tmp_idx[a + j]]) < key;
         const int o = a + rank;
-        d_pls[o] = a_pls[v]; d_obj[o] = key; d_xy[o] = a_xy[v]; d_rz[o] = a_rz[v]; d_sc[o] = a_sc[v];
+        d_pls[o] = a_pls[v]; d_obj[o] = key; d_sc[o] = a_sc[v];
+        store_out(d_xy, d_xy_h, o, a_xy[v]);
+        store_out(d_rz, d_rz_h, o, a_rz[v]);
         pt_local(w, p, key, o, n_mods, o_pls, o_obj, obj_off);
       }
     }
@@ -1291,12 +1295,12 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
                                                                    w.p3a_obj, w.pt3_off, w.p3_cur, w.grp_tmp);
   k_pt_order<TC_PT3><<<grid_for((int64_t)w.P * pt_lanes<TC_PT3>(), 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt3_off, w.grp_tmp, w.p3a_pls, w.p3a_obj, w.p3a_xy, w.p3a_rz, w.p3a_sc, w.pt3_pls, w.pt3_obj,
-      w.pt3_xy, w.pt3_rz, w.pt3_sc, w.best3, w.o_pt3_pls, w.o_pt3_obj, w.t3_off);
+      w.pt3_xy, w.pt3_rz, w.pt3_sc, w.best3, w.o_pt3_pls, w.o_pt3_obj, w.t3_off, w.pt3_xy_h, w.pt3_rz_h);
   k_pt_group<<<grid_for(w.cap.p5_slots, 256), 256, 0, L.stream>>>(w, ST_N_PT5, w.cap.p5_slots, w.p5a_pls,
                                                                    w.p5a_obj, w.pt5_off, w.p5_cur, w.grp_tmp);
   k_pt_order<TC_PT5><<<grid_for((int64_t)w.P * pt_lanes<TC_PT5>(), 32 * kPtOrderWarps), 32 * kPtOrderWarps, 0, L.stream>>>(
       w, w.pt5_off, w.grp_tmp, w.p5a_pls, w.p5a_obj, w.p5a_xy, w.p5a_rz, w.p5a_sc, w.pt5_pls, w.pt5_obj,
-      w.pt5_xy, w.pt5_rz, w.pt5_sc, w.best5, w.o_pt5_pls, w.o_pt5_obj, w.t5_off);
+      w.pt5_xy, w.pt5_rz, w.pt5_sc, w.best5, w.o_pt5_pls, w.o_pt5_obj, w.t5_off, w.pt5_xy_h, w.pt5_rz_h);
   *L.launches += 4;
 }
 

@@ -330,6 +330,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
 int plan_work(lst_ctx* ctx, const Caps& want) {
   Caps c = want;
   c.E = ctx->in_caps.E;   // event offsets (padded to E) live in the input arena
+  c.half = ctx->cfg.half_floats != 0;
   size_t zb = 0;
   const size_t total = layout_work(ctx->ws, c, ctx->geo.n_mods, nullptr, &zb);
   if (ctx->work_mem) CK(cudaFreeAsync(ctx->work_mem, ctx->stream));
@@ -393,27 +394,39 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.ms_lo, c.md_slots); pl.add(w.ms_up, c.md_slots); pl.add(w.ms_dpc, c.md_slots); pl.add(w.ms_pte, c.md_slots);
   pl.add(w.md_lo, c.md_dense); pl.add(w.md_up, c.md_dense); pl.add(w.md_vm, c.md_dense);
   pl.add(w.md_rlo, c.md_dense);
-  pl.add(w.md_dpc, c.md_dense); pl.add(w.md_pte, c.md_dense); pl.add(w.md_ec, c.md_dense);
+  // output-only floats: float32 arrays, or binary16 ones when c.half (the others stay nullptr)
+  auto out_f = [&](float*& f32, uint16_t*& f16, int64_t n) {
+    f32 = nullptr;
+    f16 = nullptr;
+    if (c.half) pl.add(f16, n);
+    else pl.add(f32, n);
+  };
+  out_f(w.md_dpc, w.md_dpc_h, c.md_dense); out_f(w.md_pte, w.md_pte_h, c.md_dense);
+  pl.add(w.md_ec, c.md_dense);
   pl.add(w.md_xyzr, c.md_dense); pl.add(w.md_sa, c.md_dense); pl.add(w.md_rphi, c.md_dense);
   pl.add(w.md_rmin, V); pl.add(w.md_rmax, V);
   // LS
   pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1); pl.add(w.lsin_off, c.md_dense + 2);
   pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
-  pl.add(w.ls_in, c.ls_dense); pl.add(w.ls_out, c.ls_dense); pl.add(w.ls_z0, c.ls_dense); pl.add(w.ls_dphi, c.ls_dense);
+  pl.add(w.ls_in, c.ls_dense); pl.add(w.ls_out, c.ls_dense);
+  out_f(w.ls_z0, w.ls_z0_h, c.ls_dense); out_f(w.ls_dphi, w.ls_dphi_h, c.ls_dense);
   pl.add(w.ls_xy_out, c.ls_dense);
   // T3
   pl.add(w.t3_cap, V); pl.add(w.t3_base, V + 1); pl.add(w.t3_off, V + 1);
   pl.add(w.t3s_a, c.t3_slots); pl.add(w.t3s_b, c.t3_slots); pl.add(w.t3s_R, c.t3_slots); pl.add(w.t3s_xc, c.t3_slots);
   pl.add(w.t3s_yc, c.t3_slots); pl.add(w.t3s_chi2, c.t3_slots); pl.add(w.t3s_pte, c.t3_slots);
   pl.add(w.t3_a, c.t3_dense); pl.add(w.t3_b, c.t3_dense); pl.add(w.t3_md0, c.t3_dense); pl.add(w.t3_md1, c.t3_dense);
-  pl.add(w.t3_md2, c.t3_dense); pl.add(w.t3_R, c.t3_dense); pl.add(w.t3_xc, c.t3_dense); pl.add(w.t3_yc, c.t3_dense);
-  pl.add(w.t3_chi2, c.t3_dense); pl.add(w.t3_pte, c.t3_dense);
+  pl.add(w.t3_md2, c.t3_dense); pl.add(w.t3_R, c.t3_dense);
+  out_f(w.t3_xc, w.t3_xc_h, c.t3_dense); out_f(w.t3_yc, w.t3_yc_h, c.t3_dense);
+  out_f(w.t3_chi2, w.t3_chi2_h, c.t3_dense); out_f(w.t3_pte, w.t3_pte_h, c.t3_dense);
   pl.add(w.t3_anc, 3 * c.t3_dense); pl.add(w.t3_anc_rlo, 3 * c.t3_dense); pl.add(w.t3_ecm, c.t3_dense);
   pl.add(w.t3md_off, c.md_dense + 2);
   // T5
   pl.add(w.t5_cap, V); pl.add(w.t5_base, V + 1); pl.add(w.t5_off, V + 1);
   pl.add(w.t5s_a, c.t5_slots); pl.add(w.t5s_b, c.t5_slots); pl.add(w.t5s_f, 8 * c.t5_slots);
   pl.add(w.t5_a, c.t5_dense); pl.add(w.t5_b, c.t5_dense); pl.add(w.t5_md, 5 * c.t5_dense); pl.add(w.t5_f, 8 * c.t5_dense);
+  w.t5_h = nullptr;
+  if (c.half) pl.add(w.t5_h, 3 * c.t5_dense);
   pl.add(w.t5_anc, 5 * c.t5_dense); pl.add(w.t5_anc_rlo, 5 * c.t5_dense); pl.add(w.t5_ecm, c.t5_dense);
   pl.add(w.t5_kept, c.t5_dense); pl.add(w.acc5t, c.t5_dense);
   pl.add(w.box3, 2 * V); pl.add(w.box5, 2 * V);
@@ -421,12 +434,12 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.pls_bin, c.P); pl.add(w.pls_ev, c.P); pl.add(w.pls_seed, 2 * c.P); pl.add(w.pls_seed_ff, 9 * c.P);
   pl.add(w.p3a_pls, c.p3_slots); pl.add(w.p3a_obj, c.p3_slots); pl.add(w.p3a_xy, c.p3_slots);
   pl.add(w.p3a_rz, c.p3_slots); pl.add(w.p3a_sc, c.p3_slots); pl.add(w.pt3_off, c.P + 1);
-  pl.add(w.pt3_pls, c.p3_slots); pl.add(w.pt3_obj, c.p3_slots); pl.add(w.pt3_xy, c.p3_slots);
-  pl.add(w.pt3_rz, c.p3_slots); pl.add(w.pt3_sc, c.p3_slots);
+  pl.add(w.pt3_pls, c.p3_slots); pl.add(w.pt3_obj, c.p3_slots);
+  out_f(w.pt3_xy, w.pt3_xy_h, c.p3_slots); out_f(w.pt3_rz, w.pt3_rz_h, c.p3_slots); pl.add(w.pt3_sc, c.p3_slots);
   pl.add(w.p5a_pls, c.p5_slots); pl.add(w.p5a_obj, c.p5_slots); pl.add(w.p5a_xy, c.p5_slots);
   pl.add(w.p5a_rz, c.p5_slots); pl.add(w.p5a_sc, c.p5_slots); pl.add(w.pt5_off, c.P + 1);
-  pl.add(w.pt5_pls, c.p5_slots); pl.add(w.pt5_obj, c.p5_slots); pl.add(w.pt5_xy, c.p5_slots);
-  pl.add(w.pt5_rz, c.p5_slots); pl.add(w.pt5_sc, c.p5_slots);
+  pl.add(w.pt5_pls, c.p5_slots); pl.add(w.pt5_obj, c.p5_slots);
+  out_f(w.pt5_xy, w.pt5_xy_h, c.p5_slots); out_f(w.pt5_rz, w.pt5_rz_h, c.p5_slots); pl.add(w.pt5_sc, c.p5_slots);
   pl.add(w.grp_tmp, std::max(c.p3_slots, c.p5_slots));
   // track candidates
   pl.add(w.best5, c.P); pl.add(w.best3, c.P); pl.add(w.pls_member, c.P); pl.add(w.acc3, c.P); pl.add(w.accl, c.P);
@@ -622,6 +635,7 @@ void lst_config_default(lst_config* c) {
   c->cap_scale = 1.0f;
   c->max_retries = 4;
   c->cycle_budget = 0;
+  c->half_floats = 0;
 }
 
 int lst_create(lst_ctx** out, const lst_config* cfg, int device) {
@@ -1111,17 +1125,33 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     const int bmd = es[11], bls = es[12], bt3 = es[13], bt5 = es[14], bp3 = es[15], bp5 = es[16], btc = es[17];
     const int64_t S5 = ctx->caps.t5_dense;
     o.md_hit_lo = w.o_md_lo + bmd; o.md_hit_up = w.o_md_up + bmd; o.md_module = w.o_md_mod + bmd;
-    o.md_dphichange = w.md_dpc + bmd; o.md_pt_est = w.md_pte + bmd;
-    o.ls_md_in = w.o_ls_in + bls; o.ls_md_out = w.o_ls_out + bls; o.ls_z0 = w.ls_z0 + bls; o.ls_dphi = w.ls_dphi + bls;
-    o.t3_ls_in = w.o_t3_a + bt3; o.t3_ls_out = w.o_t3_b + bt3; o.t3_r = w.t3_R + bt3; o.t3_xc = w.t3_xc + bt3;
-    o.t3_yc = w.t3_yc + bt3; o.t3_chi2_rz = w.t3_chi2 + bt3; o.t3_pt_est = w.t3_pte + bt3;
+    // float32 output columns, or their binary16 twins (the other pointer NULL)
+    auto f32 = [](const float* a, int64_t off) -> const float* { return a ? a + off : nullptr; };
+    auto f16 = [](const uint16_t* a, int64_t off) -> const uint16_t* { return a ? a + off : nullptr; };
+    o.md_dphichange = f32(w.md_dpc, bmd); o.md_pt_est = f32(w.md_pte, bmd);
+    o.md_dphichange_h = f16(w.md_dpc_h, bmd); o.md_pt_est_h = f16(w.md_pte_h, bmd);
+    o.ls_md_in = w.o_ls_in + bls; o.ls_md_out = w.o_ls_out + bls;
+    o.ls_z0 = f32(w.ls_z0, bls); o.ls_dphi = f32(w.ls_dphi, bls);
+    o.ls_z0_h = f16(w.ls_z0_h, bls); o.ls_dphi_h = f16(w.ls_dphi_h, bls);
+    o.t3_ls_in = w.o_t3_a + bt3; o.t3_ls_out = w.o_t3_b + bt3; o.t3_r = w.t3_R + bt3;
+    o.t3_xc = f32(w.t3_xc, bt3); o.t3_yc = f32(w.t3_yc, bt3); o.t3_chi2_rz = f32(w.t3_chi2, bt3);
+    o.t3_pt_est = f32(w.t3_pte, bt3);
+    o.t3_xc_h = f16(w.t3_xc_h, bt3); o.t3_yc_h = f16(w.t3_yc_h, bt3); o.t3_chi2_rz_h = f16(w.t3_chi2_h, bt3);
+    o.t3_pt_est_h = f16(w.t3_pte_h, bt3);
     o.t5_t3_in = w.o_t5_a + bt5; o.t5_t3_out = w.o_t5_b + bt5;
-    o.t5_kappa_in = w.t5_f + 0 * S5 + bt5; o.t5_kappa_out = w.t5_f + 1 * S5 + bt5;
+    const bool h5 = w.t5_h != nullptr;
+    o.t5_kappa_in = h5 ? nullptr : w.t5_f + 0 * S5 + bt5; o.t5_kappa_out = h5 ? nullptr : w.t5_f + 1 * S5 + bt5;
     o.t5_kappa_fit = w.t5_f + 2 * S5 + bt5; o.t5_chi2_c = w.t5_f + 3 * S5 + bt5;
-    o.t5_chi2_rz = w.t5_f + 4 * S5 + bt5; o.t5_eta = w.t5_f + 5 * S5 + bt5;
+    o.t5_chi2_rz = h5 ? nullptr : w.t5_f + 4 * S5 + bt5; o.t5_eta = w.t5_f + 5 * S5 + bt5;
     o.t5_phi = w.t5_f + 6 * S5 + bt5; o.t5_pt = w.t5_f + 7 * S5 + bt5;
-    o.pt3_pls = w.o_pt3_pls + bp3; o.pt3_t3 = w.o_pt3_obj + bp3; o.pt3_chi2_xy = w.pt3_xy + bp3; o.pt3_chi2_rz = w.pt3_rz + bp3;
-    o.pt5_pls = w.o_pt5_pls + bp5; o.pt5_t5 = w.o_pt5_obj + bp5; o.pt5_chi2_xy = w.pt5_xy + bp5; o.pt5_chi2_rz = w.pt5_rz + bp5;
+    o.t5_kappa_in_h = h5 ? w.t5_h + 0 * S5 + bt5 : nullptr; o.t5_kappa_out_h = h5 ? w.t5_h + 1 * S5 + bt5 : nullptr;
+    o.t5_chi2_rz_h = h5 ? w.t5_h + 2 * S5 + bt5 : nullptr;
+    o.pt3_pls = w.o_pt3_pls + bp3; o.pt3_t3 = w.o_pt3_obj + bp3;
+    o.pt3_chi2_xy = f32(w.pt3_xy, bp3); o.pt3_chi2_rz = f32(w.pt3_rz, bp3);
+    o.pt3_chi2_xy_h = f16(w.pt3_xy_h, bp3); o.pt3_chi2_rz_h = f16(w.pt3_rz_h, bp3);
+    o.pt5_pls = w.o_pt5_pls + bp5; o.pt5_t5 = w.o_pt5_obj + bp5;
+    o.pt5_chi2_xy = f32(w.pt5_xy, bp5); o.pt5_chi2_rz = f32(w.pt5_rz, bp5);
+    o.pt5_chi2_xy_h = f16(w.pt5_xy_h, bp5); o.pt5_chi2_rz_h = f16(w.pt5_rz_h, bp5);
     o.tc_type = w.tcd_type + btc; o.tc_obj = w.tcd_obj + btc; o.tc_hits = w.tcd_hits + (int64_t)btc * 14;
     o.tc_pt = w.tcd_pt + btc; o.tc_eta = w.tcd_eta + btc; o.tc_phi = w.tcd_phi + btc;
     o.tc_ext_t3 = w.tcd_ext_t3 + btc; o.tc_ext_n_md = w.tcd_ext_n + btc;
@@ -1261,6 +1291,7 @@ int lst_get_kernel_ms(const lst_ctx* ctx, float* ms, int32_t n) {
 int64_t lst_predict_bytes(const lst_ctx* ctx, int32_t n_events, int64_t n_hits, int64_t n_pls) {
   if (!ctx || !ctx->geo_loaded || n_events <= 0 || n_hits < 0 || n_pls < 0) return -LST_EINVAL;
   Caps c = default_caps(n_events, n_hits, n_pls, ctx->geo.n_mods);
+  c.half = ctx->cfg.half_floats != 0;
   Ws tmp{};
   size_t zb = 0;
   const size_t work = layout_work(tmp, c, ctx->geo.n_mods, nullptr, &zb);

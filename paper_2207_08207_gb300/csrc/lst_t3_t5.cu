@@ -455,7 +455,13 @@ __global__ void k_t5_dense(Ws w) {
     w.o_t5_a[d] = a - first_t3;
     w.o_t5_b[d] = b - first_t3;
 #pragma unroll
-    for (int f = 0; f < 8; ++f) w.t5_f[f * D + d] = w.t5s_f[f * S + s];
+    for (int f = 0; f < 8; ++f) {
+      // kappa_in, kappa_out and chi2_rz are outputs only (binary16 when enabled); the others are read
+      // by later selections and stay float32
+      const int h = f == 0 ? 0 : f == 1 ? 1 : f == 4 ? 2 : -1;
+      if (h >= 0 && w.t5_h) store_out(nullptr, w.t5_h + (int64_t)h * D, d, w.t5s_f[f * S + s]);
+      else w.t5_f[f * D + d] = w.t5s_f[f * S + s];
+    }
   }
 }
 

@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
     _fields_ = [(f, ctypes.c_float) for f in _CONST_FIELDS] + [
         ("t5_overlap_hits", ctypes.c_int32), ("persistent", ctypes.c_int32), ("use_graph", ctypes.c_int32),
         ("block_ls", ctypes.c_int32), ("warps_px", ctypes.c_int32), ("cap_scale", ctypes.c_float),
-        ("max_retries", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
+        ("max_retries", ctypes.c_int32), ("cycle_budget", ctypes.c_int64), ("half_floats", ctypes.c_int32)]
 
 
 class EventIn(ctypes.Structure):
@@ -80,7 +80,14 @@ OUT_FIELDS = [
     ("tc_pt", "f4", "n_tc"), ("tc_eta", "f4", "n_tc"), ("tc_phi", "f4", "n_tc"),
     ("tc_ext_t3", "i4", "n_tc"), ("tc_ext_n_md", "i4", "n_tc"), ("tc_ext_hits", "i4", "n_tc4"),
     ("tc_ext_chi2_c", "f4", "n_tc"), ("tc_ext_chi2_rz", "f4", "n_tc"),
+    # binary16 twins of the output-only columns (lst_config.half_floats = 1; NULL otherwise)
+    ("md_dphichange_h", "f2", "n_md"), ("md_pt_est_h", "f2", "n_md"), ("ls_z0_h", "f2", "n_ls"),
+    ("ls_dphi_h", "f2", "n_ls"), ("t3_xc_h", "f2", "n_t3"), ("t3_yc_h", "f2", "n_t3"),
+    ("t3_chi2_rz_h", "f2", "n_t3"), ("t3_pt_est_h", "f2", "n_t3"), ("t5_kappa_in_h", "f2", "n_t5"),
+    ("t5_kappa_out_h", "f2", "n_t5"), ("t5_chi2_rz_h", "f2", "n_t5"), ("pt3_chi2_xy_h", "f2", "n_pt3"),
+    ("pt3_chi2_rz_h", "f2", "n_pt3"), ("pt5_chi2_xy_h", "f2", "n_pt5"), ("pt5_chi2_rz_h", "f2", "n_pt5"),
 ]
+HALF_FIELDS = [f for f, t, _ in OUT_FIELDS if t == "f2"]
 
 
 class EventOut(ctypes.Structure):
@@ -286,7 +293,8 @@ class Context:
             n = lens[nk]
             ptr = getattr(o, f)
             if n == 0 or not ptr:
-                out[f] = torch.zeros(0, dtype=torch.int32 if t == "i4" else torch.float32, device=f"cuda:{self.device}")
+                dt = {"i4": torch.int32, "f4": torch.float32, "f2": torch.float16}[t]
+                out[f] = torch.zeros(0, dtype=dt, device=f"cuda:{self.device}")
             else:
                 out[f] = torch.as_tensor(_CudaArray(ptr, n, t), device=f"cuda:{self.device}")
         out["tc_hits"] = out["tc_hits"].view(-1, 14)

@@ -81,3 +81,24 @@ def test_stage_timing_with_and_without_graph(graph):
             assert [ctx.counts(e)["n_tc"] for e in range(3)] == ref
     finally:
         ctx.close()
+
+
+def test_contexts_with_different_ls_blocks_coexist():
+    """The LS kernel's shared-memory limit is process-wide: a context created later with smaller LS
+    blocks must not break the launches of an earlier context with larger ones (graph capture and
+    plain launches)."""
+    det = gen.make_detector(barrel_only=False, pt_thr=0.8)
+    evs = [gen.small_event(400, seed=90 + k)[1] for k in range(2)]
+    big = lst.Context(det, block_ls=256, use_graph=1)
+    small = lst.Context(det, block_ls=64, use_graph=0)
+    try:
+        small.run(evs)
+        ref = [small.counts(e)["n_tc"] for e in range(2)]
+        big.set_timing(True)
+        big.run(evs)
+        big.set_timing(False)   # a new capture after the small context loaded its geometry
+        big.run(evs)
+        assert [big.counts(e)["n_tc"] for e in range(2)] == ref
+    finally:
+        big.close()
+        small.close()
