@@ -1172,9 +1172,10 @@ __global__ void k_ext_cand(Ws w, Geo g, Cst<ff> c) {
   }
 }
 
-// (B) the fits of one anchor count, one thread per queued candidate
+// (B) the fits, one thread per queued candidate; blockIdx.y selects the anchor count, so a block's
+// threads all run the same fit and the four counts proceed side by side
 template <int N>
-__global__ void k_ext_fit(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
+__device__ __forceinline__ void ext_fit_region(const Ws& w, const Geo& g, const Cst<ff>& c, const ExtCuts& xc) {
   const int reg = N - 4;
   const int n = (int)min((int64_t)w.ext_qn[reg], w.ext_qcap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -1185,6 +1186,15 @@ __global__ void k_ext_fit(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
     ff ktc;
     const int K = ext_row(w, g, c, e, row, md, ktc);
     w.ext_res[reg * w.ext_qcap + k] = ext_eval<N>(w, c, md, K, d, overlap, xc.rz[N]);
+  }
+}
+
+__global__ void k_ext_fit(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
+  switch (blockIdx.y) {
+    case 0: ext_fit_region<4>(w, g, c, xc); break;
+    case 1: ext_fit_region<5>(w, g, c, xc); break;
+    case 2: ext_fit_region<6>(w, g, c, xc); break;
+    default: ext_fit_region<7>(w, g, c, xc); break;
   }
 }
 
@@ -1199,20 +1209,20 @@ __global__ void k_ext_select(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
     int md[5];
     ff ktc;
     int K = 0;
-    int best = -1, best_n = 0, best_key[6];
+    int best = -1, best_n = 0;
     float best_sc = 0.f, best_c = 0.f, best_rz = 0.f;
     auto consider = [&](int d, int overlap, float4 r) {
       if (r.w == 0.f) return;
-      int key[6];
-      t3_sorted_hits(w, d, key);
       bool better = best < 0 || r.x < best_sc;
-      if (!better && r.x == best_sc) {
+      if (!better && r.x == best_sc) {   // equal scores (rare): the sorted hit tuples decide
+        int key[6], bkey[6];
+        t3_sorted_hits(w, d, key);
+        t3_sorted_hits(w, best, bkey);
         for (int t = 0; t < 6; ++t)
-          if (key[t] != best_key[t]) { better = key[t] < best_key[t]; break; }
+          if (key[t] != bkey[t]) { better = key[t] < bkey[t]; break; }
       }
       if (better) {
         best = d; best_n = 3 - overlap; best_sc = r.x; best_c = r.y; best_rz = r.z;
-        for (int t = 0; t < 6; ++t) best_key[t] = key[t];
       }
     };
     bool slow = ncand > kExtRefs;
@@ -1340,15 +1350,12 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   for (int na = 0; na < 8; ++na) xc.rz[na] = ff(c.d.chi2_t5_rz * (na - 2) / 3.0);
   KT_BEGIN(L, K_TC_EXT);
   const int rows_grid = grid_for(w.tc_capacity, 128, 152 * 8);
-  const int fit_grid = grid_for(w.ext_qcap, 64, 152 * 8);
+  const int fit_grid = grid_for(w.ext_qcap, 64, 152 * 4);
   k_ext_cand<<<rows_grid, 128, 0, L.stream>>>(w, g, c.x);
-  k_ext_fit<4><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
-  k_ext_fit<5><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
-  k_ext_fit<6><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
-  k_ext_fit<7><<<fit_grid, 64, 0, L.stream>>>(w, g, c.x, xc);
+  k_ext_fit<<<dim3(fit_grid, 4), 64, 0, L.stream>>>(w, g, c.x, xc);
   k_ext_select<<<rows_grid, 128, 0, L.stream>>>(w, g, c.x, xc);
   KT_END(L, K_TC_EXT);
-  *L.launches += 6;
+  *L.launches += 3;
 }
 
 // the grid's cells per event
