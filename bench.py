@@ -161,7 +161,7 @@ def serving_run(det, events, rate, n_requests, batch_sizes, seed=0):
     served by resident engines of the given batch capacities."""
     from paper_2207_08207_gb300.serving import Server, poisson_arrivals
     srv = Server(det, batch_sizes=batch_sizes, max_hits=max(e.n_hits for e in events),
-                 max_pls=max(e.n_pls for e in events), budget=40e9, keep="tc", use_graph=1, persistent=1)
+                 max_pls=max(e.n_pls for e in events), budget=40e9, keep="tc", use_graph=1, persistent=2)
     reqs = [events[i % len(events)] for i in range(n_requests)]
     srv.warmup(events)   # graph capture and arena first touch on every engine
     stats, _ = srv.serve(reqs, poisson_arrivals(rate, n_requests, seed))
@@ -298,7 +298,7 @@ def main():
     torch.cuda.set_stream(stream)
 
     # batched executor: launch settings from the autotuner, chain replayed as a CUDA graph
-    tuned = {"block_ls": 128, "warps_px": 4, "persistent": 1, "cap_scale": 1.0}
+    tuned = {"block_ls": 128, "warps_px": 4, "persistent": 2, "cap_scale": 1.0}
     if not args.no_tune:
         from paper_2207_08207_gb300 import autotune
         tuned = autotune.tune(det, dev, workload=f"config{args.config}")

@@ -88,8 +88,10 @@ typedef struct {
   int32_t t5_overlap_hits;  /* T5 duplicate removal: >= this many of 10 hits shared, 7 */
 
   /* execution settings (chosen by the autotuner; defaults are safe) */
-  int32_t persistent;       /* 1 (default): persistent LS kernel over a cost-ordered list of (event, module)
-                               work items, heavy modules split in small batches; 0: grid-stride */
+  int32_t persistent;       /* LS kernel over a cost-ordered list of (event, module) work items, heavy
+                               modules split in small batches: 2 (default) persistent warps take the
+                               items from a device queue (one atomic head); 1 persistent warps with a
+                               static boustrophedon deal of the list; 0: grid-stride over modules */
   int32_t use_graph;        /* 1: capture the MD->TC chain in a CUDA graph and replay it */
   int32_t block_ls;         /* threads per LS block (64, 128, 256) */
   int32_t warps_px;         /* warps per block in the pT3/pT5 candidate kernels (1..8; else 4) */

@@ -3,7 +3,8 @@
 Tunes, on a calibration batch, the settings that change speed but never results:
   block_ls   threads per block of the Line-Segment kernel (64, 128, 256);
   warps_px   warps per block of the pT3 / pT5 candidate pre-filters (2, 4, 8);
-  persistent Line-Segment kernel pulling modules from the cost-ordered work list, or grid-stride;
+  persistent Line-Segment kernel: persistent warps pulling the cost-ordered work items from a device
+             queue (2), the same list dealt statically (1), or grid-stride over modules (0);
   cap_scale  multiplier of the predicted per-module object capacities: the smallest value whose
              first pass needs no capacity retry on the calibration batch, one step up for margin.
 Coordinate descent, each candidate timed as the median of a few CUDA-graph replays. The result is
@@ -18,7 +19,7 @@ import statistics
 _HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_DIR = os.path.join(_HERE, "_cache")
 
-SPACE = {"block_ls": [128, 64, 256], "warps_px": [4, 2, 8], "persistent": [1, 0]}
+SPACE = {"block_ls": [128, 64, 256], "warps_px": [4, 2, 8], "persistent": [2, 1, 0]}
 CAP_SCALES = [1.0, 0.75, 0.5, 0.35]
 
 

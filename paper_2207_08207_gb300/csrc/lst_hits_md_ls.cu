@@ -644,10 +644,21 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
   const float kPiF = 3.14159265f;
   int qn = 0;   // pairs waiting in this warp's queue
   const long long t0 = clock64();
-  for (int sweep = 0; (int64_t)sweep * n_warps < n_items; ++sweep) {
+  int sweep = 0;
+  for (;;) {
     if (warp_over_budget(w, t0)) break;
-    const int item = sweep * n_warps + ((sweep & 1) ? n_warps - 1 - gw : gw);
-    if (item >= n_items) continue;
+    int item;
+    if (persistent == 2) {   // device queue: each warp takes the next cost-ordered item
+      int h = 0;
+      if (lane == 0) h = atomicAdd(w.ls_head, 1);
+      item = __shfl_sync(0xffffffffu, h, 0);
+      if (item >= n_items) break;
+    } else {                 // static deal in boustrophedon order
+      if ((int64_t)sweep * n_warps >= n_items) break;
+      item = sweep * n_warps + ((sweep & 1) ? n_warps - 1 - gw : gw);
+      ++sweep;
+      if (item >= n_items) continue;
+    }
     const int vm = persistent ? w.work[item] : item;
     const int chunk = persistent ? w.work_c[item] : 0;
     const int nch = persistent ? w.work_nch[vm] : 1;
@@ -953,7 +964,7 @@ void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
     if (L.persistent) {
       // every resident warp, no more: the boustrophedon assignment is static
       const int bps = L.ls_blocks_per_sm > 0 ? L.ls_blocks_per_sm : 1;
-      k_ls<<<L.n_sm * bps, L.block_ls, smem, L.stream>>>(w, g, c.f, 1);
+      k_ls<<<L.n_sm * bps, L.block_ls, smem, L.stream>>>(w, g, c.f, L.persistent);
     } else {
       k_ls<<<grid_for((w.V + warps - 1) / warps, 1, 152 * 16), L.block_ls, smem, L.stream>>>(w, g, c.f, 0);
     }

@@ -216,6 +216,7 @@ struct Ws {
   int32_t* work_cnt = nullptr;    // [32] items per bucket
   int32_t* work_cur = nullptr;    // [32]
   int32_t* work_off = nullptr;    // [33]
+  int32_t* ls_head = nullptr;     // device-queue head of the LS work list (persistent = 2; zeroed every run)
 };
 
 // Launch settings (from lst_config).
@@ -223,7 +224,7 @@ struct Launch {
   cudaStream_t stream = nullptr;
   int block_ls = 128;
   int warps_px = 4;
-  bool persistent = false;
+  int persistent = 0;   // 0 grid-stride, 1 static cost-ordered deal, 2 device queue
   int n_sm = 152;
   int ls_blocks_per_sm = 0;        // resident blocks of the Line-Segment kernel (0: not queried)
   long long* launches = nullptr;   // host counter

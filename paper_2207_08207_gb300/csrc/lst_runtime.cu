@@ -258,7 +258,7 @@ Launch make_launch(lst_ctx* ctx) {
   L.stream = ctx->stream;
   L.block_ls = ctx->cfg.block_ls;
   L.warps_px = ctx->cfg.warps_px;
-  L.persistent = ctx->cfg.persistent != 0;
+  L.persistent = ctx->cfg.persistent == 2 ? 2 : (ctx->cfg.persistent != 0 ? 1 : 0);
   L.launches = &ctx->launches;
   L.n_sm = ctx->n_sm;
   L.ls_blocks_per_sm = ctx->ls_bps;
@@ -377,6 +377,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.work_cnt, 32); z.add(w.work_cur, 32);
   z.add(w.scan_ctr, kScanMax);
   z.add(w.ext_qn, 4);
+  z.add(w.ls_head, 1);
   // binning
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
   pl.add(w.bx, c.H); pl.add(w.by, c.H); pl.add(w.bz, c.H); pl.add(w.borig, c.H);
@@ -628,7 +629,7 @@ void lst_config_default(lst_config* c) {
   c->pls_pt_err = 0.01f;
   c->sigma_floor = 1.0e-4f;
   c->t5_overlap_hits = 7;
-  c->persistent = 1;
+  c->persistent = 2;
   c->use_graph = 0;
   c->block_ls = 128;
   c->warps_px = 4;
