@@ -14,7 +14,10 @@ with a fake engine; ``LSTEngine`` drives the CUDA library.
 from __future__ import annotations
 
 import collections
+import gc
 import math
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -75,13 +78,17 @@ class Scheduler:
     `budget`; events are admitted in arrival order (no overtaking) up to `max_batch` per batch.
     """
 
-    def __init__(self, engines, predict, budget=40e9, max_batch=64, clock=time.perf_counter, idle_sleep=0.0):
+    def __init__(self, engines, predict, budget=40e9, max_batch=64, clock=time.perf_counter, idle_sleep=0.0,
+                 wakeup=None):
         self.engines = list(engines)
         self.predict = predict
         self.budget = float(budget)
         self.max_batch = int(max_batch)
         self.clock = clock
         self.idle_sleep = idle_sleep
+        # wakeup: a threading.Event the engines set when a batch completes; with it the loop sleeps
+        # until the next completion or arrival instead of polling
+        self.wakeup = wakeup
 
     def run(self, requests):
         reqs = sorted(requests, key=lambda r: r.t_arrival)
@@ -92,18 +99,35 @@ class Scheduler:
         pending = collections.deque(reqs)
         waiting = collections.deque()
         busy = {}                     # engine index -> list of requests
+        t0 = self.clock()
+        gc_was_enabled = gc.isenabled()
+        gc.disable()   # no collector pauses inside the serving loop (collected after it)
+        try:
+            return self._loop(reqs, pending, waiting, busy, t0)
+        finally:
+            if gc_was_enabled:
+                gc.enable()
+            gc.collect()
+
+    def _loop(self, reqs, pending, waiting, busy, t0):
         inflight = 0
         max_inflight = 0
         batches = 0
         batch_sizes = []
-        t0 = self.clock()
+        self.iterations = 0
         while pending or waiting or busy:
+            self.iterations += 1
+            if self.wakeup is not None:
+                self.wakeup.clear()   # a completion from here on wakes the wait below
             now = self.clock() - t0
+            progressed = False
             while pending and pending[0].t_arrival <= now:
                 waiting.append(pending.popleft())
+                progressed = True
             # completions
             for k in list(busy):
                 if self.engines[k].done():
+                    progressed = True
                     batch = busy.pop(k)
                     res = self.engines[k].collect(len(batch))
                     t_done = self.clock() - t0
@@ -130,10 +154,16 @@ class Scheduler:
                     break
                 max_inflight = max(max_inflight, inflight)
                 self.engines[k].submit([r.event for r in batch])
+                progressed = True
                 busy[k] = batch
                 batches += 1
                 batch_sizes.append(len(batch))
-            if not busy and not waiting and pending:
+            if self.wakeup is not None:
+                if not progressed:   # sleep until a batch completes or the next request arrives
+                    wait = pending[0].t_arrival - (self.clock() - t0) if pending else 0.05
+                    if wait > 0:
+                        self.wakeup.wait(timeout=min(wait, 0.05))
+            elif not busy and not waiting and pending:
                 # idle until the next arrival
                 wait = pending[0].t_arrival - (self.clock() - t0)
                 if wait > 0 and self.idle_sleep > 0:
@@ -158,7 +188,7 @@ def poisson_arrivals(rate_hz, n, seed=0):
 class LSTEngine(Engine):
     """One library context with its own stream; batches of resident (device) or host events."""
 
-    def __init__(self, det, max_batch, max_hits, max_pls, device=0, stream=None, keep="tc", **cfg):
+    def __init__(self, det, max_batch, max_hits, max_pls, device=0, stream=None, keep="tc", notify=None, **cfg):
         import torch
         from . import lst
         self.max_batch = int(max_batch)
@@ -167,19 +197,42 @@ class LSTEngine(Engine):
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         self.keep = keep
         self._n = 0
+        # a waiter thread blocks in lst_sync (the call releases the interpreter lock) for each
+        # submitted batch and then marks it done and sets `notify`, so the scheduler needs no polling
+        self.notify = notify
+        self._done = threading.Event()
+        self._err = None
+        self._jobs = queue.SimpleQueue()
+        self._waiter = threading.Thread(target=self._wait_loop, daemon=True)
+        self._waiter.start()
+
+    def _wait_loop(self):
+        while self._jobs.get() is not None:
+            try:
+                self.ctx.sync()
+            except Exception as ex:   # reported by collect()
+                self._err = ex
+            self._done.set()
+            if self.notify is not None:
+                self.notify.set()
 
     def predict(self, n_hits, n_pls):
         return self.ctx.predict_bytes(1, n_hits, n_pls)
 
     def submit(self, events):
+        self._done.clear()
+        self._err = None
         self.ctx.submit(events, stream=self.stream, host_async=True)   # events are held until sync
         self._n = len(events)
+        self._jobs.put(True)
 
     def done(self):
-        return self.ctx.query()
+        return self._done.is_set()
 
     def collect(self, n):
-        self.ctx.sync()
+        self._done.wait()
+        if self._err is not None:
+            raise self._err
         if self.keep == "tc":   # the batch's track candidates, one transfer per array
             tc = self.ctx.copy_tc_all()
             o = tc["offsets"]
@@ -190,6 +243,8 @@ class LSTEngine(Engine):
         return [self.ctx.counts(e) for e in range(n)]
 
     def close(self):
+        self._jobs.put(None)
+        self._waiter.join(timeout=10)
         self.ctx.close()
 
 
@@ -203,8 +258,11 @@ class Server:
             # capacities growing by 4x up to max_batch (1, 4, 16, 64 for four engines): a burst goes
             # to the smallest free engine that takes it, whose capacity-shaped launches cost the least
             batch_sizes = [max(1, max_batch // 4 ** k) for k in range(n_engines)][::-1]
-        self.engines = [LSTEngine(det, b, max_hits, max_pls, device=device, keep=keep, **cfg) for b in batch_sizes]
-        self.scheduler = Scheduler(self.engines, self.engines[0].predict, budget=budget, max_batch=max(batch_sizes))
+        self.wakeup = threading.Event()
+        self.engines = [LSTEngine(det, b, max_hits, max_pls, device=device, keep=keep, notify=self.wakeup, **cfg)
+                        for b in batch_sizes]
+        self.scheduler = Scheduler(self.engines, self.engines[0].predict, budget=budget, max_batch=max(batch_sizes),
+                                   wakeup=self.wakeup)
 
     def warmup(self, events):
         """One batch on every engine (graph capture, arena first touch) before a measurement."""

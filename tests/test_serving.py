@@ -86,3 +86,42 @@ def test_request_larger_than_budget_rejected():
     sched = Scheduler([FakeEngine(clock)], predict=lambda h, p: h, budget=10, clock=clock)
     with pytest.raises(ValueError):
         sched.run(_requests(3, rate=100))
+
+
+class ThreadedEngine(Engine):
+    """Completes each batch on a timer thread after `delay` seconds and sets the scheduler's wakeup
+    event, as the library engine's waiter thread does."""
+
+    def __init__(self, notify, delay=2e-3):
+        import threading
+        self.notify, self.delay, self.threading = notify, delay, threading
+        self.batch = None
+        self.flag = threading.Event()
+
+    def submit(self, events):
+        self.batch = list(events)
+        self.flag.clear()
+
+        def finish():
+            self.flag.set()
+            self.notify.set()
+        self.threading.Timer(self.delay, finish).start()
+
+    def done(self):
+        return self.flag.is_set()
+
+    def collect(self, n):
+        self.flag.wait()
+        return [("result", e) for e in self.batch]
+
+
+def test_event_driven_loop_does_not_poll():
+    import threading
+    wake = threading.Event()
+    engines = [ThreadedEngine(wake) for _ in range(2)]
+    sched = Scheduler(engines, predict=lambda h, p: h, budget=1e9, max_batch=8, wakeup=wake)
+    reqs = _requests(150, rate=1500)
+    stats = sched.run(reqs)
+    assert stats.n == 150 and all(r.result == ("result", r.rid) for r in reqs)
+    # one pass per arrival, submission or completion (plus timeouts), not a busy poll
+    assert sched.iterations < 10 * len(reqs), sched.iterations
