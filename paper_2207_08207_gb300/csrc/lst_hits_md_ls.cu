@@ -423,9 +423,11 @@ __global__ void k_md_dense(Ws w, Geo g, Cst<float> c) {
 __device__ __forceinline__ int md_count(const Ws& w, int vm) { return w.md_off[vm + 1] - w.md_off[vm]; }
 
 // LS capacity of each module (exact bound: its MDs x the MDs of its connected modules), its number
-// of work items (chunks of its outer MDs: ceil(outer MDs / ls_chunk), at most kLsMaxChunks) and
-// their cost bucket floor(log2(pairs per chunk)) for the persistent kernel's work list
-__global__ void k_ls_caps(Ws w, Geo g) {
+// of work items (chunks of its outer MDs: ceil(outer MDs / ls_chunk), at most kLsMaxChunks), their
+// cost bucket floor(log2(pairs per chunk)) for the persistent kernel's work list, and the inputs of
+// the LS azimuth windows that depend on the module's MDs alone (alpha_thr of the largest anchor
+// radius, 1 / the smallest), computed once here instead of by every item that connects to it
+__global__ void k_ls_caps(Ws w, Geo g, Cst<float> c) {
   zero_group_counts(w.lsin_off, w.md_off[w.V]);   // LS are grouped by inner MD
   __shared__ int hist[32];
   if (threadIdx.x < 32) hist[threadIdx.x] = 0;
@@ -434,8 +436,13 @@ __global__ void k_ls_caps(Ws w, Geo g) {
     const int m = vm % g.n_mods, e0 = vm - m;
     const long long na = md_count(w, vm);
     long long nb = 0;
-    if (na > 0)
+    float2 win = make_float2(0.f, 0.f);
+    if (na > 0) {
       for (int k = g.conn_off[m]; k < g.conn_off[m + 1]; ++k) nb += md_count(w, e0 + g.conn_tgt[k]);
+      win.x = asinf(fminf(__int_as_float(w.md_rmax[vm]) * c.k2p, c.sin_max));
+      win.y = 1.0f / __int_as_float(w.md_rmin[vm]);
+    }
+    w.md_win[vm] = win;
     const long long bound = na * nb;
     const double pred = w.cap_scale * w.stage_scale[1] * (32.0 + 0.5 * (double)bound);
     const int cc = clamp_cap(pred, bound, w.ls_ovr[vm]);
@@ -552,23 +559,37 @@ __device__ __forceinline__ LsSmem ls_smem(unsigned char* base, int T) {
   return S;
 }
 
-// first index k in [0, n) with v[k] >= x (n if none); v sorted ascending
-__device__ __forceinline__ int lower_bound_f(const float* v, int n, float x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (v[mid] < x) lo = mid + 1; else hi = mid;
+// The window [lo, hi] of a connected module's MDs, sorted by relative azimuth rp[0, n): jl = the
+// number of rp below lo, jh = the number not above hi. Up to 8 MDs are counted with independent
+// loads (one memory round trip instead of a chain of dependent ones); more are bisected, both bounds
+// in the same loop so that their loads overlap.
+__device__ __forceinline__ void ls_window(const float* rp, int n, float lo, float hi, int& jl, int& jh) {
+  if (n <= 8) {
+    int a = 0, b = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < n) {
+        const float v = rp[k];
+        a += v < lo ? 1 : 0;
+        b += v <= hi ? 1 : 0;
+      }
+    jl = a;
+    jh = b;
+    return;
   }
-  return lo;
-}
-// first index k in [0, n) with v[k] > x (n if none)
-__device__ __forceinline__ int upper_bound_f(const float* v, int n, float x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (v[mid] <= x) lo = mid + 1; else hi = mid;
+  int l1 = 0, h1 = n, l2 = 0, h2 = n;
+  while (l1 < h1 || l2 < h2) {
+    if (l1 < h1) {
+      const int mid = (l1 + h1) >> 1;
+      if (rp[mid] < lo) l1 = mid + 1; else h1 = mid;
+    }
+    if (l2 < h2) {
+      const int mid = (l2 + h2) >> 1;
+      if (rp[mid] <= hi) l2 = mid + 1; else h2 = mid;
+    }
   }
-  return lo;
+  jl = l1;
+  jh = l2;
 }
 
 // Quick rejection of an (a, b) pair, exact-safe: it returns true only when the float64 evaluation
@@ -632,7 +653,7 @@ __device__ __forceinline__ void ls_flush(const Ws& w, const Cst<float>& c, const
   if (q >= 0 && q < w.cap.q_ls) w.q_ls[q] = make_int4(vm, a, b, 0);
 }
 
-__global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persistent) {
+__global__ void __launch_bounds__(256, 4) k_ls(Ws w, Geo g, Cst<float> c, int persistent) {
   extern __shared__ __align__(16) unsigned char ls_smem_raw[];
   const int T = g.ls_tcap;
   const LsSmem S = ls_smem(ls_smem_raw + (threadIdx.x >> 5) * ls_smem_per_warp(T), T);
@@ -667,22 +688,16 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
     const int m = vm % g.n_mods, e0 = vm - m;
     const int t0c = g.conn_off[m];
     const int nt = min(g.conn_off[m + 1] - t0c, T);
-    const float pcA = g.phic[m];
-    // the connected modules: their MD ranges and the window parameters that depend on them alone
+    // the connected modules: their MD ranges and the window inputs that depend on them alone
     for (int t = lane; t < nt; t += 32) {
-      const int tm = g.conn_tgt[t0c + t];
+      const int k = t0c + t;
+      const int tm = g.conn_tgt[k];
+      const float dpc = g.conn_dpc[k];
       const int vb = e0 + tm;
-      const int cnt = md_count(w, vb);
-      float dpc = 0.f, al2 = 0.f, ir2 = 0.f;
-      if (cnt > 0) {
-        dpc = pcA - g.phic[tm];
-        if (dpc > kPiF) dpc -= 6.28318531f;
-        if (dpc <= -kPiF) dpc += 6.28318531f;
-        al2 = asinf(fminf(__int_as_float(w.md_rmax[vb]) * c.k2p, c.sin_max));
-        ir2 = 1.0f / __int_as_float(w.md_rmin[vb]);
-      }
-      S.tbc[t] = make_int2(w.md_off[vb], cnt);
-      S.tinfo[t] = make_float4(dpc, al2, ir2, g.endcap[tm] ? 1.f : 0.f);
+      const int b0 = w.md_off[vb], b1 = w.md_off[vb + 1];
+      const float2 tw = w.md_win[vb];
+      S.tbc[t] = make_int2(b0, b1 - b0);
+      S.tinfo[t] = make_float4(dpc, tw.x, tw.y, g.endcap[tm] ? 1.f : 0.f);
     }
     const bool aec = g.endcap[m] != 0;
     const float sz1 = aec ? 0.f : c.sigma_z, sr1 = aec ? c.sigma_r : 0.f;
@@ -723,9 +738,7 @@ __global__ void __launch_bounds__(256) k_ls(Ws w, Geo g, Cst<float> c, int persi
             if (lo < -kPiF || hi > kPiF) {   // the window wraps: take the whole module
               jh = bc.y;
             } else if (lo <= hi) {
-              const float* rp = w.md_rphi + bc.x;
-              jl = lower_bound_f(rp, bc.y, lo);
-              jh = upper_bound_f(rp, bc.y, hi);
+              ls_window(w.md_rphi + bc.x, bc.y, lo, hi, jl, jh);
             }
           }
           S.wbeg[t] = bc.x + jl;
@@ -950,7 +963,7 @@ void run_md(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
 }
 
 void run_ls(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
-  k_ls_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, g);
+  k_ls_caps<<<grid_for(w.V, 256), 256, 0, L.stream>>>(w, g, c.f);
   LST_LAUNCH(L);
   scan_exclusive(w.ls_base, w.ls_base, w.V, w.scan_tmp, L);
   if (L.persistent) {

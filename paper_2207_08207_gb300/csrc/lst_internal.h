@@ -20,6 +20,8 @@ struct Geo {
                                      // module-map degree rounded up to 32
   const int32_t* conn_off = nullptr; // [n_mods + 1]
   const int32_t* conn_tgt = nullptr;
+  const float* conn_dpc = nullptr;   // [conn_off[n_mods]] centre azimuth of the module minus that of
+                                     // the connected module, wrapped to (-pi, pi]
   const int32_t* pix_off = nullptr;  // [n_pix_bins + 1]
   const int32_t* pix_tgt = nullptr;
 };
@@ -100,6 +102,8 @@ struct Ws {
                                  // the MDs of a module are ordered by it (hits are binned in azimuth order)
   int32_t *md_rmin = nullptr, *md_rmax = nullptr;   // [V] smallest / largest anchor radius of each
                                                     // module's MDs (float bits; set by k_md_dense)
+  float2* md_win = nullptr;   // [V] (alpha_thr of the largest anchor radius, 1 / the smallest) of each
+                              // module's MDs, the LS azimuth windows' inputs (set by k_ls_caps)
   // LS
   int32_t *ls_cap = nullptr, *ls_base = nullptr, *ls_cnt = nullptr, *ls_ovr = nullptr;
   int32_t *lss_in = nullptr, *lss_out = nullptr;

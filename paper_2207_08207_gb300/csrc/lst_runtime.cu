@@ -405,7 +405,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   out_f(w.md_dpc, w.md_dpc_h, c.md_dense); out_f(w.md_pte, w.md_pte_h, c.md_dense);
   pl.add(w.md_ec, c.md_dense);
   pl.add(w.md_xyzr, c.md_dense); pl.add(w.md_sa, c.md_dense); pl.add(w.md_rphi, c.md_dense);
-  pl.add(w.md_rmin, V); pl.add(w.md_rmax, V);
+  pl.add(w.md_rmin, V); pl.add(w.md_rmax, V); pl.add(w.md_win, V);
   // LS
   pl.add(w.ls_cap, V); pl.add(w.ls_base, V + 1); pl.add(w.ls_off, V + 1); pl.add(w.lsin_off, c.md_dense + 2);
   pl.add(w.lss_in, c.ls_slots); pl.add(w.lss_out, c.ls_slots); pl.add(w.lss_dphi, c.ls_slots);
@@ -775,10 +775,21 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
     if (!(c >= 0.0)) c = std::isfinite(c) ? c + 6.283185307179586 : 0.0;
     pc[m] = (float)c;
   }
+  // per connection: the module's centre azimuth minus the connected module's, in (-pi, pi] (the LS
+  // kernel maps azimuths between the two modules' frames with it)
+  std::vector<float> dpc(std::max<int32_t>(n_conn, 1));
+  for (int32_t m = 0; m < n_mods; ++m)
+    for (int32_t k = conn_off[m]; k < conn_off[m + 1]; ++k) {
+      float d = pc[m] - pc[conn_tgt[k]];
+      if (d > 3.14159265f) d -= 6.28318531f;
+      if (d <= -3.14159265f) d += 6.28318531f;
+      dpc[k] = d;
+    }
   Planner pl;
-  uint8_t* d_ec = nullptr; float *d_sp = nullptr, *d_pc = nullptr;
+  uint8_t* d_ec = nullptr; float *d_sp = nullptr, *d_pc = nullptr, *d_dpc = nullptr;
   int32_t *d_co = nullptr, *d_ct = nullptr, *d_po = nullptr, *d_pt = nullptr;
   pl.add(d_ec, n_mods); pl.add(d_sp, n_mods); pl.add(d_pc, n_mods); pl.add(d_co, n_mods + 1); pl.add(d_ct, n_conn);
+  pl.add(d_dpc, n_conn);
   pl.add(d_po, n_pix_bins + 1); pl.add(d_pt, n_pix);
   const size_t bytes = pl.layout();
   if (ctx->geo_mem) CK(cudaFree(ctx->geo_mem));
@@ -791,6 +802,7 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   CK(cudaMemcpy(d_pc, pc.data(), n_mods * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_co, conn_off, (n_mods + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
   if (n_conn) CK(cudaMemcpy(d_ct, conn_tgt, n_conn * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (n_conn) CK(cudaMemcpy(d_dpc, dpc.data(), n_conn * sizeof(float), cudaMemcpyHostToDevice));
   if (n_pix_bins > 0) {
     CK(cudaMemcpy(d_po, pix_off, (n_pix_bins + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (n_pix) CK(cudaMemcpy(d_pt, pix_tgt, n_pix * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -802,6 +814,7 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   ctx->geo.phic = d_pc;
   ctx->geo.conn_off = d_co;
   ctx->geo.conn_tgt = d_ct;
+  ctx->geo.conn_dpc = d_dpc;
   ctx->geo.pix_off = d_po;
   ctx->geo.pix_tgt = d_pt;
   ctx->max_degree = maxdeg;
