@@ -322,53 +322,80 @@ __device__ __forceinline__ T arc_len(T akappa, T r) {
   return arc_len(akappa, T(2) / akappa, r);
 }
 
+// The fits below take the first n of their points (n <= NMAX, a runtime count): their loops run to
+// the compile-time bound NMAX and skip the points past n, so one copy of the code serves every
+// count, with the same operations in the same order as for a fixed count. The fixed-count forms
+// (template <T, N>) are the same functions with n = N.
+
 // Weighted straight-line fit z = a + b s; returns chi2 and the slope b (centred sums).
-template <class T, int N>
-__device__ __forceinline__ T line_chi2(const T* s, const T* z, const T* sig, T& slope) {
+template <class T, int NMAX>
+__device__ __forceinline__ T line_chi2_n(const T* s, const T* z, const T* sig, int n, T& slope) {
   T S = 0, Ss = 0, Sz = 0;
-  T w[N], isig[N];
+  T w[NMAX], isig[NMAX];
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    isig[i] = T(1) / sig[i];
-    w[i] = isig[i] * isig[i];
-    S += w[i]; Ss += w[i] * s[i]; Sz += w[i] * z[i];
+  for (int i = 0; i < NMAX; ++i) {
+    if (i < n) {
+      isig[i] = T(1) / sig[i];
+      w[i] = isig[i] * isig[i];
+      S += w[i]; Ss += w[i] * s[i]; Sz += w[i] * z[i];
+    }
   }
   const T iS = T(1) / S;
   const T sm = Ss * iS, zm = Sz * iS;
   T Sss = 0, Ssz = 0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const T ds = s[i] - sm;
-    Sss += w[i] * ds * ds;
-    Ssz += w[i] * ds * (z[i] - zm);
+  for (int i = 0; i < NMAX; ++i) {
+    if (i < n) {
+      const T ds = s[i] - sm;
+      Sss += w[i] * ds * ds;
+      Ssz += w[i] * ds * (z[i] - zm);
+    }
   }
   const T b = Ssz / Sss;
   T chi2 = 0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const T r = (z[i] - zm - b * (s[i] - sm)) * isig[i];
-    chi2 += r * r;
+  for (int i = 0; i < NMAX; ++i) {
+    if (i < n) {
+      const T r = (z[i] - zm - b * (s[i] - sm)) * isig[i];
+      chi2 += r * r;
+    }
   }
   slope = b;
   return chi2;
 }
+template <class T, int N>
+__device__ __forceinline__ T line_chi2(const T* s, const T* z, const T* sig, T& slope) {
+  return line_chi2_n<T, N>(s, z, sig, N, slope);
+}
 
-// r-z chi2 in arc length for N anchors on a circle of curvature |kappa| (Sec. 2.3): barrel anchors
+// r-z chi2 in arc length for n anchors on a circle of curvature |kappa| (Sec. 2.3): barrel anchors
 // carry sigma_z, endcap anchors sigma_r |b0| (b0 = first-to-last slope), floored. Returns false
 // when the arc length does not grow from the first to the last anchor.
+template <class T, int NMAX>
+__device__ __forceinline__ bool rz_fit_n(const Cst<T>& c, T akappa, const T* r, const T* z, const bool* ec,
+                                         int n, T& chi2, T& slope) {
+  T s[NMAX], sig[NMAX];
+  const T two_r = T(2) / akappa;
+  T s_last = T(0), z_last = T(0);   // of the n-th anchor (carried along: no run-time array index)
+#pragma unroll
+  for (int i = 0; i < NMAX; ++i)
+    if (i < n) {
+      s[i] = arc_len(akappa, two_r, r[i]);
+      s_last = s[i];
+      z_last = z[i];
+    }
+  if (!(s_last > s[0])) return false;
+  const T b0 = (z_last - z[0]) / (s_last - s[0]);
+#pragma unroll
+  for (int i = 0; i < NMAX; ++i)
+    if (i < n) sig[i] = m_max(ec[i] ? c.sigma_r * m_abs(b0) : c.sigma_z, c.sigma_floor);
+  chi2 = line_chi2_n<T, NMAX>(s, z, sig, n, slope);
+  return true;
+}
 template <class T, int N>
 __device__ __forceinline__ bool rz_fit(const Cst<T>& c, T akappa, const T* r, const T* z,
                                        const bool* ec, T& chi2, T& slope) {
-  T s[N], sig[N];
-  const T two_r = T(2) / akappa;
-#pragma unroll
-  for (int i = 0; i < N; ++i) s[i] = arc_len(akappa, two_r, r[i]);
-  if (!(s[N - 1] > s[0])) return false;
-  const T b0 = (z[N - 1] - z[0]) / (s[N - 1] - s[0]);
-#pragma unroll
-  for (int i = 0; i < N; ++i) sig[i] = m_max(ec[i] ? c.sigma_r * m_abs(b0) : c.sigma_z, c.sigma_floor);
-  chi2 = line_chi2<T, N>(s, z, sig, slope);
-  return true;
+  return rz_fit_n<T, N>(c, akappa, r, z, ec, N, chi2, slope);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -376,22 +403,28 @@ __device__ __forceinline__ bool rz_fit(const Cst<T>& c, T akappa, const T* r, co
 // Circle: 1/2 rho (x^2 + y^2) - (1 + rho d)(x sin phi - y cos phi) + 1/2 rho d^2 + d = 0;
 // phi is the direction at the point of closest approach to the origin, oriented first -> last.
 // ---------------------------------------------------------------------------------------------
-template <class T, int N>
-__device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi, T& d, T& sp, T& cp) {
+template <class T, int NMAX>
+__device__ __forceinline__ void karimaki_n(const T* x, const T* y, int n, T& rho, T& phi, T& d, T& sp, T& cp) {
   T mx = 0, my = 0, mxx = 0, mxy = 0, myy = 0, mr2 = 0, mxr = 0, myr = 0, mrr = 0;
+  T x_last = x[0], y_last = y[0];   // of the n-th point (carried along: no run-time array index)
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const T r2 = x[i] * x[i] + y[i] * y[i];
-    mx += x[i]; my += y[i];
-    mxx += x[i] * x[i]; mxy += x[i] * y[i]; myy += y[i] * y[i];
-    mr2 += r2; mxr += x[i] * r2; myr += y[i] * r2; mrr += r2 * r2;
+  for (int i = 0; i < NMAX; ++i) {
+    if (i < n) {
+      x_last = x[i];
+      y_last = y[i];
+      const T r2 = x[i] * x[i] + y[i] * y[i];
+      mx += x[i]; my += y[i];
+      mxx += x[i] * x[i]; mxy += x[i] * y[i]; myy += y[i] * y[i];
+      mr2 += r2; mxr += x[i] * r2; myr += y[i] * r2; mrr += r2 * r2;
+    }
   }
-  const T inv = T(1) / T(N);
+  const T inv = T(1) / T((float)n);
   mx *= inv; my *= inv; mxx *= inv; mxy *= inv; myy *= inv; mr2 *= inv; mxr *= inv; myr *= inv; mrr *= inv;
   const T Cxx = mxx - mx * mx, Cxy = mxy - mx * my, Cyy = myy - my * my;
   const T Cxr = mxr - mx * mr2, Cyr = myr - my * mr2, Crr = mrr - mr2 * mr2;
   const T q1 = Crr * Cxy - Cxr * Cyr;
   const T q2 = Crr * (Cxx - Cyy) - Cxr * Cxr + Cyr * Cyr;
+  const T dx = x_last - x[0], dy = y_last - y[0];
   if constexpr (std::is_same<T, ff>::value) {
     // phi = atan2(2 q1, q2) / 2 in (-pi/2, pi/2], so cos phi >= 0: its sine and cosine from the
     // double angle's, (cos 2phi, sin 2phi) = (q2, 2 q1) / h, by the half-angle formulas, each in
@@ -412,7 +445,7 @@ __device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi,
         cp = sn2 / (ff(2.0f) * sp);
       }
     }
-    if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
+    if (cp * dx + sp * dy < T(0)) {
       sp = -sp;
       cp = -cp;
     }
@@ -421,7 +454,7 @@ __device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi,
     phi = T(0.5) * m_atan2(T(2) * q1, q2);
     if constexpr (sizeof(T) == 4) sincosf(phi, &sp, &cp);
     else sincos(phi, &sp, &cp);
-    if (cp * (x[N - 1] - x[0]) + sp * (y[N - 1] - y[0]) < T(0)) {
+    if (cp * dx + sp * dy < T(0)) {
       phi += T(kPiD);
       sp = -sp;
       cp = -cp;
@@ -435,21 +468,31 @@ __device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi,
   rho = T(2) * kap / root;
   d = T(2) * del / (T(1) + root);
 }
+template <class T, int N>
+__device__ __forceinline__ void karimaki(const T* x, const T* y, T& rho, T& phi, T& d, T& sp, T& cp) {
+  karimaki_n<T, N>(x, y, N, rho, phi, d, sp, cp);
+}
 
 // sum over the anchors of ((|p - c| - R) / sigma)^2 at the circle (rho, phi, d) given by rho,
 // (sin phi, cos phi) and d, each residual in
 // the exact cancellation-free form 2 eps / (1 + sqrt(1 + 2 rho eps))
-template <class T, int N>
-__device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T cp, T d, T sigma) {
+template <class T, int NMAX>
+__device__ __forceinline__ T circle_chi2_n(const T* x, const T* y, int n, T rho, T sp, T cp, T d, T sigma) {
   T chi2 = 0;
 #pragma unroll
-  for (int a = 0; a < N; ++a) {
-    const T eps = T(0.5) * rho * (x[a] * x[a] + y[a] * y[a]) - (T(1) + rho * d) * (x[a] * sp - y[a] * cp) +
-                  T(0.5) * rho * d * d + d;
-    const T res = T(2) * eps / (T(1) + m_sqrt(T(1) + T(2) * rho * eps)) / sigma;
-    chi2 += res * res;
+  for (int a = 0; a < NMAX; ++a) {
+    if (a < n) {
+      const T eps = T(0.5) * rho * (x[a] * x[a] + y[a] * y[a]) - (T(1) + rho * d) * (x[a] * sp - y[a] * cp) +
+                    T(0.5) * rho * d * d + d;
+      const T res = T(2) * eps / (T(1) + m_sqrt(T(1) + T(2) * rho * eps)) / sigma;
+      chi2 += res * res;
+    }
   }
   return chi2;
+}
+template <class T, int N>
+__device__ __forceinline__ T circle_chi2(const T* x, const T* y, T rho, T sp, T cp, T d, T sigma) {
+  return circle_chi2_n<T, N>(x, y, N, rho, sp, cp, d, sigma);
 }
 
 __host__ __device__ __forceinline__ int64_t lst_min64(int64_t a, int64_t b) { return a < b ? a : b; }

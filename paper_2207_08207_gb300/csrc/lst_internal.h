@@ -46,7 +46,7 @@ enum ErrorBit : int { ERR_BAD_SENSOR = 1, ERR_BAD_COORD = 2, ERR_BAD_PLS = 4 };
 constexpr int kEvWords = 24;
 constexpr int kEvErr = 23;
 constexpr int kEvExt = 18;
-constexpr int kExtRefs = 8;   // candidate references stored per track candidate
+constexpr int kExtRefs = 16;   // candidate references stored per track candidate
 
 // Capacities of one workspace (element counts).
 struct Caps {
@@ -184,7 +184,8 @@ struct Ws {
   int32_t* ext_ref = nullptr;     // [tc_cap][kExtRefs]: region << 28 | position
   int2* ext_q = nullptr;          // [4][ext_qcap]
   float4* ext_res = nullptr;      // [4][ext_qcap]
-  int32_t* ext_qn = nullptr;      // [4] entries pushed per region (zeroed every run)
+  int32_t* ext_qn = nullptr;      // [5] entries pushed per region, then the slow rows (zeroed every run)
+  int32_t* ext_slow = nullptr;    // [tc_cap] rows with candidates beyond their references or the queues
   int64_t ext_qcap = 0;
   int64_t tc_capacity = 0;
   // event-local output copies

@@ -129,10 +129,12 @@ struct ObjAnc {
 };
 
 // bounding boxes of the first anchors of each module's T3 and of its T5 (kBoxLanes lanes per module
-// and type: modules hold a few T3 / T5 each, most none)
+// and type: modules hold a few T3 / T5 each, most none), stored in the form the seed test reads:
+// box[vm] = (centre x, centre y, half diagonal, largest r), box[V + vm] = (smallest z, largest z,
+// smallest r, 1 for an endcap module)
 constexpr int kBoxLanes = 4;
 
-__global__ void k_obj_box(Ws w) {
+__global__ void k_obj_box(Ws w, Geo g) {
   const int sub = threadIdx.x & (kBoxLanes - 1);
   const unsigned gmask = ((1u << kBoxLanes) - 1u) << ((threadIdx.x & 31) & ~(kBoxLanes - 1));
   const int ngroups = gridDim.x * (blockDim.x / kBoxLanes);
@@ -163,48 +165,53 @@ __global__ void k_obj_box(Ws w) {
       hi.w = fmaxf(hi.w, __shfl_xor_sync(gmask, hi.w, o, kBoxLanes));
     }
     if (sub == 0) {
-      box[vm] = lo;
-      box[w.V + vm] = hi;
+      const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y);
+      box[vm] = make_float4(0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), sqrtf(hx * hx + hy * hy), hi.w);
+      box[w.V + vm] = make_float4(lo.z, hi.z, lo.w, g.endcap[vm % g.n_mods] ? 1.f : 0.f);
     }
   }
 }
 
 // Whole-module rejection for a seed, exact-safe: true only when every object of the module has a
-// first-anchor term (alone) above the pre-filter limit, so the chi-square sums are too.
+// first-anchor term (alone) above the pre-filter limit, so the chi-square sums are too. b0, b1: the
+// module's box (k_obj_box).
 //  x-y: the signed distance to the seed circle, |p - c| - R, is 1-Lipschitz, so over the anchors'
 //    box it is at least its value at the box centre minus the half diagonal; the resolution term
 //    grows with r and is taken at the box's largest r.
-//  r-z: the predicted z at radius r, z0 + s(r) cot, is monotonic in r, so over the box's r range
-//    it spans the interval between its values at the ends; the gap between that interval and the
-//    box's z range bounds |z - z_pred|, and the variance is taken at its largest (largest s).
-// Margins (1e-3 cm, relative 1e-4, 1/16 on the squared limits) lie far above float32 rounding.
-__device__ __forceinline__ bool seed_box_reject(const Seed<float>& s, const Cst<float>& c, float4 lo, float4 hi,
-                                                bool ec, float lim_xy, float lim_rz) {
-  const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y);
-  const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y);
-  const float h = sqrtf(hx * hx + hy * hy);
-  const float ux = cx - s.x0, uy = cy - s.y0;
+//  r-z: the predicted z at radius r, z0 + s(r) cot, is linear in the arc length s(r) = 2R asin(r/2R),
+//    so over the box's r range it lies between its values at bounds of s: s(r) >= min(r, pi R) and
+//    s(r) <= min(r / sqrt(1 - (r/2R)^2), pi R) (asin x <= tan(asin x); the arc length is capped at pi R
+//    where the circle does not reach r), which need no arc sine. The gap between that interval and
+//    the box's z range bounds |z - z_pred|; the variance is taken at the largest s bound.
+// Margins (1e-3 cm, relative 1e-4, 1/16 on the squared limits, pi rounded outward by 3e-5) lie far
+// above float32 rounding.
+__device__ __forceinline__ bool seed_box_reject(const Seed<float>& s, const Cst<float>& c, float4 b0, float4 b1,
+                                                float lim_xy, float lim_rz) {
+  const float ux = b0.x - s.x0, uy = b0.y - s.y0;
   // distance at the centre: at least |A| / g with A = rho/2 |u|^2 - u.n and g = 1 + |rho A| / 2
   // (the exact 2A / (1 + sqrt(1 + 2 rho A)) without its square root and division); the test
   // lb = |A| / g - margin > 0, lb^2 > limit is multiplied through by g
   const float A = 0.5f * s.rho * (ux * ux + uy * uy) - (ux * s.sp - uy * s.cp);
   const float g = 1.0f + 0.5f * fabsf(s.rho * A);
-  const float m = h * 1.0001f + 1e-3f + 1e-4f * (fabsf(ux) + fabsf(uy));
+  const float m = b0.z * 1.0001f + 1e-3f + 1e-4f * (fabsf(ux) + fabsf(uy));
   const float lbg = fabsf(A) - m * g;
+  const float r_hi = b0.w, r_lo = b1.z;
   if (lbg > 0.f) {
-    const float e1 = hi.w * c.pls_dir_err;
-    const float e2 = c.pls_pt_err * hi.w * hi.w * 0.5f * s.akap;
+    const float e1 = r_hi * c.pls_dir_err;
+    const float e2 = c.pls_pt_err * r_hi * r_hi * 0.5f * s.akap;
     const float sig2 = c.sigma_rphi * c.sigma_rphi + e1 * e1 + e2 * e2;
     if (lbg * lbg > lim_xy * sig2 * 1.0625f * g * g) return true;
   }
-  const float two_r = 2.0f * s.R;
-  const float sl = arc_len(s.akap, two_r, lo.w), sh = arc_len(s.akap, two_r, hi.w);
+  const float xh = 0.5f * s.akap * r_hi;
+  const float s_cap = 3.1416f * s.R;
+  const float sh = xh < 1.0f ? fminf(r_hi * rsqrtf(1.0f - xh * xh), s_cap) : s_cap;
+  const float sl = fminf(r_lo, 3.1415f * s.R);
   const float za = s.z0 + sl * s.cot, zb = s.z0 + sh * s.cot;
   const float zmin = fminf(za, zb), zmax = fmaxf(za, zb);
-  const float gap = fmaxf(lo.z - zmax, zmin - hi.z) - 1e-3f -
-                    1e-4f * (fabsf(zmin) + fabsf(zmax) + fabsf(lo.z) + fabsf(hi.z));
+  const float gap = fmaxf(b1.x - zmax, zmin - b1.y) - 1e-3f -
+                    1e-4f * (fabsf(zmin) + fabsf(zmax) + fabsf(b1.x) + fabsf(b1.y));
   if (gap > 0.f) {
-    const float sz = ec ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
+    const float sz = b1.w != 0.f ? c.sigma_r * fabsf(s.cot) : c.sigma_z;
     const float th = sh * (1.0f + s.cot * s.cot) * c.pls_dir_err;
     if (gap * gap > lim_rz * (sz * sz + th * th) * 1.0625f) return true;
   }
@@ -313,8 +320,7 @@ __global__ void __launch_bounds__(32 * kPxMaxWarps, 4) k_pt_pre(Ws w, Geo g, Cst
         const int vmk = e0 + mk;
         start = obj_off[vmk];
         size = obj_off[vmk + 1] - start;
-        if (size > 0 && seed_box_reject(s, c, box[vmk], box[w.V + vmk], g.endcap[mk] != 0, lim_xy, lim_rz))
-          size = 0;
+        if (size > 0 && seed_box_reject(s, c, box[vmk], box[w.V + vmk], lim_xy, lim_rz)) size = 0;
       }
       int incl = size;
 #pragma unroll
@@ -1026,32 +1032,38 @@ __global__ void k_tc_dense(Ws w, Geo g) {
 // r-z line in arc length with the T5 cut per degree of freedom, chi2_rz <= chi2_t5_rz (n - 2) / 3.
 // Karimaki's circle through the n anchors gives the arc lengths and a circle chi2 that ranks the
 // candidates (it is not cut on). Decided in double-float, like the T5 selection; of several passing
-// T3 the one with the lowest (chi2_c + chi2_rz as float32, sorted hit tuple) is taken. One thread
-// per dense track-candidate row (a row has a few candidate T3).
+// T3 the one with the lowest (chi2_c + chi2_rz as float32, sorted hit tuple) is taken. The rows'
+// candidates are queued by anchor count (A), fitted one per thread (B), and chosen per row (C, with
+// the rare rows whose candidates did not all fit the queues finished by D).
 // ---------------------------------------------------------------------------------------------
 struct ExtCuts {
   ff rz[8];   // r-z chi2 bounds for n anchors (n = 4..7)
 };
 
-template <int N>
-__device__ __forceinline__ bool ext_fit(const Ws& w, const Cst<ff>& c, const int* md, ff cut_rz, ff& chi2c,
+// the fit of the n anchors of md[0, n) (4 <= n <= kExtMaxAnchors): Karimaki's circle and its chi2,
+// and the r-z line in arc length with its cut; one copy of the code for every anchor count
+constexpr int kExtMaxAnchors = 7;
+
+__device__ __forceinline__ bool ext_fit(const Ws& w, const Cst<ff>& c, const int* md, int n, ff cut_rz, ff& chi2c,
                                         ff& chi2rz) {
-  ff x[N], y[N], z[N], r[N];
-  bool ec[N];
+  ff x[kExtMaxAnchors], y[kExtMaxAnchors], z[kExtMaxAnchors], r[kExtMaxAnchors];
+  bool ec[kExtMaxAnchors];
 #pragma unroll
-  for (int a = 0; a < N; ++a) {
-    const float4 p = w.md_xyzr[md[a]];
-    x[a] = ff(p.x);
-    y[a] = ff(p.y);
-    z[a] = ff(p.z);
-    r[a] = ff_fast_two_sum(p.w, w.md_rlo[md[a]]);
-    ec[a] = w.md_ec[md[a]] != 0;
+  for (int a = 0; a < kExtMaxAnchors; ++a) {
+    if (a < n) {
+      const float4 p = w.md_xyzr[md[a]];
+      x[a] = ff(p.x);
+      y[a] = ff(p.y);
+      z[a] = ff(p.z);
+      r[a] = ff_fast_two_sum(p.w, w.md_rlo[md[a]]);
+      ec[a] = w.md_ec[md[a]] != 0;
+    }
   }
   ff rho, phi, d, sp, cp;
-  karimaki<ff, N>(x, y, rho, phi, d, sp, cp);
-  chi2c = circle_chi2<ff, N>(x, y, rho, sp, cp, d, c.sigma_rphi);
+  karimaki_n<ff, kExtMaxAnchors>(x, y, n, rho, phi, d, sp, cp);
+  chi2c = circle_chi2_n<ff, kExtMaxAnchors>(x, y, n, rho, sp, cp, d, c.sigma_rphi);
   ff slope;
-  if (!rz_fit<ff, N>(c, m_abs(rho), r, z, ec, chi2rz, slope)) return false;
+  if (!rz_fit_n<ff, kExtMaxAnchors>(c, m_abs(rho), r, z, ec, n, chi2rz, slope)) return false;
   AccFF acc;
   acc.cut(cut_rz, chi2rz);
   return !acc.fail;
@@ -1113,31 +1125,28 @@ __device__ __forceinline__ void ext_candidates(const Ws& w, const Cst<ff>& c, co
   }
 }
 
-// the fit of one candidate with N = K + 3 - overlap anchors; result (score, chi2_c, chi2_rz, passed)
-template <int N>
-__device__ __forceinline__ float4 ext_eval(const Ws& w, const Cst<ff>& c, const int* md, int K, int t3,
-                                           int overlap, ff cut_rz) {
-  int all[N];
+// the fit of one candidate with n = K + 3 - overlap anchors; result (score, chi2_c, chi2_rz, passed)
+__device__ __forceinline__ float4 ext_eval(const Ws& w, const Cst<ff>& c, const ExtCuts& xc, const int* md, int K,
+                                           int t3, int overlap) {
+  int all[kExtMaxAnchors];
 #pragma unroll
-  for (int a = 0; a < N; ++a) {
+  for (int a = 0; a < 5; ++a)
     if (a < K) all[a] = md[a];
+  const int add1 = w.t3_md1[t3], add2 = w.t3_md2[t3];
+  // the added MDs follow the row's K (3 or 5), with the indices known at compile time
+  if (K == 3) {
+    if (overlap == 1) { all[3] = add1; all[4] = add2; } else { all[3] = add2; }
+  } else {
+    if (overlap == 1) { all[5] = add1; all[6] = add2; } else { all[5] = add2; }
   }
-  const int add[2] = {w.t3_md1[t3], w.t3_md2[t3]};
-  if (overlap == 1) { all[K] = add[0]; all[K + 1] = add[1]; }
-  else all[K] = add[1];
+  const int n = K + 3 - overlap;
+  ff cut = xc.rz[4];   // the bound for n anchors, selected without a run-time index into the parameter
+#pragma unroll
+  for (int k = 5; k <= kExtMaxAnchors; ++k)
+    if (n == k) cut = xc.rz[k];
   ff chi2c, chi2rz;
-  const bool ok = ext_fit<N>(w, c, all, cut_rz, chi2c, chi2rz);
+  const bool ok = ext_fit(w, c, all, n, cut, chi2c, chi2rz);
   return make_float4((float)(chi2c + chi2rz), (float)chi2c, (float)chi2rz, ok ? 1.f : 0.f);
-}
-
-__device__ __forceinline__ float4 ext_eval_n(const Ws& w, const Cst<ff>& c, const ExtCuts& xc, const int* md, int K,
-                                             int t3, int overlap) {
-  switch (K + 3 - overlap) {
-    case 4: return ext_eval<4>(w, c, md, K, t3, overlap, xc.rz[4]);
-    case 5: return ext_eval<5>(w, c, md, K, t3, overlap, xc.rz[5]);
-    case 6: return ext_eval<6>(w, c, md, K, t3, overlap, xc.rz[6]);
-    default: return ext_eval<7>(w, c, md, K, t3, overlap, xc.rz[7]);
-  }
 }
 
 // a queued candidate: dense T3 index (< 2^30) and overlap (1 or 2) in one word
@@ -1172,11 +1181,10 @@ __global__ void k_ext_cand(Ws w, Geo g, Cst<ff> c) {
   }
 }
 
-// (B) the fits, one thread per queued candidate; blockIdx.y selects the anchor count, so a block's
-// threads all run the same fit and the four counts proceed side by side
-template <int N>
-__device__ __forceinline__ void ext_fit_region(const Ws& w, const Geo& g, const Cst<ff>& c, const ExtCuts& xc) {
-  const int reg = N - 4;
+// (B) the fits, one thread per queued candidate; blockIdx.y selects the anchor count (4 + y), so a
+// warp's threads take the same branches through the one fit code and the four counts run side by side
+__global__ void __launch_bounds__(128, 4) k_ext_fit(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
+  const int reg = blockIdx.y;
   const int n = (int)min((int64_t)w.ext_qn[reg], w.ext_qcap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int2 q = w.ext_q[reg * w.ext_qcap + k];
@@ -1185,86 +1193,111 @@ __device__ __forceinline__ void ext_fit_region(const Ws& w, const Geo& g, const 
     int md[5];
     ff ktc;
     const int K = ext_row(w, g, c, e, row, md, ktc);
-    w.ext_res[reg * w.ext_qcap + k] = ext_eval<N>(w, c, md, K, d, overlap, xc.rz[N]);
+    w.ext_res[reg * w.ext_qcap + k] = ext_eval(w, c, xc, md, K, d, overlap);
   }
 }
 
-__global__ void k_ext_fit(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
-  switch (blockIdx.y) {
-    case 0: ext_fit_region<4>(w, g, c, xc); break;
-    case 1: ext_fit_region<5>(w, g, c, xc); break;
-    case 2: ext_fit_region<6>(w, g, c, xc); break;
-    default: ext_fit_region<7>(w, g, c, xc); break;
+// the best passing candidate of a row so far: by (score as float32, sorted hit tuple of the T3)
+struct ExtBest {
+  int t3 = -1, n_add = 0;
+  float sc = 0.f, chi2c = 0.f, chi2rz = 0.f;
+};
+
+__device__ __forceinline__ void ext_consider(const Ws& w, ExtBest& b, int d, int overlap, float4 r) {
+  if (r.w == 0.f) return;
+  bool better = b.t3 < 0 || r.x < b.sc;
+  if (!better && r.x == b.sc) {   // equal scores (rare): the sorted hit tuples decide
+    int key[6], bkey[6];
+    t3_sorted_hits(w, d, key);
+    t3_sorted_hits(w, b.t3, bkey);
+    for (int t = 0; t < 6; ++t)
+      if (key[t] != bkey[t]) { better = key[t] < bkey[t]; break; }
+  }
+  if (better) {
+    b.t3 = d; b.n_add = 3 - overlap; b.sc = r.x; b.chi2c = r.y; b.chi2rz = r.z;
   }
 }
 
-// (C) per row, the best passing candidate by (score as float32, sorted hit tuple of the T3); the
-// candidates that did not fit the queue or the row's references are listed and fitted again here
-__global__ void k_ext_select(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
+// the row's outputs (T3 index within its event, added MDs, their hits, the chi2 of the fit); the
+// extended rows are counted per event, aggregated over a thread's consecutive rows of one event
+__device__ __forceinline__ void ext_write(const Ws& w, const Geo& g, int e, int row, const ExtBest& b,
+                                          int& e_acc, int& n_acc) {
+  int h[4] = {-1, -1, -1, -1};
+  if (b.t3 >= 0) {
+    const int add[2] = {w.t3_md1[b.t3], w.t3_md2[b.t3]};
+    int m = 0;
+    for (int a = 2 - b.n_add; a < 2; ++a) m += md_hits(w, add[a], h + m);
+    if (e != e_acc) {
+      if (n_acc) atomicAdd(&w.ev_stat[e_acc * kEvWords + kEvExt], n_acc);
+      e_acc = e;
+      n_acc = 0;
+    }
+    ++n_acc;
+  }
+  w.tcd_ext_t3[row] = b.t3 >= 0 ? b.t3 - w.t3_off[e * g.n_mods] : -1;
+  w.tcd_ext_n[row] = b.n_add;
+  for (int t = 0; t < 4; ++t) w.tcd_ext_hits[(int64_t)row * 4 + t] = h[t];
+  w.tcd_ext_c[row] = b.t3 >= 0 ? b.chi2c : 0.f;
+  w.tcd_ext_rz[row] = b.t3 >= 0 ? b.chi2rz : 0.f;
+}
+
+// the queued candidates of a row; false when some candidate was not queued (the row is then slow)
+__device__ __forceinline__ bool ext_queued(const Ws& w, int row, ExtBest& b) {
+  const int ncand = w.ext_cnt[row];
+  bool all = ncand <= kExtRefs;
+  for (int k = 0; k < min(ncand, kExtRefs); ++k) {
+    const int ref = w.ext_ref[(int64_t)row * kExtRefs + k];
+    if (ref < 0) { all = false; continue; }
+    const int reg = ref >> 28, pos = ref & ((1 << 28) - 1);
+    const int2 q = w.ext_q[reg * w.ext_qcap + pos];
+    ext_consider(w, b, ext_t3(q.y), ext_overlap(q.y), w.ext_res[reg * w.ext_qcap + pos]);
+  }
+  return all;
+}
+
+// (C) per row, the best passing queued candidate. Rows with candidates beyond their references or
+// the queues are handed to (D).
+__global__ void k_ext_select(Ws w, Geo g) {
   const int nrow = w.tcd_off[w.E];
-  int n_ext_acc = 0, e_acc = -1;
+  int n_acc = 0, e_acc = -1;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrow; row += gridDim.x * blockDim.x) {
+    ExtBest b;
+    if (!ext_queued(w, row, b)) {
+      const int k = atomicAdd(&w.ext_qn[4], 1);
+      if (k < w.tc_capacity) w.ext_slow[k] = row;
+      continue;
+    }
+    ext_write(w, g, find_seg(w.tcd_off, w.E, row), row, b, e_acc, n_acc);
+  }
+  if (n_acc) atomicAdd(&w.ev_stat[e_acc * kEvWords + kEvExt], n_acc);
+}
+
+// (D) the rare slow rows: their queued candidates, and the others fitted here
+__global__ void k_ext_slow(Ws w, Geo g, Cst<ff> c, ExtCuts xc) {
+  const int n = (int)min((int64_t)w.ext_qn[4], w.tc_capacity);
+  int n_acc = 0, e_acc = -1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int row = w.ext_slow[i];
     const int e = find_seg(w.tcd_off, w.E, row);
-    const int ncand = w.ext_cnt[row];
+    ExtBest b;
+    ext_queued(w, row, b);
     int md[5];
     ff ktc;
-    int K = 0;
-    int best = -1, best_n = 0;
-    float best_sc = 0.f, best_c = 0.f, best_rz = 0.f;
-    auto consider = [&](int d, int overlap, float4 r) {
-      if (r.w == 0.f) return;
-      bool better = best < 0 || r.x < best_sc;
-      if (!better && r.x == best_sc) {   // equal scores (rare): the sorted hit tuples decide
-        int key[6], bkey[6];
-        t3_sorted_hits(w, d, key);
-        t3_sorted_hits(w, best, bkey);
-        for (int t = 0; t < 6; ++t)
-          if (key[t] != bkey[t]) { better = key[t] < bkey[t]; break; }
-      }
-      if (better) {
-        best = d; best_n = 3 - overlap; best_sc = r.x; best_c = r.y; best_rz = r.z;
-      }
-    };
-    bool slow = ncand > kExtRefs;
-    for (int k = 0; k < min(ncand, kExtRefs); ++k) {
-      const int ref = w.ext_ref[(int64_t)row * kExtRefs + k];
-      if (ref < 0) { slow = true; continue; }
-      const int reg = ref >> 28, pos = ref & ((1 << 28) - 1);
-      const int2 q = w.ext_q[reg * w.ext_qcap + pos];
-      consider(ext_t3(q.y), ext_overlap(q.y), w.ext_res[reg * w.ext_qcap + pos]);
-    }
-    if (slow) {   // rare: candidates beyond the references or the queue, fitted here
-      K = ext_row(w, g, c, e, row, md, ktc);
-      int k = 0;
-      ext_candidates(w, c, md, K, ktc, [&](int d, int overlap) {
-        const int ref = k < kExtRefs ? w.ext_ref[(int64_t)row * kExtRefs + k] : -1;
-        ++k;
-        if (ref >= 0) return;   // already considered
-        consider(d, overlap, ext_eval_n(w, c, xc, md, K, d, overlap));
-      });
-    }
-    int h[4] = {-1, -1, -1, -1};
-    if (best >= 0) {
-      const int add[2] = {w.t3_md1[best], w.t3_md2[best]};
-      int m = 0;
-      for (int a = 2 - best_n; a < 2; ++a) m += md_hits(w, add[a], h + m);
-      if (e != e_acc) {
-        if (n_ext_acc) atomicAdd(&w.ev_stat[e_acc * kEvWords + kEvExt], n_ext_acc);
-        e_acc = e;
-        n_ext_acc = 0;
-      }
-      ++n_ext_acc;
-    }
-    w.tcd_ext_t3[row] = best >= 0 ? best - w.t3_off[e * g.n_mods] : -1;
-    w.tcd_ext_n[row] = best_n;
-    for (int t = 0; t < 4; ++t) w.tcd_ext_hits[(int64_t)row * 4 + t] = h[t];
-    w.tcd_ext_c[row] = best >= 0 ? best_c : 0.f;
-    w.tcd_ext_rz[row] = best >= 0 ? best_rz : 0.f;
+    const int K = ext_row(w, g, c, e, row, md, ktc);
+    int k = 0;
+    ext_candidates(w, c, md, K, ktc, [&](int d, int overlap) {
+      const int ref = k < kExtRefs ? w.ext_ref[(int64_t)row * kExtRefs + k] : -1;
+      ++k;
+      if (ref >= 0) return;   // already considered
+      ext_consider(w, b, d, overlap, ext_eval(w, c, xc, md, K, d, overlap));
+    });
+    ext_write(w, g, e, row, b, e_acc, n_acc);
   }
-  if (n_ext_acc) atomicAdd(&w.ev_stat[e_acc * kEvWords + kEvExt], n_ext_acc);
+  if (n_acc) atomicAdd(&w.ev_stat[e_acc * kEvWords + kEvExt], n_acc);
 }
 
 }  // namespace
+
 
 void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_pls_prep<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, g, c.f, c.x);
@@ -1274,7 +1307,7 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   ObjAnc om3{w.t3_anc, w.t3_anc_rlo, w.t3_ecm, w.cap.t3_dense};
   ObjAnc om5{w.t5_anc, w.t5_anc_rlo, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
-    k_obj_box<<<grid_for((int64_t)w.V * 2 * kBoxLanes, 256), 256, 0, L.stream>>>(w);
+    k_obj_box<<<grid_for((int64_t)w.V * 2 * kBoxLanes, 256), 256, 0, L.stream>>>(w, g);
     *L.launches += 1;
     KT_BEGIN(L, K_PT3_PRE);
   k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, w.box3, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
@@ -1350,12 +1383,13 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   for (int na = 0; na < 8; ++na) xc.rz[na] = ff(c.d.chi2_t5_rz * (na - 2) / 3.0);
   KT_BEGIN(L, K_TC_EXT);
   const int rows_grid = grid_for(w.tc_capacity, 128, 152 * 8);
-  const int fit_grid = grid_for(w.ext_qcap, 64, 152 * 4);
+  const int fit_grid = grid_for(w.ext_qcap, 128, 152 * 4);
   k_ext_cand<<<rows_grid, 128, 0, L.stream>>>(w, g, c.x);
-  k_ext_fit<<<dim3(fit_grid, 4), 64, 0, L.stream>>>(w, g, c.x, xc);
-  k_ext_select<<<rows_grid, 128, 0, L.stream>>>(w, g, c.x, xc);
+  k_ext_fit<<<dim3(fit_grid, 4), 128, 0, L.stream>>>(w, g, c.x, xc);
+  k_ext_select<<<rows_grid, 128, 0, L.stream>>>(w, g);
+  k_ext_slow<<<grid_for(w.tc_capacity, 64, 152 * 8), 64, 0, L.stream>>>(w, g, c.x, xc);
   KT_END(L, K_TC_EXT);
-  *L.launches += 3;
+  *L.launches += 4;
 }
 
 // the grid's cells per event

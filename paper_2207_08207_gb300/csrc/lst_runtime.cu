@@ -376,7 +376,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   z.add(w.cell_cnt, NC); z.add(w.cell_cur, NC);
   z.add(w.work_cnt, 32); z.add(w.work_cur, 32);
   z.add(w.scan_ctr, kScanMax);
-  z.add(w.ext_qn, 4);
+  z.add(w.ext_qn, 5);
   z.add(w.ls_head, 1);
   // binning
   pl.add(w.hit_vs, c.H); pl.add(w.sens_off, S + 1); pl.add(w.bidx, c.H);
@@ -456,7 +456,7 @@ size_t layout_work(Ws& w, const Caps& c, int n_mods, void* base, size_t* zero_by
   pl.add(w.tcd_ext_t3, tc_cap); pl.add(w.tcd_ext_n, tc_cap); pl.add(w.tcd_ext_hits, 4 * tc_cap);
   pl.add(w.tcd_ext_c, tc_cap); pl.add(w.tcd_ext_rz, tc_cap);
   w.ext_qcap = tc_cap / 2 + 1024;   // candidates per anchor count (about one per candidate row in all)
-  pl.add(w.ext_cnt, tc_cap); pl.add(w.ext_ref, kExtRefs * tc_cap);
+  pl.add(w.ext_cnt, tc_cap); pl.add(w.ext_ref, kExtRefs * tc_cap); pl.add(w.ext_slow, tc_cap);
   pl.add(w.ext_q, 4 * w.ext_qcap); pl.add(w.ext_res, 4 * w.ext_qcap);
   // event-local outputs
   pl.add(w.o_md_lo, c.md_dense); pl.add(w.o_md_up, c.md_dense); pl.add(w.o_md_mod, c.md_dense);
