@@ -1155,29 +1155,63 @@ __device__ __forceinline__ int ext_t3(int v) { return (int)((unsigned)v & ((1u <
 __device__ __forceinline__ int ext_overlap(int v) { return (int)((unsigned)v >> 30); }
 
 // (A) each row's candidates that agree in curvature go to the queue region of their anchor count;
-// the row keeps up to kExtRefs references and the total
+// the row keeps up to kExtRefs references and the total. A row's candidates fall in two regions
+// (overlap 1: K + 2 anchors, overlap 2: K + 1). The rows of a warp first count theirs, reserve their
+// queue space with one atomic per warp and region (the regions' four counters would otherwise take
+// one atomic per candidate), then list them again in the same order and write them.
 __global__ void k_ext_cand(Ws w, Geo g, Cst<ff> c) {
   const int nrow = w.tcd_off[w.E];
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrow; row += gridDim.x * blockDim.x) {
-    const int e = find_seg(w.tcd_off, w.E, row);
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int row0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); row0 < nrow; row0 += stride) {
+    const int row = row0 + lane;
     int md[5];
     ff ktc;
-    const int K = ext_row(w, g, c, e, row, md, ktc);
-    int n = 0;
-    ext_candidates(w, c, md, K, ktc, [&](int d, int overlap) {
-      if (n < kExtRefs) {   // candidates beyond the row's references are evaluated by the selection pass
-        const int reg = K + 3 - overlap - 4;
-        const int pos = atomicAdd(&w.ext_qn[reg], 1);
-        if (pos < w.ext_qcap) {
-          w.ext_q[reg * w.ext_qcap + pos] = make_int2(row, ext_pack(d, overlap));
-          w.ext_ref[(int64_t)row * kExtRefs + n] = (reg << 28) | pos;
-        } else {
-          w.ext_ref[(int64_t)row * kExtRefs + n] = -1;   // not queued: evaluated by the selection pass
-        }
+    int K = 0;
+    if (row < nrow) K = ext_row(w, g, c, find_seg(w.tcd_off, w.E, row), row, md, ktc);
+    // pass 1: referenced candidates per overlap (the first kExtRefs in listing order) and the total
+    int n = 0, n1 = 0, n2 = 0;
+    ext_candidates(w, c, md, K, ktc, [&](int, int overlap) {
+      if (n < kExtRefs) {
+        if (overlap == 1) ++n1; else ++n2;
       }
       ++n;
     });
-    w.ext_cnt[row] = n;
+    // one reservation per warp and region: the region of overlap o is (K + 3 - o) - 4, so K - 2 for
+    // overlap 1 and K - 3 for overlap 2
+    int pos1 = 0, pos2 = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int mine = (K > 0 && K - 2 == r ? n1 : 0) + (K > 0 && K - 3 == r ? n2 : 0);
+      int incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      int base = 0;
+      if (lane == 31 && total > 0) base = atomicAdd(&w.ext_qn[r], total);
+      base = __shfl_sync(0xffffffffu, base, 31) + incl - mine;
+      if (K > 0 && K - 2 == r) pos1 = base;   // overlap 1 takes [base, base + n1)
+      if (K > 0 && K - 3 == r) pos2 = base;   // overlap 2 takes [base, base + n2)
+    }
+    // pass 2: the same candidates in the same order, written to the reserved positions
+    int k = 0;
+    ext_candidates(w, c, md, K, ktc, [&](int d, int overlap) {
+      if (k < kExtRefs) {   // candidates beyond the row's references are evaluated by the slow pass
+        const int reg = K + 3 - overlap - 4;
+        const int pos = overlap == 1 ? pos1++ : pos2++;
+        if (pos < w.ext_qcap) {
+          w.ext_q[reg * w.ext_qcap + pos] = make_int2(row, ext_pack(d, overlap));
+          w.ext_ref[(int64_t)row * kExtRefs + k] = (reg << 28) | pos;
+        } else {
+          w.ext_ref[(int64_t)row * kExtRefs + k] = -1;   // not queued: evaluated by the slow pass
+        }
+      }
+      ++k;
+    });
+    if (row < nrow) w.ext_cnt[row] = n;
   }
 }
 
