@@ -389,9 +389,9 @@ __global__ void k_pt_decide(Ws w, Cst<ff> c, ObjAnc oa, const int2* queue, int q
       xy += t1;
       rz += t2;
     }
-    if (!(xy <= cut_xy) || !(rz <= cut_rz)) continue;
-    const int slot = atomicAdd(&w.status[n_word], 1);
-    if (slot >= a_cap) continue;
+    const bool pass = xy <= cut_xy && rz <= cut_rz;
+    const int slot = warp_agg_slot(pass, &w.status[n_word]);   // one atomic per warp on the shared count
+    if (!pass || slot >= a_cap) continue;
     a_pls[slot] = q.x;
     a_obj[slot] = q.y;
     a_xy[slot] = (float)xy;
