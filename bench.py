@@ -374,6 +374,13 @@ def main():
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": hbm_achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
+    # the LS search's work: windowed (inner MD, outer MD) pairs per event (counted by the kernel) and,
+    # with the ncu instruction count, thread instructions per pair
+    n_pairs = counts[0]["n_ls_pairs"] if counts else 0
+    roofline["ls_pairs_per_event"] = n_pairs / B
+    ls_prof = kernel_profile("ls") if args.config == 2 else None
+    if ls_prof is not None and n_pairs:
+        roofline["ls_thread_inst_per_pair"] = ls_prof["thread_inst"] * (B / ls_prof["events_per_launch"]) / n_pairs
     roofline.update({"kernel_ms": kavg.get(dom) if dom else None,
                      "hbm": {"algorithmic_bytes": alg_bytes, "achieved": hbm_achieved, "peak": hbm_peak,
                              "unit": "GB/s", "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind},

@@ -164,6 +164,8 @@ typedef struct {
   int32_t retries;
   int32_t status;
   int32_t n_tc_ext;   /* track candidates that were extended (Sec. 2.5.1) */
+  int64_t n_ls_pairs; /* batch total: (inner MD, outer MD) candidate pairs the LS search evaluated
+                         (those inside its azimuth windows; Sec. 2.2), a measure of its work */
 } lst_counts;
 
 /*

@@ -664,6 +664,7 @@ __global__ void __launch_bounds__(256, 4) k_ls(Ws w, Geo g, Cst<float> c, int pe
   const float kwin = c.n_sigma * c.sigma_rphi + c.d0_max;
   const float kPiF = 3.14159265f;
   int qn = 0;   // pairs waiting in this warp's queue
+  unsigned long long n_pairs = 0;   // windowed pairs this warp evaluated (added once, at the end)
   const long long t0 = clock64();
   int sweep = 0;
   for (;;) {
@@ -759,6 +760,7 @@ __global__ void __launch_bounds__(256, 4) k_ls(Ws w, Geo g, Cst<float> c, int pe
       // this item's share of the windowed outer MDs: chunk `chunk` of nch equal chunks
       const int csz = (totB + nch - 1) / max(nch, 1);
       const int jbeg = chunk * csz, jend = min(totB, jbeg + csz);
+      if (jend > jbeg) n_pairs += (unsigned long long)(jend - jbeg) * (unsigned long long)nA;
       for (int j0 = jbeg; j0 < jend; j0 += 32) {
         const int j = j0 + lane;
         const bool has_b = j < jend;
@@ -811,6 +813,7 @@ __global__ void __launch_bounds__(256, 4) k_ls(Ws w, Geo g, Cst<float> c, int pe
   }
   __syncwarp();
   if (qn > 0) ls_flush(w, c, S, qn);
+  if (lane == 0 && n_pairs) atomicAdd(reinterpret_cast<unsigned long long*>(&w.status[ST_LS_PAIRS]), n_pairs);
 }
 
 // dynamic shared memory of k_ls for a block of `block` threads and T target slots per warp

@@ -36,8 +36,11 @@ enum StatusWord : int {
   ST_N_PT3, ST_N_PT5,    // appended pT3 / pT5 objects
   ST_DENSE_MD, ST_DENSE_LS, ST_DENSE_T3, ST_DENSE_T5,   // dense totals beyond the dense capacity
   ST_TIMEOUT,            // blocks that ran out of their cycle budget
+  ST_LS_PAIRS,           // (with the next word: one 64-bit count) (inner MD, outer MD) pairs the LS
+  ST_LS_PAIRS_HI,        //   kernel evaluated, inside its azimuth windows
   ST_N_WORDS
 };
+static_assert(ST_LS_PAIRS % 2 == 0, "the 64-bit pair count needs an 8-byte aligned word");
 enum ErrorBit : int { ERR_BAD_SENSOR = 1, ERR_BAD_COORD = 2, ERR_BAD_PLS = 4 };
 
 // Per-event summary written by the final kernel: object counts [0..6] (MD, LS, T3, T5, pT3, pT5, TC),

@@ -1113,6 +1113,7 @@ int lst_sync(lst_ctx* ctx, int32_t* status_per_event) {
     c.n_md = es[0]; c.n_ls = es[1]; c.n_t3 = es[2]; c.n_t5 = es[3]; c.n_pt3 = es[4]; c.n_pt5 = es[5]; c.n_tc = es[6];
     for (int k = 0; k < 4; ++k) c.n_tc_type[k] = es[7 + k];
     c.n_tc_ext = es[kEvExt];
+    c.n_ls_pairs = (int64_t)(((uint64_t)(uint32_t)st[ST_LS_PAIRS_HI] << 32) | (uint32_t)st[ST_LS_PAIRS]);
     for (int s = 0; s < LST_N_STAGES; ++s) c.overflow[s] = ctx->first_ovf[s];
     c.recheck[LST_STAGE_MD] = st[ST_REC_MD];
     c.recheck[LST_STAGE_LS] = st[ST_REC_LS];

@@ -51,11 +51,12 @@ class Counts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("n_hits", "n_pls", "n_md", "n_ls", "n_t3", "n_t5", "n_pt3",
                                               "n_pt5", "n_tc")] + [
         ("n_tc_type", ctypes.c_int32 * 4), ("overflow", ctypes.c_int32 * 8), ("recheck", ctypes.c_int32 * 8),
-        ("retries", ctypes.c_int32), ("status", ctypes.c_int32), ("n_tc_ext", ctypes.c_int32)]
+        ("retries", ctypes.c_int32), ("status", ctypes.c_int32), ("n_tc_ext", ctypes.c_int32),
+        ("n_ls_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         d = {n: getattr(self, n) for n in ("n_hits", "n_pls", "n_md", "n_ls", "n_t3", "n_t5", "n_pt3", "n_pt5",
-                                           "n_tc", "retries", "status", "n_tc_ext")}
+                                           "n_tc", "retries", "status", "n_tc_ext", "n_ls_pairs")}
         d["n_tc_type"] = dict(zip(TC_TYPES, list(self.n_tc_type)))
         d["overflow"] = dict(zip(STAGES, list(self.overflow)))
         d["recheck"] = dict(zip(STAGES, list(self.recheck)))

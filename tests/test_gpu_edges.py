@@ -102,3 +102,30 @@ def test_contexts_with_different_ls_blocks_coexist():
     finally:
         big.close()
         small.close()
+
+
+def test_ls_pair_count_lies_between_accepted_and_connected_pairs():
+    """The LS search's work count (n_ls_pairs, the (inner MD, outer MD) pairs it evaluated inside its
+    azimuth windows) is at least the number of LS it accepted and at most the pairs the module map
+    connects (each module's MDs times those of its connected modules), in a batch of PU200 events,
+    with one context per LS execution mode."""
+    det = gen.make_detector(barrel_only=False, pt_thr=0.8)
+    evs = [gen.config_event(2, e)[1] for e in range(3)]
+    for persistent in (2, 1, 0):
+        ctx = lst.Context(det, persistent=persistent)
+        try:
+            ctx.run(evs)
+            n_ls, connected = 0, 0
+            for e in range(len(evs)):
+                r = ctx.results(e)
+                n_ls += r["counts"]["n_ls"]
+                na = np.bincount(r["md_module"], minlength=det.n_mods).astype(np.int64)
+                cs = np.concatenate([[0], np.cumsum(na[det.conn_tgt])])
+                nb = cs[det.conn_off[1:]] - cs[det.conn_off[:-1]]   # MDs of each module's connected modules
+                connected += int((na * nb).sum())
+            pairs = ctx.counts(0)["n_ls_pairs"]
+            assert all(ctx.counts(e)["n_ls_pairs"] == pairs for e in range(len(evs)))
+            assert n_ls <= pairs <= connected, (persistent, n_ls, pairs, connected)
+            assert pairs < 0.7 * connected   # the windows remove a large share of the connected pairs
+        finally:
+            ctx.close()
