@@ -163,7 +163,7 @@ def serving_run(det, events, rate, n_requests, batch_sizes, seed=0):
     srv = Server(det, batch_sizes=batch_sizes, max_hits=max(e.n_hits for e in events),
                  max_pls=max(e.n_pls for e in events), budget=40e9, keep="tc", use_graph=1, persistent=2)
     reqs = [events[i % len(events)] for i in range(n_requests)]
-    srv.warmup(events)   # graph capture and arena first touch on every engine
+    srv.warmup(events)   # graph capture, arena first touch, arenas sized for the heaviest batch
     stats, _ = srv.serve(reqs, poisson_arrivals(rate, n_requests, seed))
     srv.close()
     d = stats.as_dict()

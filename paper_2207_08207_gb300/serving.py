@@ -265,10 +265,15 @@ class Server:
                                    wakeup=self.wakeup)
 
     def warmup(self, events):
-        """One batch on every engine (graph capture, arena first touch) before a measurement."""
+        """Batches on every engine before a measurement: graph capture and arena first touch, then a
+        full batch of the heaviest of `events`, so that the engines' arenas already hold any batch of
+        these events (an arena that grows during serving makes its engine capture its graph again,
+        a stall of a few hundred milliseconds for the requests waiting on it)."""
+        heavy = max(events, key=lambda ev: (_n_hits(ev), _n_pls(ev)))
         for e in self.engines:
-            e.submit(list(events[: e.max_batch]))
-            e.collect(min(len(events), e.max_batch))
+            for batch in (list(events[: e.max_batch]), [heavy] * e.max_batch):
+                e.submit(batch)
+                e.collect(len(batch))
 
     def serve(self, events, arrivals):
         reqs = [Request(i, float(t), ev, _n_hits(ev), _n_pls(ev)) for i, (t, ev) in enumerate(zip(arrivals, events))]
