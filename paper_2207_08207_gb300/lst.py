@@ -47,6 +47,62 @@ class EventIn(ctypes.Structure):
                 ("n_pls", ctypes.c_int32), ("mem_space", ctypes.c_int32)]
 
 
+# EventIn as a numpy structured dtype (same offsets and size): a batch of device events is marshalled
+# column by column instead of one ctypes structure per event
+_EVENT_IN_DTYPE = np.dtype({
+    "names": [f for f, _ in EventIn._fields_],
+    "formats": ["<u8" if t is ctypes.c_void_p else "<i4" for _, t in EventIn._fields_],
+    "offsets": [getattr(EventIn, f).offset for f, _ in EventIn._fields_],
+    "itemsize": ctypes.sizeof(EventIn)})
+
+
+def _tensor_events_in(events, host_async):
+    """The EventIn records of a batch of events given as dicts of torch tensors, as a numpy array.
+    CUDA tensors are device inputs; CPU tensors (pinned or pageable) are host inputs, held until
+    sync with host_async, else copied before the call returns."""
+    buf = np.zeros(len(events), dtype=_EVENT_IN_DTYPE)
+    for f in ("x", "y", "z", "sensor"):
+        buf[f] = [ev[f].data_ptr() for ev in events]
+    buf["n_hits"] = [ev["x"].shape[0] for ev in events]
+    n_pls = [int(ev.get("n_pls", 0)) for ev in events]
+    buf["n_pls"] = n_pls
+    buf["pls"] = [ev["pls"].data_ptr() if k else 0 for ev, k in zip(events, n_pls)]
+    host = LST_MEM_HOST_ASYNC if host_async else LST_MEM_HOST
+    buf["mem_space"] = [LST_MEM_DEVICE if ev["x"].is_cuda else host for ev in events]
+    return buf
+
+
+def _addr(a):
+    """Address of a contiguous numpy array's data (the buffer protocol where the array is writable:
+    cheaper than the .ctypes attribute, which stays the fallback)."""
+    try:
+        return ctypes.addressof(ctypes.c_char.from_buffer(a))
+    except (TypeError, ValueError, BufferError):
+        return a.ctypes.data
+
+
+def _host_events_in(events, host_async):
+    """The EventIn records of a batch of host events (gen.Event objects with numpy arrays), as a
+    numpy array, and the contiguous arrays they point to (to be kept alive until sync)."""
+    buf = np.zeros(len(events), dtype=_EVENT_IN_DTYPE)
+    keep = []
+    cols = {f: [] for f in ("x", "y", "z", "sensor", "pls", "n_hits", "n_pls")}
+    asc, f32, i32 = np.ascontiguousarray, np.float32, np.int32
+    for ev in events:
+        x, y, z = asc(ev.x, dtype=f32), asc(ev.y, dtype=f32), asc(ev.z, dtype=f32)
+        s = asc(ev.sensor, dtype=i32)
+        k = ev.n_pls
+        p = asc(ev.pls) if k else None
+        keep += (x, y, z, s, p)
+        cols["x"].append(_addr(x)); cols["y"].append(_addr(y)); cols["z"].append(_addr(z))
+        cols["sensor"].append(_addr(s)); cols["pls"].append(_addr(p) if k else 0)
+        cols["n_hits"].append(x.shape[0]); cols["n_pls"].append(k)
+    for f, v in cols.items():
+        buf[f] = v
+    buf["mem_space"] = LST_MEM_HOST_ASYNC if host_async else LST_MEM_HOST
+    return buf, keep
+
+
 class Counts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("n_hits", "n_pls", "n_md", "n_ls", "n_t3", "n_t5", "n_pt3",
                                               "n_pt5", "n_tc")] + [
@@ -223,10 +279,36 @@ class Context:
 
     # -- running ----------------------------------------------------------------------------
     def submit(self, events, stream=None, host_async=False):
-        """Enqueue a batch. `events`: gen.Event objects (host numpy) or dicts of torch CUDA tensors
-        with keys x, y, z, sensor, pls (uint8/int32 tensor viewing lst_pls records or None).
+        """Enqueue a batch. `events`: gen.Event objects (host numpy) or dicts of torch tensors with
+        keys x, y, z, sensor, pls (uint8/int32 tensor viewing lst_pls records or None) and n_pls;
+        CUDA tensors are device inputs, CPU tensors host inputs.
         host_async: pass host events as LST_MEM_HOST_ASYNC (the arrays are held until sync; pinned
         arrays are then read by the device in place instead of being packed on the host)."""
+        n = len(events)
+        is_dict = [isinstance(ev, dict) for ev in events]
+        if n and all(is_dict):            # dicts of tensors: the records built one column at a time
+            buf = _tensor_events_in(events, host_async)
+            arr = ctypes.cast(buf.ctypes.data, ctypes.POINTER(EventIn))
+            keep = [buf, list(events)]
+        elif n and not any(is_dict):      # host events
+            buf, keep = _host_events_in(events, host_async)
+            arr = ctypes.cast(buf.ctypes.data, ctypes.POINTER(EventIn))
+            keep.append(buf)
+        else:                             # a mixed batch: record by record
+            arr, keep = self._events_in(events, host_async)
+        outs = (EventOut * n)()
+        st = None
+        if stream is not None:
+            st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self._check(self._L.lst_run_events(self._h, arr, n, outs, st))
+        self._keep = keep
+        self._outs = outs
+        self._n_ev = n
+        return outs
+
+    @staticmethod
+    def _events_in(events, host_async):
+        """EventIn records of a mixed batch (dicts of tensors and gen.Event objects), one by one."""
         n = len(events)
         arr = (EventIn * n)()
         keep = []
@@ -234,7 +316,7 @@ class Context:
             if isinstance(ev, dict):
                 x, y, z, s, p = ev["x"], ev["y"], ev["z"], ev["sensor"], ev.get("pls")
                 n_pls = int(ev.get("n_pls", 0))
-                mem = LST_MEM_DEVICE
+                mem = LST_MEM_DEVICE if x.is_cuda else (LST_MEM_HOST_ASYNC if host_async else LST_MEM_HOST)
             else:
                 x = np.ascontiguousarray(ev.x, dtype=np.float32)
                 y = np.ascontiguousarray(ev.y, dtype=np.float32)
@@ -246,15 +328,7 @@ class Context:
             keep += [x, y, z, s, p]
             nh = int(x.shape[0]) if hasattr(x, "shape") else len(x)
             arr[i] = EventIn(_ptr(x), _ptr(y), _ptr(z), _ptr(s), nh, _ptr(p) if n_pls else None, n_pls, mem)
-        outs = (EventOut * n)()
-        st = None
-        if stream is not None:
-            st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-        self._check(self._L.lst_run_events(self._h, arr, n, outs, st))
-        self._keep = keep
-        self._outs = outs
-        self._n_ev = n
-        return outs
+        return arr, keep
 
     def sync(self):
         status = np.zeros(max(self._n_ev, 1), dtype=np.int32)
