@@ -235,6 +235,8 @@ struct Launch {
   int persistent = 0;   // 0 grid-stride, 1 static cost-ordered deal, 2 device queue
   int n_sm = 152;
   int ls_blocks_per_sm = 0;        // resident blocks of the Line-Segment kernel (0: not queried)
+  int t3_blocks_per_sm = 0;        // resident blocks of the T3 / T5 candidate kernels (0: not queried)
+  int t5_blocks_per_sm = 0;
   long long* launches = nullptr;   // host counter
   bool capturing = false;          // the chain is being captured into a CUDA graph
   cudaEvent_t* kev = nullptr;      // when set: [2 * kernel id] start / end events of timed kernels
@@ -267,6 +269,10 @@ enum KernelId : int {
 
 // resident blocks per SM of the Line-Segment kernel at `block` threads (0 when the query fails)
 int ls_resident_blocks(int block, int targets);
+// resident blocks per SM of the T3 and T5 candidate kernels (their grids hold exactly these, so that
+// their statically divided work runs in one wave); 0 when the query fails
+int t3_pre_resident_blocks();
+int t5_pre_resident_blocks();
 
 // scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);

@@ -178,6 +178,7 @@ struct lst_ctx {
   long long launches = 0;
   int n_sm = 152;
   int ls_bps = 0;
+  int t3_bps = 0, t5_bps = 0;   // resident blocks per SM of the T3 / T5 candidate kernels
   bool pageable_access = false;   // the GPU reads pageable host memory coherently (e.g. NVLink-C2C)
   // CUDA graph of the whole chain for the current arenas (shape-independent within capacities)
   cudaGraphExec_t graph_exec = nullptr;
@@ -262,6 +263,8 @@ Launch make_launch(lst_ctx* ctx) {
   L.launches = &ctx->launches;
   L.n_sm = ctx->n_sm;
   L.ls_blocks_per_sm = ctx->ls_bps;
+  L.t3_blocks_per_sm = ctx->t3_bps;
+  L.t5_blocks_per_sm = ctx->t5_bps;
   L.kev = ctx->timing ? ctx->ev_kern : nullptr;
   return L;
 }
@@ -820,6 +823,8 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   ctx->max_degree = maxdeg;
   ctx->geo.ls_tcap = std::max(32, (maxdeg + 31) / 32 * 32);
   ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls, ctx->geo.ls_tcap);
+  ctx->t3_bps = t3_pre_resident_blocks();
+  ctx->t5_bps = t5_pre_resident_blocks();
   ctx->geo_loaded = true;
   // arenas depend on the module count
   if (ctx->in_mem) CK(cudaFreeAsync(ctx->in_mem, ctx->stream));

@@ -465,7 +465,19 @@ __global__ void k_t5_dense(Ws w) {
   }
 }
 
+int resident_blocks(const void* kernel, int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 }  // namespace
+
+int t3_pre_resident_blocks() { return resident_blocks(reinterpret_cast<const void*>(k_t3_pre), 32 * kT3Warps); }
+int t5_pre_resident_blocks() { return resident_blocks(reinterpret_cast<const void*>(k_t5_pre), 32 * kT5Warps); }
 
 void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   (void)g;
@@ -473,7 +485,9 @@ void run_t3(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.t3_base, w.t3_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T3_PRE);
-  k_t3_pre<<<L.n_sm * 8, 32 * kT3Warps, 0, L.stream>>>(w, c.f);
+  // every resident block and no more: the blocks divide the inner LS statically, so a second,
+  // partly filled wave would hold up the launch
+  k_t3_pre<<<L.n_sm * (L.t3_blocks_per_sm > 0 ? L.t3_blocks_per_sm : 8), 32 * kT3Warps, 0, L.stream>>>(w, c.f);
   KT_END(L, K_T3_PRE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T3_DECIDE);
@@ -497,7 +511,7 @@ void run_t5(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   LST_LAUNCH(L);
   scan_exclusive(w.t5_base, w.t5_base, w.V, w.scan_tmp, L);
   KT_BEGIN(L, K_T5_PRE);
-  k_t5_pre<<<L.n_sm * 8, 32 * kT5Warps, 0, L.stream>>>(w, c.f);
+  k_t5_pre<<<L.n_sm * (L.t5_blocks_per_sm > 0 ? L.t5_blocks_per_sm : 8), 32 * kT5Warps, 0, L.stream>>>(w, c.f);
   KT_END(L, K_T5_PRE);
   LST_LAUNCH(L);
   KT_BEGIN(L, K_T5_DECIDE);
