@@ -125,3 +125,35 @@ def test_event_driven_loop_does_not_poll():
     assert stats.n == 150 and all(r.result == ("result", r.rid) for r in reqs)
     # one pass per arrival, submission or completion (plus timeouts), not a busy poll
     assert sched.iterations < 10 * len(reqs), sched.iterations
+
+
+def test_warmup_sizes_every_engine_for_a_full_batch_of_the_heaviest_event():
+    """Server.warmup runs, on every engine, a batch of the given events and then a full batch of the
+    heaviest of them, so that no batch of these events makes an engine grow its arenas (and capture
+    its graph again) while it is being measured."""
+    from types import SimpleNamespace
+
+    from paper_2207_08207_gb300.serving import Server
+
+    class Recorder(Engine):
+        def __init__(self, max_batch):
+            self.max_batch = max_batch
+            self.batches = []
+
+        def submit(self, events):
+            self.batches.append(list(events))
+
+        def done(self):
+            return True
+
+        def collect(self, n):
+            assert n == len(self.batches[-1])
+            return [None] * n
+
+    events = [SimpleNamespace(n_hits=h, n_pls=p, name=i) for i, (h, p) in enumerate([(10, 5), (90, 1), (40, 9), (90, 3)])]
+    srv = object.__new__(Server)
+    srv.engines = [Recorder(1), Recorder(4), Recorder(16)]
+    srv.warmup(events)
+    for e in srv.engines:
+        assert e.batches[0] == events[: e.max_batch]
+        assert [ev.name for ev in e.batches[1]] == [3] * e.max_batch   # most hits, then most seeds
