@@ -237,6 +237,8 @@ struct Launch {
   int ls_blocks_per_sm = 0;        // resident blocks of the Line-Segment kernel (0: not queried)
   int t3_blocks_per_sm = 0;        // resident blocks of the T3 / T5 candidate kernels (0: not queried)
   int t5_blocks_per_sm = 0;
+  int pt3_blocks_per_sm = 0;       // resident blocks of the pT3 / pT5 pre-filters at warps_px warps
+  int pt5_blocks_per_sm = 0;       //   per block (0: not queried)
   long long* launches = nullptr;   // host counter
   bool capturing = false;          // the chain is being captured into a CUDA graph
   cudaEvent_t* kev = nullptr;      // when set: [2 * kernel id] start / end events of timed kernels
@@ -273,6 +275,8 @@ int ls_resident_blocks(int block, int targets);
 // their statically divided work runs in one wave); 0 when the query fails
 int t3_pre_resident_blocks();
 int t5_pre_resident_blocks();
+// the same for the pT3 (n = 3) and pT5 (n = 5) pre-filters with `warps` warps per block
+int pt_pre_resident_blocks(int n, int warps);
 
 // scan: out[0..n] exclusive prefix sums of in[0..n-1] (out[n] = total); in and out may alias
 void scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, const Launch& L);

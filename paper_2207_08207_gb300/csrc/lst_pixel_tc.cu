@@ -1337,19 +1337,21 @@ void run_pixel(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_pls_prep<<<grid_for(w.P, 256), 256, 0, L.stream>>>(w, g, c.f, c.x);
   LST_LAUNCH(L);
   const int threads = 32 * L.warps_px;
-  const int blocks = grid_for((int64_t)w.P * 32, threads, 152 * 16);
+  // at most the resident blocks: the warps divide the seeds statically, so a second wave of blocks
+  // would only start as the first one drains
+  auto pt_blocks = [&](int bps) { return grid_for((int64_t)w.P * 32, threads, L.n_sm * (bps > 0 ? bps : 16)); };
   ObjAnc om3{w.t3_anc, w.t3_anc_rlo, w.t3_ecm, w.cap.t3_dense};
   ObjAnc om5{w.t5_anc, w.t5_anc_rlo, w.t5_ecm, w.cap.t5_dense};
   if (g.n_pix_bins > 0) {
     k_obj_box<<<grid_for((int64_t)w.V * 2 * kBoxLanes, 256), 256, 0, L.stream>>>(w, g);
     *L.launches += 1;
     KT_BEGIN(L, K_PT3_PRE);
-  k_pt_pre<3><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t3_off, w.box3, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
+  k_pt_pre<3><<<pt_blocks(L.pt3_blocks_per_sm), threads, 0, L.stream>>>(w, g, c.f, w.t3_off, w.box3, om3, w.q_p3, ST_Q_PT3, w.cap.q_p3,
                                                    c.f.chi2_pt3_xy, c.f.chi2_pt3_rz);
   KT_END(L, K_PT3_PRE);
     LST_LAUNCH(L);
     KT_BEGIN(L, K_PT5_PRE);
-  k_pt_pre<5><<<blocks, threads, 0, L.stream>>>(w, g, c.f, w.t5_off, w.box5, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5,
+  k_pt_pre<5><<<pt_blocks(L.pt5_blocks_per_sm), threads, 0, L.stream>>>(w, g, c.f, w.t5_off, w.box5, om5, w.q_p5, ST_Q_PT5, w.cap.q_p5,
                                                    c.f.chi2_pt5_xy, c.f.chi2_pt5_rz);
   KT_END(L, K_PT5_PRE);
     LST_LAUNCH(L);
@@ -1424,6 +1426,16 @@ void run_tc(const Ws& w, const Geo& g, const Consts& c, const Launch& L) {
   k_ext_slow<<<grid_for(w.tc_capacity, 64, 152 * 8), 64, 0, L.stream>>>(w, g, c.x, xc);
   KT_END(L, K_TC_EXT);
   *L.launches += 4;
+}
+
+int pt_pre_resident_blocks(int n, int warps) {
+  const void* k = n == 3 ? reinterpret_cast<const void*>(k_pt_pre<3>) : reinterpret_cast<const void*>(k_pt_pre<5>);
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 32 * warps, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b;
 }
 
 // the grid's cells per event

@@ -179,6 +179,7 @@ struct lst_ctx {
   int n_sm = 152;
   int ls_bps = 0;
   int t3_bps = 0, t5_bps = 0;   // resident blocks per SM of the T3 / T5 candidate kernels
+  int pt3_bps = 0, pt5_bps = 0; // and of the pT3 / pT5 pre-filters
   bool pageable_access = false;   // the GPU reads pageable host memory coherently (e.g. NVLink-C2C)
   // CUDA graph of the whole chain for the current arenas (shape-independent within capacities)
   cudaGraphExec_t graph_exec = nullptr;
@@ -265,6 +266,8 @@ Launch make_launch(lst_ctx* ctx) {
   L.ls_blocks_per_sm = ctx->ls_bps;
   L.t3_blocks_per_sm = ctx->t3_bps;
   L.t5_blocks_per_sm = ctx->t5_bps;
+  L.pt3_blocks_per_sm = ctx->pt3_bps;
+  L.pt5_blocks_per_sm = ctx->pt5_bps;
   L.kev = ctx->timing ? ctx->ev_kern : nullptr;
   return L;
 }
@@ -825,6 +828,8 @@ int lst_load_geometry(lst_ctx* ctx, const lst_module* mods, int32_t n_mods, cons
   ctx->ls_bps = ls_resident_blocks(ctx->cfg.block_ls, ctx->geo.ls_tcap);
   ctx->t3_bps = t3_pre_resident_blocks();
   ctx->t5_bps = t5_pre_resident_blocks();
+  ctx->pt3_bps = pt_pre_resident_blocks(3, ctx->cfg.warps_px);
+  ctx->pt5_bps = pt_pre_resident_blocks(5, ctx->cfg.warps_px);
   ctx->geo_loaded = true;
   // arenas depend on the module count
   if (ctx->in_mem) CK(cudaFreeAsync(ctx->in_mem, ctx->stream));
