@@ -261,7 +261,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=None,
+                    help="events per step (default: 16 for the PU300 stress workload, which is defined on 16, else 64)")
     ap.add_argument("--config", type=int, default=2, choices=sorted(WORKLOADS),
                     help="event configuration of the batched / plain measurement (2: PU200)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -288,7 +289,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2207_08207_gb300 import lst
 
-    B = args.batch
+    B = args.batch if args.batch else (16 if args.config == 4 else 64)
     # every rank processes its own events (events are independent: no collective on the data path)
     det, evs = make_events(B, seed0=rank_seed0(rank), config=args.config)
     # inputs resident in HBM
