@@ -614,9 +614,17 @@ __global__ void k_t5_clean(Ws w, int overlap) {
   const unsigned gmask = ((1u << kCleanLanes) - 1u) << ((threadIdx.x & 31) & ~(kCleanLanes - 1));
   const int ngroups = gridDim.x * (blockDim.x / kCleanLanes);
   for (int a = (blockIdx.x * blockDim.x + threadIdx.x) / kCleanLanes; a < n; a += ngroups) {
+    // a T5's 10 hits are 40 bytes from an 8-byte aligned base: five independent 8-byte loads
     int ha[10];
+    {
+      const int2* pa = reinterpret_cast<const int2*>(w.t5_hit + (int64_t)a * 10);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) ha[k] = w.t5_hit[(int64_t)a * 10 + k];
+      for (int k = 0; k < 5; ++k) {
+        const int2 v = pa[k];
+        ha[2 * k] = v.x;
+        ha[2 * k + 1] = v.y;
+      }
+    }
     const float ca = w.t5_f[3 * S + a];
     // the probed lists, concatenated: list t covers [beg[t], beg[t] + len[t])
     int beg[10], end_[10];
@@ -630,25 +638,33 @@ __global__ void k_t5_clean(Ws w, int overlap) {
     }
     bool drop = false;
     for (int k = sub; k < total && !drop; k += kCleanLanes) {
-      int t = 0;
+      // the list holding entry k (the lists end at end_[0] <= end_[1] <= ...): its start in the
+      // concatenation and in h5_idx, carried along the scan (no run-time index into the arrays)
+      int start = 0, bt = beg[0];
 #pragma unroll
-      for (int u = 0; u < 9; ++u) t += k >= end_[u];
-      int start = 0;
-#pragma unroll
-      for (int u = 0; u < 10; ++u) if (u == t) start = u > 0 ? end_[u - 1] : 0;
-      int bt = 0;
-#pragma unroll
-      for (int u = 0; u < 10; ++u) if (u == t) bt = beg[u];
+      for (int u = 0; u < 9; ++u)
+        if (k >= end_[u]) {
+          start = end_[u];
+          bt = beg[u + 1];
+        }
       const int b = w.h5_idx[bt + (k - start)];
       if (b == a) continue;
+      // b's hits loaded together (no chain of dependent loads), then all 100 comparisons
+      int hb[10];
+      {
+        const int2* pb = reinterpret_cast<const int2*>(w.t5_hit + (int64_t)b * 10);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const int2 v = pb[k];
+          hb[2 * k] = v.x;
+          hb[2 * k + 1] = v.y;
+        }
+      }
       int shared = 0;
 #pragma unroll
-      for (int kb = 0; kb < 10; ++kb) {
-        if (shared + (10 - kb) < overlap) break;   // the rest cannot reach the overlap
-        const int hb = w.t5_hit[(int64_t)b * 10 + kb];
+      for (int kb = 0; kb < 10; ++kb)
 #pragma unroll
-        for (int u = 0; u < 10; ++u) shared += ha[u] == hb;
-      }
+        for (int u = 0; u < 10; ++u) shared += ha[u] == hb[kb];
       if (shared < overlap) continue;
       const float cb = w.t5_f[3 * S + b];
       if (cb < ca || (cb == ca && key_less(w, TC_T5, b, a))) drop = true;
