@@ -326,7 +326,11 @@ __global__ void __launch_bounds__(32 * kMdWarps) k_md(Ws w, Geo g, Cst<float> c,
       bool keep = false;
       int l = 0, u = 0;
       if (p < total) {
-        const int il = pj / nupj;
+        // pj / nupj from a float estimate corrected by one step either way (exact: pj < 2^24, and
+        // the estimate is within one of the quotient)
+        int il = __float2int_rz(__fdividef((float)pj, (float)nupj));
+        if (il * nupj > pj) --il;
+        else if ((il + 1) * nupj <= pj) ++il;
         l = lo0j + il;
         u = up0j + (pj - il * nupj);
         keep = !md_quick_reject(c, ecj, deltaj, gmax, w.bx[l], w.by[l], w.bz[l], w.bx[u], w.by[u], w.bz[u]);
