@@ -527,6 +527,7 @@ __global__ void k_ls_work_fill(Ws w) {
 // evens out the sums); otherwise warps stride over all modules in index order.
 constexpr int kLsAW = 32;   // inner MDs staged per chunk
 constexpr int kLsQ = 64;    // survivor queue per warp (at most 31 carried + 32 new)
+constexpr int kLsGrab = 8;   // most items a warp takes from the device queue per atomic
 
 // Per-warp shared memory of k_ls: T target slots (the loaded map's largest degree rounded up to 32).
 struct LsSmem {
@@ -671,13 +672,22 @@ __global__ void __launch_bounds__(256, 4) k_ls(Ws w, Geo g, Cst<float> c, int pe
   unsigned long long n_pairs = 0;   // windowed pairs this warp evaluated (added once, at the end)
   const long long t0 = clock64();
   int sweep = 0;
+  // device queue: a warp takes `grab` consecutive items per atomic on the queue head (one atomic per
+  // item would serialise on that one address when there are many items); with few items per warp
+  // it takes them one at a time, so that no warp holds items the others could run
+  const int grab = max(1, min(kLsGrab, n_items / max(1, n_warps * 16)));
+  int q_next = 0, q_end = 0;
   for (;;) {
     if (warp_over_budget(w, t0)) break;
     int item;
-    if (persistent == 2) {   // device queue: each warp takes the next cost-ordered item
-      int h = 0;
-      if (lane == 0) h = atomicAdd(w.ls_head, 1);
-      item = __shfl_sync(0xffffffffu, h, 0);
+    if (persistent == 2) {   // device queue: the next cost-ordered item
+      if (q_next >= q_end) {
+        int h = 0;
+        if (lane == 0) h = atomicAdd(w.ls_head, grab);
+        q_next = __shfl_sync(0xffffffffu, h, 0);
+        q_end = min(q_next + grab, n_items);
+      }
+      item = q_next++;
       if (item >= n_items) break;
     } else {                 // static deal in boustrophedon order
       if ((int64_t)sweep * n_warps >= n_items) break;
