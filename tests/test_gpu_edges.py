@@ -108,9 +108,10 @@ def test_ls_pair_count_lies_between_accepted_and_connected_pairs():
     """The LS search's work count (n_ls_pairs, the (inner MD, outer MD) pairs it evaluated inside its
     azimuth windows) is at least the number of LS it accepted and at most the pairs the module map
     connects (each module's MDs times those of its connected modules), in a batch of PU200 events,
-    with one context per LS execution mode."""
+    and is the same in every LS execution mode."""
     det = gen.make_detector(barrel_only=False, pt_thr=0.8)
     evs = [gen.config_event(2, e)[1] for e in range(3)]
+    seen = {}
     for persistent in (2, 1, 0):
         ctx = lst.Context(det, persistent=persistent)
         try:
@@ -127,5 +128,8 @@ def test_ls_pair_count_lies_between_accepted_and_connected_pairs():
             assert all(ctx.counts(e)["n_ls_pairs"] == pairs for e in range(len(evs)))
             assert n_ls <= pairs <= connected, (persistent, n_ls, pairs, connected)
             assert pairs < 0.7 * connected   # the windows remove a large share of the connected pairs
+            seen[persistent] = pairs
         finally:
             ctx.close()
+    # every execution mode evaluates the same windows (split into chunks or not)
+    assert len(set(seen.values())) == 1, seen
